@@ -1,0 +1,61 @@
+"""Dense classical Ewald grand mobility (oracle, test infrastructure only).
+
+The exact periodic mobility of Eqs. MUF-MDC (Hasimoto's sum, Eq. hasimoto),
+restricted to (U, E) x (F, S) in the stresslet basis, split as in Sec. 2.2:
+    M = sum_images M^(r)(x_a - x_b + n L)  +  sum_{k != 0} H M_hat(k) e^{ik.r}/V,
+with the real-space part from ``realspace`` (all periodic images with
+|r| < rmax, including a particle's own images, plus the r -> 0 self term) and
+the wave-space part from ``wavesum`` (all |k| <= kmax).  Both truncations are
+chosen from the splitting parameter so the neglected terms are below ``tol``.
+
+Parity: pinned (tests/test_oracle_ewald.py: xi-independence, Cholesky of each
+part, Hasimoto's periodic self-mobility, free-space limits, symmetry).
+"""
+import itertools
+import math
+
+import numpy as np
+
+from . import realspace, wavesum
+
+
+def cutoffs(xi, tol):
+    """rmax, kmax with exp(-xi^2 rmax^2) and H(kmax) below tol (generous margins)."""
+    rmax = math.sqrt(math.log(1.0 / tol)) / xi + 2.0
+    u = math.log(1.0 / tol) + 6.0
+    kmax = 2.0 * xi * math.sqrt(u)
+    return rmax, kmax
+
+
+def dense_real(pos, L, a, eta, xi, rmax):
+    N = pos.shape[0]
+    M = np.zeros((8 * N, 8 * N))
+    nimg = int(math.ceil(rmax / L))
+    rng = range(-nimg, nimg + 1)
+    ia, ib = np.meshgrid(np.arange(N), np.arange(N), indexing='ij')
+    ia, ib = ia.ravel(), ib.ravel()
+    for n in itertools.product(rng, rng, rng):
+        d = pos[ia] - pos[ib] + L * np.array(n, dtype=float)
+        r = np.linalg.norm(d, axis=1)
+        sel = (r < rmax) & (r > 0)
+        if not np.any(sel):
+            continue
+        B = realspace.pair_blocks(d[sel], xi, a, eta)
+        for (p, q, blk) in zip(ia[sel], ib[sel], B):
+            M[8 * p:8 * p + 8, 8 * q:8 * q + 8] += blk
+    S = realspace.self_block(xi, a, eta)
+    for p in range(N):
+        M[8 * p:8 * p + 8, 8 * p:8 * p + 8] += S
+    return M
+
+
+def dense_mobility(pos, L, a=1.0, eta=1.0, xi=None, tol=1e-14, parts=False):
+    """Exact (to ~tol) periodic grand mobility, 8N x 8N, ordering [F(3), s(5)] per particle."""
+    if xi is None:
+        xi = math.sqrt(math.pi) / L * 2.0
+    rmax, kmax = cutoffs(xi, tol)
+    Mr = dense_real(np.asarray(pos, float), L, a, eta, xi, rmax)
+    Mw = wavesum.dense_wave(np.asarray(pos, float), L, a, eta, xi, wavesum.kset_sphere(L, kmax))
+    if parts:
+        return Mr, Mw
+    return Mr + Mw

@@ -1,0 +1,370 @@
+"""The PSE algorithm in plain FP64 NumPy/SciPy (oracle, test infrastructure only).
+
+Steps, in the paper's order:
+
+* Real space (Sec. 2.3.1): pair sum over all pairs with r < r_cut of the
+  real-space blocks (``realspace``), plus the self term (App. A, Case 3).
+* Wave space (Sec. 2.3.2, Eq. WSops2):  M_w = sigma Q^T F^+ P^+ B P F Q.
+  - Q: Gaussian spreading of every moment component onto its own grid with
+    K(r) = (2 xi^2/(pi eta_g))^{3/2} exp(-2 xi^2 r^2/eta_g) on the P^3 grid
+    points nearest the particle.
+  - F: FFT.  The spread density approximates the particles' point moments
+    filtered by K_hat(k) = exp(-eta_g k^2 / (8 xi^2)); spreading and
+    interpolation together filter by exp(-eta_g k^2/(4 xi^2)), which the
+    scaling step divides out (reading of the normalisation).
+  - P, B: f = s0 F_hat - 3i s1 S_hat.k;  u = H/(eta V k^2) (I - kk) f;
+    U_hat = s0 u;  D_hat = 3i s1 u k^T;  E = Y-projection of D.
+  - k = 0 and every mode with an index at the Nyquist plane are excluded.
+  - F^+: inverse FFT;  sigma Q^T: interpolation weighted by the cell volume.
+* Split sampling (Sec. 3, Eq. split): M^{1/2} dW =d M_r^{1/2} dW1 + M_w^{1/2} dW2.
+  - M_r^{1/2} z by the Lanczos method (Sec. 3.2) with full reorthogonalisation
+    and the stopping rule |y_m - y_{m-1}| / |y_m| <= tol.
+  - M_w^{1/2} dW2 = sigma^{1/2} Q^T F^+ P^+ B^{1/2} dW2 (Eq. FFTsqrt) with
+    Hermitian dW2(-k) = conj dW2(k) (Re, Im ~ N(0, 1/2)).
+  - Velocities are scaled by sqrt(2 kT / dt) (App. B covariance).
+* Mid-point step (Sec. 3.4, App. B): sample [U^B; E^B] at x_k, move to
+  x_{k+1/2} = x_k + dt/2 U^B, solve M_ES S = -E^B - M_EF F^P at x_{k+1/2} by
+  unrestarted GMRES (x0 = 0), then U = U^B + M_UF F^P + M_US S and
+  x_{k+1} = x_k + dt U.
+
+Layout conventions shared with the product through the documented C ABI (not
+through code): grid arrays are [component][z][y][x]; the R2C half spectrum
+halves x; 8-vectors per particle are [F_x, F_y, F_z, s_1..s_5].
+
+Parity: pinned against the dense Ewald oracle (within tol) and the direct
+k-sum on the same k set (tests/test_oracle_pse.py); Lanczos against a dense
+symmetric square root; GMRES against the dense Schur complement.
+"""
+import math
+
+import numpy as np
+from scipy.linalg import eigh_tridiagonal
+from scipy.spatial import cKDTree
+
+from . import realspace
+from .basis import Y
+from .wavesum import shape_factors
+
+
+# ---------------------------------------------------------------- wave space
+def _support(pos, p):
+    """Base index i0 and displacements of the P support points per dimension.
+
+    Reading: the P grid points nearest the particle; i0 = round(x/h) - (P-1)/2 for
+    odd P, floor(x/h) - P/2 + 1 for even P (taken mod Ng).
+    """
+    x = np.mod(pos, p.L)
+    q = x / p.h
+    if p.P % 2:
+        i0 = np.rint(q).astype(np.int64) - (p.P - 1) // 2
+    else:
+        i0 = np.floor(q).astype(np.int64) - p.P // 2 + 1
+    j = np.arange(p.P)
+    idx = i0[:, :, None] + j[None, None, :]                    # (N, 3, P)
+    disp = idx * p.h - x[:, :, None]                           # (N, 3, P)
+    return np.mod(idx, p.Ng), disp
+
+
+def _weights(pos, p):
+    idx, disp = _support(pos, p)
+    alpha = 2 * p.xi ** 2 / p.eta_g
+    w1 = np.exp(-alpha * disp ** 2)                            # (N, 3, P)
+    pref = (2 * p.xi ** 2 / (np.pi * p.eta_g)) ** 1.5
+    W = pref * np.einsum('ni,nj,nk->nijk', w1[:, 2], w1[:, 1], w1[:, 0])   # [z][y][x]
+    flat = ((idx[:, 2, :, None, None] * p.Ng + idx[:, 1, None, :, None]) * p.Ng
+            + idx[:, 0, None, None, :])
+    return flat.reshape(pos.shape[0], -1), W.reshape(pos.shape[0], -1)
+
+
+def spread(pos, comps, p):
+    """Q: spread (N, C) moment components onto C grids of shape (Ng, Ng, Ng)."""
+    flat, W = _weights(pos, p)
+    n3 = p.Ng ** 3
+    C = comps.shape[1]
+    grid = np.empty((C, n3))
+    for c in range(C):
+        grid[c] = np.bincount(flat.ravel(), weights=(W * comps[:, c:c + 1]).ravel(), minlength=n3)
+    return grid.reshape(C, p.Ng, p.Ng, p.Ng)
+
+
+def interpolate(grid, pos, p):
+    """Q^T (without sigma): sum over the support of K times the grid values."""
+    flat, W = _weights(pos, p)
+    C = grid.shape[0]
+    g = grid.reshape(C, -1)
+    return np.stack([np.sum(W * g[c][flat], axis=1) for c in range(C)], axis=1)
+
+
+def kgrid(p):
+    """Wave vectors of the R2C half spectrum [z][y][x-half] and the Nyquist/zero mask."""
+    n = p.Ng
+    f = np.fft.fftfreq(n, d=1.0 / n)
+    fx = np.arange(n // 2 + 1)
+    kz, ky, kx = np.meshgrid(f, f, fx, indexing='ij')
+    keep = (np.abs(kz) != n // 2) & (np.abs(ky) != n // 2) & (kx != n // 2)
+    keep &= ~((kz == 0) & (ky == 0) & (kx == 0))
+    scale = 2 * np.pi / p.L
+    return kx * scale, ky * scale, kz * scale, keep
+
+
+def _project_out(uh, kvec, kk, keep, s0, s1, want):
+    """P^+: U_hat = s0 u, E_hat_l = Y_l : (3i s1 u k^T)."""
+    out = []
+    if 'U' in want:
+        out += [s0 * uh[i] for i in range(3)]
+    if 'E' in want:
+        D = 3j * s1[None, None] * uh[:, None] * kvec[None, :]       # [i][j]
+        out += [np.einsum('ij...,ij->...', D, Y[l]) for l in range(5)]
+    return [np.where(keep, o, 0.0) for o in out]
+
+
+def _k_arrays(p):
+    kx, ky, kz, keep = kgrid(p)
+    kvec = np.stack([kx, ky, kz])
+    kk2 = kx ** 2 + ky ** 2 + kz ** 2
+    kk = np.sqrt(np.where(keep, kk2, 1.0))
+    s0, s1 = shape_factors(kk.ravel(), p.a)
+    return kvec, kk, keep, s0.reshape(kk.shape), s1.reshape(kk.shape)
+
+
+def wave_apply(pos, F, S, p, want=('U', 'E')):
+    """Wave-space part M_w [F; S] by the NUFFT route of Eq. WSops2."""
+    N = pos.shape[0]
+    comps = np.concatenate([F, S], axis=1)
+    grid = spread(pos, comps, p)
+    gh = np.fft.rfftn(grid, axes=(1, 2, 3))
+    kvec, kk, keep, s0, s1 = _k_arrays(p)
+    Sh = np.einsum('l...,lij->ij...', gh[3:], Y)                     # (3,3,...)
+    f = s0[None] * gh[:3] - 3j * s1[None] * np.einsum('ij...,j...->i...', Sh, kvec)
+    u = kk ** 2 / (4 * p.xi ** 2)
+    c = (p.sigma ** 2 / p.V) / p.eta * (1 + u) * np.exp(-(1 - p.eta_g) * u) / kk ** 2
+    kh = kvec / kk[None]
+    f = f - kh * np.sum(kh * f, axis=0)[None]
+    uh = c[None] * f
+    outs = _project_out(uh, kvec, kk, keep, s0, s1, want)
+    n = p.Ng
+    grids = np.stack([np.fft.irfftn(o, s=(n, n, n), axes=(0, 1, 2)) * n ** 3 for o in outs])
+    vals = interpolate(grids, pos, p)
+    res = {}
+    col = 0
+    if 'U' in want:
+        res['U'] = vals[:, :3]
+        col = 3
+    if 'E' in want:
+        res['E'] = vals[:, col:col + 5]
+    return res
+
+
+def hermitian_noise(w2, p):
+    """dW2 on the half spectrum from standard normals w2 of shape (3, Ng, Ng, Ng/2+1, 2).
+
+    dW2 = (re + i im)/sqrt(2) on representatives; on the kx = 0 plane the entry
+    (z, y) with z > Ng/2, or z = 0 and y > Ng/2, is the conjugate of entry
+    (-z, -y) mod Ng; Nyquist modes and k = 0 are zero.
+    """
+    n = p.Ng
+    dw = (w2[..., 0] + 1j * w2[..., 1]) / math.sqrt(2.0)
+    dw = dw.copy()
+    z = np.arange(n)[:, None]
+    y = np.arange(n)[None, :]
+    partner = (z > n // 2) | ((z == 0) & (y > n // 2))
+    zm = (-np.arange(n)) % n
+    plane = dw[:, :, :, 0]
+    mirror = np.conj(plane[:, zm][:, :, zm])
+    plane = np.where(partner[None], mirror, plane)
+    dw[:, :, :, 0] = plane
+    _, _, _, keep = kgrid(p)
+    return np.where(keep[None], dw, 0.0)
+
+
+def wave_noise(pos, w2, p):
+    """M_w^{1/2} dW2 (Eq. FFTsqrt), returned as (N, 8) [U, E] without sqrt(2kT/dt)."""
+    dw = hermitian_noise(w2, p)
+    kvec, kk, keep, s0, s1 = _k_arrays(p)
+    u = kk ** 2 / (4 * p.xi ** 2)
+    Hk = (1 + u) * np.exp(-u)
+    c = p.sigma * np.exp(p.eta_g * u / 2.0) * np.sqrt(Hk / (p.eta * p.V * kk ** 2))
+    kh = kvec / kk[None]
+    dw = dw - kh * np.sum(kh * dw, axis=0)[None]
+    uh = c[None] * dw
+    outs = _project_out(uh, kvec, kk, keep, s0, s1, ('U', 'E'))
+    n = p.Ng
+    grids = np.stack([np.fft.irfftn(o, s=(n, n, n), axes=(0, 1, 2)) * n ** 3 for o in outs])
+    return interpolate(grids, pos, p)
+
+
+# ---------------------------------------------------------------- real space
+class RealOp:
+    """Real-space operator M_r for a fixed configuration (pairs with r < r_cut)."""
+
+    def __init__(self, pos, p, chunk=20000):
+        self.N = pos.shape[0]
+        x = np.mod(pos, p.L)
+        tree = cKDTree(x, boxsize=p.L)
+        pr = tree.query_pairs(p.rcut, output_type='ndarray')
+        if pr.size == 0:
+            pr = np.zeros((0, 2), dtype=np.int64)
+        d = x[pr[:, 0]] - x[pr[:, 1]]
+        d -= p.L * np.rint(d / p.L)
+        keep = np.linalg.norm(d, axis=1) < p.rcut
+        pr, d = pr[keep], d[keep]
+        blocks = np.empty((pr.shape[0], 8, 8))
+        for c0 in range(0, pr.shape[0], chunk):
+            blocks[c0:c0 + chunk] = realspace.pair_blocks(d[c0:c0 + chunk], p.xi, p.a, p.eta)
+        self.i, self.j, self.B = pr[:, 0], pr[:, 1], blocks
+        self.self = realspace.self_block(p.xi, p.a, p.eta)
+
+    def apply(self, v):
+        """(N, 8) -> (N, 8) real-space product."""
+        out = v @ self.self.T
+        np.add.at(out, self.i, np.einsum('pab,pb->pa', self.B, v[self.j]))
+        np.add.at(out, self.j, np.einsum('pba,pb->pa', self.B, v[self.i]))
+        return out
+
+    def dense(self):
+        M = np.zeros((8 * self.N, 8 * self.N))
+        for n in range(self.N):
+            M[8 * n:8 * n + 8, 8 * n:8 * n + 8] = self.self
+        for i, j, b in zip(self.i, self.j, self.B):
+            M[8 * i:8 * i + 8, 8 * j:8 * j + 8] += b
+            M[8 * j:8 * j + 8, 8 * i:8 * i + 8] += b.T
+        return M
+
+
+def mobility_apply(pos, F, S, p, parts=('real', 'wave'), real_op=None):
+    """[U; E] = M [F; S] with the PSE split (Sec. 2.3)."""
+    N = pos.shape[0]
+    U = np.zeros((N, 3))
+    E = np.zeros((N, 5))
+    if 'real' in parts:
+        op = real_op if real_op is not None else RealOp(pos, p)
+        v = op.apply(np.concatenate([F, S], axis=1))
+        U += v[:, :3]
+        E += v[:, 3:]
+    if 'wave' in parts:
+        w = wave_apply(pos, F, S, p)
+        U += w['U']
+        E += w['E']
+    return U, E
+
+
+# ---------------------------------------------------------------- Lanczos
+def lanczos_sqrt(apply, z, tol, maxiter):
+    """y ~= M^{1/2} z by the Lanczos method with full reorthogonalisation (Sec. 3.2).
+
+    Stops when |c_m - [c_{m-1}; 0]| / |c_m| <= tol where y_m = |z| V_m c_m and
+    c_m = T_m^{1/2} e_1 (V_m orthonormal); tol = 0 runs exactly maxiter steps.
+    Returns (y, iterations, last relative change).
+    """
+    n = z.size
+    beta0 = np.linalg.norm(z)
+    if beta0 == 0.0:
+        return np.zeros_like(z), 0, 0.0
+    V = np.zeros((maxiter + 1, n))
+    V[0] = z / beta0
+    alpha, beta = [], []
+    c_prev = None
+    err = np.inf
+    it = 0
+    for j in range(maxiter):
+        it = j + 1
+        w = apply(V[j])
+        if j > 0:
+            w = w - beta[j - 1] * V[j - 1]
+        a_j = V[j] @ w
+        w = w - a_j * V[j]
+        for _ in range(2):                       # full reorthogonalisation
+            w = w - V[:j + 1].T @ (V[:j + 1] @ w)
+        alpha.append(a_j)
+        b_j = np.linalg.norm(w)
+        if j == 0:
+            c = np.array([math.sqrt(max(a_j, 0.0))])
+        else:
+            th, Q = eigh_tridiagonal(np.array(alpha), np.array(beta))
+            c = Q @ (np.sqrt(np.maximum(th, 0.0)) * Q[0])
+        if c_prev is not None:
+            err = np.linalg.norm(c - np.append(c_prev, 0.0)) / np.linalg.norm(c)
+            if tol > 0 and err <= tol:
+                break
+        c_prev = c
+        if b_j == 0.0 or j == maxiter - 1:
+            break
+        beta.append(b_j)
+        V[j + 1] = w / b_j
+    y = beta0 * (V[:it].T @ c)
+    return y, it, err
+
+
+# ---------------------------------------------------------------- GMRES
+def gmres(apply, b, tol, maxiter):
+    """Unrestarted GMRES with x0 = 0; stops at |r|/|b| <= tol (reading of the
+    unnamed Krylov solve, Sec. 4 text on 8-10 iterations).  Returns (x, iters, relres)."""
+    beta = np.linalg.norm(b)
+    if beta == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    n = b.size
+    V = np.zeros((maxiter + 1, n))
+    Hm = np.zeros((maxiter + 1, maxiter))
+    V[0] = b / beta
+    rel = 1.0
+    it = 0
+    y = np.zeros(0)
+    for j in range(maxiter):
+        it = j + 1
+        w = apply(V[j])
+        for _ in range(2):
+            h = V[:j + 1] @ w
+            w = w - V[:j + 1].T @ h
+            Hm[:j + 1, j] += h
+        Hm[j + 1, j] = np.linalg.norm(w)
+        e1 = np.zeros(j + 2)
+        e1[0] = beta
+        y, *_ = np.linalg.lstsq(Hm[:j + 2, :j + 1], e1, rcond=None)
+        rel = np.linalg.norm(e1 - Hm[:j + 2, :j + 1] @ y) / beta
+        if rel <= tol or Hm[j + 1, j] == 0.0:
+            break
+        V[j + 1] = w / Hm[j + 1, j]
+    x = V[:it].T @ y
+    return x, it, rel
+
+
+# ---------------------------------------------------------------- sampling / step
+def brownian_sample(pos, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=100, real_op=None):
+    """[U^B; E^B] = sqrt(2kT/dt) (M_r^{1/2} w1 + M_w^{1/2} dW2(w2)) as (N, 8)."""
+    op = real_op if real_op is not None else RealOp(pos, p)
+    N = pos.shape[0]
+    tol = p.tol if lanczos_tol is None else lanczos_tol
+    yr, it, err = lanczos_sqrt(lambda v: op.apply(v.reshape(N, 8)).ravel(), w1.reshape(-1), tol,
+                               lanczos_maxiter)
+    yw = wave_noise(pos, w2, p)
+    scale = math.sqrt(2 * p.kT / dt)
+    return scale * (yr.reshape(N, 8) + yw), {'lanczos_iters': it, 'lanczos_err': err}
+
+
+def constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=100,
+                     krylov_tol=None, krylov_maxiter=50):
+    """One mid-point step (Sec. 3.4).  Returns (x_{k+1}, S_{k+1/2}, stats)."""
+    N = pos.shape[0]
+    x0 = np.mod(pos, p.L)
+    B, st = brownian_sample(x0, dt, w1, w2, p, lanczos_tol, lanczos_maxiter)
+    UB, EB = B[:, :3], B[:, 3:]
+    xh = np.mod(x0 + 0.5 * dt * UB, p.L)
+    op = RealOp(xh, p)
+    zF = np.zeros((N, 3)) if FP is None else FP
+    rhs = -EB
+    if FP is not None:
+        _, EF = mobility_apply(xh, zF, np.zeros((N, 5)), p, real_op=op)
+        rhs = rhs - EF
+
+    def mes(s):
+        _, E = mobility_apply(xh, np.zeros((N, 3)), s.reshape(N, 5), p, real_op=op)
+        return E.ravel()
+
+    ktol = p.tol if krylov_tol is None else krylov_tol
+    S, kit, rel = gmres(mes, rhs.ravel(), ktol, krylov_maxiter)
+    S = S.reshape(N, 5)
+    U, _ = mobility_apply(xh, zF, S, p, real_op=op)
+    U = UB + U
+    x1 = np.mod(x0 + dt * U, p.L)
+    st.update({'krylov_iters': kit, 'krylov_relres': rel})
+    return x1, S, st
