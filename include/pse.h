@@ -1,0 +1,188 @@
+/*
+ * pse.h -- C ABI of the GB300 positively-split Ewald (PSE) library with
+ * stresslet constraints (Fiore & Swan, arXiv:1709.06946).
+ *
+ * The library computes, for N identical spheres of radius a in a cubic
+ * periodic box of side L (fluid viscosity eta, thermal energy kT):
+ *
+ *   [U; E] = M [F; S]            the periodic grand mobility restricted to
+ *                                (velocity, rate of strain) x (force, stresslet)
+ *                                (Sec. 2.1 Eqs. MUF-MDC, Sec. 2.2.1 rigid-particle
+ *                                relation), split as M = M_r + M_w (Sec. 2.2) and
+ *                                evaluated with a cell-list real-space sum
+ *                                (Sec. 2.3.1) and a Gaussian NUFFT wave-space sum
+ *                                (Sec. 2.3.2, Eq. WSops2);
+ *   [U^B; E^B]                   Brownian slip velocities with covariance
+ *                                (2 kT/dt) M (App. B), sampled as
+ *                                M_r^{1/2} dW1 + M_w^{1/2} dW2 (Sec. 3, Eq. split)
+ *                                with Lanczos for M_r^{1/2} (Sec. 3.2) and the
+ *                                wave-space square root (Sec. 3.3, Eq. FFTsqrt);
+ *   one constrained mid-point step (Sec. 3.4, App. B): x_{k+1/2} = x_k + dt/2 U^B,
+ *                                M_ES S = -E^B - M_EF F^P at x_{k+1/2} (GMRES),
+ *                                x_{k+1} = x_k + dt (U^B + M_UF F^P + M_US S).
+ *
+ * Conventions (all arrays dense, C order, little endian):
+ *   pos   N x 3 float64, any real values (wrapped into [0, L) internally).
+ *   F, U  N x 3, S, E  N x 5: the 5 stresslet / strain components in the
+ *         orthonormal symmetric traceless basis
+ *         Y1=(xx-yy)/sqrt2, Y2=(xx+yy-2zz)/sqrt6, Y3=(xy+yx)/sqrt2,
+ *         Y4=(xz+zx)/sqrt2, Y5=(yz+zy)/sqrt2  (s_k = S:Y_k, e_k = E:Y_k),
+ *         so every block of M is symmetric.
+ *   Element type of F, S, U, E, noise arrays: float32 in PSE_MIXED,
+ *         float64 in PSE_FP64 (positions are always float64).
+ *   Pointers may be device or host memory (the library checks with
+ *         cudaPointerGetAttributes and stages host arrays through its own
+ *         device buffers).  The caller owns every array it passes; the library
+ *         owns everything reachable from a handle.
+ *   All work is issued on the given stream.  pse_mobility_apply returns
+ *         without waiting; the sampling and step calls wait on the stream
+ *         (the Krylov loops read their scalars on the host).
+ *   Errors are returned as pse_status; pse_last_error gives a message.
+ *   There is no CPU fallback: without a CUDA device every call that needs
+ *         one returns PSE_ERR_CUDA.
+ */
+#ifndef PSE_H
+#define PSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pse_ctx *pse_handle;
+typedef void *pse_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  PSE_OK = 0,
+  PSE_ERR_INVALID_ARG = 1,   /* bad size, parameter or pointer; nothing was done */
+  PSE_ERR_OOM = 2,           /* device allocation failed */
+  PSE_ERR_CUDA = 3,          /* CUDA / cuFFT error (message in pse_last_error) */
+  PSE_ERR_NOT_CONVERGED = 4, /* Lanczos or GMRES hit its iteration cap; results of
+                                the last iterate were still written */
+  PSE_ERR_NONFINITE = 5,     /* NaN or Inf in the inputs; nothing was written */
+  PSE_ERR_TIMEOUT = 6        /* reserved for bounded device-side waits */
+} pse_status;
+
+typedef enum {
+  PSE_MIXED = 0, /* FP32 grids, FFTs, pair sums and vectors; FP64 Krylov/Lanczos
+                    scalars (inner products, tridiagonal/Hessenberg algebra) */
+  PSE_FP64 = 1   /* everything in FP64 (comparison form) */
+} pse_precision;
+
+typedef enum {
+  PSE_RULE_STRICT = 0, /* r_cut = a + sqrt(ln(10/tol))/xi, support P from Eq. bound at
+                          tol/10: measured error vs. the exact Ewald sum stays below tol */
+  PSE_RULE_PAPER = 1   /* r_cut = sqrt(ln(1/tol))/xi, P from Eq. bound at tol with C = 1
+                          (Table tab:lmax: P = 5 at 1e-3); error is a few x tol */
+} pse_rule;
+
+enum { PSE_PART_REAL = 1, PSE_PART_WAVE = 2, PSE_PART_ALL = 3 };
+
+typedef struct pse_options {
+  int32_t rule;            /* pse_rule (default PSE_RULE_STRICT) */
+  int32_t Ng;              /* FFT grid points per side; 0 = rule (even, 2,3,5,7-smooth) */
+  int32_t P;               /* Gaussian support points per side; 0 = rule */
+  int32_t table_points;    /* real-space table points per 2a; 0 = default */
+  double rcut;             /* real-space cutoff; 0 = rule (must be <= L/2) */
+  double lanczos_tol;      /* < 0: use tol; 0: run exactly lanczos_maxiter steps */
+  int32_t lanczos_maxiter; /* 0 = 100 */
+  double krylov_tol;       /* GMRES |r|/|b| target; < 0: use tol */
+  int32_t krylov_maxiter;  /* 0 = 50 */
+  int32_t tile[3];         /* spreading/interpolation tile (x, y, z); 0 = auto */
+  int32_t reserved[8];
+} pse_options;
+
+typedef struct pse_info {
+  int64_t N;
+  double L, a, eta, kT, xi, tol;
+  int32_t precision, rule;
+  double rcut, kcut, h, eta_g, m;
+  int32_t Ng, P;
+  int32_t cells_per_side;
+  int32_t tile[3];
+  int32_t table_len;
+  double table_dr;
+  int64_t device_bytes;    /* bytes allocated on the device by this handle */
+} pse_info;
+
+typedef struct pse_stats {
+  int32_t lanczos_iters;
+  int32_t krylov_iters;
+  double lanczos_change;   /* last relative change |y_m - y_{m-1}|/|y_m| */
+  double krylov_relres;    /* final |r|/|b| of the stresslet solve */
+  int64_t neighbor_pairs;  /* ordered pairs in the last real-space list */
+  int32_t products;        /* mobility products issued by the call */
+  int32_t reserved[5];
+} pse_stats;
+
+/* Fills *opt with the defaults listed above. */
+void pse_default_options(pse_options *opt);
+
+/* Creates a handle for N particles.  Chooses r_cut, P, m = sqrt(pi P), the
+ * grid Ng (k_cut from H(k_cut, xi) = tol, Ng >= k_cut L/pi) and the Gaussian
+ * width eta_g = (h P xi / m)^2 < 1 (Sec. 2.3.2-2.3.3), builds the real-space
+ * tables (inverse Fourier transform of M - M^(w), Sec. 2.2 / App. A), the
+ * cuFFT plans and all device work space on the current device.
+ * Returns INVALID_ARG for N < 1, L, a, eta, xi <= 0, kT < 0, tol outside
+ * (0, 0.1], r_cut > L/2 or eta_g >= 1.  opt may be NULL (defaults). */
+pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT,
+                      double xi, double tol, pse_precision prec, const pse_options *opt);
+
+pse_status pse_destroy(pse_handle h);
+
+pse_status pse_get_info(pse_handle h, pse_info *out);
+
+/* [U; E] = M [F; S] at positions pos (Sec. 2.2 Eq. pairsums, rigid-particle
+ * form).  F or S may be NULL (treated as zero); U or E may be NULL (not
+ * written).  Asynchronous on stream. */
+pse_status pse_mobility_apply(pse_handle h, const double *pos, const void *F, const void *S,
+                              void *U, void *E, pse_stream stream);
+
+/* As pse_mobility_apply, restricted to the real-space (PSE_PART_REAL) or
+ * wave-space (PSE_PART_WAVE) part of the split, or both (PSE_PART_ALL). */
+pse_status pse_mobility_apply_parts(pse_handle h, const double *pos, const void *F, const void *S,
+                                    void *U, void *E, int32_t parts, pse_stream stream);
+
+/* Brownian slip velocities [U^B; E^B] = sqrt(2 kT/dt) (M_r^{1/2} w1 + M_w^{1/2} dW2)
+ * (Sec. 3 Eq. split, Sec. 3.2-3.3).  Noise is either external or drawn in-kernel:
+ *   w1  N x 8 standard normals in the order [F_x F_y F_z s1..s5] per particle;
+ *   w2  3 x Ng x Ng x (Ng/2+1) x 2 standard normals (component, z, y, x-half,
+ *       re/im) of the R2C half spectrum; dW2 = (re + i im)/sqrt2, and on the
+ *       kx = 0 plane the entry (z, y) with z > Ng/2 or (z = 0, y > Ng/2) is the
+ *       conjugate of entry (-z, -y) mod Ng; k = 0 and Nyquist modes are unused.
+ *   If w1 (w2) is NULL the library draws it with Philox4x32-10 (Salmon et al.
+ *   2011): counter (index_lo, index_hi, counter, stream), key (seed_lo, seed_hi),
+ *   Box-Muller on words 0 and 1; stream 1 = w1 (index = 8 n + c), stream 2 = w2
+ *   (index over the half spectrum in the layout above; z0 = re, z1 = im).
+ * UB: N x 3, EB: N x 5.  Waits on the stream (Lanczos scalars are read back). */
+pse_status pse_brownian_sample(pse_handle h, const double *pos, double dt, uint64_t seed,
+                               uint64_t counter, const void *w1, const void *w2, void *UB, void *EB,
+                               pse_stats *stats, pse_stream stream);
+
+/* One constrained mid-point step (Sec. 3.4 / App. B), positions updated in
+ * place and wrapped into [0, L).  FP (N x 3, may be NULL) is the conservative
+ * force evaluated at x_k; S_out (N x 5, may be NULL) receives the mid-point
+ * stresslets; stats may be NULL.  Noise is drawn in-kernel from (seed, step).
+ * Returns NOT_CONVERGED (after completing the step) if a Krylov cap was hit. */
+pse_status pse_constrained_step(pse_handle h, double *pos, const void *FP, double dt, uint64_t seed,
+                                uint64_t step, void *S_out, pse_stats *stats, pse_stream stream);
+
+/* As pse_constrained_step with external noise arrays w1, w2 (layouts as in
+ * pse_brownian_sample; both required). */
+pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP, double dt,
+                                      const void *w1, const void *w2, void *S_out, pse_stats *stats,
+                                      pse_stream stream);
+
+/* Waits for all work of the handle and reports any pending CUDA error. */
+pse_status pse_sync(pse_handle h);
+
+const char *pse_status_string(pse_status s);
+
+/* Message for the last error on this handle (or the last create failure if h is NULL). */
+const char *pse_last_error(pse_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSE_H */

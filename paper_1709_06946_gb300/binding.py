@@ -1,0 +1,222 @@
+"""Thin ctypes binding of the C ABI in include/pse.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``libpse.so`` built in this
+directory; importing this module never falls back to anything else, and the
+first call fails with an explicit error if the library is missing.
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they must be
+C-contiguous with float64 positions and float32 (PSE_MIXED) / float64
+(PSE_FP64) moments.  Results are returned as torch tensors on the device of
+``pos`` (torch input) or as numpy arrays (numpy input).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'libpse.so')
+
+PSE_MIXED, PSE_FP64 = 0, 1
+PSE_RULE_STRICT, PSE_RULE_PAPER = 0, 1
+PARTS = {'real': 1, 'wave': 2, 'all': 3}
+STATUS = {0: 'ok', 1: 'invalid argument', 2: 'out of device memory', 3: 'CUDA error',
+          4: 'Krylov iteration cap reached', 5: 'non-finite input', 6: 'device wait timed out'}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [('rule', ctypes.c_int32), ('Ng', ctypes.c_int32), ('P', ctypes.c_int32),
+                ('table_points', ctypes.c_int32), ('rcut', ctypes.c_double),
+                ('lanczos_tol', ctypes.c_double), ('lanczos_maxiter', ctypes.c_int32),
+                ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
+                ('tile', ctypes.c_int32 * 3), ('reserved', ctypes.c_int32 * 8)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [('N', ctypes.c_int64), ('L', ctypes.c_double), ('a', ctypes.c_double),
+                ('eta', ctypes.c_double), ('kT', ctypes.c_double), ('xi', ctypes.c_double),
+                ('tol', ctypes.c_double), ('precision', ctypes.c_int32), ('rule', ctypes.c_int32),
+                ('rcut', ctypes.c_double), ('kcut', ctypes.c_double), ('h', ctypes.c_double),
+                ('eta_g', ctypes.c_double), ('m', ctypes.c_double), ('Ng', ctypes.c_int32),
+                ('P', ctypes.c_int32), ('cells_per_side', ctypes.c_int32), ('tile', ctypes.c_int32 * 3),
+                ('table_len', ctypes.c_int32), ('table_dr', ctypes.c_double),
+                ('device_bytes', ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [('lanczos_iters', ctypes.c_int32), ('krylov_iters', ctypes.c_int32),
+                ('lanczos_change', ctypes.c_double), ('krylov_relres', ctypes.c_double),
+                ('neighbor_pairs', ctypes.c_int64), ('products', ctypes.c_int32),
+                ('reserved', ctypes.c_int32 * 5)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != 'reserved'}
+
+
+# (name, restype, argtypes) of every symbol declared in include/pse.h
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_U64 = ctypes.c_uint64
+SIGNATURES = [
+    ('pse_default_options', None, [ctypes.POINTER(Options)]),
+    ('pse_create', ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, _D, _D, _D, _D, _D, _D, ctypes.c_int,
+                                  ctypes.POINTER(Options)]),
+    ('pse_destroy', ctypes.c_int, [_P]),
+    ('pse_get_info', ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    ('pse_mobility_apply', ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    ('pse_mobility_apply_parts', ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    ('pse_brownian_sample', ctypes.c_int, [_P, _P, _D, _U64, _U64, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_constrained_step', ctypes.c_int, [_P, _P, _P, _D, _U64, _U64, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_constrained_step_noise', ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_sync', ctypes.c_int, [_P]),
+    ('pse_status_string', ctypes.c_char_p, [ctypes.c_int]),
+    ('pse_last_error', ctypes.c_char_p, [_P]),
+]
+
+_lib = None
+
+
+def load():
+    """Loads libpse.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError('libpse.so is not built: run paper_1709_06946_gb300.build.build() '
+                               '(nvcc for sm_103a); there is no CPU fallback')
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class PSEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__('%s: %s' % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags['C_CONTIGUOUS']:
+            raise ValueError('arrays must be C-contiguous')
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError('tensors must be contiguous')
+    return x.data_ptr()
+
+
+def _stream(x):
+    try:
+        torch = _torch()
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            return torch.cuda.current_stream(x.device).cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class PSE:
+    """One PSE handle (N particles in a cubic periodic box)."""
+
+    def __init__(self, N, L, a=1.0, eta=1.0, kT=1.0, xi=0.5, tol=1e-3, precision='mixed', rule='strict',
+                 Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
+                 krylov_maxiter=50, table_points=0, tile=(0, 0, 0)):
+        lib = load()
+        o = Options()
+        lib.pse_default_options(ctypes.byref(o))
+        o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
+        o.Ng, o.P, o.rcut = int(Ng), int(P), float(rcut)
+        o.lanczos_tol, o.lanczos_maxiter = float(lanczos_tol), int(lanczos_maxiter)
+        o.krylov_tol, o.krylov_maxiter = float(krylov_tol), int(krylov_maxiter)
+        o.table_points = int(table_points)
+        for d in range(3):
+            o.tile[d] = int(tile[d])
+        self.prec = PSE_FP64 if precision in ('fp64', 'double', PSE_FP64) else PSE_MIXED
+        self.dtype = np.float64 if self.prec == PSE_FP64 else np.float32
+        h = _P()
+        st = lib.pse_create(ctypes.byref(h), int(N), float(L), float(a), float(eta), float(kT), float(xi),
+                            float(tol), self.prec, ctypes.byref(o))
+        if st != 0:
+            raise PSEError(st, lib.pse_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        self.N = int(N)
+        self.info = self.get_info()
+
+    def _check(self, st):
+        if st not in (0,):
+            raise PSEError(st, self._lib.pse_last_error(self._h).decode())
+
+    def get_info(self):
+        inf = Info()
+        self._check(self._lib.pse_get_info(self._h, ctypes.byref(inf)))
+        d = {k: getattr(inf, k) for k, _ in Info._fields_}
+        d['tile'] = tuple(inf.tile)
+        return d
+
+    def close(self):
+        if getattr(self, '_h', None):
+            self._lib.pse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------- helpers
+    def _like(self, ref, shape, dtype):
+        if isinstance(ref, np.ndarray):
+            return np.zeros(shape, dtype=dtype)
+        torch = _torch()
+        tdt = torch.float64 if dtype == np.float64 else torch.float32
+        return torch.zeros(shape, dtype=tdt, device=ref.device)
+
+    def mobility(self, pos, F=None, S=None, parts='all', want=('U', 'E')):
+        """[U, E] = M [F; S] (or its real / wave part)."""
+        U = self._like(pos, (self.N, 3), self.dtype) if 'U' in want else None
+        E = self._like(pos, (self.N, 5), self.dtype) if 'E' in want else None
+        st = self._lib.pse_mobility_apply_parts(self._h, _ptr(pos), _ptr(F), _ptr(S), _ptr(U), _ptr(E),
+                                                PARTS[parts], _stream(pos))
+        self._check(st)
+        return U, E
+
+    def brownian(self, pos, dt, seed=0, counter=0, w1=None, w2=None):
+        """Brownian slip velocities (U^B, E^B) with covariance (2kT/dt) M."""
+        U = self._like(pos, (self.N, 3), self.dtype)
+        E = self._like(pos, (self.N, 5), self.dtype)
+        stats = Stats()
+        st = self._lib.pse_brownian_sample(self._h, _ptr(pos), float(dt), int(seed), int(counter), _ptr(w1),
+                                           _ptr(w2), _ptr(U), _ptr(E), ctypes.byref(stats), _stream(pos))
+        if st not in (0, 4):
+            self._check(st)
+        return U, E, stats.as_dict()
+
+    def step(self, pos, dt, FP=None, seed=0, step=0, w1=None, w2=None, want_S=False, allow_cap=True):
+        """One constrained mid-point step; pos (N x 3 float64) is updated in place."""
+        S = self._like(pos, (self.N, 5), self.dtype) if want_S else None
+        stats = Stats()
+        if w1 is not None or w2 is not None:
+            st = self._lib.pse_constrained_step_noise(self._h, _ptr(pos), _ptr(FP), float(dt), _ptr(w1), _ptr(w2),
+                                                      _ptr(S), ctypes.byref(stats), _stream(pos))
+        else:
+            st = self._lib.pse_constrained_step(self._h, _ptr(pos), _ptr(FP), float(dt), int(seed), int(step),
+                                                _ptr(S), ctypes.byref(stats), _stream(pos))
+        if not (st == 0 or (allow_cap and st == 4)):
+            self._check(st)
+        d = stats.as_dict()
+        d['status'] = st
+        return S, d
+
+    def sync(self):
+        self._check(self._lib.pse_sync(self._h))

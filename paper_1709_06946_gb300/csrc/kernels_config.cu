@@ -1,0 +1,367 @@
+// Configuration set-up: wrapping, binning by spreading tile, counting sort,
+// per-particle spreading/real-space records, linked-cell list and neighbour list.
+//
+// Sorted order = by the spreading tile that holds the first grid index of a
+// particle's Gaussian support; the spreading and interpolation kernels visit the
+// 2x2x2 neighbouring bins of their tile, and the pair sum walks a neighbour list
+// built from cells of side >= r_cut (Sec. 2.3.1, linked-cell lists).
+#include <cmath>
+
+#include "device_common.cuh"
+#include "pse_internal.cuh"
+
+namespace pse {
+namespace {
+
+constexpr int SCAN_NT = 256, SCAN_IPT = 8, SCAN_BLK = SCAN_NT * SCAN_IPT;
+
+// Exclusive scan of in[0..n) into out (in-place allowed) per block of SCAN_BLK items.
+__global__ void k_scan_block(const int *in, int *out, int64_t n, int *block_sums) {
+  __shared__ int warp_tot[SCAN_NT / 32];
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLK + (int64_t)threadIdx.x * SCAN_IPT;
+  int v[SCAN_IPT], tot = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_IPT; ++i) {
+    int64_t idx = base + i;
+    v[i] = idx < n ? in[idx] : 0;
+    tot += v[i];
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int x = lane < SCAN_NT / 32 ? warp_tot[lane] : 0, xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    if (lane < SCAN_NT / 32) warp_tot[lane] = xi - x;  // exclusive warp offsets
+    if (lane == SCAN_NT / 32 - 1 && block_sums) block_sums[blockIdx.x] = xi;
+  }
+  __syncthreads();
+  int run = warp_tot[w] + incl - tot;
+#pragma unroll
+  for (int i = 0; i < SCAN_IPT; ++i) {
+    int64_t idx = base + i;
+    if (idx < n) out[idx] = run;
+    run += v[i];
+  }
+}
+
+__global__ void k_scan_add(int *out, int64_t n, const int *offs) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_BLK;
+  int add = offs[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < SCAN_BLK; i += blockDim.x) {
+    int64_t idx = base + i;
+    if (idx < n) out[idx] += add;
+  }
+}
+
+struct BinArgs {
+  int N;
+  double L, h, cs;
+  int Ng, P, nc;
+  int T[3], nt[3];
+};
+
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+  x = fmod(x, L);
+  if (x < 0) x += L;
+  if (x >= L) x = 0.0;
+  return x;
+}
+
+__device__ __forceinline__ int support_start(double x, double h, int P) {
+  double q = x / h;
+  return (P & 1) ? (int)rint(q) - (P - 1) / 2 : (int)floor(q) - P / 2 + 1;
+}
+
+__global__ void k_bin(BinArgs b, const double *pos, double *posw, int *tile_key, int *tile_cnt, int *bad) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= b.N) return;
+  int iw[3];
+  for (int d = 0; d < 3; ++d) {
+    double x = pos[3 * (int64_t)u + d];
+    if (!isfinite(x)) {
+      atomicOr(bad, 1);
+      x = 0.0;
+    }
+    x = wrap_coord(x, b.L);
+    posw[3 * (int64_t)u + d] = x;
+    iw[d] = wrapi(support_start(x, b.h, b.P), b.Ng);
+  }
+  int tk = ((iw[2] / b.T[2]) * b.nt[1] + iw[1] / b.T[1]) * b.nt[0] + iw[0] / b.T[0];
+  tile_key[u] = tk;
+  atomicAdd(&tile_cnt[tk], 1);
+}
+
+__global__ void k_scatter(int N, const int *key, const int *start, int *cur, int *perm, int *inv) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= N) return;
+  int k = key[u];
+  int i = start[k] + atomicAdd(&cur[k], 1);
+  perm[i] = u;
+  inv[u] = i;
+}
+
+template <typename T>
+__global__ void k_derive(BinArgs b, const int *perm, const double *posw, int4 *sp_i0,
+                         typename V4<T>::t *sp_d0, void *rs, int *cell_key, int *cell_cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= b.N) return;
+  int u = perm[i];
+  double x[3];
+  int iw[3], c[3];
+  T d0[3];
+  for (int d = 0; d < 3; ++d) {
+    x[d] = posw[3 * (int64_t)u + d];
+    int i0 = support_start(x[d], b.h, b.P);
+    iw[d] = wrapi(i0, b.Ng);
+    d0[d] = (T)(i0 * b.h - x[d]);
+    c[d] = min((int)(x[d] / b.cs), b.nc - 1);
+  }
+  sp_i0[i] = make_int4(iw[0], iw[1], iw[2], 0);
+  typename V4<T>::t dd;
+  dd.x = d0[0];
+  dd.y = d0[1];
+  dd.z = d0[2];
+  dd.w = 0;
+  sp_d0[i] = dd;
+  if (sizeof(T) == 4) {
+    int packed = c[0] | (c[1] << 10) | (c[2] << 20);
+    ((float4 *)rs)[i] = make_float4((float)(x[0] - c[0] * b.cs), (float)(x[1] - c[1] * b.cs),
+                                    (float)(x[2] - c[2] * b.cs), __int_as_float(packed));
+  } else {
+    ((double4_32a *)rs)[i] = make_double4_32a(x[0], x[1], x[2], 0.0);
+  }
+  int ck = (c[2] * b.nc + c[1]) * b.nc + c[0];
+  cell_key[i] = ck;
+  atomicAdd(&cell_cnt[ck], 1);
+}
+
+__global__ void k_cell_scatter(int N, const int *cell_key, const int *start, int *cur, int *list) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int ck = cell_key[i];
+  list[start[ck] + atomicAdd(&cur[ck], 1)] = i;
+}
+
+struct NbrArgs {
+  int N, nc;
+  float csf, Lf, rc2f;
+  double L, rc2;
+};
+
+__device__ __forceinline__ void unpack_cell(float w, int c[3]) {
+  int p = __float_as_int(w);
+  c[0] = p & 1023;
+  c[1] = (p >> 10) & 1023;
+  c[2] = (p >> 20) & 1023;
+}
+
+// Separation x_i - x_j (minimum image) for the two position representations.
+__device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const float4 &pj, const NbrArgs &a) {
+  int cj[3];
+  unpack_cell(pj.w, cj);
+  int dc[3];
+  for (int d = 0; d < 3; ++d) {
+    int t = ci[d] - cj[d];
+    if (t > a.nc / 2) t -= a.nc;
+    if (t < -(a.nc / 2)) t += a.nc;
+    dc[d] = t;
+  }
+  float3 r = make_float3(dc[0] * a.csf + (pi.x - pj.x), dc[1] * a.csf + (pi.y - pj.y),
+                         dc[2] * a.csf + (pi.z - pj.z));
+  if (a.nc < 3) {
+    r.x -= a.Lf * rintf(r.x / a.Lf);
+    r.y -= a.Lf * rintf(r.y / a.Lf);
+    r.z -= a.Lf * rintf(r.z / a.Lf);
+  }
+  return r;
+}
+
+template <typename T, bool FILL>
+__global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const int *cell_list, int *cnt_or_start,
+                      int *list) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  int ci[3];
+  float4 pf;
+  double4_32a pd;
+  if (sizeof(T) == 4) {
+    pf = ((const float4 *)rs)[i];
+    unpack_cell(pf.w, ci);
+  } else {
+    pd = ((const double4_32a *)rs)[i];
+    ci[0] = min((int)(pd.x / (a.L / a.nc)), a.nc - 1);
+    ci[1] = min((int)(pd.y / (a.L / a.nc)), a.nc - 1);
+    ci[2] = min((int)(pd.z / (a.L / a.nc)), a.nc - 1);
+  }
+  int lo = a.nc >= 3 ? -1 : 0, hi = a.nc >= 2 ? 1 : 0;
+  int n = 0, off = FILL ? cnt_or_start[i] : 0;
+  for (int dz = lo; dz <= hi; ++dz)
+    for (int dy = lo; dy <= hi; ++dy)
+      for (int dx = lo; dx <= hi; ++dx) {
+        int c = (wrapi(ci[2] + dz, a.nc) * a.nc + wrapi(ci[1] + dy, a.nc)) * a.nc + wrapi(ci[0] + dx, a.nc);
+        int e = cell_start[c + 1];
+        for (int k = cell_start[c]; k < e; ++k) {
+          int j = cell_list[k];
+          if (j == i) continue;
+          bool in;
+          if (sizeof(T) == 4) {
+            float3 r = sep(pf, ci, ((const float4 *)rs)[j], a);
+            in = r.x * r.x + r.y * r.y + r.z * r.z < a.rc2f;
+          } else {
+            double4_32a q = ((const double4_32a *)rs)[j];
+            double rx = pd.x - q.x, ry = pd.y - q.y, rz = pd.z - q.z;
+            rx -= a.L * rint(rx / a.L);
+            ry -= a.L * rint(ry / a.L);
+            rz -= a.L * rint(rz / a.L);
+            in = rx * rx + ry * ry + rz * rz < a.rc2;
+          }
+          if (in) {
+            if (FILL) list[off + n] = j;
+            ++n;
+          }
+        }
+      }
+  if (!FILL) cnt_or_start[i] = n;
+}
+
+void *alloc_dev(pse_ctx *c, size_t bytes) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  c->allocs.push_back(p);
+  c->dev_bytes += (int64_t)bytes;
+  return p;
+}
+
+}  // namespace
+
+// Exclusive scan of n+1 ints (in[n] must be 0) so that out[n] is the total.
+pse_status exclusive_scan(pse_ctx *c, int *buf, int64_t n1, cudaStream_t s) {
+  // level sizes
+  int64_t sizes[8];
+  int levels = 0;
+  int64_t len = n1;
+  while (true) {
+    sizes[levels++] = len;
+    if (len <= SCAN_BLK) break;
+    len = ceil_div(len, SCAN_BLK);
+    if (levels >= 7) break;
+  }
+  int *bufs[8];
+  bufs[0] = buf;
+  int64_t off = 0;
+  for (int l = 1; l < levels; ++l) {
+    bufs[l] = c->d_scan_tmp + off;
+    off += sizes[l];
+  }
+  for (int l = 0; l < levels; ++l) {
+    int64_t nb = ceil_div(sizes[l], SCAN_BLK);
+    k_scan_block<<<(unsigned)nb, SCAN_NT, 0, s>>>(bufs[l], bufs[l], sizes[l], l + 1 < levels ? bufs[l + 1] : nullptr);
+  }
+  for (int l = levels - 2; l >= 0; --l) {
+    int64_t nb = ceil_div(sizes[l], SCAN_BLK);
+    k_scan_add<<<(unsigned)nb, SCAN_NT, 0, s>>>(bufs[l], sizes[l], bufs[l + 1]);
+  }
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+int64_t scan_tmp_ints(int64_t n1) {
+  int64_t tot = 0, len = n1;
+  while (len > SCAN_BLK) {
+    len = ceil_div(len, SCAN_BLK);
+    tot += len;
+  }
+  return tot + 16;
+}
+
+// Builds the sorted configuration for positions d_pos (device, user order, FP64).
+pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
+  const Params &p = c->p;
+  int N = (int)p.N;
+  BinArgs b;
+  b.N = N;
+  b.L = p.L;
+  b.h = p.h;
+  b.cs = p.cs;
+  b.Ng = p.Ng;
+  b.P = p.P;
+  b.nc = p.nc;
+  for (int d = 0; d < 3; ++d) {
+    b.T[d] = p.tile[d];
+    b.nt[d] = p.ntile[d];
+  }
+  unsigned nb = (unsigned)ceil_div(N, 256);
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_start, 0, sizeof(int) * (c->ntiles + 1), s));
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_cur, 0, sizeof(int) * (c->ntiles + 1), s));
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->ncells + 1), s));
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cur, 0, sizeof(int) * (c->ncells + 1), s));
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+  k_bin<<<nb, 256, 0, s>>>(b, d_pos, c->d_posw, c->d_tile_key, c->d_tile_start, c->d_flag);
+  PSE_TRY(exclusive_scan(c, c->d_tile_start, c->ntiles + 1, s));
+  k_scatter<<<nb, 256, 0, s>>>(N, c->d_tile_key, c->d_tile_start, c->d_tile_cur, c->d_perm, c->d_inv);
+  if (c->prec == PSE_MIXED)
+    k_derive<float><<<nb, 256, 0, s>>>(b, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0, (float4 *)c->d_sp_d0,
+                                       c->d_rs, c->d_cell_key, c->d_cell_start);
+  else
+    k_derive<double><<<nb, 256, 0, s>>>(b, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0, (double4_32a *)c->d_sp_d0,
+                                        c->d_rs, c->d_cell_key, c->d_cell_start);
+  PSE_TRY(exclusive_scan(c, c->d_cell_start, c->ncells + 1, s));
+  k_cell_scatter<<<nb, 256, 0, s>>>(N, c->d_cell_key, c->d_cell_start, c->d_cell_cur, c->d_cell_list);
+  NbrArgs a;
+  a.N = N;
+  a.nc = p.nc;
+  a.csf = (float)p.cs;
+  a.Lf = (float)p.L;
+  a.L = p.L;
+  a.rc2 = p.rcut * p.rcut;
+  a.rc2f = (float)a.rc2;
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_start + N, 0, sizeof(int), s));
+  if (c->prec == PSE_MIXED)
+    k_nbr<float, false><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
+  else
+    k_nbr<double, false><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
+  PSE_TRY(exclusive_scan(c, c->d_nbr_start, (int64_t)N + 1, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int, c->d_nbr_start + N, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (c->h_pinned_int[1]) {
+    c->err = "non-finite particle position";
+    return PSE_ERR_NONFINITE;
+  }
+  int64_t total = (int64_t)(unsigned)c->h_pinned_int[0];
+  if (total > 2000000000LL) {
+    c->err = "neighbour list exceeds 2^31 entries";
+    return PSE_ERR_INVALID_ARG;
+  }
+  if (total > c->nbr_cap) {
+    int64_t cap = total + total / 4 + 1024;
+    void *q = alloc_dev(c, sizeof(int) * (size_t)cap);
+    if (!q) {
+      c->err = "cannot allocate neighbour list";
+      return PSE_ERR_OOM;
+    }
+    c->d_nbr = (int *)q;  // the old list stays in c->allocs and is freed at destroy
+    c->nbr_cap = cap;
+  }
+  c->npairs = total;
+  if (c->prec == PSE_MIXED)
+    k_nbr<float, true><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
+  else
+    k_nbr<double, true><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+}  // namespace pse

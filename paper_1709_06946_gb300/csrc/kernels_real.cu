@@ -1,0 +1,206 @@
+// Real-space part of the split mobility (Sec. 2.3.1): for every particle the sum
+// over neighbours closer than r_cut of the 8x8 real-space block (Eqs. MUFr-MDCr)
+// applied to [F; S], plus the real-space self term (App. A, Case 3).
+//
+// One thread per particle, neighbour list in CSR form, sorted particle order so
+// that neighbours' records are close in memory.  The seven scalar functions
+// come from a table on r: linear interpolation in FP32 (mixed form), cubic
+// Lagrange interpolation in FP64 with one-sided stencils at the r = 2a node
+// where the functions have a kink.
+#include "device_common.cuh"
+#include "pse_internal.cuh"
+
+namespace pse {
+namespace {
+
+struct RealArgs {
+  int N, nc, len, k2;
+  float csf, Lf;
+  double L;
+  double inv_dr, self_uf, self_es;
+};
+
+template <typename T> struct Pos;
+template <> struct Pos<float> {
+  float4 p;
+  int c[3];
+  __device__ void load(const void *rs, int i) {
+    p = ((const float4 *)rs)[i];
+    int q = __float_as_int(p.w);
+    c[0] = q & 1023;
+    c[1] = (q >> 10) & 1023;
+    c[2] = (q >> 20) & 1023;
+  }
+  __device__ void sep(const void *rs, int j, const RealArgs &a, float d[3]) const {
+    float4 o = ((const float4 *)rs)[j];
+    int q = __float_as_int(o.w);
+    int cj[3] = {q & 1023, (q >> 10) & 1023, (q >> 20) & 1023};
+    float po[3] = {p.x - o.x, p.y - o.y, p.z - o.z};
+    for (int k = 0; k < 3; ++k) {
+      int t = c[k] - cj[k];
+      if (t > a.nc / 2) t -= a.nc;
+      if (t < -(a.nc / 2)) t += a.nc;
+      d[k] = t * a.csf + po[k];
+      if (a.nc < 3) d[k] -= a.Lf * rintf(d[k] / a.Lf);
+    }
+  }
+};
+template <> struct Pos<double> {
+  double4_32a p;
+  __device__ void load(const void *rs, int i) { p = ((const double4_32a *)rs)[i]; }
+  __device__ void sep(const void *rs, int j, const RealArgs &a, double d[3]) const {
+    double4_32a o = ((const double4_32a *)rs)[j];
+    d[0] = p.x - o.x;
+    d[1] = p.y - o.y;
+    d[2] = p.z - o.z;
+    for (int k = 0; k < 3; ++k) d[k] -= a.L * rint(d[k] / a.L);
+  }
+};
+
+__device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, float r, float f[7]) {
+  float x = r * (float)a.inv_dr;
+  int q = min((int)x, a.len - 2);
+  float t = x - (float)q;
+  const float4 *t4 = (const float4 *)tab;
+  float4 a0 = __ldg(t4 + 2 * q), a1 = __ldg(t4 + 2 * q + 1), b0 = __ldg(t4 + 2 * q + 2), b1 = __ldg(t4 + 2 * q + 3);
+  f[0] = fmaf(t, b0.x - a0.x, a0.x);
+  f[1] = fmaf(t, b0.y - a0.y, a0.y);
+  f[2] = fmaf(t, b0.z - a0.z, a0.z);
+  f[3] = fmaf(t, b0.w - a0.w, a0.w);
+  f[4] = fmaf(t, b1.x - a1.x, a1.x);
+  f[5] = fmaf(t, b1.y - a1.y, a1.y);
+  f[6] = fmaf(t, b1.z - a1.z, a1.z);
+}
+
+__device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, double r, double f[7]) {
+  double x = r * a.inv_dr;
+  int q = min((int)x, a.len - 2);
+  int b = q - 1;
+  if (q < a.k2) b = min(b, a.k2 - 3);
+  else b = max(b, a.k2);
+  b = max(0, min(b, a.len - 4));
+  double t = x - (double)b;
+  double w0 = -(t - 1) * (t - 2) * (t - 3) / 6.0, w1 = t * (t - 2) * (t - 3) / 2.0;
+  double w2 = -t * (t - 1) * (t - 3) / 2.0, w3 = t * (t - 1) * (t - 2) / 6.0;
+  const double *r0 = tab + 8 * (size_t)b;
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+    f[k] = w0 * __ldg(r0 + k) + w1 * __ldg(r0 + 8 + k) + w2 * __ldg(r0 + 16 + k) + w3 * __ldg(r0 + 24 + k);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) k_real(RealArgs a, const void *rs, const int *__restrict__ nstart,
+                                              const int *__restrict__ nbr, const T *__restrict__ vin,
+                                              T *__restrict__ vout, const T *__restrict__ tab) {
+  constexpr bool HAS_F = MODE != M_SE, WANT_U = MODE != M_SE, WANT_E = MODE != M_FSU;
+  using T4 = typename V4<T>::t;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.N) return;
+  Pos<T> pi;
+  pi.load(rs, i);
+  const T4 *v4 = (const T4 *)vin;
+  T4 s0 = v4[2 * i], s1 = v4[2 * i + 1];
+  T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
+  if (WANT_U && HAS_F) {
+    U[0] = (T)a.self_uf * s0.x;
+    U[1] = (T)a.self_uf * s0.y;
+    U[2] = (T)a.self_uf * s0.z;
+  }
+  if (WANT_E) {
+    E[0] = (T)a.self_es * s0.w;
+    E[1] = (T)a.self_es * s1.x;
+    E[2] = (T)a.self_es * s1.y;
+    E[3] = (T)a.self_es * s1.z;
+    E[4] = (T)a.self_es * s1.w;
+  }
+  int e = nstart[i + 1];
+  for (int k = nstart[i]; k < e; ++k) {
+    int j = nbr[k];
+    T d[3];
+    pi.sep(rs, j, a, d);
+    T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    T r = sqrt(r2), ir = (T)1 / r;
+    T rh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+    T f[7];
+    lookup(tab, a, r, f);
+    T4 q0 = v4[2 * j], q1 = v4[2 * j + 1];
+    T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
+    T v[3];
+    Smul(s, rh, v);
+    T q = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+    if (WANT_U) {
+      T c = f[3] * q;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) U[m] += f[2] * v[m] + c * rh[m];
+      if (HAS_F) {
+        T F[3] = {q0.x, q0.y, q0.z};
+        T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
+        T cf = (f[1] - f[0]) * rf;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) U[m] += f[0] * F[m] + cf * rh[m];
+      }
+    }
+    if (WANT_E) {
+      T sy[5], yr[5];
+      symY(v, rh, sy);
+      symY(rh, rh, yr);  // = 2 y(rh)
+#pragma unroll
+      for (int m = 0; m < 5; ++m) E[m] += f[4] * s[m] + f[5] * sy[m] + (T)0.5 * f[6] * q * yr[m];
+      if (HAS_F) {
+        T F[3] = {q0.x, q0.y, q0.z};
+        T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
+        T sf[5];
+        symY(F, rh, sf);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) E[m] += (T)(-0.5) * f[2] * sf[m] - (T)0.5 * f[3] * rf * yr[m];
+      }
+    }
+  }
+  T4 o0, o1;
+  o0.x = U[0];
+  o0.y = U[1];
+  o0.z = U[2];
+  o0.w = E[0];
+  o1.x = E[1];
+  o1.y = E[2];
+  o1.z = E[3];
+  o1.w = E[4];
+  T4 *o4 = (T4 *)vout;
+  o4[2 * i] = o0;
+  o4[2 * i + 1] = o1;
+}
+
+template <typename T>
+void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int mode, cudaStream_t s) {
+  unsigned nb = (unsigned)ceil_div(a.N, 128);
+  const T *tab = (const T *)c->d_table;
+  if (mode == M_FULL)
+    k_real<T, M_FULL><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+  else if (mode == M_SE)
+    k_real<T, M_SE><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+  else
+    k_real<T, M_FSU><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+}
+
+}  // namespace
+
+// vout = M_r vin for the current configuration (sorted order, [N][8]).
+pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStream_t s) {
+  RealArgs a;
+  a.N = (int)c->p.N;
+  a.nc = c->p.nc;
+  a.len = c->table_len;
+  a.k2 = c->table_k2;
+  a.csf = (float)c->p.cs;
+  a.Lf = (float)c->p.L;
+  a.L = c->p.L;
+  a.inv_dr = 1.0 / c->table_dr;
+  a.self_uf = c->self_uf;
+  a.self_es = c->self_es;
+  if (c->prec == PSE_MIXED) launch_real<float>(c, a, vin, vout, mode, s);
+  else launch_real<double>(c, a, vin, vout, mode, s);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+}  // namespace pse

@@ -1,0 +1,305 @@
+// Wave-space part of the split mobility (Sec. 2.3.2, Eq. WSops2) and the
+// wave-space square root (Sec. 3.3, Eq. FFTsqrt):
+//   spread (Q) -> R2C FFT -> per-k scaling (P^+ B P with the Gaussian
+//   deconvolution) -> C2R FFT -> interpolate (sigma Q^T).
+//
+// Spreading: one CTA owns one output tile of the grid and accumulates it in
+// shared memory; it visits the particles of the 2x2x2 bins whose Gaussian
+// supports can reach the tile (bins hold particles by the grid index where their
+// support starts), so every grid value is written exactly once with coalesced
+// stores and no global atomics or zeroing pass.  Interpolation mirrors it: the
+// CTA stages its tile in shared memory, each visiting particle sums its
+// in-tile support, and the partial sums are added to the particle outputs.
+// The Gaussian K(r) = (2 xi^2/(pi eta_g))^{3/2} exp(-2 xi^2 r^2/eta_g) is
+// evaluated separably (3P exponentials per particle visit, not P^3).
+#include <cmath>
+
+#include "wave_common.cuh"
+
+namespace pse {
+namespace {
+
+struct ScaleArgs {
+  int Ng, nkx;
+  double kfac, a, q4, eta_g, cscale;
+  size_t cstride;
+};
+
+template <typename T>
+__device__ __forceinline__ void shape(T x, T &s0, T &s1) {
+  if (x < (T)0.5) {  // series: cancellation in sin x - x cos x
+    T x2 = x * x;
+    s0 = (T)1 + x2 * ((T)(-1.0 / 6) + x2 * ((T)(1.0 / 120) + x2 * ((T)(-1.0 / 5040) + x2 * (T)(1.0 / 362880))));
+    s1 = (T)(1.0 / 3) + x2 * ((T)(-1.0 / 30) + x2 * ((T)(1.0 / 840) + x2 * ((T)(-1.0 / 45360) +
+                                x2 * ((T)(1.0 / 3991680) + x2 * (T)(-1.0 / 518918400)))));
+  } else {
+    T sn, cs;
+    if (sizeof(T) == 4) {
+      float a, b;
+      sincosf((float)x, &a, &b);
+      sn = a;
+      cs = b;
+    } else {
+      double a, b;
+      sincos((double)x, &a, &b);
+      sn = a;
+      cs = b;
+    }
+    s0 = sn / x;
+    s1 = (sn - x * cs) / (x * x * x);
+  }
+}
+
+__device__ __forceinline__ bool kvector(const ScaleArgs &s, size_t idx, int &ix, int &iy, int &iz) {
+  ix = (int)(idx % s.nkx);
+  iy = (int)((idx / s.nkx) % s.Ng);
+  iz = (int)(idx / ((size_t)s.nkx * s.Ng));
+  int h = s.Ng / 2;
+  return !(ix == h || iy == h || iz == h || (ix == 0 && iy == 0 && iz == 0));
+}
+
+// P^+ of a velocity mode uh: U = s0 uh, e = (3i s1 / 2) symY(uh, k)   (D = 3i s1 uh k^T)
+template <typename T, bool WU, bool WE>
+__device__ __forceinline__ void project_out(typename Cx<T>::t *g, size_t idx, size_t cs, int slotU, int slotE,
+                                            const T k[3], T s0, T s1, const T ur[3], const T ui[3]) {
+  using C2 = typename Cx<T>::t;
+  if (WU) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      C2 o;
+      o.x = s0 * ur[m];
+      o.y = s0 * ui[m];
+      g[(slotU + m) * cs + idx] = o;
+    }
+  }
+  if (WE) {
+    T er[5], ei[5];
+    symY(ur, k, er);
+    symY(ui, k, ei);
+    T f = (T)1.5 * s1;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      C2 o;
+      o.x = -f * ei[m];
+      o.y = f * er[m];
+      g[(slotE + m) * cs + idx] = o;
+    }
+  }
+}
+
+template <typename T, int MODE>
+__global__ void k_scale(ScaleArgs s, typename Cx<T>::t *g, size_t nk) {
+  using C2 = typename Cx<T>::t;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nk) return;
+  constexpr bool HF = MODE != M_SE, WU = MODE != M_SE, WE = MODE != M_FSU;
+  constexpr int sIn = HF ? 3 : 0, uOut = 0, eOut = (MODE == M_SE) ? 0 : 3;
+  int ix, iy, iz;
+  bool live = kvector(s, idx, ix, iy, iz);
+  const size_t cs = s.cstride;
+  if (!live) {
+    C2 z;
+    z.x = 0;
+    z.y = 0;
+    if (WU)
+      for (int m = 0; m < 3; ++m) g[(uOut + m) * cs + idx] = z;
+    if (WE)
+      for (int m = 0; m < 5; ++m) g[(eOut + m) * cs + idx] = z;
+    return;
+  }
+  int h = s.Ng / 2;
+  T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - s.Ng) * s.kfac), (T)((iz <= h ? iz : iz - s.Ng) * s.kfac)};
+  T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  T kk = sqrt(k2), ik = (T)1 / kk;
+  T s0, s1;
+  shape<T>(kk * (T)s.a, s0, s1);
+  T u = k2 * (T)s.q4;
+  T c = (T)s.cscale * ((T)1 + u) * exp(-((T)1 - (T)s.eta_g) * u) / k2;
+  T fr[3] = {0, 0, 0}, fi[3] = {0, 0, 0};
+  if (HF) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      C2 v = g[m * cs + idx];
+      fr[m] = s0 * v.x;
+      fi[m] = s0 * v.y;
+    }
+  }
+  T sr[5], si[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    C2 v = g[(sIn + m) * cs + idx];
+    sr[m] = v.x;
+    si[m] = v.y;
+  }
+  T skr[3], ski[3];
+  Smul(sr, k, skr);
+  Smul(si, k, ski);
+  T t3 = (T)3 * s1;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {  // f = s0 F - 3i s1 S.k
+    fr[m] += t3 * ski[m];
+    fi[m] -= t3 * skr[m];
+  }
+  T kh[3] = {k[0] * ik, k[1] * ik, k[2] * ik};
+  T pr = kh[0] * fr[0] + kh[1] * fr[1] + kh[2] * fr[2], pi = kh[0] * fi[0] + kh[1] * fi[1] + kh[2] * fi[2];
+  T ur[3], ui[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    ur[m] = c * (fr[m] - kh[m] * pr);
+    ui[m] = c * (fi[m] - kh[m] * pi);
+  }
+  project_out<T, WU, WE>(g, idx, cs, uOut, eOut, k, s0, s1, ur, ui);
+}
+
+// Wave-space noise: dW2 on the half spectrum (Hermitian partners on kx = 0),
+// u = sigma e^{eta_g k^2/8xi^2} sqrt(H/(eta V k^2)) (I - kk) dW2, then P^+.
+template <typename T, bool EXT>
+__global__ void k_noise(ScaleArgs s, const T *__restrict__ w2, uint64_t seed, uint64_t counter,
+                        typename Cx<T>::t *g, size_t nk) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nk) return;
+  using C2 = typename Cx<T>::t;
+  int ix, iy, iz;
+  bool live = kvector(s, idx, ix, iy, iz);
+  const size_t cs = s.cstride;
+  if (!live) {
+    C2 z;
+    z.x = 0;
+    z.y = 0;
+    for (int m = 0; m < 8; ++m) g[m * cs + idx] = z;
+    return;
+  }
+  int h = s.Ng / 2, Ng = s.Ng;
+  bool partner = ix == 0 && (iz > h || (iz == 0 && iy > h));
+  size_t src = idx;
+  if (partner) src = ((size_t)((Ng - iz) % Ng) * Ng + (size_t)((Ng - iy) % Ng)) * s.nkx;
+  T dr[3], di[3];
+  const T isq2 = (T)0.70710678118654752;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T re, im;
+    size_t n = (size_t)m * nk + src;
+    if (EXT) {
+      re = w2[2 * n];
+      im = w2[2 * n + 1];
+    } else {
+      normal_pair<T>(seed, counter, 2u, (uint64_t)n, re, im);
+    }
+    dr[m] = re * isq2;
+    di[m] = (partner ? -im : im) * isq2;
+  }
+  T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - Ng) * s.kfac), (T)((iz <= h ? iz : iz - Ng) * s.kfac)};
+  T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  T kk = sqrt(k2), ik = (T)1 / kk;
+  T s0, s1;
+  shape<T>(kk * (T)s.a, s0, s1);
+  T u = k2 * (T)s.q4;
+  T c = (T)s.cscale * sqrt(((T)1 + u) / k2) * exp(-(T)0.5 * ((T)1 - (T)s.eta_g) * u);
+  T kh[3] = {k[0] * ik, k[1] * ik, k[2] * ik};
+  T pr = kh[0] * dr[0] + kh[1] * dr[1] + kh[2] * dr[2], pi = kh[0] * di[0] + kh[1] * di[1] + kh[2] * di[2];
+  T ur[3], ui[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    ur[m] = c * (dr[m] - kh[m] * pr);
+    ui[m] = c * (di[m] - kh[m] * pi);
+  }
+  project_out<T, true, true>(g, idx, cs, 0, 3, k, s0, s1, ur, ui);
+}
+
+WaveArgs wave_args(const pse_ctx *c) {
+  const Params &p = c->p;
+  WaveArgs a;
+  a.N = (int)p.N;
+  a.Ng = p.Ng;
+  a.P = p.P;
+  for (int d = 0; d < 3; ++d) {
+    a.T[d] = p.tile[d];
+    a.nt[d] = p.ntile[d];
+  }
+  a.h = p.h;
+  a.alpha = 2.0 * p.xi * p.xi / p.eta_g;
+  a.pref = std::pow(2.0 * p.xi * p.xi / (M_PI * p.eta_g), 1.5);
+  return a;
+}
+
+ScaleArgs scale_args(const pse_ctx *c, double cscale) {
+  const Params &p = c->p;
+  ScaleArgs s;
+  s.Ng = p.Ng;
+  s.nkx = p.nkx;
+  s.kfac = 2.0 * M_PI / p.L;
+  s.a = p.a;
+  s.q4 = 1.0 / (4.0 * p.xi * p.xi);
+  s.eta_g = p.eta_g;
+  s.cscale = cscale;
+  s.cstride = (size_t)p.Ng * p.Ng * p.nkx;
+  return s;
+}
+
+template <typename T>
+pse_status fft(pse_ctx *c, bool forward, int batch, cudaStream_t s) {
+  cufftHandle plan = forward ? c->plan_r2c[batch] : c->plan_c2r[batch];
+  PSE_CUFFT_TRY(c, cufftSetStream(plan, s));
+  if (sizeof(T) == 4) {
+    if (forward) PSE_CUFFT_TRY(c, cufftExecR2C(plan, (cufftReal *)c->d_grid, (cufftComplex *)c->d_cgrid));
+    else PSE_CUFFT_TRY(c, cufftExecC2R(plan, (cufftComplex *)c->d_cgrid, (cufftReal *)c->d_grid));
+  } else {
+    if (forward) PSE_CUFFT_TRY(c, cufftExecD2Z(plan, (cufftDoubleReal *)c->d_grid, (cufftDoubleComplex *)c->d_cgrid));
+    else PSE_CUFFT_TRY(c, cufftExecZ2D(plan, (cufftDoubleComplex *)c->d_cgrid, (cufftDoubleReal *)c->d_grid));
+  }
+  return PSE_OK;
+}
+
+template <typename T>
+pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s) {
+  WaveArgs a = wave_args(c);
+  const Params &p = c->p;
+  if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout, 0, sizeof(T) * 8 * (size_t)p.N, s));
+  int cin = mode == M_SE ? 5 : 8, cout = mode == M_FULL ? 8 : (mode == M_SE ? 5 : 3);
+  spread_launch(c, a, vin, mode, s);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  PSE_TRY(fft<T>(c, true, cin, s));
+  ScaleArgs sa = scale_args(c, p.sigma() * p.sigma() / (p.V() * p.eta));
+  size_t nk = (size_t)p.Ng * p.Ng * p.nkx;
+  unsigned nb = (unsigned)ceil_div((int64_t)nk, 256);
+  using C2 = typename Cx<T>::t;
+  if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+  else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+  else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  PSE_TRY(fft<T>(c, false, cout, s));
+  interp_launch(c, a, vout, mode, s);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+template <typename T>
+pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t counter, void *vout, cudaStream_t s) {
+  const Params &p = c->p;
+  WaveArgs a = wave_args(c);
+  ScaleArgs sa = scale_args(c, p.sigma() / std::sqrt(p.eta * p.V()));
+  size_t nk = (size_t)p.Ng * p.Ng * p.nkx;
+  unsigned nb = (unsigned)ceil_div((int64_t)nk, 256);
+  using C2 = typename Cx<T>::t;
+  if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, (C2 *)c->d_cgrid, nk);
+  else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, (C2 *)c->d_cgrid, nk);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  PSE_TRY(fft<T>(c, false, 8, s));
+  interp_launch(c, a, vout, M_FULL, s);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+}  // namespace
+
+pse_status wave_apply(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s) {
+  return c->prec == PSE_MIXED ? wave_apply_t<float>(c, vin, vout, mode, add, s)
+                              : wave_apply_t<double>(c, vin, vout, mode, add, s);
+}
+
+pse_status wave_noise(pse_ctx *c, const void *w2, uint64_t seed, uint64_t counter, void *vout, cudaStream_t s) {
+  return c->prec == PSE_MIXED ? wave_noise_t<float>(c, w2, seed, counter, vout, s)
+                              : wave_noise_t<double>(c, w2, seed, counter, vout, s);
+}
+
+}  // namespace pse

@@ -1,0 +1,253 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 over all outputs): 1e-10 for the FP64 form and 2e-5
+for the mixed form against the oracle PSE with identical parameters and
+identical noise; both forms within the PSE tolerance eps of the dense Ewald
+sum.  Sizes span several spreading tiles and cells; edge cases cover a single
+particle, overlapping pairs, positions outside the box, one-sided inputs,
+boxes with fewer than three cells per side and even/odd support sizes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import pse_inputs
+from oracle import ewald, params, philox, pse as opse
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+TOL = {'fp64': 1e-10, 'mixed': 2e-5}
+
+
+@pytest.fixture(scope='module')
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    import paper_1709_06946_gb300 as p
+    p.build()
+    p.load()
+    return p
+
+
+def _dt(prec):
+    return torch.float64 if prec == 'fp64' else torch.float32
+
+
+def _cuda(x, dtype=None):
+    return torch.tensor(np.ascontiguousarray(x), device='cuda', dtype=dtype)
+
+
+def _oracle_params(h, N, L, xi, tol, **kw):
+    inf = h.info
+    return params.choose(N, L, 1.0, 1.0, 1.0, xi, tol, Ng=inf['Ng'], P=inf['P'], rcut=inf['rcut'], **kw)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _mob(pkg, h, pos, F, S, prec, parts='all'):
+    dt = _dt(prec)
+    U, E = h.mobility(_cuda(pos, torch.float64), None if F is None else _cuda(F, dt),
+                      None if S is None else _cuda(S, dt), parts=parts)
+    return np.concatenate([U.double().cpu().numpy(), E.double().cpu().numpy()], 1)
+
+
+@pytest.mark.parametrize('prec', ['fp64', 'mixed'])
+def test_mobility_config1(pkg, prec):
+    """N=100, phi=0.1, eps=1e-3 (RSA); parity per part and in total, and within eps of Ewald."""
+    N, phi, xi, tol = 100, 0.1, 0.5, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=1)
+    F, S = pse_inputs.moments(N, seed=2)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision=prec)
+    p = _oracle_params(h, N, L, xi, tol)
+    op = opse.RealOp(pos, p)
+    for parts in ('real', 'wave', 'all'):
+        got = _mob(pkg, h, pos, F, S, prec, parts)
+        oparts = {'real': ('real',), 'wave': ('wave',), 'all': ('real', 'wave')}[parts]
+        Uo, Eo = opse.mobility_apply(pos, F, S, p, parts=oparts, real_op=op)
+        assert _rel(got, np.concatenate([Uo, Eo], 1)) < TOL[prec], parts
+    M = ewald.dense_mobility(pos, L, xi=0.6, tol=1e-15)
+    ref = (M @ np.concatenate([F, S], 1).ravel()).reshape(N, 8)
+    assert _rel(got, ref) < tol
+    h.close()
+
+
+@pytest.mark.parametrize('prec', ['fp64', 'mixed'])
+def test_mobility_dense_many_tiles(pkg, prec):
+    """N=3000 at phi=0.3: several spreading tiles per side and many cells."""
+    N, phi, xi, tol = 3000, 0.3, 0.7, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=5)
+    F, S = pse_inputs.moments(N, seed=6)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision=prec, tile=(8, 8, 8))
+    p = _oracle_params(h, N, L, xi, tol)
+    assert h.info['Ng'] // 8 >= 3 and h.info['cells_per_side'] >= 3
+    got = _mob(pkg, h, pos, F, S, prec)
+    Uo, Eo = opse.mobility_apply(pos, F, S, p)
+    assert _rel(got, np.concatenate([Uo, Eo], 1)) < TOL[prec]
+    h.close()
+
+
+@pytest.mark.parametrize('prec', ['fp64', 'mixed'])
+def test_edge_cases(pkg, prec):
+    # single particle: only self terms and its periodic images (wave space)
+    L = 12.0
+    pos = np.array([[1.0, 11.5, 6.0]])
+    F, S = pse_inputs.moments(1, seed=3)
+    h = pkg.PSE(1, L, xi=0.9, tol=1e-3, precision=prec)
+    p = _oracle_params(h, 1, L, 0.9, 1e-3)
+    Uo, Eo = opse.mobility_apply(pos, F, S, p)
+    assert _rel(_mob(pkg, h, pos, F, S, prec), np.concatenate([Uo, Eo], 1)) < TOL[prec]
+    h.close()
+    # overlapping pairs, positions outside [0, L), tiny box (< 3 cells), even support, one-sided inputs
+    N, L = 40, 8.0
+    rng = np.random.default_rng(7)
+    pos = rng.uniform(-L, 2 * L, (N, 3))
+    pos[1] = pos[0] + np.array([0.9, 0.3, -0.2])          # deep overlap r ~ 0.97a
+    pos[2] = pos[0] + np.array([2.0, 0.0, 0.0])           # exact contact
+    F, S = pse_inputs.moments(N, seed=8)
+    for tol, rule in ((1e-3, 'paper'), (1e-4, 'paper')):
+        h = pkg.PSE(N, L, xi=0.9, tol=tol, precision=prec, rule=rule)
+        assert h.info['cells_per_side'] < 3
+        p = _oracle_params(h, N, L, 0.9, tol, rule=rule)
+        Uo, Eo = opse.mobility_apply(pos, F, S, p)
+        assert _rel(_mob(pkg, h, pos, F, S, prec), np.concatenate([Uo, Eo], 1)) < TOL[prec]
+        Uo, Eo = opse.mobility_apply(pos, F, 0 * S, p)
+        assert _rel(_mob(pkg, h, pos, F, None, prec), np.concatenate([Uo, Eo], 1)) < TOL[prec]
+        Uo, Eo = opse.mobility_apply(pos, 0 * F, S, p)
+        assert _rel(_mob(pkg, h, pos, None, S, prec), np.concatenate([Uo, Eo], 1)) < TOL[prec]
+        h.close()
+
+
+def test_host_arrays_through_the_abi(pkg):
+    """numpy (host) arrays are staged by the library and give the same result."""
+    N, phi, xi, tol = 100, 0.1, 0.5, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=1)
+    F, S = pse_inputs.moments(N, seed=2)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='fp64')
+    U, E = h.mobility(pos, F, S)
+    got = _mob(pkg, h, pos, F, S, 'fp64')
+    assert np.abs(np.concatenate([U, E], 1) - got).max() < 1e-14 * np.abs(got).max()
+    h.close()
+
+
+@pytest.mark.parametrize('prec', ['fp64', 'mixed'])
+def test_brownian_sample_external_noise(pkg, prec):
+    N, phi, xi, tol, dt = 200, 0.2, 0.6, 1e-3, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=9)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision=prec, lanczos_tol=0.0, lanczos_maxiter=12)
+    p = _oracle_params(h, N, L, xi, tol)
+    w1 = pse_inputs.lanczos_noise(N, seed=10)
+    w2 = pse_inputs.wave_noise(p.Ng, seed=11)
+    U, E, st = h.brownian(_cuda(pos, torch.float64), dt, w1=_cuda(w1, _dt(prec)), w2=_cuda(w2, _dt(prec)))
+    B, sto = opse.brownian_sample(pos, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=12)
+    assert st['lanczos_iters'] == 12 and sto['lanczos_iters'] == 12
+    got = np.concatenate([U.double().cpu().numpy(), E.double().cpu().numpy()], 1)
+    assert _rel(got, B) < TOL[prec]
+
+
+def test_in_kernel_noise_matches_published_generator(pkg):
+    """In-kernel Philox4x32-10 noise equals the same stream generated by the oracle."""
+    N, phi, xi, tol, dt = 150, 0.15, 0.6, 1e-3, 1e-2
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=12)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='fp64', lanczos_tol=1e-12)
+    Ng = h.info['Ng']
+    seed, counter = 0x1234567890ABCDEF, 77
+    U, E, _ = h.brownian(_cuda(pos, torch.float64), dt, seed=seed, counter=counter)
+    w1 = philox.lanczos_noise(seed, counter, N)
+    w2 = philox.wave_noise(seed, counter, Ng)
+    U2, E2, _ = h.brownian(_cuda(pos, torch.float64), dt, w1=_cuda(w1, torch.float64), w2=_cuda(w2, torch.float64))
+    a = np.concatenate([U.cpu().numpy(), E.cpu().numpy()], 1)
+    b = np.concatenate([U2.cpu().numpy(), E2.cpu().numpy()], 1)
+    assert _rel(a, b) < 1e-12
+
+
+@pytest.mark.parametrize('prec', ['fp64', 'mixed'])
+@pytest.mark.parametrize('with_force', [False, True])
+def test_constrained_step(pkg, prec, with_force):
+    N, phi, xi, tol, dt = 150, 0.2, 0.7, 1e-3, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=13)
+    ktol = 1e-10 if prec == 'fp64' else 1e-6
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision=prec, lanczos_tol=0.0, lanczos_maxiter=10, krylov_tol=ktol,
+                krylov_maxiter=100)
+    p = _oracle_params(h, N, L, xi, tol)
+    w1 = pse_inputs.lanczos_noise(N, seed=14)
+    w2 = pse_inputs.wave_noise(p.Ng, seed=15)
+    FP = pse_inputs.moments(N, seed=16)[0] * 5.0 if with_force else None
+    x = _cuda(pos, torch.float64)
+    S, st = h.step(x, dt, FP=None if FP is None else _cuda(FP, _dt(prec)), w1=_cuda(w1, _dt(prec)),
+                   w2=_cuda(w2, _dt(prec)), want_S=True)
+    x1, So, sto = opse.constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=10,
+                                        krylov_tol=1e-12, krylov_maxiter=200)
+    disp_o = x1 - pos
+    disp_o -= L * np.rint(disp_o / L)
+    disp_g = x.cpu().numpy() - pos
+    disp_g -= L * np.rint(disp_g / L)
+    assert _rel(disp_g, disp_o) < (1e-9 if prec == 'fp64' else 2e-5)
+    assert _rel(S.double().cpu().numpy(), So) < (1e-9 if prec == 'fp64' else 2e-5)
+    assert 1 <= st['krylov_iters'] <= 100
+
+
+def test_step_internal_noise_is_reproducible(pkg):
+    N, phi, xi, tol = 300, 0.25, 0.7, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=17)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed')
+    xa = _cuda(pos, torch.float64)
+    xb = _cuda(pos, torch.float64)
+    _, sa = h.step(xa, 1e-3, seed=5, step=3)
+    _, sb = h.step(xb, 1e-3, seed=5, step=3)
+    assert torch.max(torch.abs(xa - xb)).item() < 1e-6
+    assert 1 <= sa['lanczos_iters'] <= 100 and 1 <= sa['krylov_iters'] <= 50
+    d = (xa.cpu().numpy() - pos)
+    d -= L * np.rint(d / L)
+    assert 0 < np.abs(d).max() < 0.5
+
+
+def test_nonfinite_input_rejected(pkg):
+    N, L = 20, 12.0
+    pos = pse_inputs.random_positions(N, L, seed=2)
+    pos[3, 1] = np.nan
+    h = pkg.PSE(N, L, xi=1.0, tol=1e-3, precision='mixed')
+    with pytest.raises(pkg.PSEError) as e:
+        h.mobility(_cuda(pos, torch.float64), _cuda(np.ones((N, 3)), torch.float32))
+    assert e.value.code == 5
+    h.close()
+
+
+@pytest.mark.parametrize('prec', ['mixed'])
+def test_full_size_sampled(pkg, prec):
+    """N = 1,048,576 at phi = 0.3, eps = 1e-3 (the benchmark workload, launch as in bench.py):
+    wave part against the oracle's NUFFT at full size, real part on sampled
+    particles, symmetry u.Mv = v.Mu of the full product."""
+    from scipy.spatial import cKDTree
+    from oracle import realspace as R
+    N, phi, xi, tol = 1048576, 0.3, 0.5, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=1)
+    F, S = pse_inputs.moments(N, seed=2)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision=prec)
+    p = _oracle_params(h, N, L, xi, tol)
+    wave = _mob(pkg, h, pos, F, S, prec, 'wave')
+    w = opse.wave_apply(pos, F, S, p)
+    assert _rel(wave, np.concatenate([w['U'], w['E']], 1)) < TOL[prec]
+    real = _mob(pkg, h, pos, F, S, prec, 'real')
+    idx = np.random.default_rng(3).choice(N, 64, replace=False)
+    tree = cKDTree(np.mod(pos, L), boxsize=L)
+    v = np.concatenate([F, S], 1)
+    ref = np.zeros((idx.size, 8))
+    selfb = R.self_block(xi, 1.0, 1.0)
+    for n, i in enumerate(idx):
+        nb = np.array([j for j in tree.query_ball_point(pos[i], p.rcut) if j != i])
+        d = pos[i] - pos[nb]
+        d -= L * np.rint(d / L)
+        B = R.pair_blocks(d, xi, 1.0, 1.0)
+        ref[n] = selfb @ v[i] + np.einsum('pab,pb->a', B, v[nb])
+    assert _rel(real[idx], ref) < TOL[prec]
+    # symmetry of the whole operator at full size
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((N, 8))
+    Mu = _mob(pkg, h, pos, u[:, :3], u[:, 3:], prec)
+    Mv = _mob(pkg, h, pos, F, S, prec)
+    assert abs(np.sum(u * Mv) - np.sum(v * Mu)) < 1e-5 * abs(np.sum(v * Mv))
+    h.close()

@@ -1,0 +1,105 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol that
+include/pse.h declares, and its host-side pieces (real-space table generator,
+tridiagonal square root) agree with the oracle.  No GPU compute is issued."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1709_06946_gb300 as pkg
+from oracle import realspace as R
+from oracle.basis import Y
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope='module')
+def lib():
+    pkg.build()
+    return pkg.load()
+
+
+def test_exports_every_header_symbol(lib):
+    hdr = open(os.path.join(ROOT, 'include', 'pse.h')).read()
+    names = set(re.findall(r'^(?:pse_status|void|const char)\s*\*?\s*(pse_[a-z_0-9]+)\s*\(', hdr, re.M))
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    declared = {n for n, _, _ in pkg.binding.SIGNATURES}
+    assert names == declared
+
+
+def test_default_options(lib):
+    o = pkg.binding.Options()
+    lib.pse_default_options(ctypes.byref(o))
+    assert o.rule == 0 and o.lanczos_maxiter == 100 and o.krylov_maxiter == 50
+    assert o.lanczos_tol < 0 and o.krylov_tol < 0
+
+
+def test_invalid_arguments_rejected(lib):
+    h = ctypes.c_void_p()
+    o = pkg.binding.Options()
+    lib.pse_default_options(ctypes.byref(o))
+    # r_cut = 1 + sqrt(ln(1e4))/0.5 = 7.07 > L/2 = 5: rejected before any device call
+    assert lib.pse_create(ctypes.byref(h), 10, 10.0, 1.0, 1.0, 1.0, 0.5, 1e-3, 0, ctypes.byref(o)) == 1
+    assert b'exceeds L/2' in lib.pse_last_error(None)
+    assert lib.pse_create(ctypes.byref(h), 0, 30.0, 1.0, 1.0, 1.0, 0.5, 1e-3, 0, ctypes.byref(o)) == 1
+    assert lib.pse_create(ctypes.byref(h), 10, 30.0, 1.0, 1.0, 1.0, 0.5, 0.5, 0, ctypes.byref(o)) == 1
+    assert lib.pse_status_string(4) == b'Krylov iteration cap reached'
+
+
+def _yv(M):
+    return np.einsum('ij,kij->k', M, Y)
+
+
+def _block(f, rh):
+    fp, fr, gS, gR, kS, kX, kR = f
+    B = np.zeros((8, 8))
+    for c in range(8):
+        e = np.zeros(8)
+        e[c] = 1
+        F, s = e[:3], e[3:]
+        S = np.einsum('k,kij->ij', s, Y)
+        v = S @ rh
+        q = rh @ v
+        U = fp * F + (fr - fp) * (rh @ F) * rh + gS * v + gR * q * rh
+        E = (-(gS / 2) * _yv(np.outer(F, rh) + np.outer(rh, F)) - gR * (rh @ F) * _yv(np.outer(rh, rh))
+             + kS * s + kX * _yv(np.outer(v, rh) + np.outer(rh, v)) + kR * q * _yv(np.outer(rh, rh)))
+        B[:, c] = np.concatenate([U, E])
+    return B
+
+
+@pytest.mark.parametrize('xi,eta,a', [(0.5, 1.0, 1.0), (0.8, 1.7, 1.3)])
+def test_table_functions_match_oracle(lib, xi, eta, a):
+    rs = np.array([0.5, 1.0, 1.7, 1.999, 2.0, 2.001, 2.6, 3.5, 5.0, 7.0]) * a
+    out = np.zeros((rs.size, 7))
+    self2 = np.zeros(2)
+    lib.pse_internal_real_functions(ctypes.c_double(a), ctypes.c_double(eta), ctypes.c_double(xi), rs.size,
+                                    rs.ctypes.data_as(ctypes.c_void_p), out.ctypes.data_as(ctypes.c_void_p),
+                                    self2.ctypes.data_as(ctypes.c_void_p))
+    Bs = R.self_block(xi, a, eta)
+    assert self2[0] == pytest.approx(Bs[0, 0], rel=1e-13)
+    assert self2[1] == pytest.approx(Bs[3, 3], rel=1e-13)
+    rng = np.random.default_rng(0)
+    for r, f in zip(rs, out):
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        Bo = R.pair_blocks((d * r)[None], xi, a, eta)[0]
+        assert np.abs(_block(f, d) - Bo).max() < 1e-13 * max(1.0, np.abs(Bo).max() / 1e-3)
+
+
+def test_tridiagonal_square_root(lib):
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 7, 40):
+        d = rng.uniform(0.5, 2.0, n)
+        e = rng.uniform(-0.4, 0.4, max(n - 1, 1))[:max(n - 1, 0)]
+        c = np.zeros(n)
+        ep = e if n > 1 else np.zeros(1)
+        assert lib.pse_internal_tridiag_sqrt_e1(n, d.ctypes.data_as(ctypes.c_void_p),
+                                                ep.ctypes.data_as(ctypes.c_void_p),
+                                                c.ctypes.data_as(ctypes.c_void_p)) == 0
+        T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+        w, Q = np.linalg.eigh(T)
+        assert np.abs(c - Q @ (np.sqrt(w) * Q[0])).max() < 1e-13
