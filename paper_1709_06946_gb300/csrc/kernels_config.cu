@@ -327,10 +327,11 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   a.rc2 = p.rcut * p.rcut;
   a.rc2f = (float)a.rc2;
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_start + N, 0, sizeof(int), s));
+  unsigned nb128 = (unsigned)ceil_div(N, 128);
   if (c->prec == PSE_MIXED)
-    k_nbr<float, false><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
+    k_nbr<float, false><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
   else
-    k_nbr<double, false><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
+    k_nbr<double, false><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
   PSE_TRY(exclusive_scan(c, c->d_nbr_start, (int64_t)N + 1, s));
   PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int, c->d_nbr_start + N, sizeof(int), cudaMemcpyDeviceToHost, s));
   PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -357,9 +358,9 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   }
   c->npairs = total;
   if (c->prec == PSE_MIXED)
-    k_nbr<float, true><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
+    k_nbr<float, true><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
   else
-    k_nbr<double, true><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
+    k_nbr<double, true><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
