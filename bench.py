@@ -1,0 +1,331 @@
+"""Benchmark: constrained Brownian mid-point steps per second of the stresslet PSE method.
+
+Workload (synthetic, seeded): N = 1,048,576 hard spheres of radius a = 1 at
+volume fraction phi = 0.3 by random sequential addition in a cubic periodic
+box L = (4 pi N / (3 phi))^{1/3}; eta = kT = 1; PSE tolerance eps = 1e-3;
+mixed precision (FP32 grids, FFTs, pair sums and vectors; FP64 Krylov and
+Lanczos scalars).  One step = one full constrained mid-point step: Brownian
+slip by Lanczos + wave-space noise, mid-point move, GMRES stresslet solve,
+final product and position update (no work skipped).  Inputs (grids 0.9 GB,
+Krylov basis, particle data) exceed the 129 MB L2 between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (a bounded sample of the same workload).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = 'Brownian steps/s, N=1M phi=0.3 eps=1e-3, mixed vs FP64; served p50/p99 latency'
+FP32_PEAK_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=10)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--N', type=int, default=1048576)
+    ap.add_argument('--phi', type=float, default=0.3)
+    ap.add_argument('--tol', type=float, default=1e-3)
+    ap.add_argument('--xi', type=float, default=0.7)
+    ap.add_argument('--dt', type=float, default=1e-3)
+    ap.add_argument('--fp64-steps', type=int, default=2)
+    ap.add_argument('--e2e-steps', type=int, default=3)
+    ap.add_argument('--cpu-N', type=int, default=1000)
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        os.environ.setdefault('MASTER_ADDR', '127.0.0.1')
+        backend = 'nccl' if args.impl == 'ours' and torch.cuda.is_available() else 'gloo'
+        if backend == 'nccl':
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.Q,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(',')]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith('active'):
+                    reasons.add(nm)
+        return {'sm_mhz': float(np.median(sm)) if sm else None, 'sm_max_mhz': smax, 'reasons': sorted(reasons),
+                'samples': len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def oracle_step_rate(N_s, phi, tol, xi, dt, seed=1):
+    """Seconds for one oracle constrained step at N_s particles (same phi, tol, xi)."""
+    import pse_inputs
+    from oracle import params, philox, pse as opse
+    pos, L = pse_inputs.rsa_positions(N_s, phi, seed=seed)
+    p = params.choose(N_s, L, 1.0, 1.0, 1.0, xi, tol)
+    w1 = philox.lanczos_noise(seed, 0, N_s)
+    w2 = philox.wave_noise(seed, 0, p.Ng)
+    t0 = time.perf_counter()
+    opse.constrained_step(pos, None, dt, w1, w2, p)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args):
+    dt_s = oracle_step_rate(args.cpu_N, args.phi, args.tol, args.xi, args.dt)
+    value = (args.cpu_N / args.N) / dt_s          # linear-in-N scaling (PTPS constant, Sec. 4)
+    return {'value': value, 'unit': 'steps/s', 'cores': 1, 'kind': 'oracle',
+            'sample': 'one FP64 oracle constrained step at N=%d (phi=%g, eps=%g, xi=%g) took %.2f s; '
+                      'scaled to N=%d by particle count' % (args.cpu_N, args.phi, args.tol, args.xi, dt_s, args.N)}
+
+
+def run_reference(args, world, rank, pg):
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    times = []
+    for k in range(args.warmup + steps):
+        t = oracle_step_rate(args.cpu_N, args.phi, args.tol, args.xi, args.dt, seed=1 + k)
+        if k >= args.warmup:
+            times.append(t)
+    per = float(np.mean(times))
+    value = (args.cpu_N / args.N) / per
+    line = {'metric': METRIC, 'value': value, 'unit': 'steps/s', 'n_gpus': args.gpus, 'steps': steps,
+            'warmup': args.warmup, 'ms_per_step': 1000.0 / value, 'higher_is_better': True, 'scaling': 'weak',
+            'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic', 'impl': 'reference',
+            'config': {'workload': 'N=%d hard spheres phi=%g eps=%g constrained mid-point step' % (args.N, args.phi, args.tol),
+                       'N': args.N, 'phi': args.phi, 'tol': args.tol, 'xi': args.xi},
+            'cpu_baseline': {'value': value, 'unit': 'steps/s', 'cores': 1, 'kind': 'oracle',
+                             'sample': 'FP64 oracle constrained steps at N=%d, scaled to N=%d by particle count'
+                                       % (args.cpu_N, args.N)},
+            'e2e': {'value': value, 'unit': 'steps/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line), flush=True)
+
+
+def real_flops_per_pair():
+    # FP32 operations of the pair kernel per neighbour, counted from its formulas (FMA = 2):
+    # full 8->8 product (Lanczos), S->E (GMRES), [F;S]->U (final velocity).
+    return {'full': 233, 'se': 150, 'fsu': 102}
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    import pse_inputs
+    import paper_1709_06946_gb300 as pkg
+
+    pkg.load()
+    dev = torch.device('cuda', local)
+    torch.cuda.set_device(dev)
+    pos_np, L = pse_inputs.rsa_positions(args.N, args.phi, seed=1 + rank)
+    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed')
+    inf = h.info
+    x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+    stream = torch.cuda.current_stream(dev)
+    st_last = {}
+    for k in range(args.warmup):
+        _, st_last = h.step(x, args.dt, seed=1234 + rank, step=k)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    h.set_profiling(True)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    lat = []
+    iters = []
+    ev0.record(stream)
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        _, st = h.step(x, args.dt, seed=1234 + rank, step=args.warmup + k)
+        lat.append((time.perf_counter() - t0) * 1000.0)
+        iters.append((st['lanczos_iters'], st['krylov_iters'], st['neighbor_pairs']))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    clk = clocks.stop()
+    prof = h.profile()
+    h.set_profiling(False)
+    if pg is not None:
+        t = torch.tensor([elapsed], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+
+    # roofline of the dominant stage (device time per stage from CUDA events on the launching stream)
+    peaks = measured_peaks()
+    stage_ms = prof['ms']
+    Li = sum(i[0] for i in iters)
+    Ki = sum(i[1] for i in iters)
+    npairs = float(np.mean([i[2] for i in iters]))
+    Ng, N = inf['Ng'], args.N
+    n3 = Ng ** 3
+    nkh = Ng * Ng * (Ng // 2 + 1)
+    K = args.steps
+    # per step: GMRES products (5 -> 5) Ki/K times, one final [F;S] -> U product, one noise pass
+    spread_comps = [5] * Ki + [8] * K
+    interp_comps = [5] * Ki + [3] * K + [8] * K
+    algo = {
+        'spread': sum(N * (32 + 4 * c) + c * n3 * 4 for c in spread_comps),
+        'interp': sum(c * n3 * 4 + N * (32 + 4 * c) for c in interp_comps),
+        'scale': sum((ci + co) * nkh * 8 for ci, co in [(5, 5)] * Ki + [(8, 3)] * K),
+        'noise': K * 8 * nkh * 8,
+    }
+    dom = max(('real', 'spread', 'interp', 'scale', 'noise', 'fft'), key=lambda s: stage_ms[s])
+    fl = real_flops_per_pair()
+    if dom == 'real' or dom == 'fft':
+        flops = npairs * (fl['full'] * Li + fl['se'] * Ki + fl['fsu'] * K)
+        achieved = flops / (stage_ms['real'] / 1000.0) / 1e12
+        peak = FP32_PEAK_TFLOPS_AT_MAX
+        roof = {'bound': 'alu', 'kernel': 'k_real (real-space pair sum)', 'achieved': achieved, 'peak': peak,
+                'unit': 'TFLOP/s', 'frac': achieved / peak, 'traffic': None,
+                'peak_note': 'derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz',
+                'launches': prof['calls']['real'], 'flops_per_pair': fl}
+    else:
+        hbm = peaks.get('hbm_gbs', 6800.0)
+        achieved = algo[dom] / (stage_ms[dom] / 1000.0) / 1e9
+        roof = {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s',
+                'frac': achieved / hbm, 'traffic': None, 'peak_note': 'measured hbm_gbs (MEASURED_PEAKS.json)'}
+    wave_rates = {k: {'GB/s': algo[k] / (stage_ms[k] / 1000.0) / 1e9 if stage_ms[k] > 0 else None,
+                      'frac_of_measured_hbm': (algo[k] / (stage_ms[k] / 1000.0) / 1e9) / peaks.get('hbm_gbs', 6800.0)
+                      if stage_ms[k] > 0 else None} for k in algo}
+
+    result = {'metric': METRIC, 'value': value, 'unit': 'steps/s', 'n_gpus': world, 'steps': args.steps,
+              'warmup': args.warmup, 'ms_per_step': 1000.0 * elapsed / args.steps, 'higher_is_better': True,
+              'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
+              'config': {'workload': 'N=%d hard spheres (RSA) phi=%g eps=%g constrained mid-point step, mixed '
+                                     'precision' % (args.N, args.phi, args.tol),
+                         'N': args.N, 'phi': args.phi, 'tol': args.tol, 'xi': args.xi, 'L': L,
+                         'Ng': Ng, 'P': inf['P'], 'rcut': inf['rcut'], 'tile': list(inf['tile']),
+                         'precision': 'mixed (FP32 grids/pairs/vectors, FP64 Krylov scalars)',
+                         'parallelism': 'replicas' if world > 1 else 'single GPU',
+                         'l2': 'inputs larger than L2 (FFT grids %.2f GB)' % (8 * n3 * 4 * 2 / 1e9)},
+              'ptps': value * args.N / world,
+              'iterations': {'lanczos_mean': Li / K, 'krylov_mean': Ki / K, 'neighbor_pairs': npairs},
+              'latency_ms': {'p50': float(np.percentile(lat, 50)), 'p99': float(np.percentile(lat, 99)),
+                             'note': 'per constrained-step call (single stream, no serving loop)'},
+              'stage_ms_per_step': {k: v / K for k, v in stage_ms.items()},
+              'wave_stage_hbm': wave_rates,
+              'roofline': roof, 'clocks': clk, 'gpu_launches': int(prof['launches']),
+              'fft_execs': int(prof['fft_execs'])}
+
+    # end-to-end through the C ABI with host arrays (H2D positions in, D2H positions out, every step)
+    pos_host = np.ascontiguousarray(pos_np.copy())
+    h.step(pos_host, args.dt, seed=7, step=0)
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        h.step(pos_host, args.dt, seed=7, step=1 + k)
+    e2e_t = (time.perf_counter() - t0) / max(1, args.e2e_steps)
+    if pg is not None:
+        t = torch.tensor([e2e_t], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    result['e2e'] = {'value': world / e2e_t, 'unit': 'steps/s', 'h2d_bytes_per_step': 24 * args.N,
+                     'd2h_bytes_per_step': 24 * args.N}
+    h.close()
+
+    # all-FP64 form on the same workload (comparison for the mixed-precision speed-up)
+    if args.fp64_steps > 0:
+        h64 = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='fp64')
+        x64 = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+        h64.step(x64, args.dt, seed=99, step=0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(args.fp64_steps):
+            h64.step(x64, args.dt, seed=99, step=1 + k)
+        torch.cuda.synchronize(dev)
+        t64 = (time.perf_counter() - t0) / args.fp64_steps
+        result['fp64'] = {'steps_per_s': 1.0 / t64, 'ms_per_step': 1000.0 * t64,
+                          'mixed_speedup': t64 / (elapsed / args.steps)}
+        h64.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result['cpu_baseline'] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == 'reference':
+        run_reference(args, world, rank, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == '__main__':
+    main()

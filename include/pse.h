@@ -116,6 +116,27 @@ typedef struct pse_stats {
   int32_t reserved[5];
 } pse_stats;
 
+/* Per-stage device-time profile (CUDA events recorded on the caller's stream
+ * around each stage while profiling is enabled).  Stage indices: */
+enum {
+  PSE_STAGE_SETUP = 0,  /* wrap, sort by spreading tile, cell and neighbour lists */
+  PSE_STAGE_REAL = 1,   /* real-space pair sum */
+  PSE_STAGE_SPREAD = 2, /* Gaussian spreading */
+  PSE_STAGE_FFT = 3,    /* cuFFT transforms (forward and inverse) */
+  PSE_STAGE_SCALE = 4,  /* per-k scaling of the wave-space product */
+  PSE_STAGE_INTERP = 5, /* Gaussian interpolation */
+  PSE_STAGE_NOISE = 6,  /* wave-space noise generation and scaling */
+  PSE_STAGE_VECTOR = 7, /* Krylov inner products, combinations, permutations, updates */
+  PSE_NSTAGES = 8
+};
+
+typedef struct pse_profile {
+  double ms[PSE_NSTAGES];      /* accumulated device time per stage */
+  int64_t calls[PSE_NSTAGES];  /* timed sections per stage */
+  int64_t launches;            /* kernels of this library launched (cuFFT's excluded) */
+  int64_t fft_execs;           /* cuFFT executions */
+} pse_profile;
+
 /* Fills *opt with the defaults listed above. */
 void pse_default_options(pse_options *opt);
 
@@ -173,6 +194,16 @@ pse_status pse_constrained_step(pse_handle h, double *pos, const void *FP, doubl
 pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP, double dt,
                                       const void *w1, const void *w2, void *S_out, pse_stats *stats,
                                       pse_stream stream);
+
+/* Enables (1) or disables (0) stage timing and resets the profile and the
+ * launch counters.  Timing adds two event records per stage section. */
+pse_status pse_set_profiling(pse_handle h, int32_t enable);
+
+/* Waits for the recorded events and returns the accumulated profile. */
+pse_status pse_get_profile(pse_handle h, pse_profile *out);
+
+/* Name of a stage index ("setup", "real", ...), or "" when out of range. */
+const char *pse_stage_name(int32_t stage);
 
 /* Waits for all work of the handle and reports any pending CUDA error. */
 pse_status pse_sync(pse_handle h);

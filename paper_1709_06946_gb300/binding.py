@@ -52,6 +52,15 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != 'reserved'}
 
 
+NSTAGES = 8
+STAGES = ['setup', 'real', 'spread', 'fft', 'scale', 'interp', 'noise', 'vector']
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [('ms', ctypes.c_double * NSTAGES), ('calls', ctypes.c_int64 * NSTAGES),
+                ('launches', ctypes.c_int64), ('fft_execs', ctypes.c_int64)]
+
+
 # (name, restype, argtypes) of every symbol declared in include/pse.h
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -67,6 +76,9 @@ SIGNATURES = [
     ('pse_brownian_sample', ctypes.c_int, [_P, _P, _D, _U64, _U64, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step', ctypes.c_int, [_P, _P, _P, _D, _U64, _U64, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step_noise', ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_set_profiling', ctypes.c_int, [_P, ctypes.c_int32]),
+    ('pse_get_profile', ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
+    ('pse_stage_name', ctypes.c_char_p, [ctypes.c_int32]),
     ('pse_sync', ctypes.c_int, [_P]),
     ('pse_status_string', ctypes.c_char_p, [ctypes.c_int]),
     ('pse_last_error', ctypes.c_char_p, [_P]),
@@ -217,6 +229,17 @@ class PSE:
         d = stats.as_dict()
         d['status'] = st
         return S, d
+
+    def set_profiling(self, enable=True):
+        self._check(self._lib.pse_set_profiling(self._h, 1 if enable else 0))
+
+    def profile(self):
+        """{'ms': {stage: ms}, 'calls': {stage: n}, 'launches': n, 'fft_execs': n}."""
+        pr = Profile()
+        self._check(self._lib.pse_get_profile(self._h, ctypes.byref(pr)))
+        return {'ms': {STAGES[i]: pr.ms[i] for i in range(NSTAGES)},
+                'calls': {STAGES[i]: pr.calls[i] for i in range(NSTAGES)},
+                'launches': pr.launches, 'fft_execs': pr.fft_execs}
 
     def sync(self):
         self._check(self._lib.pse_sync(self._h))

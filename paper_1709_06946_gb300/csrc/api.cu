@@ -78,6 +78,17 @@ pse_status unstage(pse_ctx *c, void *host, const void *dev, size_t bytes, cudaSt
 
 namespace pse {
 
+cudaEvent_t prof_event(pse_ctx *c) {
+  cudaEvent_t e = nullptr;
+  if (!c->ev_pool.empty()) {
+    e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+
 pse_status mobility(pse_ctx *c, const void *vin, void *vout, int mode, int parts, cudaStream_t s) {
   if (parts & PSE_PART_REAL) PSE_TRY(real_apply(c, vin, vout, mode, s));
   if (parts & PSE_PART_WAVE) PSE_TRY(wave_apply(c, vin, vout, mode, (parts & PSE_PART_REAL) != 0, s));
@@ -459,7 +470,22 @@ pse_status create_impl(pse_ctx *c, const pse_options &o) {
   return PSE_OK;
 }
 
+void resolve_profile(pse_ctx *c) {
+  for (auto &q : c->pending) {
+    cudaEventSynchronize(q.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) c->prof_ms[q.stage] += ms;
+    c->ev_pool.push_back(q.a);
+    c->ev_pool.push_back(q.b);
+  }
+  c->pending.clear();
+  cudaGetLastError();
+}
+
 void destroy_impl(pse_ctx *c) {
+  resolve_profile(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
   for (int b = 0; b < 9; ++b) {
     if (c->plan_r2c[b]) cufftDestroy(c->plan_r2c[b]);
     if (c->plan_c2r[b]) cufftDestroy(c->plan_c2r[b]);
@@ -628,6 +654,37 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
                                       const void *w2, void *S_out, pse_stats *stats, pse_stream stream) {
   if (!h || !w1 || !w2) return PSE_ERR_INVALID_ARG;
   return step_impl(h, pos, FP, dt, w1, w2, 0, 0, S_out, stats, (cudaStream_t)stream);
+}
+
+pse_status pse_set_profiling(pse_handle h, int32_t enable) {
+  if (!h) return PSE_ERR_INVALID_ARG;
+  resolve_profile(h);
+  h->prof_on = enable != 0;
+  for (int i = 0; i < PSE_NSTAGES; ++i) {
+    h->prof_ms[i] = 0;
+    h->prof_calls[i] = 0;
+  }
+  h->nlaunch = 0;
+  h->nfft = 0;
+  return PSE_OK;
+}
+
+pse_status pse_get_profile(pse_handle h, pse_profile *out) {
+  if (!h || !out) return PSE_ERR_INVALID_ARG;
+  resolve_profile(h);
+  std::memset(out, 0, sizeof(*out));
+  for (int i = 0; i < PSE_NSTAGES; ++i) {
+    out->ms[i] = h->prof_ms[i];
+    out->calls[i] = h->prof_calls[i];
+  }
+  out->launches = h->nlaunch;
+  out->fft_execs = h->nfft;
+  return PSE_OK;
+}
+
+const char *pse_stage_name(int32_t stage) {
+  static const char *names[PSE_NSTAGES] = {"setup", "real", "spread", "fft", "scale", "interp", "noise", "vector"};
+  return (stage >= 0 && stage < PSE_NSTAGES) ? names[stage] : "";
 }
 
 pse_status pse_sync(pse_handle h) {

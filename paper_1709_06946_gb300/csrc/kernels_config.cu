@@ -264,6 +264,7 @@ pse_status exclusive_scan(pse_ctx *c, int *buf, int64_t n1, cudaStream_t s) {
     bufs[l] = c->d_scan_tmp + off;
     off += sizes[l];
   }
+  c->nlaunch += 2 * levels - 1;
   for (int l = 0; l < levels; ++l) {
     int64_t nb = ceil_div(sizes[l], SCAN_BLK);
     k_scan_block<<<(unsigned)nb, SCAN_NT, 0, s>>>(bufs[l], bufs[l], sizes[l], l + 1 < levels ? bufs[l + 1] : nullptr);
@@ -287,6 +288,8 @@ int64_t scan_tmp_ints(int64_t n1) {
 
 // Builds the sorted configuration for positions d_pos (device, user order, FP64).
 pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_SETUP, s);
+  c->nlaunch += 6;  // bin, scatter, derive, cell scatter, neighbour count and fill (+ scans)
   const Params &p = c->p;
   int N = (int)p.N;
   BinArgs b;

@@ -186,6 +186,8 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
 
 // vout = M_r vin for the current configuration (sorted order, [N][8]).
 pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_REAL, s);
+  c->nlaunch += 1;
   RealArgs a;
   a.N = (int)c->p.N;
   a.nc = c->p.nc;

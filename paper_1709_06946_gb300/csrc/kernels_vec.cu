@@ -176,6 +176,8 @@ unsigned grid_for(int64_t n, int nt = 256) { return (unsigned)ceil_div(n, nt); }
   } while (0)
 
 pse_status gather_in(pse_ctx *c, const void *F, const void *S, void *vout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_gather_in<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)F, (const float *)S, (float *)vout)),
            (k_gather_in<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)F, (const double *)S, (double *)vout)));
@@ -184,6 +186,8 @@ pse_status gather_in(pse_ctx *c, const void *F, const void *S, void *vout, cudaS
 }
 
 pse_status scatter_out(pse_ctx *c, const void *vin, void *U, void *E, double scale, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_scatter_out<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)vin, (float *)U, (float *)E, (float)scale)),
            (k_scatter_out<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)vin, (double *)U, (double *)E, scale)));
@@ -192,6 +196,8 @@ pse_status scatter_out(pse_ctx *c, const void *vin, void *U, void *E, double sca
 }
 
 pse_status gather_user8(pse_ctx *c, const void *user8, void *vout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_gather8<float><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const float *)user8, (float *)vout)),
            (k_gather8<double><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const double *)user8, (double *)vout)));
@@ -200,6 +206,8 @@ pse_status gather_user8(pse_ctx *c, const void *user8, void *vout, cudaStream_t 
 }
 
 pse_status scatter_user8(pse_ctx *c, const void *vin, void *user8, double scale, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_scatter8<float><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const float *)vin, (float *)user8, (float)scale)),
            (k_scatter8<double><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const double *)vin, (double *)user8, scale)));
@@ -208,6 +216,8 @@ pse_status scatter_user8(pse_ctx *c, const void *vin, void *user8, double scale,
 }
 
 pse_status philox_w1(pse_ctx *c, uint64_t seed, uint64_t counter, void *vout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_philox_w1<float><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, seed, counter, (float *)vout)),
            (k_philox_w1<double><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, seed, counter, (double *)vout)));
@@ -217,6 +227,7 @@ pse_status philox_w1(pse_ctx *c, uint64_t seed, uint64_t counter, void *vout, cu
 
 // d_out[r] = rows[r] . w for r < nrows (rows contiguous with stride n).
 pse_status multidot(pse_ctx *c, const void *rows, int nrows, int64_t n, const void *w, double *d_out, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
   int nb = c->dots_blocks;
   double *partial = c->d_dots;
   for (int r0 = 0; r0 < nrows; r0 += DOT_ROWS) {
@@ -224,15 +235,18 @@ pse_status multidot(pse_ctx *c, const void *rows, int nrows, int64_t n, const vo
     DISPATCH(c, (k_multidot<float><<<nb, DOT_NT, 0, s>>>((const float *)rows + (size_t)r0 * n, n, nr, n, (const float *)w, partial)),
              (k_multidot<double><<<nb, DOT_NT, 0, s>>>((const double *)rows + (size_t)r0 * n, n, nr, n, (const double *)w, partial)));
     k_dot_final<<<1, 32 * DOT_ROWS, 0, s>>>(partial, nb, nr, d_out + r0);
+    c->nlaunch += 2;
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
 
 pse_status combine_sub(pse_ctx *c, void *w, const void *rows, int nrows, int64_t n, const double *d_coef, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
   unsigned nb = std::min<unsigned>(grid_for(n), 4096);
   for (int r0 = 0; r0 < nrows; r0 += 128) {
     int nr = std::min(128, nrows - r0);
+    c->nlaunch += 1;
     DISPATCH(c, (k_combine<float, false><<<nb, 256, 0, s>>>((float *)w, (const float *)rows + (size_t)r0 * n, n, nr, n, d_coef + r0, -1.0f)),
              (k_combine<double, false><<<nb, 256, 0, s>>>((double *)w, (const double *)rows + (size_t)r0 * n, n, nr, n, d_coef + r0, -1.0)));
   }
@@ -241,9 +255,11 @@ pse_status combine_sub(pse_ctx *c, void *w, const void *rows, int nrows, int64_t
 }
 
 pse_status combine_set(pse_ctx *c, void *y, const void *rows, int nrows, int64_t n, const double *d_coef, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
   unsigned nb = std::min<unsigned>(grid_for(n), 4096);
   for (int r0 = 0; r0 < nrows; r0 += 128) {
     int nr = std::min(128, nrows - r0);
+    c->nlaunch += 1;
     if (r0 == 0) {
       DISPATCH(c, (k_combine<float, true><<<nb, 256, 0, s>>>((float *)y, (const float *)rows, n, nr, n, d_coef, 1.0f)),
                (k_combine<double, true><<<nb, 256, 0, s>>>((double *)y, (const double *)rows, n, nr, n, d_coef, 1.0)));
@@ -257,6 +273,8 @@ pse_status combine_set(pse_ctx *c, void *y, const void *rows, int nrows, int64_t
 }
 
 pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int64_t n, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   unsigned nb = std::min<unsigned>(grid_for(n), 4096);
   DISPATCH(c, (k_vscale<float><<<nb, 256, 0, s>>>((float *)dst, (const float *)src, (float)a, n)),
            (k_vscale<double><<<nb, 256, 0, s>>>((double *)dst, (const double *)src, a, n)));
@@ -265,6 +283,8 @@ pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int64_t n, c
 }
 
 pse_status vzero_slots(pse_ctx *c, void *v, int slot0, int nslot, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_zero_slots<float><<<grid_for((int64_t)N * nslot), 256, 0, s>>>((float *)v, N, slot0, nslot)),
            (k_zero_slots<double><<<grid_for((int64_t)N * nslot), 256, 0, s>>>((double *)v, N, slot0, nslot)));
@@ -273,6 +293,8 @@ pse_status vzero_slots(pse_ctx *c, void *v, int slot0, int nslot, cudaStream_t s
 }
 
 pse_status midpoint(pse_ctx *c, const double *x0, const void *B_user, double fac, double *xout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_midpoint<float><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, x0, (const float *)B_user, fac, xout)),
            (k_midpoint<double><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, x0, (const double *)B_user, fac, xout)));
@@ -282,6 +304,8 @@ pse_status midpoint(pse_ctx *c, const double *x0, const void *B_user, double fac
 
 pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const void *U_sorted, double dt,
                         double *xout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   int N = (int)c->p.N;
   DISPATCH(c, (k_final<float><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, c->d_inv, x0, (const float *)B_user, (const float *)U_sorted, dt, xout)),
            (k_final<double><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, c->d_inv, x0, (const double *)B_user, (const double *)U_sorted, dt, xout)));
@@ -290,6 +314,8 @@ pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const 
 }
 
 pse_status check_finite(pse_ctx *c, const void *ptr, int64_t n, bool dbl, int *bad, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
   unsigned nb = std::min<unsigned>(grid_for(n), 2048);
   if (dbl) k_finite<double><<<nb, 256, 0, s>>>((const double *)ptr, n, bad);
   else k_finite<float><<<nb, 256, 0, s>>>((const float *)ptr, n, bad);

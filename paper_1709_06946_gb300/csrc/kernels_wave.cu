@@ -238,6 +238,8 @@ ScaleArgs scale_args(const pse_ctx *c, double cscale) {
 
 template <typename T>
 pse_status fft(pse_ctx *c, bool forward, int batch, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_FFT, s);
+  c->nfft += 1;
   cufftHandle plan = forward ? c->plan_r2c[batch] : c->plan_c2r[batch];
   PSE_CUFFT_TRY(c, cufftSetStream(plan, s));
   if (sizeof(T) == 4) {
@@ -256,19 +258,31 @@ pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool 
   const Params &p = c->p;
   if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout, 0, sizeof(T) * 8 * (size_t)p.N, s));
   int cin = mode == M_SE ? 5 : 8, cout = mode == M_FULL ? 8 : (mode == M_SE ? 5 : 3);
-  spread_launch(c, a, vin, mode, s);
+  {
+    StageTimer timer(c, PSE_STAGE_SPREAD, s);
+    c->nlaunch += 1;
+    spread_launch(c, a, vin, mode, s);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, true, cin, s));
   ScaleArgs sa = scale_args(c, p.sigma() * p.sigma() / (p.V() * p.eta));
   size_t nk = (size_t)p.Ng * p.Ng * p.nkx;
   unsigned nb = (unsigned)ceil_div((int64_t)nk, 256);
   using C2 = typename Cx<T>::t;
-  if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
-  else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
-  else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+  {
+    StageTimer timer(c, PSE_STAGE_SCALE, s);
+    c->nlaunch += 1;
+    if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+    else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+    else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, false, cout, s));
-  interp_launch(c, a, vout, mode, s);
+  {
+    StageTimer timer(c, PSE_STAGE_INTERP, s);
+    c->nlaunch += 1;
+    interp_launch(c, a, vout, mode, s);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -281,11 +295,19 @@ pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t coun
   size_t nk = (size_t)p.Ng * p.Ng * p.nkx;
   unsigned nb = (unsigned)ceil_div((int64_t)nk, 256);
   using C2 = typename Cx<T>::t;
-  if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, (C2 *)c->d_cgrid, nk);
-  else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, (C2 *)c->d_cgrid, nk);
+  {
+    StageTimer timer(c, PSE_STAGE_NOISE, s);
+    c->nlaunch += 1;
+    if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, (C2 *)c->d_cgrid, nk);
+    else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, (C2 *)c->d_cgrid, nk);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, false, 8, s));
-  interp_launch(c, a, vout, M_FULL, s);
+  {
+    StageTimer timer(c, PSE_STAGE_INTERP, s);
+    c->nlaunch += 1;
+    interp_launch(c, a, vout, M_FULL, s);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

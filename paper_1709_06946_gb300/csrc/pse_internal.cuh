@@ -112,7 +112,41 @@ struct pse_ctx {
 
   cudaStream_t side = nullptr;  // second stream for the real-space sum
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
+  // profiling
+  bool prof_on = false;
+  double prof_ms[PSE_NSTAGES] = {0};
+  int64_t prof_calls[PSE_NSTAGES] = {0};
+  int64_t nlaunch = 0, nfft = 0;
+  struct Pending { int stage; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
 };
+
+namespace pse {
+cudaEvent_t prof_event(pse_ctx *c);
+// Records events around one stage section on stream s while profiling is on.
+struct StageTimer {
+  pse_ctx *c;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageTimer(pse_ctx *c_, int stage_, cudaStream_t s_) : c(c_), stage(stage_), s(s_) {
+    if (c->prof_on) {
+      a = prof_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~StageTimer() {
+    if (c->prof_on && a) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, s);
+      c->pending.push_back({stage, a, b});
+      c->prof_calls[stage] += 1;
+    }
+  }
+};
+}  // namespace pse
 
 #define PSE_CUDA_TRY(ctx, call)                                                          \
   do {                                                                                   \
