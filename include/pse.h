@@ -195,6 +195,29 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
                                       const void *w1, const void *w2, void *S_out, pse_stats *stats,
                                       pse_stream stream);
 
+/* Real-space part M_r [F; S] of the mobility product without any device
+ * allocation.  No counterpart in the paper: this is a convenience for callers
+ * that cannot allocate device memory -- host codes that must never make the
+ * device wait inside their loop (cudaMalloc/cudaFree synchronise the device)
+ * and applications whose device memory belongs to their own pool allocator.
+ * Mixed precision only (F, S, U, E float32; pos float64), all five arrays must
+ * be device memory (nothing is staged), F or S may be NULL (zero), U or E may be
+ * NULL (not written).  Same physics as pse_mobility_apply_parts(PSE_PART_REAL)
+ * with the default (strict) cutoff r_cut = a + sqrt(ln(10/tol))/xi, which must
+ * not exceed L/2.  Limit: N <= 65536 (INVALID_ARG beyond it, or if r_cut/a
+ * needs more than 16384 table rows).  Scratch is a fixed 1.3 MB static device
+ * array held by every GPU that loads the library until exit; the first call on
+ * a device looks up its address (call it once before any stream capture); the
+ * call clears what must start at zero; calls that overlap on the GPU race on
+ * the shared array.  Asynchronous on stream except when the table parameters
+ * change (the new table is uploaded and the call waits for the copy). */
+pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, double eta, double xi, double tol,
+                                     const double *pos, const float *F, const float *S, float *U, float *E,
+                                     pse_stream stream);
+
+/* Message for the last error of pse_mobility_real_noalloc on this thread. */
+const char *pse_noalloc_last_error(void);
+
 /* Enables (1) or disables (0) stage timing and resets the profile and the
  * launch counters.  Timing adds two event records per stage section. */
 pse_status pse_set_profiling(pse_handle h, int32_t enable);

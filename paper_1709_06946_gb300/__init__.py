@@ -7,5 +7,5 @@ from .binding import PSE, PSEError, load, LIB_PATH, PSE_MIXED, PSE_FP64  # noqa:
 
 
 def build(verbose=False, force=False):
-    from .build import build as _build
+    from .builder import build as _build
     return _build(verbose=verbose, force=force)

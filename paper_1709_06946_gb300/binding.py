@@ -76,6 +76,8 @@ SIGNATURES = [
     ('pse_brownian_sample', ctypes.c_int, [_P, _P, _D, _U64, _U64, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step', ctypes.c_int, [_P, _P, _P, _D, _U64, _U64, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step_noise', ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_mobility_real_noalloc', ctypes.c_int, [ctypes.c_int64, _D, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P]),
+    ('pse_noalloc_last_error', ctypes.c_char_p, []),
     ('pse_set_profiling', ctypes.c_int, [_P, ctypes.c_int32]),
     ('pse_get_profile', ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     ('pse_stage_name', ctypes.c_char_p, [ctypes.c_int32]),
@@ -92,7 +94,7 @@ def load():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError('libpse.so is not built: run paper_1709_06946_gb300.build.build() '
+            raise RuntimeError('libpse.so is not built: run paper_1709_06946_gb300.build() '
                                '(nvcc for sm_103a); there is no CPU fallback')
         lib = ctypes.CDLL(LIB_PATH)
         for name, res, args in SIGNATURES:
@@ -134,6 +136,24 @@ def _stream(x):
     except ImportError:
         pass
     return None
+
+
+def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
+    """Real-space product M_r [F; S] without device allocation (CUDA tensors, float32 moments).
+
+    For callers that cannot allocate device memory: the scratch is a fixed static
+    device array inside the library (N <= 65536).  Calls that overlap on the GPU race.
+    """
+    torch = _torch()
+    lib = load()
+    N = pos.shape[0]
+    U = torch.empty((N, 3), dtype=torch.float32, device=pos.device)
+    E = torch.empty((N, 5), dtype=torch.float32, device=pos.device)
+    st = lib.pse_mobility_real_noalloc(int(N), float(L), float(a), float(eta), float(xi), float(tol), _ptr(pos),
+                                       _ptr(F), _ptr(S), _ptr(U), _ptr(E), _stream(pos))
+    if st != 0:
+        raise PSEError(st, lib.pse_noalloc_last_error().decode())
+    return U, E
 
 
 class PSE:

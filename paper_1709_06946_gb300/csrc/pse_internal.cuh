@@ -42,6 +42,9 @@ struct RealTable {
   std::vector<double> v;   // len x 8
 };
 void build_real_table(const Params &p, int points_per_2a, RealTable &t);
+// The same table rounded to FP32 into a caller buffer of len x 8 floats (no allocation).
+void fill_real_table_f32(const Params &p, int points_per_2a, int len, float *out, double *self_uf,
+                         double *self_es);
 // Direct evaluation of the 7 functions at r > 0 (host, FP64); used for the table and tests.
 void real_functions(const Params &p, double r, double out[7]);
 

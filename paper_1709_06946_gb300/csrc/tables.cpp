@@ -305,6 +305,33 @@ void build_real_table(const Params &p, int points_per_2a, RealTable &t) {
   }
 }
 
+void fill_real_table_f32(const Params &p, int points_per_2a, int len, float *out, double *self_uf,
+                         double *self_es) {
+  static const GL gl(40);
+  double dr = 2.0 * p.a / points_per_2a;
+  double suf = (2.0 / 3.0) * (-conv(gl, 0, 3, 0.0, p.xi, p.a)) / p.eta;
+  double ses = conv(gl, 2, 5, 0.0, p.xi, p.a) / (5.0 * p.eta);
+  int ismall = (int)std::ceil(0.05 * p.a / dr);
+  double f[7], fs[7] = {0, 0, 0, 0, 0, 0, 0};
+  const double z[7] = {suf, suf, 0.0, 0.0, ses, 0.0, 0.0};
+  for (int i = len - 1; i >= 0; --i) {
+    if (i == 0) {
+      for (int q = 0; q < 7; ++q) f[q] = z[q];
+    } else if (i < ismall) {
+      double w = (double)i / ismall;
+      for (int q = 0; q < 7; ++q) f[q] = (1 - w) * z[q] + w * fs[q];
+    } else {
+      real_functions(p, i * dr, f);
+      if (i == ismall)
+        for (int q = 0; q < 7; ++q) fs[q] = f[q];
+    }
+    for (int q = 0; q < 7; ++q) out[(size_t)i * 8 + q] = (float)f[q];
+    out[(size_t)i * 8 + 7] = 0.0f;
+  }
+  *self_uf = suf;
+  *self_es = ses;
+}
+
 bool tridiag_eigen(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z) {
   Z.assign((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
