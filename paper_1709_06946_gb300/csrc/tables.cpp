@@ -220,14 +220,21 @@ int choose_params(Params &p, const pse_options &opt, std::string &err) {
   p.nc = std::max(1, std::min(1023, (int)std::floor(p.L / p.rcut)));
   p.cs = p.L / p.nc;
   int mins = std::max(1, p.P - 1);
-  p.tile[0] = opt.tile[0] > 0 ? opt.tile[0] : pick_tile(p.Ng, mins, 32, true);
-  p.tile[1] = opt.tile[1] > 0 ? opt.tile[1] : pick_tile(p.Ng, mins, 16, false);
-  p.tile[2] = opt.tile[2] > 0 ? opt.tile[2] : pick_tile(p.Ng, mins, 8, false);
-  // shared-memory budget of the spreading/interpolation tile (8 components, padded rows)
-  auto smem = [&]() { return (size_t)8 * p.tile[2] * p.tile[1] * (p.tile[0] + 1) * p.ts; };
-  const size_t budget = 100 * 1024;
+  // z planes are owned by the 16 warps of a spreading CTA: aim for 16 planes, x rows of up
+  // to 16 points (coalesced stores), y up to 8
+  p.tile[0] = opt.tile[0] > 0 ? opt.tile[0] : pick_tile(p.Ng, mins, 16, true);
+  p.tile[1] = opt.tile[1] > 0 ? opt.tile[1] : pick_tile(p.Ng, mins, 8, false);
+  p.tile[2] = opt.tile[2] > 0 ? opt.tile[2] : pick_tile(p.Ng, mins, 16, false);
+  // shared memory of a spreading/interpolation CTA: the tile ([z][y][x][8 components], rows
+  // padded by 2 points when Tx is a multiple of 4) plus a 256-entry particle list
+  auto smem = [&]() {
+    int rx = p.tile[0] + ((p.tile[0] & 3) == 0 ? 2 : 0);
+    return (size_t)8 * p.tile[2] * p.tile[1] * rx * p.ts + (size_t)128 * (16 + 36 * p.ts);
+  };
+  const size_t budget = 110 * 1024;
   while (smem() > budget && (opt.tile[0] <= 0 || opt.tile[1] <= 0 || opt.tile[2] <= 0)) {
-    int d = (p.tile[0] >= p.tile[1] && p.tile[0] >= p.tile[2]) ? 0 : (p.tile[1] >= p.tile[2] ? 1 : 2);
+    int d = p.tile[0] >= p.tile[1] ? 0 : 1;  // keep the 16 z planes; shrink x or y
+    if (p.tile[d] <= mins) d = 2;
     int nt = pick_tile(p.Ng, mins, p.tile[d] - 1, d == 0);
     if (nt >= p.tile[d]) break;
     p.tile[d] = nt;

@@ -1,4 +1,13 @@
 // Spreading / interpolation kernels shared by wave_spread.cu and wave_interp.cu.
+//
+// Both kernels run one CTA per grid tile (Tx x Ty x Tz points) and keep the
+// tile in shared memory as [z][y][x][component] with the components padded to
+// CP = 4 or 8 so that one lane moves four components with one vector access.
+// The CTA walks the particles of the 2x2x2 bins whose Gaussian supports can
+// reach the tile (bins hold particles by the grid index where their support
+// starts) in chunks: the particles that overlap the tile are compacted into a
+// shared-memory list together with their offsets, weights' origins and
+// moments, then processed by the warps.
 #pragma once
 
 #include <cmath>
@@ -18,36 +27,103 @@ struct WaveArgs {
   double h, alpha, pref;
 };
 
-// x-direction weight of support point `lane` (lanes 0..P-1), read by the other
-// lanes with a shuffle inside a warp-uniform loop.
-template <typename T>
-__device__ __forceinline__ T weight_lane(const WaveArgs &a, T d0x, int lane) {
-  T d = d0x + (T)lane * (T)a.h;
-  return lane < a.P ? exp(-(T)a.alpha * d * d) : (T)0;
+constexpr int WAVE_THREADS = 512;
+constexpr int WAVE_WARPS = WAVE_THREADS / 32;
+constexpr int LIST_CAP = 128;
+constexpr int WMAX = 8;   // weights kept in the list for supports up to WMAX points per side
+
+// padded row length (points) of the shared tile: keeps vector accesses of
+// neighbouring rows in different banks
+__host__ __device__ inline int tile_rx(int Tx) { return Tx + ((Tx & 3) == 0 ? 2 : 0); }
+
+template <int C> struct CPad { static constexpr int v = C <= 4 ? 4 : 8; };
+
+// shared memory of a spreading/interpolation CTA (tile + particle list)
+template <typename T, int C>
+__host__ __device__ inline size_t wave_smem(const int T3[3]) {
+  constexpr int CP = CPad<C>::v;
+  return (size_t)T3[2] * T3[1] * tile_rx(T3[0]) * CP * sizeof(T) +
+         (size_t)LIST_CAP * (sizeof(int4) + 4 * sizeof(T) + CP * sizeof(T) + 3 * WMAX * sizeof(T));
 }
 
-__device__ __forceinline__ int tile_bins(const WaveArgs &a, int tile, int t0[3], int bins[8]) {
-  int t[3] = {tile % a.nt[0], (tile / a.nt[0]) % a.nt[1], tile / (a.nt[0] * a.nt[1])};
+__device__ __forceinline__ void tile_of(const WaveArgs &a, int tile, int t[3], int t0[3]) {
+  t[0] = tile % a.nt[0];
+  t[1] = (tile / a.nt[0]) % a.nt[1];
+  t[2] = tile / (a.nt[0] * a.nt[1]);
   for (int d = 0; d < 3; ++d) t0[d] = t[d] * a.T[d];
+}
+
+// The (up to) 8 source bins of a tile and the running offsets of their ranges.
+__device__ __forceinline__ int tile_bins(const WaveArgs &a, const int t[3], const int *tile_start, int beg[8],
+                                         int cum[9]) {
   int nb = 0;
   int nz = a.nt[2] > 1 ? 2 : 1, ny = a.nt[1] > 1 ? 2 : 1, nx = a.nt[0] > 1 ? 2 : 1;
+  cum[0] = 0;
   for (int bz = 0; bz < nz; ++bz)
     for (int by = 0; by < ny; ++by)
       for (int bx = 0; bx < nx; ++bx) {
         int z = wrapi(t[2] - bz, a.nt[2]), y = wrapi(t[1] - by, a.nt[1]), x = wrapi(t[0] - bx, a.nt[0]);
-        bins[nb++] = (z * a.nt[1] + y) * a.nt[0] + x;
+        int b = (z * a.nt[1] + y) * a.nt[0] + x;
+        beg[nb] = tile_start[b];
+        cum[nb + 1] = cum[nb] + (tile_start[b + 1] - tile_start[b]);
+        ++nb;
       }
   return nb;
 }
 
-
-template <typename K>
-inline void set_smem(K kern) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+// Compacts the candidates [c0, c0 + LIST_CAP) of the tile's bins that overlap
+// the tile into the shared list (offsets, weight origins, moments when vin is
+// given, and the 3 x P one-dimensional Gaussian weights when P <= WMAX);
+// returns the number of entries (after a barrier).
+template <typename T, int C, int SLOT0>
+__device__ __forceinline__ int build_list(const WaveArgs &a, const int t0[3], int nb, const int beg[8], const int cum[9],
+                                          int c0, const int4 *__restrict__ sp_i0,
+                                          const typename V4<T>::t *__restrict__ sp_d0, const T *__restrict__ vin,
+                                          int4 *s_meta, typename V4<T>::t *s_d0, T *s_m, T *s_w, int *s_count) {
+  constexpr int CP = CPad<C>::v;
+  const int Ng = a.Ng, P = a.P;
+  for (int q = threadIdx.x; q < LIST_CAP; q += blockDim.x) {
+    int v = c0 + q;
+    if (v >= cum[nb]) break;
+    int b = 0;
+    while (v >= cum[b + 1]) ++b;
+    int k = beg[b] + (v - cum[b]);
+    int4 i0 = sp_i0[k];
+    int ox = wrapi(i0.x - t0[0], Ng), oy = wrapi(i0.y - t0[1], Ng), oz = wrapi(i0.z - t0[2], Ng);
+    bool hit = (ox < a.T[0] || ox + P - 1 >= Ng) && (oy < a.T[1] || oy + P - 1 >= Ng) &&
+               (oz < a.T[2] || oz + P - 1 >= Ng);
+    if (hit) {
+      int e = atomicAdd(s_count, 1);
+      s_meta[e] = make_int4(k, ox, oy, oz);
+      typename V4<T>::t d0 = sp_d0[k];
+      s_d0[e] = d0;
+      if (vin) {
+#pragma unroll
+        for (int c = 0; c < CP; ++c) s_m[e * CP + c] = c < C ? vin[8 * (size_t)k + SLOT0 + c] : (T)0;
+      }
+      if (P <= WMAX) {
+        const T al = (T)a.alpha, hs = (T)a.h;
+        T *w = s_w + e * 3 * WMAX;
+        for (int j = 0; j < P; ++j) {
+          T dx = d0.x + (T)j * hs, dy = d0.y + (T)j * hs, dz = d0.z + (T)j * hs;
+          w[j] = exp(-al * dx * dx);
+          w[WMAX + j] = exp(-al * dy * dy);
+          w[2 * WMAX + j] = exp(-al * dz * dz);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return *s_count;
 }
 
 // launchers (wave_spread.cu / wave_interp.cu)
 void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
+
+template <typename K>
+inline void set_smem(K kern) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
 
 }  // namespace pse

@@ -1,67 +1,132 @@
-// Gaussian spreading Q (Sec. 2.3.2, Eq. WSops2): one CTA per output tile,
-// shared-memory accumulation, coalesced tile write-out (no global atomics).
+// Gaussian spreading Q (Sec. 2.3.2, Eq. WSops2).
+//
+// One CTA per output tile.  Warp w owns the tile's z-planes w, w + 8, ...; for
+// every particle overlapping the tile it adds the particle's P x P footprint in
+// its plane to the shared tile with plain vector read-modify-writes (lanes map
+// to distinct (x, y, component-half) items, and no other warp touches the
+// plane), so there are no atomics and the result is deterministic.  The tile is
+// then written once to the component-major grids with coalesced stores; no grid
+// zeroing pass is needed because the tiles cover the grid.
 #include "wave_common.cuh"
 
 namespace pse {
 namespace {
 
 template <typename T, int C, int SLOT0, int PT>
-__global__ void __launch_bounds__(256) k_spread(WaveArgs a, const int4 *__restrict__ sp_i0,
-                                                const typename V4<T>::t *__restrict__ sp_d0,
-                                                const T *__restrict__ vin, const int *__restrict__ tile_start,
-                                                T *__restrict__ grid) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *acc = (T *)smem_raw;
-  const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], Rx = Tx + 1;
-  const int vol = Tz * Ty * Rx;
-  for (int q = threadIdx.x; q < C * vol; q += blockDim.x) acc[q] = 0;
-  int t0[3], bins[8];
-  int nbins = tile_bins(a, blockIdx.x, t0, bins);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int P = PT > 0 ? PT : a.P, Ng = a.Ng, PP = P * P;
-  for (int b = 0; b < nbins; ++b) {
-    int beg = tile_start[bins[b]], end = tile_start[bins[b] + 1];
-    for (int k = beg + warp; k < end; k += nw) {
-      int4 i0 = sp_i0[k];
-      int ox = wrapi(i0.x - t0[0], Ng), oy = wrapi(i0.y - t0[1], Ng), oz = wrapi(i0.z - t0[2], Ng);
-      if (!((ox < Tx || ox + P - 1 >= Ng) && (oy < Ty || oy + P - 1 >= Ng) && (oz < Tz || oz + P - 1 >= Ng)))
-        continue;  // warp-uniform: the support misses this tile
-      typename V4<T>::t d0 = sp_d0[k];
-      T m[C];
+__global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs a, const int4 *__restrict__ sp_i0,
+                                                         const typename V4<T>::t *__restrict__ sp_d0,
+                                                         const T *__restrict__ vin, const int *__restrict__ tile_start,
+                                                         T *__restrict__ grid) {
+  constexpr int CP = CPad<C>::v, H = CP / 4;
+  constexpr int NPASS = PT > 0 ? (PT * PT * H + 31) / 32 : 1;
+  using T4 = typename V4<T>::t;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  __shared__ int s_count;
+  const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
+  const int npts = Tz * Ty * RX;
+  T4 *acc = (T4 *)smem_raw;
+  int4 *s_meta = (int4 *)(acc + (size_t)npts * H);
+  T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
+  T *s_m = (T *)(s_d0 + LIST_CAP);
+  T *s_w = s_m + LIST_CAP * CP;
+  T4 zero;
+  zero.x = zero.y = zero.z = zero.w = (T)0;
+  for (int q = threadIdx.x; q < npts * H; q += blockDim.x) acc[q] = zero;
+  int t[3], t0[3], beg[8], cum[9];
+  tile_of(a, blockIdx.x, t, t0);
+  const int nb = tile_bins(a, t, tile_start, beg, cum);
+  const int P = PT > 0 ? PT : a.P, Ng = a.Ng, nitem = P * P * H;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
+  const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
+  // this lane's (x, y) footprint item in every pass (fixed for the whole kernel)
+  int pjx[NPASS], pjy[NPASS];
+  bool pok[NPASS];
 #pragma unroll
-      for (int c = 0; c < C; ++c) m[c] = vin[8 * (size_t)k + SLOT0 + c];
-      T wxl = weight_lane<T>(a, d0.x, lane);
-      for (int base = 0; base < PP; base += 32) {
-        int pq = base + lane;
-        int jy = pq % P, jz = pq / P;
-        int ly = oy + jy, lz = oz + jz;
-        if (ly >= Ng) ly -= Ng;
-        if (lz >= Ng) lz -= Ng;
-        bool ok = pq < PP && ly < Ty && lz < Tz;
-        T dy = d0.y + (T)jy * (T)a.h, dz = d0.z + (T)jz * (T)a.h;
-        T wyz = ok ? (T)a.pref * exp(-(T)a.alpha * (dy * dy + dz * dz)) : (T)0;
-        int row = (lz * Ty + ly) * Rx;
+  for (int ps = 0; ps < NPASS; ++ps) {
+    int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
+    pok[ps] = it < nitem;
+    pjx[ps] = pok[ps] ? q % P : 0;
+    pjy[ps] = pok[ps] ? q / P : 0;
+  }
+  for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    const int n = build_list<T, C, SLOT0>(a, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m, s_w,
+                                          &s_count);
+    for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
+      // the warp finds the particles whose support crosses its plane 32 list entries at a time
+      for (int base = 0; base < n; base += 32) {
+        int jzl = P;
+        if (base + lane < n) {
+          jzl = lz - s_meta[base + lane].w;
+          if (jzl < 0) jzl += Ng;
+        }
+        unsigned hits = __ballot_sync(0xffffffffu, jzl < P);
+        while (hits) {
+          const int b = __ffs(hits) - 1;
+          hits &= hits - 1;
+          const int e = base + b;
+          const int jz = __shfl_sync(0xffffffffu, jzl, b);
+          const int4 m4 = s_meta[e];
+          const T4 mv = ((const T4 *)s_m)[e * H + hh];
+          T4 *plane = acc + (size_t)lz * Ty * RX * H;
+          if (PT > 0) {
+            const T *w = s_w + e * 3 * WMAX;
+            const T wz = pref * w[2 * WMAX + jz];
 #pragma unroll
-        for (int jx = 0; jx < P; ++jx) {
-          T wx = __shfl_sync(0xffffffffu, wxl, jx);
-          int lx = ox + jx;
-          if (lx >= Ng) lx -= Ng;
-          if (ok && lx < Tx) {
-            T w = wyz * wx;
-#pragma unroll
-            for (int c = 0; c < C; ++c) atomicAdd(&acc[c * vol + row + lx], w * m[c]);
+            for (int ps = 0; ps < NPASS; ++ps) {
+              int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
+              if (lx >= Ng) lx -= Ng;
+              if (ly >= Ng) ly -= Ng;
+              if (pok[ps] && lx < Tx && ly < Ty) {
+                const T wt = w[pjx[ps]] * w[WMAX + pjy[ps]] * wz;
+                T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
+                T4 v = *p;
+                v.x += wt * mv.x;
+                v.y += wt * mv.y;
+                v.z += wt * mv.z;
+                v.w += wt * mv.w;
+                *p = v;
+              }
+            }
+          } else {  // any support size: weights on the fly
+            const T4 d0 = s_d0[e];
+            const T dz = d0.z + (T)jz * hs;
+            const T wz = pref * exp(-alpha * dz * dz);
+            for (int ib = 0; ib < nitem; ib += 32) {
+              const int it = ib + lane;
+              const int q = H == 2 ? (it >> 1) : it;
+              const int jx = q % P, jy = q / P;
+              int lx = m4.y + jx, ly = m4.z + jy;
+              if (lx >= Ng) lx -= Ng;
+              if (ly >= Ng) ly -= Ng;
+              if (it < nitem && lx < Tx && ly < Ty) {
+                const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
+                const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
+                T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
+                T4 v = *p;
+                v.x += wt * mv.x;
+                v.y += wt * mv.y;
+                v.z += wt * mv.z;
+                v.w += wt * mv.w;
+                *p = v;
+              }
+            }
           }
+          __syncwarp();  // the next particle may update the same points from other lanes
         }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
   const size_t n3 = (size_t)Ng * Ng * Ng;
   const int tv = Tx * Ty * Tz;
-  for (int q = threadIdx.x; q < C * tv; q += blockDim.x) {
-    int x = q % Tx, y = (q / Tx) % Ty, z = (q / (Tx * Ty)) % Tz, c = q / tv;
-    grid[c * n3 + ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x)] = acc[c * vol + (z * Ty + y) * Rx + x];
+  for (int q = threadIdx.x; q < tv; q += blockDim.x) {
+    int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
+    size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
+    const T *src = (const T *)(acc + ((size_t)(z * Ty + y) * RX + x) * H);
+#pragma unroll
+    for (int c = 0; c < C; ++c) grid[c * n3 + g] = src[c];
   }
 }
 
@@ -73,9 +138,10 @@ void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t 
     set_smem(kern);
     init = true;
   }
-  size_t sm = (size_t)C * a.T[2] * a.T[1] * (a.T[0] + 1) * sizeof(T);
-  kern<<<(unsigned)c->ntiles, 256, sm, s>>>(a, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
-                                            (const T *)vin, c->d_tile_start, (T *)c->d_grid);
+  size_t sm = wave_smem<T, C>(a.T);
+  kern<<<(unsigned)c->ntiles, WAVE_THREADS, sm, s>>>(a, (const int4 *)c->d_sp_i0,
+                                                      (const typename V4<T>::t *)c->d_sp_d0, (const T *)vin,
+                                                      c->d_tile_start, (T *)c->d_grid);
 }
 
 template <typename T, int C, int SLOT0>
