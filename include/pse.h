@@ -90,7 +90,8 @@ typedef struct pse_options {
   double krylov_tol;       /* GMRES |r|/|b| target; < 0: use tol */
   int32_t krylov_maxiter;  /* 0 = 50 */
   int32_t tile[3];         /* spreading/interpolation tile (x, y, z); 0 = auto */
-  int32_t reserved[8];
+  int32_t real_lanes;      /* lanes sharing one particle in the pair sum (1,4,8,16,32); 0 = auto */
+  int32_t reserved[7];
 } pse_options;
 
 typedef struct pse_info {

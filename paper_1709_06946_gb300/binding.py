@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
                 ('table_points', ctypes.c_int32), ('rcut', ctypes.c_double),
                 ('lanczos_tol', ctypes.c_double), ('lanczos_maxiter', ctypes.c_int32),
                 ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
-                ('tile', ctypes.c_int32 * 3), ('reserved', ctypes.c_int32 * 8)]
+                ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('reserved', ctypes.c_int32 * 7)]
 
 
 class Info(ctypes.Structure):
@@ -161,7 +161,7 @@ class PSE:
 
     def __init__(self, N, L, a=1.0, eta=1.0, kT=1.0, xi=0.5, tol=1e-3, precision='mixed', rule='strict',
                  Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
-                 krylov_maxiter=50, table_points=0, tile=(0, 0, 0)):
+                 krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0):
         lib = load()
         o = Options()
         lib.pse_default_options(ctypes.byref(o))
@@ -170,6 +170,7 @@ class PSE:
         o.lanczos_tol, o.lanczos_maxiter = float(lanczos_tol), int(lanczos_maxiter)
         o.krylov_tol, o.krylov_maxiter = float(krylov_tol), int(krylov_maxiter)
         o.table_points = int(table_points)
+        o.real_lanes = int(real_lanes)
         for d in range(3):
             o.tile[d] = int(tile[d])
         self.prec = PSE_FP64 if precision in ('fp64', 'double', PSE_FP64) else PSE_MIXED

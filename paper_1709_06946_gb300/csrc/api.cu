@@ -400,8 +400,12 @@ pse_status create_impl(pse_ctx *c, const pse_options &o) {
   c->d_cell_list = (int *)A(sizeof(int) * N);
   c->d_nbr_start = (int *)A(sizeof(int) * (N + 1));
   double dens = N / p.V();
-  c->nbr_cap = (int64_t)(N * (4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * dens * 1.3 + 16));
+  double mean_nbr = 4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * dens;
+  c->nbr_slots = (int)std::min<double>(N, (std::ceil((1.4 * mean_nbr + 24) / 8.0) * 8.0));
+  c->nbr_slots = std::max(c->nbr_slots, 8);
+  c->nbr_cap = (int64_t)c->nbr_slots * N;
   c->d_nbr = (int *)A(sizeof(int) * (size_t)c->nbr_cap);
+  c->d_nbr_tot = (unsigned long long *)A(2 * sizeof(unsigned long long));
   c->d_sp_i0 = A(sizeof(int4) * N);
   c->d_sp_d0 = A(4 * ts * N);
   c->d_rs = A(4 * ts * N);

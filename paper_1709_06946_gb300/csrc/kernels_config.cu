@@ -179,7 +179,7 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
   }
   float3 r = make_float3(dc[0] * a.csf + (pi.x - pj.x), dc[1] * a.csf + (pi.y - pj.y),
                          dc[2] * a.csf + (pi.z - pj.z));
-  if (a.nc < 3) {
+  if (a.nc < 5) {
     r.x -= a.Lf * rintf(r.x / a.Lf);
     r.y -= a.Lf * rintf(r.y / a.Lf);
     r.z -= a.Lf * rintf(r.z / a.Lf);
@@ -187,9 +187,12 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
   return r;
 }
 
-template <typename T, bool FILL>
-__global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const int *cell_list, int *cnt_or_start,
-                      int *list) {
+// Neighbour list in one pass: particle i writes the indices of its neighbours
+// (r < r_cut, minimum image) into its own slots and records their number; the
+// largest count and the total are accumulated for the host's capacity check.
+template <typename T>
+__global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const int *cell_list, int *cnt, int *list,
+                      int slots, unsigned long long *tot) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.N) return;
   int ci[3];
@@ -204,12 +207,16 @@ __global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const in
     ci[1] = min((int)(pd.y / (a.L / a.nc)), a.nc - 1);
     ci[2] = min((int)(pd.z / (a.L / a.nc)), a.nc - 1);
   }
-  int lo = a.nc >= 3 ? -1 : 0, hi = a.nc >= 2 ? 1 : 0;
-  int n = 0, off = FILL ? cnt_or_start[i] : 0;
+  // 5-cell stencil per dimension, or every cell once when there are fewer than 5
+  int lo = a.nc >= 5 ? -2 : 0, hi = a.nc >= 5 ? 2 : a.nc - 1;
+  int n = 0;
+  int *mine = list + (size_t)i * slots;
   for (int dz = lo; dz <= hi; ++dz)
     for (int dy = lo; dy <= hi; ++dy)
       for (int dx = lo; dx <= hi; ++dx) {
-        int c = (wrapi(ci[2] + dz, a.nc) * a.nc + wrapi(ci[1] + dy, a.nc)) * a.nc + wrapi(ci[0] + dx, a.nc);
+        int cz = a.nc >= 5 ? wrapi(ci[2] + dz, a.nc) : dz, cy = a.nc >= 5 ? wrapi(ci[1] + dy, a.nc) : dy;
+        int cx = a.nc >= 5 ? wrapi(ci[0] + dx, a.nc) : dx;
+        int c = (cz * a.nc + cy) * a.nc + cx;
         int e = cell_start[c + 1];
         for (int k = cell_start[c]; k < e; ++k) {
           int j = cell_list[k];
@@ -227,12 +234,14 @@ __global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const in
             in = rx * rx + ry * ry + rz * rz < a.rc2;
           }
           if (in) {
-            if (FILL) list[off + n] = j;
+            if (n < slots) mine[n] = j;
             ++n;
           }
         }
       }
-  if (!FILL) cnt_or_start[i] = n;
+  cnt[i] = n;
+  atomicAdd(&tot[0], (unsigned long long)n);
+  atomicMax(&tot[1], (unsigned long long)n);
 }
 
 void *alloc_dev(pse_ctx *c, size_t bytes) {
@@ -329,41 +338,41 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   a.L = p.L;
   a.rc2 = p.rcut * p.rcut;
   a.rc2f = (float)a.rc2;
-  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_start + N, 0, sizeof(int), s));
   unsigned nb128 = (unsigned)ceil_div(N, 128);
-  if (c->prec == PSE_MIXED)
-    k_nbr<float, false><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
-  else
-    k_nbr<double, false><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, nullptr);
-  PSE_TRY(exclusive_scan(c, c->d_nbr_start, (int64_t)N + 1, s));
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int, c->d_nbr_start + N, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  PSE_CUDA_TRY(c, cudaGetLastError());
-  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
-  if (c->h_pinned_int[1]) {
-    c->err = "non-finite particle position";
-    return PSE_ERR_NONFINITE;
-  }
-  int64_t total = (int64_t)(unsigned)c->h_pinned_int[0];
-  if (total > 2000000000LL) {
-    c->err = "neighbour list exceeds 2^31 entries";
-    return PSE_ERR_INVALID_ARG;
-  }
-  if (total > c->nbr_cap) {
-    int64_t cap = total + total / 4 + 1024;
-    void *q = alloc_dev(c, sizeof(int) * (size_t)cap);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long), s));
+    if (c->prec == PSE_MIXED)
+      k_nbr<float><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr,
+                                         c->nbr_slots, c->d_nbr_tot);
+    else
+      k_nbr<double><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr,
+                                          c->nbr_slots, c->d_nbr_tot);
+    unsigned long long tm[2];
+    PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PSE_CUDA_TRY(c, cudaMemcpyAsync(tm, c->d_nbr_tot, sizeof(tm), cudaMemcpyDeviceToHost, s));
+    PSE_CUDA_TRY(c, cudaGetLastError());
+    PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (c->h_pinned_int[1]) {
+      c->err = "non-finite particle position";
+      return PSE_ERR_NONFINITE;
+    }
+    c->npairs = (int64_t)tm[0];
+    if ((int64_t)tm[1] <= c->nbr_slots) break;
+    // a particle has more neighbours than slots: enlarge and rebuild once
+    int slots = (int)((tm[1] + 15) / 8 * 8);
+    if ((double)slots * N > 2.0e9) {
+      c->err = "neighbour list exceeds 2^31 entries";
+      return PSE_ERR_INVALID_ARG;
+    }
+    void *q = alloc_dev(c, sizeof(int) * (size_t)slots * N);
     if (!q) {
       c->err = "cannot allocate neighbour list";
       return PSE_ERR_OOM;
     }
     c->d_nbr = (int *)q;  // the old list stays in c->allocs and is freed at destroy
-    c->nbr_cap = cap;
+    c->nbr_slots = slots;
+    c->nbr_cap = (int64_t)slots * N;
   }
-  c->npairs = total;
-  if (c->prec == PSE_MIXED)
-    k_nbr<float, true><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
-  else
-    k_nbr<double, true><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr);
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

@@ -14,7 +14,7 @@ namespace pse {
 namespace {
 
 struct RealArgs {
-  int N, nc, len, k2;
+  int N, nc, len, k2, slots;
   float csf, Lf;
   double L;
   double inv_dr, self_uf, self_es;
@@ -41,7 +41,7 @@ template <> struct Pos<float> {
       if (t > a.nc / 2) t -= a.nc;
       if (t < -(a.nc / 2)) t += a.nc;
       d[k] = t * a.csf + po[k];
-      if (a.nc < 3) d[k] -= a.Lf * rintf(d[k] / a.Lf);
+      if (a.nc < 5) d[k] -= a.Lf * rintf(d[k] / a.Lf);
     }
   }
 };
@@ -88,33 +88,26 @@ __device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, dou
     f[k] = w0 * __ldg(r0 + k) + w1 * __ldg(r0 + 8 + k) + w2 * __ldg(r0 + 16 + k) + w3 * __ldg(r0 + 24 + k);
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(128) k_real(RealArgs a, const void *rs, const int *__restrict__ nstart,
+// G lanes share one particle: they walk its neighbour list with stride G (so
+// the neighbours' records are fetched in parallel) and the partial sums are
+// reduced with shuffles; the first lane of the group adds the self term.
+template <typename T, int MODE, int G>
+__global__ void __launch_bounds__(256) k_real(RealArgs a, const void *rs, const int *__restrict__ nstart,
                                               const int *__restrict__ nbr, const T *__restrict__ vin,
                                               T *__restrict__ vout, const T *__restrict__ tab) {
   constexpr bool HAS_F = MODE != M_SE, WANT_U = MODE != M_SE, WANT_E = MODE != M_FSU;
   using T4 = typename V4<T>::t;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
+  const int gid = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G);
+  const int sub = threadIdx.x % G;
+  const bool active = gid < a.N;
+  const int i = active ? gid : a.N - 1;
   Pos<T> pi;
   pi.load(rs, i);
   const T4 *v4 = (const T4 *)vin;
-  T4 s0 = v4[2 * i], s1 = v4[2 * i + 1];
   T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
-  if (WANT_U && HAS_F) {
-    U[0] = (T)a.self_uf * s0.x;
-    U[1] = (T)a.self_uf * s0.y;
-    U[2] = (T)a.self_uf * s0.z;
-  }
-  if (WANT_E) {
-    E[0] = (T)a.self_es * s0.w;
-    E[1] = (T)a.self_es * s1.x;
-    E[2] = (T)a.self_es * s1.y;
-    E[3] = (T)a.self_es * s1.z;
-    E[4] = (T)a.self_es * s1.w;
-  }
-  int e = nstart[i + 1];
-  for (int k = nstart[i]; k < e; ++k) {
+  const int64_t k0 = (int64_t)i * a.slots;
+  const int64_t e = active ? k0 + nstart[i] : 0;
+  for (int64_t k = (active ? k0 : 0) + sub; k < e; k += G) {
     int j = nbr[k];
     T d[3];
     pi.sep(rs, j, a, d);
@@ -156,30 +149,69 @@ __global__ void __launch_bounds__(128) k_real(RealArgs a, const void *rs, const 
       }
     }
   }
-  T4 o0, o1;
-  o0.x = U[0];
-  o0.y = U[1];
-  o0.z = U[2];
-  o0.w = E[0];
-  o1.x = E[1];
-  o1.y = E[2];
-  o1.z = E[3];
-  o1.w = E[4];
-  T4 *o4 = (T4 *)vout;
-  o4[2 * i] = o0;
-  o4[2 * i + 1] = o1;
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) U[m] += __shfl_xor_sync(0xffffffffu, U[m], o, G);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) E[m] += __shfl_xor_sync(0xffffffffu, E[m], o, G);
+  }
+  if (active && sub == 0) {
+    T4 s0 = v4[2 * i], s1 = v4[2 * i + 1];
+    if (WANT_U && HAS_F) {
+      U[0] += (T)a.self_uf * s0.x;
+      U[1] += (T)a.self_uf * s0.y;
+      U[2] += (T)a.self_uf * s0.z;
+    }
+    if (WANT_E) {
+      E[0] += (T)a.self_es * s0.w;
+      E[1] += (T)a.self_es * s1.x;
+      E[2] += (T)a.self_es * s1.y;
+      E[3] += (T)a.self_es * s1.z;
+      E[4] += (T)a.self_es * s1.w;
+    }
+    T4 o0, o1;
+    o0.x = U[0];
+    o0.y = U[1];
+    o0.z = U[2];
+    o0.w = E[0];
+    o1.x = E[1];
+    o1.y = E[2];
+    o1.z = E[3];
+    o1.w = E[4];
+    T4 *o4 = (T4 *)vout;
+    o4[2 * i] = o0;
+    o4[2 * i + 1] = o1;
+  }
+}
+
+template <typename T, int G>
+void launch_real_g(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int mode, cudaStream_t s) {
+  unsigned nb = (unsigned)ceil_div((int64_t)a.N * G, 256);
+  const T *tab = (const T *)c->d_table;
+  if (mode == M_FULL)
+    k_real<T, M_FULL, G><<<nb, 256, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+  else if (mode == M_SE)
+    k_real<T, M_SE, G><<<nb, 256, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+  else
+    k_real<T, M_FSU, G><<<nb, 256, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
 }
 
 template <typename T>
 void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int mode, cudaStream_t s) {
-  unsigned nb = (unsigned)ceil_div(a.N, 128);
-  const T *tab = (const T *)c->d_table;
-  if (mode == M_FULL)
-    k_real<T, M_FULL><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
-  else if (mode == M_SE)
-    k_real<T, M_SE><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
-  else
-    k_real<T, M_FSU><<<nb, 128, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+  // lanes per particle from the mean neighbour count of the current list
+  int g = c->opt.real_lanes;
+  if (g <= 0) {
+    double mean = a.N > 0 ? (double)c->npairs / a.N : 0.0;
+    g = mean >= 64.0 ? 8 : (mean >= 24.0 ? 4 : 1);
+  }
+  switch (g) {
+    case 32: launch_real_g<T, 32>(c, a, vin, vout, mode, s); break;
+    case 16: launch_real_g<T, 16>(c, a, vin, vout, mode, s); break;
+    case 8: launch_real_g<T, 8>(c, a, vin, vout, mode, s); break;
+    case 4: launch_real_g<T, 4>(c, a, vin, vout, mode, s); break;
+    default: launch_real_g<T, 1>(c, a, vin, vout, mode, s);
+  }
 }
 
 }  // namespace
@@ -193,6 +225,7 @@ pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStr
   a.nc = c->p.nc;
   a.len = c->table_len;
   a.k2 = c->table_k2;
+  a.slots = c->nbr_slots;
   a.csf = (float)c->p.cs;
   a.Lf = (float)c->p.L;
   a.L = c->p.L;

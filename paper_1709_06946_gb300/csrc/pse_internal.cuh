@@ -82,9 +82,11 @@ struct pse_ctx {
   int *d_tile_start = nullptr, *d_tile_cur = nullptr;   // ntiles + 1
   int *d_cell_start = nullptr, *d_cell_cur = nullptr;   // ncells + 1
   int *d_cell_list = nullptr;
-  int *d_nbr_start = nullptr;   // N + 1
-  int *d_nbr = nullptr;
+  int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
+  int *d_nbr = nullptr;         // neighbour slots: particle i owns [i*nbr_slots, (i+1)*nbr_slots)
+  int nbr_slots = 0;            // slots per particle
   int64_t nbr_cap = 0, npairs = 0;
+  unsigned long long *d_nbr_tot = nullptr;  // total pairs and maximum count
   void *d_sp_i0 = nullptr;      // int4 per particle: wrapped support start
   void *d_sp_d0 = nullptr;      // real4: i0*h - x per dimension
   void *d_rs = nullptr;         // float4 (cell offset + packed cell) or double4_32a positions

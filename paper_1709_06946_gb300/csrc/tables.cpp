@@ -217,7 +217,8 @@ int choose_params(Params &p, const pse_options &opt, std::string &err) {
           " (minimum-image pair sum): enlarge the box or increase xi";
     return 1;
   }
-  p.nc = std::max(1, std::min(1023, (int)std::floor(p.L / p.rcut)));
+  // linked cells of side >= r_cut/2, searched with a 5 x 5 x 5 stencil (all cells when nc < 5)
+  p.nc = std::max(1, std::min(1023, (int)std::floor(2.0 * p.L / p.rcut)));
   p.cs = p.L / p.nc;
   int mins = std::max(1, p.P - 1);
   // z planes are owned by the 16 warps of a spreading CTA: aim for 16 planes, x rows of up

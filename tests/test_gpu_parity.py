@@ -5,7 +5,7 @@ for the mixed form against the oracle PSE with identical parameters and
 identical noise; both forms within the PSE tolerance eps of the dense Ewald
 sum.  Sizes span several spreading tiles and cells; edge cases cover a single
 particle, overlapping pairs, positions outside the box, one-sided inputs,
-boxes with fewer than three cells per side and even/odd support sizes.
+boxes with fewer than five cells per side and even/odd support sizes.
 """
 import math
 
@@ -109,9 +109,9 @@ def test_edge_cases(pkg, prec):
     pos[2] = pos[0] + np.array([2.0, 0.0, 0.0])           # exact contact
     F, S = pse_inputs.moments(N, seed=8)
     for tol, rule in ((1e-3, 'paper'), (1e-4, 'paper')):
-        h = pkg.PSE(N, L, xi=0.9, tol=tol, precision=prec, rule=rule)
-        assert h.info['cells_per_side'] < 3
-        p = _oracle_params(h, N, L, 0.9, tol, rule=rule)
+        h = pkg.PSE(N, L, xi=0.8, tol=tol, precision=prec, rule=rule)
+        assert h.info["cells_per_side"] < 5
+        p = _oracle_params(h, N, L, 0.8, tol, rule=rule)
         Uo, Eo = opse.mobility_apply(pos, F, S, p)
         assert _rel(_mob(pkg, h, pos, F, S, prec), np.concatenate([Uo, Eo], 1)) < TOL[prec]
         Uo, Eo = opse.mobility_apply(pos, F, 0 * S, p)
