@@ -9,7 +9,7 @@ The oracle is plain and slow on purpose.  It follows the paper
 Simulations with Stresslet Constraints", arXiv:1709.06946) step by step:
 
 * ``params``     -- parameter rules (Sec. 2.3.1 real-space cutoff; Eq. bound with
-                    m = sqrt(pi P); the grid/k_cut readings listed in the design doc).
+                    m = sqrt(pi P); readings for k_cut and the grid size where the paper is silent).
 * ``basis``      -- orthonormal symmetric-traceless basis for the 5 stresslet
                     components (Sec. 2.2.1 rigid-particle relation).
 * ``realspace``  -- real-space split mobility M^(r) (Eqs. MUFr-MDCr, defined as

@@ -1,7 +1,7 @@
 """Orthonormal basis of symmetric traceless 3x3 tensors (oracle, test infrastructure).
 
 The paper (Sec. 2.2.1, text after Fig. ptpsopt) states that the stresslet has 5
-independent components but gives no basis.  Reading (DESIGN.md): the
+independent components but gives no basis.  Reading: the
 orthonormal basis
     Y1 = (xx - yy)/sqrt2, Y2 = (xx + yy - 2zz)/sqrt6,
     Y3 = (xy + yx)/sqrt2, Y4 = (xz + zx)/sqrt2, Y5 = (yz + zy)/sqrt2,

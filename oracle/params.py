@@ -7,7 +7,7 @@ Follows
   integer meeting the tolerance (C = 1 reading).
 * eta = (h P xi / m)^2 (text before Eq. bound), Gaussian kernel
   K(r) = (2 xi^2/(pi eta))^{3/2} exp(-2 xi^2 r^2 / eta).
-* Readings where the paper is silent (listed in the design doc): k_cut from
+* Readings where the paper is silent: k_cut from
   H(k_cut, xi) <= eps with H the Hasimoto splitting function; N_g the smallest
   even 2,3,5,7-smooth integer >= k_cut L / pi; the grid is refined until eta < 1.
 * Error budget.  With the bounds taken literally (C = 1, rule='paper') the

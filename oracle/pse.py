@@ -11,7 +11,7 @@ Steps, in the paper's order:
   - F: FFT.  The spread density approximates the particles' point moments
     filtered by K_hat(k) = exp(-eta_g k^2 / (8 xi^2)); spreading and
     interpolation together filter by exp(-eta_g k^2/(4 xi^2)), which the
-    scaling step divides out (reading of the normalisation).
+    scaling step divides out (a reading of the normalisation, which the paper leaves implicit).
   - P, B: f = s0 F_hat - 3i s1 S_hat.k;  u = H/(eta V k^2) (I - kk) f;
     U_hat = s0 u;  D_hat = 3i s1 u k^T;  E = Y-projection of D.
   - k = 0 and every mode with an index at the Nyquist plane are excluded.

@@ -5,7 +5,7 @@ sequential addition (RSA, compiled C in rsa.c), standard-normal forces and
 stresslets, and standard-normal noise arrays in the layouts of the C ABI.
 Both the oracle side and the CUDA side of a test receive the same arrays.
 
-Workload recipe (DESIGN.md): a = eta = kT = 1, box L = (4 pi N / (3 phi))^{1/3},
+Workload recipe: a = eta = kT = 1, box L = (4 pi N / (3 phi))^{1/3},
 positions by RSA (valid for phi <= 0.35), forces and stresslet components
 (orthonormal basis) i.i.d. N(0, 1) from numpy's PCG64 with the given seed.
 """

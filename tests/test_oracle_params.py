@@ -31,7 +31,7 @@ def test_support_size_rows_that_follow_the_bound():
         assert params.support_rule(1e-3, ls) == int(Ps)
         assert params.support_rule(1e-3, le) == int(Pe)
     # The remaining rows of the printed table are not reproduced by the bound
-    # (reading recorded in the design doc); the bound is monotone in lambda.
+    # (a reading of the table); the bound is monotone in lambda.
     prev = 0
     for g in (0.0, 0.1, 0.5, 1.0):
         P = params.support_rule(1e-3, params.lambda_max_shear(g))
