@@ -39,7 +39,7 @@ def parse():
     ap.add_argument('--N', type=int, default=1048576)
     ap.add_argument('--phi', type=float, default=0.3)
     ap.add_argument('--tol', type=float, default=1e-3)
-    ap.add_argument('--xi', type=float, default=0.7)
+    ap.add_argument('--xi', type=float, default=0.5)
     ap.add_argument('--dt', type=float, default=1e-3)
     ap.add_argument('--fp64-steps', type=int, default=2)
     ap.add_argument('--e2e-steps', type=int, default=3)
