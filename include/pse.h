@@ -91,7 +91,9 @@ typedef struct pse_options {
   int32_t krylov_maxiter;  /* 0 = 50 */
   int32_t tile[3];         /* spreading/interpolation tile (x, y, z); 0 = auto */
   int32_t real_lanes;      /* lanes sharing one particle in the pair sum (1,4,8,16,32); 0 = auto */
-  int32_t reserved[7];
+  int32_t grid_ladder;     /* 1: round the rule's grid up to an even 3-smooth size (2^i 3^j), so that
+                              a batch has few distinct grids and therefore few FFT groups; 0 = off */
+  int32_t reserved[6];
 } pse_options;
 
 typedef struct pse_info {
@@ -151,9 +153,43 @@ void pse_default_options(pse_options *opt);
 pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT,
                       double xi, double tol, pse_precision prec, const pse_options *opt);
 
+/* Creates one handle for nsys independent suspensions (no counterpart in the
+ * paper, which treats one suspension: this is the batching layer).  Suspension s
+ * has N[s] particles in a cubic box of side L[s]; a, eta, kT, xi and tol are
+ * shared (so is the real-space table), and every suspension gets its own r_cut
+ * check, grid, cells and tiles by the same rules as pse_create.  Every array
+ * argument of the other calls is the concatenation of the suspensions' arrays
+ * in suspension order (positions, forces, stresslets, velocities, w1), and w2
+ * the concatenation of the suspensions' half-spectrum noise blocks.  Each stage
+ * runs as one launch over all suspensions (one cuFFT plan per group of equal
+ * grids); the Krylov iterations run in lockstep and a converged suspension drops
+ * out.  Results equal those of separate handles up to rounding (the noise
+ * indices are global: suspension s's Philox indices follow those of 0..s-1).
+ * Errors name the suspension.  1 <= nsys <= 65536. */
+pse_status pse_create_batch(pse_handle *out, int32_t nsys, const int64_t *N, const double *L, double a,
+                            double eta, double kT, double xi, double tol, pse_precision prec,
+                            const pse_options *opt);
+
+/* Device bytes a handle with these arguments would allocate (an estimate that
+ * bounds the real figure from above; no device memory is touched).  Same
+ * argument checks as pse_create_batch. */
+pse_status pse_estimate_bytes(int32_t nsys, const int64_t *N, const double *L, double a, double eta,
+                              double kT, double xi, double tol, pse_precision prec,
+                              const pse_options *opt, int64_t *bytes);
+
 pse_status pse_destroy(pse_handle h);
 
+/* For a batch handle: N is the total and the grid fields are suspension 0's. */
 pse_status pse_get_info(pse_handle h, pse_info *out);
+
+/* Number of suspensions of a handle (0 for NULL). */
+int32_t pse_num_systems(pse_handle h);
+
+/* Parameters of suspension s. */
+pse_status pse_get_system_info(pse_handle h, int32_t s, pse_info *out);
+
+/* Statistics of suspension s in the last sample or step call. */
+pse_status pse_get_system_stats(pse_handle h, int32_t s, pse_stats *out);
 
 /* [U; E] = M [F; S] at positions pos (Sec. 2.2 Eq. pairsums, rigid-particle
  * form).  F or S may be NULL (treated as zero); U or E may be NULL (not
@@ -218,6 +254,71 @@ pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, double eta, 
 
 /* Message for the last error of pse_mobility_real_noalloc on this thread. */
 const char *pse_noalloc_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper).  A server owns `slots` worker
+ * threads, each with its own CUDA stream on the current device.  Requests for
+ * suspensions of any size arrive at any time and run concurrently on the
+ * device; a request starts when a slot is free and its suspension's state fits
+ * the device-memory budget.  State stays resident: a later request with the
+ * same parameters (N, L, a, eta, kT, xi, tol, precision) reuses the handle
+ * (tables, cuFFT plans, grids, neighbour lists); a new handle is created when
+ * its estimate (pse_estimate_bytes) fits, after evicting idle resident handles,
+ * least recently used first.  Requests that do not fit yet wait in arrival
+ * order while later ones that fit go ahead.  A request whose estimate alone
+ * exceeds the budget is rejected (OOM) at submission.
+ * ------------------------------------------------------------------------ */
+typedef struct pse_server pse_server;
+
+enum { PSE_REQ_MOBILITY = 0, PSE_REQ_SAMPLE = 1, PSE_REQ_STEP = 2 };
+
+typedef struct pse_request {
+  int32_t kind;              /* PSE_REQ_* */
+  int32_t precision;         /* pse_precision */
+  int64_t N;
+  double L, a, eta, kT, xi, tol;
+  const pse_options *options; /* may be NULL (defaults); read at submission and at handle creation */
+  double *pos;               /* N x 3 FP64 positions (host or device); updated in place by a step */
+  const void *F, *S;         /* mobility: forces / stresslets; step: F = conservative force (may be NULL) */
+  void *U, *E;               /* mobility: U, E; sample: U^B, E^B */
+  void *S_out;               /* step: mid-point stresslets (may be NULL) */
+  double dt;                 /* sample, step */
+  uint64_t seed, counter;    /* sample: (seed, counter); step: (seed, step) */
+  pse_stats *stats;          /* may be NULL */
+} pse_request;
+
+typedef struct pse_server_stats {
+  int64_t completed, queued;
+  int32_t running, peak_running;     /* requests on the device now / at most at once */
+  double p50_ms, p99_ms;             /* latency, submission to completion */
+  double wait_p50_ms, wait_p99_ms;   /* submission to start */
+  double service_p50_ms;             /* start to completion */
+  double requests_per_s;             /* completed / (first submission .. last completion) */
+  int64_t resident_bytes, peak_resident_bytes;
+  int32_t resident_handles;
+  int64_t handles_created, handles_reused, handles_evicted, rejected;
+} pse_server_stats;
+
+/* 1 <= slots <= 64, budget_bytes > 0.  CUDA error if no device is present. */
+pse_status pse_server_create(pse_server **out, int32_t slots, int64_t budget_bytes);
+
+/* Queues a request (the arrays must stay valid until it completes); returns its ticket. */
+pse_status pse_server_submit(pse_server *srv, const pse_request *req, uint64_t *ticket);
+
+/* Waits at most timeout_ms for the request; TIMEOUT if it has not completed (it
+ * stays queued or running and can be waited for again), else OK with the
+ * request's own status in *result and its latency in *latency_ms. */
+pse_status pse_server_wait(pse_server *srv, uint64_t ticket, double timeout_ms, pse_status *result,
+                           double *latency_ms);
+
+pse_status pse_server_get_stats(pse_server *srv, pse_server_stats *out);
+
+/* Clears the latency record and counters (not the resident handles). */
+pse_status pse_server_reset_stats(pse_server *srv);
+
+/* Stops the workers after their current requests (queued ones are dropped) and
+ * frees every resident handle. */
+pse_status pse_server_destroy(pse_server *srv);
 
 /* Enables (1) or disables (0) stage timing and resets the profile and the
  * launch counters.  Timing adds two event records per stage section. */

@@ -60,14 +60,14 @@ def normals(seed, step, stream, index):
     return rad * np.cos(2 * np.pi * u2), rad * np.sin(2 * np.pi * u2)
 
 
-def lanczos_noise(seed, step, N):
-    """w1: (N, 8) standard normals of stream 1."""
-    z0, _ = normals(seed, step, 1, np.arange(8 * N))
+def lanczos_noise(seed, step, N, index0=0):
+    """w1: (N, 8) standard normals of stream 1 (indices index0 + 8 n + c)."""
+    z0, _ = normals(seed, step, 1, index0 + np.arange(8 * N, dtype=np.uint64))
     return z0.reshape(N, 8)
 
 
-def wave_noise(seed, step, Ng):
-    """w2: (3, Ng, Ng, Ng/2+1, 2) standard normals of stream 2."""
+def wave_noise(seed, step, Ng, index0=0):
+    """w2: (3, Ng, Ng, Ng/2+1, 2) standard normals of stream 2 (indices index0 + flat position)."""
     n = 3 * Ng * Ng * (Ng // 2 + 1)
-    z0, z1 = normals(seed, step, 2, np.arange(n))
+    z0, z1 = normals(seed, step, 2, index0 + np.arange(n, dtype=np.uint64))
     return np.stack([z0, z1], axis=-1).reshape(3, Ng, Ng, Ng // 2 + 1, 2)

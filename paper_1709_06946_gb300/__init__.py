@@ -3,7 +3,7 @@
 The compute path is the CUDA library ``libpse.so`` (sm_103a kernels + cuFFT)
 behind the C ABI in ``include/pse.h``; this package only builds it and binds it.
 """
-from .binding import PSE, PSEError, load, LIB_PATH, PSE_MIXED, PSE_FP64  # noqa: F401
+from .binding import PSE, PSEError, Server, estimate_bytes, load, LIB_PATH, PSE_MIXED, PSE_FP64  # noqa: F401
 
 
 def build(verbose=False, force=False):

@@ -28,7 +28,8 @@ class Options(ctypes.Structure):
                 ('table_points', ctypes.c_int32), ('rcut', ctypes.c_double),
                 ('lanczos_tol', ctypes.c_double), ('lanczos_maxiter', ctypes.c_int32),
                 ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
-                ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('reserved', ctypes.c_int32 * 7)]
+                ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('grid_ladder', ctypes.c_int32),
+                ('reserved', ctypes.c_int32 * 6)]
 
 
 class Info(ctypes.Structure):
@@ -61,6 +62,31 @@ class Profile(ctypes.Structure):
                 ('launches', ctypes.c_int64), ('fft_execs', ctypes.c_int64)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [('kind', ctypes.c_int32), ('precision', ctypes.c_int32), ('N', ctypes.c_int64),
+                ('L', ctypes.c_double), ('a', ctypes.c_double), ('eta', ctypes.c_double), ('kT', ctypes.c_double),
+                ('xi', ctypes.c_double), ('tol', ctypes.c_double), ('options', ctypes.POINTER(Options)),
+                ('pos', ctypes.c_void_p), ('F', ctypes.c_void_p), ('S', ctypes.c_void_p), ('U', ctypes.c_void_p),
+                ('E', ctypes.c_void_p), ('S_out', ctypes.c_void_p), ('dt', ctypes.c_double),
+                ('seed', ctypes.c_uint64), ('counter', ctypes.c_uint64), ('stats', ctypes.POINTER(Stats))]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [('completed', ctypes.c_int64), ('queued', ctypes.c_int64), ('running', ctypes.c_int32),
+                ('peak_running', ctypes.c_int32), ('p50_ms', ctypes.c_double), ('p99_ms', ctypes.c_double),
+                ('wait_p50_ms', ctypes.c_double), ('wait_p99_ms', ctypes.c_double),
+                ('service_p50_ms', ctypes.c_double), ('requests_per_s', ctypes.c_double),
+                ('resident_bytes', ctypes.c_int64), ('peak_resident_bytes', ctypes.c_int64),
+                ('resident_handles', ctypes.c_int32), ('handles_created', ctypes.c_int64),
+                ('handles_reused', ctypes.c_int64), ('handles_evicted', ctypes.c_int64),
+                ('rejected', ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_KINDS = {'mobility': 0, 'sample': 1, 'step': 2}
+
 # (name, restype, argtypes) of every symbol declared in include/pse.h
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -69,8 +95,15 @@ SIGNATURES = [
     ('pse_default_options', None, [ctypes.POINTER(Options)]),
     ('pse_create', ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, _D, _D, _D, _D, _D, _D, ctypes.c_int,
                                   ctypes.POINTER(Options)]),
+    ('pse_create_batch', ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _D, _D, _D, _D, _D,
+                                        ctypes.c_int, ctypes.POINTER(Options)]),
+    ('pse_estimate_bytes', ctypes.c_int, [ctypes.c_int32, _P, _P, _D, _D, _D, _D, _D, ctypes.c_int,
+                                          ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_int64)]),
     ('pse_destroy', ctypes.c_int, [_P]),
     ('pse_get_info', ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    ('pse_num_systems', ctypes.c_int32, [_P]),
+    ('pse_get_system_info', ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Info)]),
+    ('pse_get_system_stats', ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Stats)]),
     ('pse_mobility_apply', ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ('pse_mobility_apply_parts', ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     ('pse_brownian_sample', ctypes.c_int, [_P, _P, _D, _U64, _U64, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
@@ -78,6 +111,13 @@ SIGNATURES = [
     ('pse_constrained_step_noise', ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     ('pse_mobility_real_noalloc', ctypes.c_int, [ctypes.c_int64, _D, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P]),
     ('pse_noalloc_last_error', ctypes.c_char_p, []),
+    ('pse_server_create', ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64]),
+    ('pse_server_submit', ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    ('pse_server_wait', ctypes.c_int, [_P, ctypes.c_uint64, _D, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(_D)]),
+    ('pse_server_get_stats', ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    ('pse_server_reset_stats', ctypes.c_int, [_P]),
+    ('pse_server_destroy', ctypes.c_int, [_P]),
     ('pse_set_profiling', ctypes.c_int, [_P, ctypes.c_int32]),
     ('pse_get_profile', ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     ('pse_stage_name', ctypes.c_char_p, [ctypes.c_int32]),
@@ -156,34 +196,85 @@ def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
     return U, E
 
 
-class PSE:
-    """One PSE handle (N particles in a cubic periodic box)."""
+def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
+             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=0):
+    o = Options()
+    load().pse_default_options(ctypes.byref(o))
+    o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
+    o.Ng, o.P, o.rcut = int(Ng), int(P), float(rcut)
+    o.lanczos_tol, o.lanczos_maxiter = float(lanczos_tol), int(lanczos_maxiter)
+    o.krylov_tol, o.krylov_maxiter = float(krylov_tol), int(krylov_maxiter)
+    o.table_points = int(table_points)
+    o.real_lanes = int(real_lanes)
+    o.grid_ladder = int(grid_ladder)
+    for d in range(3):
+        o.tile[d] = int(tile[d])
+    return o
 
-    def __init__(self, N, L, a=1.0, eta=1.0, kT=1.0, xi=0.5, tol=1e-3, precision='mixed', rule='strict',
-                 Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
-                 krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0):
+
+def _precision(precision):
+    return PSE_FP64 if precision in ('fp64', 'double', PSE_FP64) else PSE_MIXED
+
+
+def estimate_bytes(N, L, a=1.0, eta=1.0, kT=1.0, xi=0.5, tol=1e-3, precision='mixed', **opts):
+    """Device bytes a handle for suspensions N[i], L[i] would allocate (upper estimate)."""
+    lib = load()
+    Ns = np.ascontiguousarray(np.atleast_1d(N), dtype=np.int64)
+    Ls = np.ascontiguousarray(np.atleast_1d(L), dtype=np.float64)
+    out = ctypes.c_int64(0)
+    o = _options(**opts)
+    st = lib.pse_estimate_bytes(len(Ns), Ns.ctypes.data, Ls.ctypes.data, float(a), float(eta), float(kT), float(xi),
+                                float(tol), _precision(precision), ctypes.byref(o), ctypes.byref(out))
+    if st != 0:
+        raise PSEError(st, lib.pse_last_error(None).decode())
+    return int(out.value)
+
+
+class PSE:
+    """One PSE handle: N particles in a cubic periodic box of side L, or (N and L
+    sequences) a batch of independent suspensions whose arrays are concatenated."""
+
+    def __init__(self, N, L, a=1.0, eta=1.0, kT=1.0, xi=0.5, tol=1e-3, precision='mixed', **opts):
         lib = load()
-        o = Options()
-        lib.pse_default_options(ctypes.byref(o))
-        o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
-        o.Ng, o.P, o.rcut = int(Ng), int(P), float(rcut)
-        o.lanczos_tol, o.lanczos_maxiter = float(lanczos_tol), int(lanczos_maxiter)
-        o.krylov_tol, o.krylov_maxiter = float(krylov_tol), int(krylov_maxiter)
-        o.table_points = int(table_points)
-        o.real_lanes = int(real_lanes)
-        for d in range(3):
-            o.tile[d] = int(tile[d])
-        self.prec = PSE_FP64 if precision in ('fp64', 'double', PSE_FP64) else PSE_MIXED
+        o = _options(**opts)
+        self.prec = _precision(precision)
         self.dtype = np.float64 if self.prec == PSE_FP64 else np.float32
         h = _P()
-        st = lib.pse_create(ctypes.byref(h), int(N), float(L), float(a), float(eta), float(kT), float(xi),
-                            float(tol), self.prec, ctypes.byref(o))
+        self.batch = np.ndim(N) > 0
+        if self.batch:
+            Ns = np.ascontiguousarray(N, dtype=np.int64)
+            Ls = np.ascontiguousarray(L, dtype=np.float64)
+            if Ns.shape != Ls.shape:
+                raise ValueError('N and L must have the same length')
+            st = lib.pse_create_batch(ctypes.byref(h), len(Ns), Ns.ctypes.data, Ls.ctypes.data, float(a), float(eta),
+                                      float(kT), float(xi), float(tol), self.prec, ctypes.byref(o))
+            self.Ns = [int(v) for v in Ns]
+        else:
+            st = lib.pse_create(ctypes.byref(h), int(N), float(L), float(a), float(eta), float(kT), float(xi),
+                                float(tol), self.prec, ctypes.byref(o))
+            self.Ns = [int(N)]
         if st != 0:
             raise PSEError(st, lib.pse_last_error(None).decode())
         self._h = h
         self._lib = lib
-        self.N = int(N)
+        self.N = int(sum(self.Ns))
+        self.nsys = int(lib.pse_num_systems(h))
+        self.offsets = np.concatenate([[0], np.cumsum(self.Ns)]).astype(np.int64)
         self.info = self.get_info()
+
+    def system_info(self, s):
+        """Parameters of suspension s (grid, cells, tiles, ...)."""
+        inf = Info()
+        self._check(self._lib.pse_get_system_info(self._h, int(s), ctypes.byref(inf)))
+        d = {k: getattr(inf, k) for k, _ in Info._fields_}
+        d['tile'] = tuple(inf.tile)
+        return d
+
+    def system_stats(self, s):
+        """Statistics of suspension s in the last sample or step call."""
+        st = Stats()
+        self._check(self._lib.pse_get_system_stats(self._h, int(s), ctypes.byref(st)))
+        return st.as_dict()
 
     def _check(self, st):
         if st not in (0,):
@@ -264,3 +355,94 @@ class PSE:
 
     def sync(self):
         self._check(self._lib.pse_sync(self._h))
+
+
+class Server:
+    """Serving loop of the C ABI: `slots` concurrent workers (one CUDA stream each)
+    under a device-memory budget; suspension state stays resident between
+    requests with the same parameters.  Arrays are numpy (host) or torch tensors
+    and must stay alive until the request completes (the Server keeps them)."""
+
+    def __init__(self, slots=4, budget_bytes=64 << 30):
+        self._lib = load()
+        h = _P()
+        st = self._lib.pse_server_create(ctypes.byref(h), int(slots), int(budget_bytes))
+        if st != 0:
+            raise PSEError(st, 'cannot create the server')
+        self._h = h
+        self._keep = {}
+
+    def submit(self, kind, pos, L, a=1.0, eta=1.0, kT=1.0, xi=0.5, tol=1e-3, precision='mixed', F=None, S=None,
+               dt=1e-3, seed=0, counter=0, **opts):
+        """Queues a request; returns (ticket, outputs).  kind: 'mobility' (outputs U, E),
+        'sample' (U^B, E^B), 'step' (pos updated in place; outputs S_out)."""
+        prec = _precision(precision)
+        dtype = np.float64 if prec == PSE_FP64 else np.float32
+        N = pos.shape[0]
+        out = {}
+        r = Request()
+        r.kind = REQ_KINDS[kind]
+        r.precision = prec
+        r.N, r.L, r.a, r.eta, r.kT, r.xi, r.tol = int(N), float(L), float(a), float(eta), float(kT), float(xi), float(tol)
+        o = _options(**opts) if opts else None
+        if o is not None:
+            r.options = ctypes.pointer(o)
+        r.pos = _ptr(pos)
+        r.dt, r.seed, r.counter = float(dt), int(seed), int(counter)
+        stats = Stats()
+        r.stats = ctypes.pointer(stats)
+
+        def like(shape):
+            if isinstance(pos, np.ndarray):
+                return np.zeros(shape, dtype=dtype)
+            torch = _torch()
+            return torch.zeros(shape, dtype=torch.float64 if dtype == np.float64 else torch.float32,
+                               device=pos.device)
+        if kind in ('mobility', 'sample'):
+            out['U'], out['E'] = like((N, 3)), like((N, 5))
+            r.U, r.E = _ptr(out['U']), _ptr(out['E'])
+            if kind == 'mobility':
+                r.F, r.S = _ptr(F), _ptr(S)
+        else:
+            r.F = _ptr(F)
+            out['S'] = like((N, 5))
+            r.S_out = _ptr(out['S'])
+        t = ctypes.c_uint64(0)
+        st = self._lib.pse_server_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        if st != 0:
+            raise PSEError(st, 'request rejected')
+        out['stats'] = stats
+        self._keep[t.value] = (r, o, stats, pos, F, S, out)
+        return t.value, out
+
+    def wait(self, ticket, timeout_ms=600000.0):
+        """(status, latency_ms) of a request; raises TimeoutError if it has not completed in time."""
+        res = ctypes.c_int(0)
+        lat = ctypes.c_double(0)
+        st = self._lib.pse_server_wait(self._h, int(ticket), float(timeout_ms), ctypes.byref(res), ctypes.byref(lat))
+        if st == 6:
+            raise TimeoutError('request %d still running' % ticket)
+        if st != 0:
+            raise PSEError(st, 'unknown ticket')
+        self._keep.pop(ticket, None)
+        return res.value, lat.value
+
+    def stats(self):
+        s = ServerStats()
+        self._lib.pse_server_get_stats(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+    def reset_stats(self):
+        self._lib.pse_server_reset_stats(self._h)
+
+    def close(self):
+        if getattr(self, '_h', None):
+            self._lib.pse_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

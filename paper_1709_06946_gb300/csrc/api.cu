@@ -1,10 +1,17 @@
 // C ABI entry points (include/pse.h): handle set-up, the mobility product,
 // split Brownian sampling (Lanczos + wave-space noise) and the constrained
-// mid-point step.  Krylov scalars (Lanczos tridiagonal, GMRES Hessenberg and
-// Givens rotations) are FP64 on the host; vectors live on the device.
+// mid-point step.
+//
+// A handle holds one suspension (pse_create) or a group of independent
+// suspensions (pse_create_batch) that every kernel processes in one launch.
+// The Krylov iterations of the suspensions run in lockstep, each with its own
+// FP64 scalars on the host (Lanczos tridiagonal, GMRES Hessenberg and Givens
+// rotations); a suspension that has converged drops out of the launches.
+// Vectors live on the device.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "device_common.cuh"
@@ -13,6 +20,7 @@
 namespace pse {
 pse_status exclusive_scan(pse_ctx *c, int *buf, int64_t n1, cudaStream_t s);
 int64_t scan_tmp_ints(int64_t n1);
+int64_t layout_neighbours(pse_ctx *c);
 }  // namespace pse
 
 using namespace pse;
@@ -98,186 +106,306 @@ pse_status mobility(pse_ctx *c, const void *vin, void *vout, int mode, int parts
 
 }  // namespace pse
 
-namespace {
+namespace pse {
 
-// Reads `count` doubles at d_src into h (waits on the stream).
-pse_status read_doubles(pse_ctx *c, const double *d_src, int count, double *h, cudaStream_t s) {
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_dots, d_src, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
-  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
-  std::memcpy(h, c->h_dots, sizeof(double) * count);
+// Host-to-device copies read pinned staging buffers; a buffer is rewritten only
+// after the stream has passed the copies that read it.
+pse_status staging_ready(pse_ctx *c, cudaStream_t s) {
+  if (c->h2d_pending) {
+    PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+    c->h2d_pending = false;
+  }
   return PSE_OK;
 }
 
-pse_status write_doubles(pse_ctx *c, double *d_dst, const double *h, int count, cudaStream_t s) {
-  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));  // h_dots may still be read by an earlier copy
-  std::memcpy(c->h_dots, h, sizeof(double) * count);
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(d_dst, c->h_dots, sizeof(double) * count, cudaMemcpyHostToDevice, s));
+pse_status upload_active(pse_ctx *c, cudaStream_t s) {
+  PSE_TRY(staging_ready(c, s));
+  std::copy(c->h_active.begin(), c->h_active.end(), c->h_pinned_int + 8);
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_active, c->h_pinned_int + 8, sizeof(int) * c->nsys, cudaMemcpyHostToDevice, s));
+  c->h2d_pending = true;
+  return PSE_OK;
+}
+
+}  // namespace pse
+
+namespace {
+
+// Per-suspension coefficient block (COEF_STRIDE doubles): first and second
+// Gram-Schmidt projections, |w|^2, a scale factor, the constants +1 and -1, and
+// the coefficients of the final Krylov combination.
+constexpr int CO_H1 = 0, CO_H2 = 128, CO_NRM = 256, CO_FAC = 257, CO_ONE = 258, CO_MONE = 259, CO_Y = 384;
+
+pse_status set_all_active(pse_ctx *c, cudaStream_t s) {
+  bool all = true;
+  for (int v : c->h_active) all = all && v;
+  if (all) return PSE_OK;
+  std::fill(c->h_active.begin(), c->h_active.end(), 1);
+  return upload_active(c, s);
+}
+
+// h[s * count + k] = coefficient (off + k) of suspension s (waits on the stream).
+pse_status read_coef(pse_ctx *c, int off, int count, std::vector<double> &h, cudaStream_t s) {
+  PSE_CUDA_TRY(c, cudaMemcpy2DAsync(c->h_dots, sizeof(double) * count, c->d_coef + off, sizeof(double) * COEF_STRIDE,
+                                    sizeof(double) * count, c->nsys, cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  c->h2d_pending = false;
+  h.assign(c->h_dots, c->h_dots + (size_t)count * c->nsys);
+  return PSE_OK;
+}
+
+// Coefficients (off .. off + count) of every suspension from h[s * count + k].
+pse_status write_coef(pse_ctx *c, int off, int count, const std::vector<double> &h, cudaStream_t s) {
+  PSE_TRY(staging_ready(c, s));
+  std::memcpy(c->h_wbuf, h.data(), sizeof(double) * count * c->nsys);
+  PSE_CUDA_TRY(c, cudaMemcpy2DAsync(c->d_coef + off, sizeof(double) * COEF_STRIDE, c->h_wbuf, sizeof(double) * count,
+                                    sizeof(double) * count, c->nsys, cudaMemcpyHostToDevice, s));
+  c->h2d_pending = true;
+  return PSE_OK;
+}
+
+pse_status write_nrows(pse_ctx *c, const std::vector<int> &nr, cudaStream_t s) {
+  PSE_TRY(staging_ready(c, s));
+  int *h = c->h_pinned_int + 8 + c->nsys;
+  std::copy(nr.begin(), nr.end(), h);
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_nrows, h, sizeof(int) * c->nsys, cudaMemcpyHostToDevice, s));
+  c->h2d_pending = true;
   return PSE_OK;
 }
 
 void *row(pse_ctx *c, int r) { return (char *)c->d_basis + (size_t)r * 8 * c->p.N * c->ts; }
 
 // Orthogonalise w against rows 0..j of the basis twice (classical Gram-Schmidt,
-// FP64 coefficients); returns the summed coefficients in h and |w|^2 in nrm2.
-pse_status cgs2(pse_ctx *c, void *w, int j, std::vector<double> &h, double &nrm2, cudaStream_t s) {
-  int64_t n = 8 * c->p.N;
-  double *h1 = c->d_coef, *h2 = c->d_coef + 128, *nr = c->d_coef + 256;
-  PSE_TRY(multidot(c, c->d_basis, j + 1, n, w, h1, s));
-  PSE_TRY(combine_sub(c, w, c->d_basis, j + 1, n, h1, s));
-  PSE_TRY(multidot(c, c->d_basis, j + 1, n, w, h2, s));
-  PSE_TRY(combine_sub(c, w, c->d_basis, j + 1, n, h2, s));
-  PSE_TRY(multidot(c, w, 1, n, w, nr, s));
-  std::vector<double> buf(257);
-  PSE_TRY(read_doubles(c, c->d_coef, 257, buf.data(), s));
-  h.resize(j + 1);
-  for (int i = 0; i <= j; ++i) h[i] = buf[i] + buf[128 + i];
-  nrm2 = buf[256];
+// FP64 coefficients) for every active suspension; h[s * (j+1) + i] receives the
+// summed coefficients and nrm2[s] = |w|^2.
+pse_status cgs2(pse_ctx *c, void *w, int j, std::vector<double> &h, std::vector<double> &nrm2, cudaStream_t s) {
+  PSE_TRY(multidot(c, c->d_basis, j + 1, w, CO_H1, s));
+  PSE_TRY(combine_sub(c, w, c->d_basis, j + 1, CO_H1, s));
+  PSE_TRY(multidot(c, c->d_basis, j + 1, w, CO_H2, s));
+  PSE_TRY(combine_sub(c, w, c->d_basis, j + 1, CO_H2, s));
+  PSE_TRY(multidot(c, w, 1, w, CO_NRM, s));
+  std::vector<double> buf;
+  PSE_TRY(read_coef(c, 0, CO_NRM + 1, buf, s));
+  const int ns = c->nsys;
+  h.assign((size_t)ns * (j + 1), 0.0);
+  nrm2.assign(ns, 0.0);
+  for (int q = 0; q < ns; ++q) {
+    const double *b = buf.data() + (size_t)q * (CO_NRM + 1);
+    for (int i = 0; i <= j; ++i) h[(size_t)q * (j + 1) + i] = b[CO_H1 + i] + b[CO_H2 + i];
+    nrm2[q] = b[CO_NRM];
+  }
   return PSE_OK;
 }
 
-// y = M_r^{1/2} z by Lanczos with full reorthogonalisation (Sec. 3.2); mirrors the
-// stopping rule |c_m - [c_{m-1}; 0]| / |c_m| <= tol (tol = 0: fixed maxiter steps).
-pse_status lanczos(pse_ctx *c, const void *z, void *y, void *w, double tol, int maxiter, pse_stats *st,
-                   cudaStream_t s) {
-  int64_t n = 8 * c->p.N;
-  double *nr = c->d_coef + 256;
-  PSE_TRY(multidot(c, z, 1, n, z, nr, s));
-  double b0;
-  PSE_TRY(read_doubles(c, nr, 1, &b0, s));
-  b0 = std::sqrt(b0);
-  if (b0 == 0.0) {
-    PSE_CUDA_TRY(c, cudaMemsetAsync(y, 0, c->ts * n, s));
-    return PSE_OK;
+// y = M_r^{1/2} z by Lanczos with full reorthogonalisation (Sec. 3.2), per
+// suspension, with the stopping rule |c_m - [c_{m-1}; 0]| / |c_m| <= tol
+// (tol = 0: fixed maxiter steps).
+pse_status lanczos(pse_ctx *c, const void *z, void *y, void *w, double tol, int maxiter, cudaStream_t s) {
+  const int ns = c->nsys;
+  struct St {
+    std::vector<double> alpha, beta, cvec, cprev;
+    double b0 = 0, err = INFINITY;
+    int it = 0;
+  };
+  std::vector<St> st(ns);
+  PSE_TRY(set_all_active(c, s));
+  PSE_TRY(multidot(c, z, 1, z, CO_NRM, s));
+  std::vector<double> nrm, fac(ns, 0.0);
+  PSE_TRY(read_coef(c, CO_NRM, 1, nrm, s));
+  for (int q = 0; q < ns; ++q) {
+    st[q].b0 = std::sqrt(std::max(nrm[q], 0.0));
+    c->h_active[q] = st[q].b0 > 0.0;
+    fac[q] = st[q].b0 > 0.0 ? 1.0 / st[q].b0 : 0.0;
   }
-  PSE_TRY(vscale(c, row(c, 0), z, 1.0 / b0, n, s));
-  std::vector<double> alpha, beta, cvec, cprev;
-  double err = INFINITY;
-  int it = 0;
+  PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
+  PSE_TRY(upload_active(c, s));
+  PSE_TRY(vscale(c, row(c, 0), z, 0.0, CO_FAC, s));
   for (int j = 0; j < maxiter; ++j) {
-    it = j + 1;
+    bool any = false;
+    for (int v : c->h_active) any = any || v;
+    if (!any) break;
     PSE_TRY(real_apply(c, row(c, j), w, M_FULL, s));
-    std::vector<double> h;
-    double n2;
+    std::vector<double> h, n2;
     PSE_TRY(cgs2(c, w, j, h, n2, s));
-    alpha.push_back(h[j]);
-    double bj = std::sqrt(std::max(n2, 0.0));
-    int m = j + 1;
-    cvec.assign(m, 0.0);
-    if (j == 0) {
-      cvec[0] = std::sqrt(std::max(alpha[0], 0.0));
-    } else {
-      std::vector<double> d(alpha), e(beta), Z;
-      if (!tridiag_eigen(m, d, e, Z)) {
-        c->err = "tridiagonal eigen-solver failed";
-        return PSE_ERR_NOT_CONVERGED;
+    for (int q = 0; q < ns; ++q) {
+      if (!c->h_active[q]) continue;
+      St &L = st[q];
+      L.it = j + 1;
+      L.alpha.push_back(h[(size_t)q * (j + 1) + j]);
+      double bj = std::sqrt(std::max(n2[q], 0.0));
+      int m = j + 1;
+      L.cvec.assign(m, 0.0);
+      if (j == 0) {
+        L.cvec[0] = std::sqrt(std::max(L.alpha[0], 0.0));
+      } else {
+        std::vector<double> d(L.alpha), e(L.beta), Z;
+        if (!tridiag_eigen(m, d, e, Z)) {
+          c->err = "tridiagonal eigen-solver failed";
+          return PSE_ERR_NOT_CONVERGED;
+        }
+        for (int i = 0; i < m; ++i) {
+          double sum = 0;
+          for (int k = 0; k < m; ++k) sum += Z[(size_t)i * m + k] * std::sqrt(std::max(d[k], 0.0)) * Z[k];
+          L.cvec[i] = sum;
+        }
       }
-      for (int i = 0; i < m; ++i) {
-        double sum = 0;
-        for (int k = 0; k < m; ++k) sum += Z[(size_t)i * m + k] * std::sqrt(std::max(d[k], 0.0)) * Z[k];
-        cvec[i] = sum;
+      bool stop = false;
+      if (!L.cprev.empty()) {
+        double num = 0, den = 0;
+        for (int i = 0; i < m; ++i) {
+          double dv = L.cvec[i] - (i < m - 1 ? L.cprev[i] : 0.0);
+          num += dv * dv;
+          den += L.cvec[i] * L.cvec[i];
+        }
+        L.err = std::sqrt(num / den);
+        if (tol > 0 && L.err <= tol) stop = true;
+      }
+      if (!stop) {
+        L.cprev = L.cvec;
+        if (bj == 0.0 || j == maxiter - 1) stop = true;
+      }
+      if (stop) {
+        c->h_active[q] = 0;
+      } else {
+        L.beta.push_back(bj);
+        fac[q] = 1.0 / bj;
       }
     }
-    bool stop = false;
-    if (!cprev.empty()) {
-      double num = 0, den = 0;
-      for (int i = 0; i < m; ++i) {
-        double dv = cvec[i] - (i < m - 1 ? cprev[i] : 0.0);
-        num += dv * dv;
-        den += cvec[i] * cvec[i];
-      }
-      err = std::sqrt(num / den);
-      if (tol > 0 && err <= tol) stop = true;
-    }
-    if (stop) break;
-    cprev = cvec;
-    if (bj == 0.0 || j == maxiter - 1) break;
-    beta.push_back(bj);
-    PSE_TRY(vscale(c, row(c, j + 1), w, 1.0 / bj, n, s));
+    any = false;
+    for (int v : c->h_active) any = any || v;
+    if (!any) break;
+    PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
+    PSE_TRY(upload_active(c, s));
+    PSE_TRY(vscale(c, row(c, j + 1), w, 0.0, CO_FAC, s));
   }
-  std::vector<double> coef(it);
-  for (int i = 0; i < it; ++i) coef[i] = b0 * cvec[i];
-  PSE_TRY(write_doubles(c, c->d_coef + 384, coef.data(), it, s));
-  PSE_TRY(combine_set(c, y, c->d_basis, it, n, c->d_coef + 384, s));
-  if (st) {
-    st->lanczos_iters = it;
-    st->lanczos_change = std::isfinite(err) ? err : 0.0;
+  int maxit = 0;
+  std::vector<double> coef((size_t)ns * 128, 0.0);
+  std::vector<int> nr(ns, 0);
+  for (int q = 0; q < ns; ++q) {
+    nr[q] = st[q].it;
+    maxit = std::max(maxit, st[q].it);
+    for (int i = 0; i < st[q].it; ++i) coef[(size_t)q * 128 + i] = st[q].b0 * st[q].cvec[i];
   }
-  bool capped = tol > 0 && !(err <= tol) && it == maxiter;
+  PSE_TRY(write_coef(c, CO_Y, 128, coef, s));
+  PSE_TRY(write_nrows(c, nr, s));
+  PSE_TRY(set_all_active(c, s));
+  PSE_TRY(combine_set(c, y, c->d_basis, c->d_nrows, std::max(maxit, 1), CO_Y, s));
+  bool capped = false;
+  for (int q = 0; q < ns; ++q) {
+    pse_stats &o = c->sys_stats[q];
+    o.lanczos_iters = st[q].it;
+    o.lanczos_change = std::isfinite(st[q].err) ? st[q].err : 0.0;
+    capped = capped || (tol > 0 && !(st[q].err <= tol) && st[q].it == maxiter);
+  }
   return capped ? PSE_ERR_NOT_CONVERGED : PSE_OK;
 }
 
-// Unrestarted GMRES (x0 = 0) for M_ES x = b at the current configuration;
-// stops at |r|/|b| <= tol.  b and x hold the stresslet in slots 3..7.
-pse_status gmres(pse_ctx *c, const void *b, void *x, void *w, double tol, int maxiter, pse_stats *st,
-                 cudaStream_t s) {
-  int64_t n = 8 * c->p.N;
-  double *nr = c->d_coef + 256;
-  PSE_TRY(multidot(c, b, 1, n, b, nr, s));
-  double beta;
-  PSE_TRY(read_doubles(c, nr, 1, &beta, s));
-  beta = std::sqrt(beta);
-  if (beta == 0.0) {
-    PSE_CUDA_TRY(c, cudaMemsetAsync(x, 0, c->ts * n, s));
-    if (st) {
-      st->krylov_iters = 0;
-      st->krylov_relres = 0;
+// Unrestarted GMRES (x0 = 0) for M_ES x = b at the current configuration, per
+// suspension; stops at |r|/|b| <= tol.  b and x hold the stresslet in slots 3..7.
+pse_status gmres(pse_ctx *c, const void *b, void *x, void *w, double tol, int maxiter, cudaStream_t s) {
+  const int ns = c->nsys, M = maxiter;
+  struct St {
+    std::vector<double> H, cs, sn, g;
+    double beta = 0, rel = 0;
+    int it = 0;
+  };
+  std::vector<St> st(ns);
+  PSE_TRY(set_all_active(c, s));
+  PSE_TRY(multidot(c, b, 1, b, CO_NRM, s));
+  std::vector<double> nrm, fac(ns, 0.0);
+  PSE_TRY(read_coef(c, CO_NRM, 1, nrm, s));
+  for (int q = 0; q < ns; ++q) {
+    St &G = st[q];
+    G.beta = std::sqrt(std::max(nrm[q], 0.0));
+    c->h_active[q] = G.beta > 0.0;
+    fac[q] = G.beta > 0.0 ? 1.0 / G.beta : 0.0;
+    G.rel = G.beta > 0.0 ? 1.0 : 0.0;
+    if (G.beta > 0.0) {
+      G.H.assign((size_t)(M + 1) * M, 0.0);
+      G.cs.assign(M, 0.0);
+      G.sn.assign(M, 0.0);
+      G.g.assign(M + 1, 0.0);
+      G.g[0] = G.beta;
     }
-    return PSE_OK;
   }
-  PSE_TRY(vscale(c, row(c, 0), b, 1.0 / beta, n, s));
-  int M = maxiter;
-  std::vector<double> H((size_t)(M + 1) * M, 0.0), cs(M), sn(M), g(M + 1, 0.0);
-  g[0] = beta;
-  double rel = 1.0;
-  int it = 0;
+  PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
+  PSE_TRY(upload_active(c, s));
+  PSE_TRY(vscale(c, row(c, 0), b, 0.0, CO_FAC, s));
   for (int j = 0; j < M; ++j) {
-    it = j + 1;
+    bool any = false;
+    for (int v : c->h_active) any = any || v;
+    if (!any) break;
     PSE_TRY(mobility(c, row(c, j), w, M_SE, PSE_PART_ALL, s));
-    std::vector<double> h;
-    double n2;
+    std::vector<double> h, n2;
     PSE_TRY(cgs2(c, w, j, h, n2, s));
-    for (int i = 0; i <= j; ++i) H[(size_t)i * M + j] = h[i];
-    double hn = std::sqrt(std::max(n2, 0.0));
-    H[(size_t)(j + 1) * M + j] = hn;
-    for (int i = 0; i < j; ++i) {  // previous rotations
-      double a = H[(size_t)i * M + j], bb = H[(size_t)(i + 1) * M + j];
-      H[(size_t)i * M + j] = cs[i] * a + sn[i] * bb;
-      H[(size_t)(i + 1) * M + j] = -sn[i] * a + cs[i] * bb;
+    for (int q = 0; q < ns; ++q) {
+      if (!c->h_active[q]) continue;
+      St &G = st[q];
+      std::vector<double> &H = G.H;
+      G.it = j + 1;
+      for (int i = 0; i <= j; ++i) H[(size_t)i * M + j] = h[(size_t)q * (j + 1) + i];
+      double hn = std::sqrt(std::max(n2[q], 0.0));
+      H[(size_t)(j + 1) * M + j] = hn;
+      for (int i = 0; i < j; ++i) {  // previous rotations
+        double a = H[(size_t)i * M + j], bb = H[(size_t)(i + 1) * M + j];
+        H[(size_t)i * M + j] = G.cs[i] * a + G.sn[i] * bb;
+        H[(size_t)(i + 1) * M + j] = -G.sn[i] * a + G.cs[i] * bb;
+      }
+      double a = H[(size_t)j * M + j], bb = H[(size_t)(j + 1) * M + j];
+      double r = std::hypot(a, bb);
+      G.cs[j] = r == 0 ? 1.0 : a / r;
+      G.sn[j] = r == 0 ? 0.0 : bb / r;
+      H[(size_t)j * M + j] = r;
+      H[(size_t)(j + 1) * M + j] = 0.0;
+      G.g[j + 1] = -G.sn[j] * G.g[j];
+      G.g[j] = G.cs[j] * G.g[j];
+      G.rel = std::fabs(G.g[j + 1]) / G.beta;
+      if (G.rel <= tol || hn == 0.0 || j == M - 1) {
+        c->h_active[q] = 0;
+      } else {
+        fac[q] = 1.0 / hn;
+      }
     }
-    double a = H[(size_t)j * M + j], bb = H[(size_t)(j + 1) * M + j];
-    double r = std::hypot(a, bb);
-    cs[j] = r == 0 ? 1.0 : a / r;
-    sn[j] = r == 0 ? 0.0 : bb / r;
-    H[(size_t)j * M + j] = r;
-    H[(size_t)(j + 1) * M + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    rel = std::fabs(g[j + 1]) / beta;
-    if (rel <= tol || hn == 0.0) break;
-    PSE_TRY(vscale(c, row(c, j + 1), w, 1.0 / hn, n, s));
+    any = false;
+    for (int v : c->h_active) any = any || v;
+    if (!any) break;
+    PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
+    PSE_TRY(upload_active(c, s));
+    PSE_TRY(vscale(c, row(c, j + 1), w, 0.0, CO_FAC, s));
   }
-  std::vector<double> yv(it);
-  for (int i = it - 1; i >= 0; --i) {
-    double sum = g[i];
-    for (int k = i + 1; k < it; ++k) sum -= H[(size_t)i * M + k] * yv[k];
-    yv[i] = sum / H[(size_t)i * M + i];
+  int maxit = 0;
+  std::vector<double> coef((size_t)ns * 128, 0.0);
+  std::vector<int> nr(ns, 0);
+  for (int q = 0; q < ns; ++q) {
+    St &G = st[q];
+    nr[q] = G.it;
+    maxit = std::max(maxit, G.it);
+    for (int i = G.it - 1; i >= 0; --i) {
+      double sum = G.g[i];
+      for (int k = i + 1; k < G.it; ++k) sum -= G.H[(size_t)i * M + k] * coef[(size_t)q * 128 + k];
+      coef[(size_t)q * 128 + i] = sum / G.H[(size_t)i * M + i];
+    }
   }
-  PSE_TRY(write_doubles(c, c->d_coef + 384, yv.data(), it, s));
-  PSE_TRY(combine_set(c, x, c->d_basis, it, n, c->d_coef + 384, s));
-  if (st) {
-    st->krylov_iters = it;
-    st->krylov_relres = rel;
+  PSE_TRY(write_coef(c, CO_Y, 128, coef, s));
+  PSE_TRY(write_nrows(c, nr, s));
+  PSE_TRY(set_all_active(c, s));
+  PSE_TRY(combine_set(c, x, c->d_basis, c->d_nrows, std::max(maxit, 1), CO_Y, s));
+  bool capped = false;
+  for (int q = 0; q < ns; ++q) {
+    c->sys_stats[q].krylov_iters = st[q].it;
+    c->sys_stats[q].krylov_relres = st[q].rel;
+    capped = capped || (!(st[q].rel <= tol) && st[q].it == M);
   }
-  return rel <= tol ? PSE_OK : (it == M ? PSE_ERR_NOT_CONVERGED : PSE_OK);
+  return capped ? PSE_ERR_NOT_CONVERGED : PSE_OK;
 }
 
 // Unscaled Brownian slip [M_r^{1/2} w1 + M_w^{1/2} dW2] in sorted order into out.
 pse_status sample_sorted(pse_ctx *c, const void *d_w1, const void *d_w2, uint64_t seed, uint64_t counter, void *out,
-                         pse_stats *st, cudaStream_t s) {
+                         cudaStream_t s) {
   if (d_w1) PSE_TRY(gather_user8(c, d_w1, c->d_v[0], s));
   else PSE_TRY(philox_w1(c, seed, counter, c->d_v[0], s));
-  pse_status ls = lanczos(c, c->d_v[0], out, c->d_v[1], c->lanczos_tol, c->lanczos_max, st, s);
+  pse_status ls = lanczos(c, c->d_v[0], out, c->d_v[1], c->lanczos_tol, c->lanczos_max, s);
   if (ls != PSE_OK && ls != PSE_ERR_NOT_CONVERGED) return ls;
+  PSE_TRY(set_all_active(c, s));
   PSE_TRY(wave_noise(c, d_w2, seed, counter, out, s));
   return ls;
 }
@@ -288,12 +416,35 @@ pse_status check_inputs(pse_ctx *c, const void *p, int64_t n, bool dbl, cudaStre
   PSE_TRY(check_finite(c, p, n, dbl, c->d_flag, s));
   PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 2, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  c->h2d_pending = false;
   if (c->h_pinned_int[2]) {
     c->err = "non-finite input";
     return PSE_ERR_NONFINITE;
   }
   return PSE_OK;
 }
+
+// Aggregate of the per-suspension statistics (largest iteration counts and
+// residuals, total neighbour pairs).
+void gather_stats(pse_ctx *c, pse_stats *st) {
+  for (int q = 0; q < c->nsys; ++q) c->sys_stats[q].neighbor_pairs = c->npairs_sys.empty() ? 0 : c->npairs_sys[q];
+  if (!st) return;
+  pse_stats o{};
+  for (const pse_stats &q : c->sys_stats) {
+    o.lanczos_iters = std::max(o.lanczos_iters, q.lanczos_iters);
+    o.krylov_iters = std::max(o.krylov_iters, q.krylov_iters);
+    o.lanczos_change = std::max(o.lanczos_change, q.lanczos_change);
+    o.krylov_relres = std::max(o.krylov_relres, q.krylov_relres);
+  }
+  o.neighbor_pairs = c->npairs;
+  *st = o;
+}
+
+void reset_stats(pse_ctx *c) {
+  for (pse_stats &q : c->sys_stats) q = pse_stats{};
+}
+
+size_t w2_bytes(const pse_ctx *c) { return c->ts * 6 * (size_t)c->nk_tot; }
 
 pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const void *w1, const void *w2, uint64_t seed,
                      uint64_t stepno, void *S_out, pse_stats *st, cudaStream_t s) {
@@ -304,17 +455,18 @@ pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const v
     c->err = "dt must be > 0 and pos non-NULL";
     return PSE_ERR_INVALID_ARG;
   }
+  reset_stats(c);
+  PSE_TRY(set_all_active(c, s));
   void *dpos, *dFP, *dw1, *dw2;
   PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
   PSE_TRY(stage(c, 1, FP, c->ts * 3 * N, true, s, &dFP));
   PSE_TRY(stage(c, 2, w1, vb, true, s, &dw1));
-  PSE_TRY(stage(c, 3, w2, c->ts * 6 * (size_t)p.Ng * p.Ng * p.nkx, true, s, &dw2));
+  PSE_TRY(stage(c, 3, w2, w2_bytes(c), true, s, &dw2));
   PSE_TRY(check_inputs(c, dFP, 3 * N, c->prec == PSE_FP64, s));
-  pse_stats local{};
   // 1. Brownian slip at x_k (unconstrained), user order, scaled by sqrt(2kT/dt)
   PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_pos0, dpos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
   PSE_TRY(setup_config(c, c->d_pos0, s));
-  pse_status sst = sample_sorted(c, dw1, dw2, seed, stepno, c->d_v[2], &local, s);
+  pse_status sst = sample_sorted(c, dw1, dw2, seed, stepno, c->d_v[2], s);
   if (sst != PSE_OK && sst != PSE_ERR_NOT_CONVERGED) return sst;
   PSE_TRY(scatter_user8(c, c->d_v[2], c->d_B, std::sqrt(2.0 * p.kT / dt), s));
   // 2. x_{k+1/2} = x_k + dt/2 U^B
@@ -322,20 +474,20 @@ pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const v
   PSE_TRY(setup_config(c, c->d_posh, s));
   // 3. M_ES S = -E^B - M_EF F^P at x_{k+1/2}
   PSE_TRY(gather_user8(c, c->d_B, c->d_v[2], s));
-  PSE_TRY(vscale(c, c->d_v[2], c->d_v[2], -1.0, 8 * N, s));
+  PSE_TRY(vscale(c, c->d_v[2], c->d_v[2], -1.0, -1, s));
   if (dFP) {
     PSE_TRY(gather_in(c, dFP, nullptr, c->d_v[3], s));
     PSE_TRY(mobility(c, c->d_v[3], c->d_v[4], M_FULL, PSE_PART_ALL, s));
-    PSE_TRY(combine_sub(c, c->d_v[2], c->d_v[4], 1, 8 * N, c->d_coef + 510, s));  // coef[510] = 1
+    PSE_TRY(combine_sub(c, c->d_v[2], c->d_v[4], 1, CO_ONE, s));
   }
   PSE_TRY(vzero_slots(c, c->d_v[2], 0, 3, s));
-  pse_status gst = gmres(c, c->d_v[2], c->d_v[5], c->d_v[1], c->krylov_tol, c->krylov_max, &local, s);
+  pse_status gst = gmres(c, c->d_v[2], c->d_v[5], c->d_v[1], c->krylov_tol, c->krylov_max, s);
   if (gst != PSE_OK && gst != PSE_ERR_NOT_CONVERGED) return gst;
   PSE_TRY(vzero_slots(c, c->d_v[5], 0, 3, s));
   // 4. U = U^B + M_UF F^P + M_US S;  x_{k+1} = x_k + dt U
   if (dFP) {
     PSE_TRY(gather_in(c, dFP, nullptr, c->d_v[3], s));
-    PSE_TRY(combine_sub(c, c->d_v[3], c->d_v[5], 1, 8 * N, c->d_coef + 511, s));  // coef[511] = -1
+    PSE_TRY(combine_sub(c, c->d_v[3], c->d_v[5], 1, CO_MONE, s));
   } else {
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_v[3], c->d_v[5], vb, cudaMemcpyDeviceToDevice, s));
   }
@@ -349,33 +501,156 @@ pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const v
     PSE_TRY(unstage(c, S_out, dS, c->ts * 5 * N, s));
   }
   PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
-  local.neighbor_pairs = c->npairs;
-  if (st) *st = local;
+  c->h2d_pending = false;
+  gather_stats(c, st);
   return (sst == PSE_ERR_NOT_CONVERGED || gst == PSE_ERR_NOT_CONVERGED) ? PSE_ERR_NOT_CONVERGED : PSE_OK;
 }
 
-pse_status create_impl(pse_ctx *c, const pse_options &o) {
-  Params &p = c->p;
-  if (choose_params(p, o, c->err)) return PSE_ERR_INVALID_ARG;
-  if (p.N > 200000000LL) {
+// Device memory of a handle before it is created (the admission estimate of a
+// serving loop); mirrors the allocations of create_group.
+int64_t estimate_bytes(const pse_ctx *c) {
+  const size_t ts = c->ts;
+  int64_t Nt = 0, ntile = 0, ncell = 0, n3 = 0, nk = 0, nbr = 0, vblk = 0;
+  for (const Params &q : c->ps) {
+    Nt += q.N;
+    ntile += (int64_t)q.ntile[0] * q.ntile[1] * q.ntile[2];
+    ncell += (int64_t)q.nc * q.nc * q.nc;
+    n3 += (int64_t)q.Ng * q.Ng * q.Ng;
+    nk += (int64_t)q.Ng * q.Ng * q.nkx;
+    double mean = 4.0 / 3.0 * M_PI * q.rcut * q.rcut * q.rcut * q.N / q.V();
+    nbr += (int64_t)std::max(8.0, std::ceil((1.4 * mean + 24) / 8.0) * 8.0) * q.N;
+    vblk += ceil_div(8 * q.N, VEC_CHUNK);
+  }
+  int rows = std::max(c->lanczos_max, c->krylov_max) + 1;
+  int64_t b = 0;
+  b += (int64_t)ts * 8 * 2048 * 16;                 // table (upper bound)
+  b += Nt * (24 + 4 * 6 + 16 + 8 * (int64_t)ts);   // positions, keys, perm/inv, cells, records
+  b += nbr * 4 + (Nt + 1) * 4;
+  b += (ntile + ncell) * 16;
+  b += (int64_t)ts * 8 * n3 + 2 * (int64_t)ts * 8 * nk;   // grids and half spectra
+  b += (int64_t)ts * 8 * n3;                               // cuFFT work area (upper bound)
+  b += (int64_t)ts * 8 * Nt * (7 + rows);                 // vectors and Krylov basis
+  b += Nt * 48;                                            // FP64 positions (x_k, x_{k+1/2})
+  b += vblk * 64 + (int64_t)c->nsys * (COEF_STRIDE * 8 + 256);
+  return b;
+}
+
+pse_status choose_group(pse_ctx *c, int nsys, const int64_t *N, const double *L, const pse_options &o) {
+  c->nsys = nsys;
+  c->ps.assign(nsys, c->p);
+  int64_t Nt = 0;
+  for (int q = 0; q < nsys; ++q) {
+    Params &p = c->ps[q];
+    p.N = N[q];
+    p.L = L[q];
+    std::string e;
+    if (choose_params(p, o, e)) {
+      c->err = nsys > 1 ? "suspension " + std::to_string(q) + ": " + e : e;
+      return PSE_ERR_INVALID_ARG;
+    }
+    Nt += p.N;
+  }
+  if (Nt > 200000000LL) {
     c->err = "N too large for 32-bit particle indices";
     return PSE_ERR_INVALID_ARG;
   }
+  Params shared = c->ps[0];
+  shared.N = Nt;
+  c->p = shared;
   c->lanczos_max = o.lanczos_maxiter > 0 ? o.lanczos_maxiter : 100;
   c->krylov_max = o.krylov_maxiter > 0 ? o.krylov_maxiter : 50;
   c->lanczos_max = std::min(c->lanczos_max, 120);
   c->krylov_max = std::min(c->krylov_max, 120);
-  c->lanczos_tol = o.lanczos_tol < 0 ? p.tol : o.lanczos_tol;
-  c->krylov_tol = o.krylov_tol < 0 ? p.tol : o.krylov_tol;
-  PSE_CUDA_TRY(c, cudaGetDevice(&c->device));
+  c->lanczos_tol = o.lanczos_tol < 0 ? shared.tol : o.lanczos_tol;
+  c->krylov_tol = o.krylov_tol < 0 ? shared.tol : o.krylov_tol;
+  return PSE_OK;
+}
+
+pse_status create_group(pse_ctx *c, const pse_options &o) {
+  const int ns = c->nsys;
   const size_t ts = c->ts;
-  const int64_t N = p.N;
-  c->ntiles = (int64_t)p.ntile[0] * p.ntile[1] * p.ntile[2];
-  c->ncells = (int64_t)p.nc * p.nc * p.nc;
-  // real-space table
+  const int64_t N = c->p.N;
+  PSE_CUDA_TRY(c, cudaGetDevice(&c->device));
+  PSE_CUDA_TRY(c, cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+  // per-suspension layout: particles, tiles, cells, half spectra, vector blocks
+  c->hs.assign(ns, SysDev{});
+  std::vector<int64_t> p0(ns + 1, 0), k0(ns + 1, 0);
+  std::vector<int> tile0(ns + 1, 0), blk0(ns + 1, 0);
+  int64_t cell_tot = 0;
+  for (int q = 0; q < ns; ++q) {
+    const Params &p = c->ps[q];
+    SysDev &d = c->hs[q];
+    d.p0 = p0[q];
+    d.N = (int)p.N;
+    d.Ng = p.Ng;
+    d.nkx = p.nkx;
+    d.nc = p.nc;
+    for (int k = 0; k < 3; ++k) {
+      d.T[k] = p.tile[k];
+      d.nt[k] = p.ntile[k];
+    }
+    d.L = p.L;
+    d.h = p.h;
+    d.cs = p.cs;
+    d.Lf = (float)p.L;
+    d.csf = (float)p.cs;
+    d.alpha = 2.0 * p.xi * p.xi / p.eta_g;
+    d.pref = std::pow(2.0 * p.xi * p.xi / (M_PI * p.eta_g), 1.5);
+    d.kfac = 2.0 * M_PI / p.L;
+    d.eta_g = p.eta_g;
+    d.c_apply = p.sigma() * p.sigma() / (p.V() * p.eta);
+    d.c_noise = p.sigma() / std::sqrt(p.eta * p.V());
+    double mean = 4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * p.N / p.V();
+    d.slots = (int)std::min<double>(std::max<int64_t>(p.N, 8), std::ceil((1.4 * mean + 24) / 8.0) * 8.0);
+    d.slots = std::max(d.slots, 8);
+    d.tile0 = tile0[q];
+    d.cell0 = (int)cell_tot;
+    d.k0 = k0[q];
+    d.blk0 = blk0[q];
+    p0[q + 1] = p0[q] + p.N;
+    tile0[q + 1] = tile0[q] + p.ntile[0] * p.ntile[1] * p.ntile[2];
+    cell_tot += (int64_t)p.nc * p.nc * p.nc;
+    k0[q + 1] = k0[q] + (int64_t)p.Ng * p.Ng * p.nkx;
+    blk0[q + 1] = blk0[q] + (int)ceil_div(8 * p.N, VEC_CHUNK);
+  }
+  if (cell_tot > 1500000000LL || (int64_t)tile0[ns] > 1500000000LL) {
+    c->err = "too many cells or tiles";
+    return PSE_ERR_INVALID_ARG;
+  }
+  c->ntiles = tile0[ns];
+  c->ncells = cell_tot;
+  c->nk_tot = k0[ns];
+  c->nvblk = blk0[ns];
+  // FFT groups: suspensions with equal grids share one strided batch, [component][suspension][Ng^3]
+  std::map<int, std::vector<int>> by_ng;
+  for (int q = 0; q < ns; ++q) by_ng[c->ps[q].Ng].push_back(q);
+  int64_t g0 = 0, cg0 = 0;
+  c->groups.clear();
+  for (auto &kv : by_ng) {
+    FftGroup g;
+    g.Ng = kv.first;
+    g.nsys = (int)kv.second.size();
+    g.members = kv.second;
+    g.grid0 = g0;
+    g.cgrid0 = cg0;
+    const int64_t n3 = (int64_t)g.Ng * g.Ng * g.Ng, nk = (int64_t)g.Ng * g.Ng * (g.Ng / 2 + 1);
+    for (int j = 0; j < g.nsys; ++j) {
+      SysDev &d = c->hs[kv.second[j]];
+      d.grid0 = g0 + j * n3;
+      d.gstride = g.nsys * n3;
+      d.cgrid0 = cg0 + j * nk;
+      d.cstride = g.nsys * nk;
+    }
+    g0 += 8 * g.nsys * n3;
+    cg0 += 8 * g.nsys * nk;
+    c->groups.push_back(g);
+  }
+  c->grid_elems = g0;
+  c->cgrid_elems = cg0;
+  // real-space table (shared: it depends on a, eta, xi and r_cut only)
   RealTable t;
   int ppa = o.table_points > 0 ? o.table_points : (c->prec == PSE_MIXED ? 1024 : 2048);
-  build_real_table(p, ppa, t);
+  build_real_table(c->p, ppa, t);
   c->table_len = t.len;
   c->table_k2 = t.k2;
   c->table_dr = t.dr;
@@ -387,6 +662,14 @@ pse_status create_impl(pse_ctx *c, const pse_options &o) {
     if (!q) fail = true;
     return q;
   };
+  c->d_sys = (SysDev *)A(sizeof(SysDev) * ns);
+  c->d_p0 = (int64_t *)A(sizeof(int64_t) * (ns + 1));
+  c->d_k0 = (int64_t *)A(sizeof(int64_t) * (ns + 1));
+  c->d_tile0 = (int *)A(sizeof(int) * (ns + 1));
+  c->d_blk0 = (int *)A(sizeof(int) * (ns + 1));
+  c->d_active = (int *)A(sizeof(int) * ns);
+  c->d_nrows = (int *)A(sizeof(int) * ns);
+  c->d_queue = (int *)A(sizeof(int) * 64);
   c->d_table = A(ts * 8 * (size_t)t.len);
   c->d_posw = (double *)A(sizeof(double) * 3 * N);
   c->d_tile_key = (int *)A(sizeof(int) * N);
@@ -399,40 +682,46 @@ pse_status create_impl(pse_ctx *c, const pse_options &o) {
   c->d_cell_cur = (int *)A(sizeof(int) * (c->ncells + 1));
   c->d_cell_list = (int *)A(sizeof(int) * N);
   c->d_nbr_start = (int *)A(sizeof(int) * (N + 1));
-  double dens = N / p.V();
-  double mean_nbr = 4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * dens;
-  c->nbr_slots = (int)std::min<double>(N, (std::ceil((1.4 * mean_nbr + 24) / 8.0) * 8.0));
-  c->nbr_slots = std::max(c->nbr_slots, 8);
-  c->nbr_cap = (int64_t)c->nbr_slots * N;
+  c->nbr_cap = layout_neighbours(c);
+  if ((double)c->nbr_cap > 2.0e9) {
+    c->err = "neighbour list exceeds 2^31 entries";
+    return PSE_ERR_INVALID_ARG;
+  }
   c->d_nbr = (int *)A(sizeof(int) * (size_t)c->nbr_cap);
-  c->d_nbr_tot = (unsigned long long *)A(2 * sizeof(unsigned long long));
+  c->d_nbr_tot = (unsigned long long *)A(2 * sizeof(unsigned long long) * ns);
   c->d_sp_i0 = A(sizeof(int4) * N);
   c->d_sp_d0 = A(4 * ts * N);
   c->d_rs = A(4 * ts * N);
   int64_t big = std::max<int64_t>(std::max<int64_t>(c->ntiles, c->ncells), N) + 1;
   c->d_scan_tmp = (int *)A(sizeof(int) * (size_t)scan_tmp_ints(big));
   c->d_flag = (int *)A(sizeof(int) * 4);
-  size_t n3 = (size_t)p.Ng * p.Ng * p.Ng, nk = (size_t)p.Ng * p.Ng * p.nkx;
-  if (8 * n3 > (size_t)2147483647) {
-    c->err = "FFT grid too large";
-    return PSE_ERR_INVALID_ARG;
-  }
-  c->d_grid = A(ts * 8 * n3);
-  c->d_cgrid = A(2 * ts * 8 * nk);
+  c->d_grid = A(ts * (size_t)c->grid_elems);
+  c->d_cgrid = A(2 * ts * (size_t)c->cgrid_elems);
   for (int i = 0; i < 6; ++i) c->d_v[i] = A(ts * 8 * N);
   c->d_B = A(ts * 8 * N);
   c->d_basis = A(ts * 8 * N * (size_t)(std::max(c->lanczos_max, c->krylov_max) + 1));
-  c->dots_blocks = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(8 * N, 256), 1), 1024);
-  c->d_dots = (double *)A(sizeof(double) * 8 * c->dots_blocks);
-  c->d_coef = (double *)A(sizeof(double) * 512);
+  c->d_dots = (double *)A(sizeof(double) * 8 * (size_t)c->nvblk);
+  c->d_coef = (double *)A(sizeof(double) * COEF_STRIDE * (size_t)ns);
   c->d_pos0 = (double *)A(sizeof(double) * 3 * N);
   c->d_posh = (double *)A(sizeof(double) * 3 * N);
   if (fail) {
     c->err = "device allocation failed (" + std::to_string(c->dev_bytes) + " bytes so far)";
     return PSE_ERR_OOM;
   }
-  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_dots, sizeof(double) * 512));
-  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_pinned_int, sizeof(int) * 8));
+  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_dots, sizeof(double) * COEF_STRIDE * (size_t)ns));
+  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_wbuf, sizeof(double) * COEF_STRIDE * (size_t)ns));
+  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_pinned_int, sizeof(int) * (8 + 2 * (size_t)ns)));
+  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_nbr_tot, 2 * sizeof(unsigned long long) * ns));
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_sys, c->hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice));
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_p0, p0.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_k0, k0.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_tile0, tile0.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_blk0, blk0.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice));
+  c->h_active.assign(ns, 1);
+  std::vector<int> ones(ns, 1);
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_active, ones.data(), sizeof(int) * ns, cudaMemcpyHostToDevice));
+  PSE_CUDA_TRY(c, cudaMemset(c->d_queue, 0, sizeof(int) * 64));
+  c->sys_stats.assign(ns, pse_stats{});
   // table to device in the working precision
   if (c->prec == PSE_MIXED) {
     std::vector<float> f(t.v.begin(), t.v.end());
@@ -440,36 +729,47 @@ pse_status create_impl(pse_ctx *c, const pse_options &o) {
   } else {
     PSE_CUDA_TRY(c, cudaMemcpy(c->d_table, t.v.data(), sizeof(double) * t.v.size(), cudaMemcpyHostToDevice));
   }
-  double consts[2] = {1.0, -1.0};
-  PSE_CUDA_TRY(c, cudaMemcpy(c->d_coef + 510, consts, sizeof(consts), cudaMemcpyHostToDevice));
-  // cuFFT plans (shared work area)
-  int n[3] = {p.Ng, p.Ng, p.Ng};
+  {
+    std::vector<double> consts((size_t)COEF_STRIDE * ns, 0.0);
+    for (int q = 0; q < ns; ++q) {
+      consts[(size_t)q * COEF_STRIDE + CO_ONE] = 1.0;
+      consts[(size_t)q * COEF_STRIDE + CO_MONE] = -1.0;
+    }
+    PSE_CUDA_TRY(c, cudaMemcpy(c->d_coef, consts.data(), sizeof(double) * consts.size(), cudaMemcpyHostToDevice));
+  }
+  // cuFFT plans per group (shared work area)
   size_t work = 0;
-  const int batches_r2c[2] = {5, 8}, batches_c2r[3] = {3, 5, 8};
+  const int comps_r2c[2] = {5, 8}, comps_c2r[3] = {3, 5, 8};
   cufftType tr = c->prec == PSE_MIXED ? CUFFT_R2C : CUFFT_D2Z, tc = c->prec == PSE_MIXED ? CUFFT_C2R : CUFFT_Z2D;
-  for (int b : batches_r2c) {
-    size_t ws = 0;
-    PSE_CUFFT_TRY(c, cufftCreate(&c->plan_r2c[b]));
-    PSE_CUFFT_TRY(c, cufftSetAutoAllocation(c->plan_r2c[b], 0));
-    PSE_CUFFT_TRY(c, cufftMakePlanMany(c->plan_r2c[b], 3, n, nullptr, 1, (int)n3, nullptr, 1, (int)nk, tr, b, &ws));
-    work = std::max(work, ws);
+  for (FftGroup &g : c->groups) {
+    int n[3] = {g.Ng, g.Ng, g.Ng};
+    const int n3 = g.Ng * g.Ng * g.Ng, nk = g.Ng * g.Ng * (g.Ng / 2 + 1);
+    for (int b : comps_r2c) {
+      size_t ws = 0;
+      PSE_CUFFT_TRY(c, cufftCreate(&g.r2c[b]));
+      g.ok[0][b] = true;
+      PSE_CUFFT_TRY(c, cufftSetAutoAllocation(g.r2c[b], 0));
+      PSE_CUFFT_TRY(c, cufftMakePlanMany(g.r2c[b], 3, n, nullptr, 1, n3, nullptr, 1, nk, tr, b * g.nsys, &ws));
+      work = std::max(work, ws);
+    }
+    for (int b : comps_c2r) {
+      size_t ws = 0;
+      PSE_CUFFT_TRY(c, cufftCreate(&g.c2r[b]));
+      g.ok[1][b] = true;
+      PSE_CUFFT_TRY(c, cufftSetAutoAllocation(g.c2r[b], 0));
+      PSE_CUFFT_TRY(c, cufftMakePlanMany(g.c2r[b], 3, n, nullptr, 1, nk, nullptr, 1, n3, tc, b * g.nsys, &ws));
+      work = std::max(work, ws);
+    }
   }
-  for (int b : batches_c2r) {
-    size_t ws = 0;
-    PSE_CUFFT_TRY(c, cufftCreate(&c->plan_c2r[b]));
-    PSE_CUFFT_TRY(c, cufftSetAutoAllocation(c->plan_c2r[b], 0));
-    PSE_CUFFT_TRY(c, cufftMakePlanMany(c->plan_c2r[b], 3, n, nullptr, 1, (int)nk, nullptr, 1, (int)n3, tc, b, &ws));
-    work = std::max(work, ws);
-  }
-  c->d_fft_work = A(work);
+  c->d_fft_work = A(std::max<size_t>(work, 16));
   if (fail) {
     c->err = "cannot allocate cuFFT work area";
     return PSE_ERR_OOM;
   }
-  for (int b : batches_r2c) PSE_CUFFT_TRY(c, cufftSetWorkArea(c->plan_r2c[b], c->d_fft_work));
-  for (int b : batches_c2r) PSE_CUFFT_TRY(c, cufftSetWorkArea(c->plan_c2r[b], c->d_fft_work));
-  for (int b : batches_r2c) c->plan_ok[b] = true;
-  for (int b : batches_c2r) c->plan_ok[b] = true;
+  for (FftGroup &g : c->groups) {
+    for (int b : comps_r2c) PSE_CUFFT_TRY(c, cufftSetWorkArea(g.r2c[b], c->d_fft_work));
+    for (int b : comps_c2r) PSE_CUFFT_TRY(c, cufftSetWorkArea(g.c2r[b], c->d_fft_work));
+  }
   PSE_CUDA_TRY(c, cudaDeviceSynchronize());
   return PSE_OK;
 }
@@ -490,56 +790,56 @@ void destroy_impl(pse_ctx *c) {
   resolve_profile(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
-  for (int b = 0; b < 9; ++b) {
-    if (c->plan_r2c[b]) cufftDestroy(c->plan_r2c[b]);
-    if (c->plan_c2r[b]) cufftDestroy(c->plan_c2r[b]);
-  }
+  for (FftGroup &g : c->groups)
+    for (int b = 0; b < 9; ++b) {
+      if (g.ok[0][b]) cufftDestroy(g.r2c[b]);
+      if (g.ok[1][b]) cufftDestroy(g.c2r[b]);
+    }
+  c->groups.clear();
   for (void *q : c->allocs) cudaFree(q);
   if (c->h_dots) cudaFreeHost(c->h_dots);
+  if (c->h_wbuf) cudaFreeHost(c->h_wbuf);
   if (c->h_pinned_int) cudaFreeHost(c->h_pinned_int);
+  if (c->h_nbr_tot) cudaFreeHost(c->h_nbr_tot);
   c->allocs.clear();
 }
 
-}  // namespace
-
-extern "C" {
-
-void pse_default_options(pse_options *o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->rule = PSE_RULE_STRICT;
-  o->lanczos_tol = -1.0;
-  o->krylov_tol = -1.0;
-  o->lanczos_maxiter = 100;
-  o->krylov_maxiter = 50;
+pse_ctx *new_ctx(pse_precision prec, const pse_options &o, double a, double eta, double kT, double xi, double tol) {
+  pse_ctx *c = new (std::nothrow) pse_ctx();
+  if (!c) return nullptr;
+  c->prec = prec;
+  c->ts = prec == PSE_MIXED ? 4 : 8;
+  c->opt = o;
+  Params &p = c->p;
+  std::memset(&p, 0, sizeof(p));
+  p.ts = (int)c->ts;
+  p.a = a;
+  p.eta = eta;
+  p.kT = kT;
+  p.xi = xi;
+  p.tol = tol;
+  return c;
 }
 
-pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT, double xi, double tol,
-                      pse_precision prec, const pse_options *opt) {
+pse_status create_common(pse_handle *out, int32_t nsys, const int64_t *N, const double *L, double a, double eta,
+                         double kT, double xi, double tol, pse_precision prec, const pse_options *opt) {
   if (!out) return PSE_ERR_INVALID_ARG;
   *out = nullptr;
   if (prec != PSE_MIXED && prec != PSE_FP64) {
     g_create_err = "unknown precision";
     return PSE_ERR_INVALID_ARG;
   }
+  if (nsys < 1 || nsys > 65536 || !N || !L) {
+    g_create_err = "need 1 <= nsys <= 65536 and N, L arrays";
+    return PSE_ERR_INVALID_ARG;
+  }
   pse_options o;
   pse_default_options(&o);
   if (opt) o = *opt;
-  pse_ctx *c = new (std::nothrow) pse_ctx();
+  pse_ctx *c = new_ctx(prec, o, a, eta, kT, xi, tol);
   if (!c) return PSE_ERR_OOM;
-  c->prec = prec;
-  c->ts = prec == PSE_MIXED ? 4 : 8;
-  c->opt = o;
-  Params &p = c->p;
-  p.ts = (int)c->ts;
-  p.N = N;
-  p.L = L;
-  p.a = a;
-  p.eta = eta;
-  p.kT = kT;
-  p.xi = xi;
-  p.tol = tol;
-  pse_status st = create_impl(c, o);
+  pse_status st = choose_group(c, nsys, N, L, o);
+  if (st == PSE_OK) st = create_group(c, o);
   if (st != PSE_OK) {
     g_create_err = c->err;
     destroy_impl(c);
@@ -550,17 +850,7 @@ pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta
   return PSE_OK;
 }
 
-pse_status pse_destroy(pse_handle h) {
-  if (!h) return PSE_ERR_INVALID_ARG;
-  cudaDeviceSynchronize();
-  destroy_impl(h);
-  delete h;
-  return PSE_OK;
-}
-
-pse_status pse_get_info(pse_handle h, pse_info *o) {
-  if (!h || !o) return PSE_ERR_INVALID_ARG;
-  const Params &p = h->p;
+void fill_info(const pse_ctx *h, const Params &p, int64_t bytes, pse_info *o) {
   std::memset(o, 0, sizeof(*o));
   o->N = p.N;
   o->L = p.L;
@@ -582,7 +872,74 @@ pse_status pse_get_info(pse_handle h, pse_info *o) {
   for (int d = 0; d < 3; ++d) o->tile[d] = p.tile[d];
   o->table_len = h->table_len;
   o->table_dr = h->table_dr;
-  o->device_bytes = h->dev_bytes;
+  o->device_bytes = bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pse_default_options(pse_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rule = PSE_RULE_STRICT;
+  o->lanczos_tol = -1.0;
+  o->krylov_tol = -1.0;
+  o->lanczos_maxiter = 100;
+  o->krylov_maxiter = 50;
+}
+
+pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT, double xi, double tol,
+                      pse_precision prec, const pse_options *opt) {
+  return create_common(out, 1, &N, &L, a, eta, kT, xi, tol, prec, opt);
+}
+
+pse_status pse_create_batch(pse_handle *out, int32_t nsys, const int64_t *N, const double *L, double a, double eta,
+                            double kT, double xi, double tol, pse_precision prec, const pse_options *opt) {
+  return create_common(out, nsys, N, L, a, eta, kT, xi, tol, prec, opt);
+}
+
+pse_status pse_estimate_bytes(int32_t nsys, const int64_t *N, const double *L, double a, double eta, double kT,
+                              double xi, double tol, pse_precision prec, const pse_options *opt, int64_t *bytes) {
+  if (!bytes || nsys < 1 || !N || !L || (prec != PSE_MIXED && prec != PSE_FP64)) return PSE_ERR_INVALID_ARG;
+  pse_options o;
+  pse_default_options(&o);
+  if (opt) o = *opt;
+  pse_ctx *c = new_ctx(prec, o, a, eta, kT, xi, tol);
+  if (!c) return PSE_ERR_OOM;
+  pse_status st = choose_group(c, nsys, N, L, o);
+  if (st == PSE_OK) *bytes = estimate_bytes(c);
+  else g_create_err = c->err;
+  delete c;
+  return st;
+}
+
+pse_status pse_destroy(pse_handle h) {
+  if (!h) return PSE_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  destroy_impl(h);
+  delete h;
+  return PSE_OK;
+}
+
+pse_status pse_get_info(pse_handle h, pse_info *o) {
+  if (!h || !o) return PSE_ERR_INVALID_ARG;
+  fill_info(h, h->ps.empty() ? h->p : h->ps[0], h->dev_bytes, o);
+  o->N = h->p.N;
+  return PSE_OK;
+}
+
+int32_t pse_num_systems(pse_handle h) { return h ? h->nsys : 0; }
+
+pse_status pse_get_system_info(pse_handle h, int32_t s, pse_info *o) {
+  if (!h || !o || s < 0 || s >= h->nsys) return PSE_ERR_INVALID_ARG;
+  fill_info(h, h->ps[s], h->dev_bytes, o);
+  return PSE_OK;
+}
+
+pse_status pse_get_system_stats(pse_handle h, int32_t s, pse_stats *o) {
+  if (!h || !o || s < 0 || s >= h->nsys) return PSE_ERR_INVALID_ARG;
+  *o = h->sys_stats[s];
   return PSE_OK;
 }
 
@@ -596,6 +953,7 @@ pse_status pse_mobility_apply_parts(pse_handle h, const double *pos, const void 
   cudaStream_t s = (cudaStream_t)stream;
   pse_ctx *c = h;
   int64_t N = c->p.N;
+  PSE_TRY(set_all_active(c, s));
   void *dpos, *dF, *dS, *dU, *dE;
   PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
   PSE_TRY(stage(c, 1, F, c->ts * 3 * N, true, s, &dF));
@@ -628,23 +986,24 @@ pse_status pse_brownian_sample(pse_handle h, const double *pos, double dt, uint6
   pse_ctx *c = h;
   const Params &p = c->p;
   int64_t N = p.N;
+  reset_stats(c);
+  PSE_TRY(set_all_active(c, s));
   void *dpos, *dw1, *dw2, *dU, *dE;
   PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
   PSE_TRY(stage(c, 1, w1, c->ts * 8 * N, true, s, &dw1));
-  PSE_TRY(stage(c, 2, w2, c->ts * 6 * (size_t)p.Ng * p.Ng * p.nkx, true, s, &dw2));
+  PSE_TRY(stage(c, 2, w2, w2_bytes(c), true, s, &dw2));
   PSE_TRY(stage(c, 3, UB, c->ts * 3 * N, false, s, &dU));
   PSE_TRY(stage(c, 4, EB, c->ts * 5 * N, false, s, &dE));
   PSE_TRY(check_inputs(c, dw1, 8 * N, c->prec == PSE_FP64, s));
   PSE_TRY(setup_config(c, (const double *)dpos, s));
-  pse_stats local{};
-  pse_status st = sample_sorted(c, dw1, dw2, seed, counter, c->d_v[2], &local, s);
+  pse_status st = sample_sorted(c, dw1, dw2, seed, counter, c->d_v[2], s);
   if (st != PSE_OK && st != PSE_ERR_NOT_CONVERGED) return st;
   PSE_TRY(scatter_out(c, c->d_v[2], dU, dE, std::sqrt(2.0 * p.kT / dt), s));
   PSE_TRY(unstage(c, UB, dU, c->ts * 3 * N, s));
   PSE_TRY(unstage(c, EB, dE, c->ts * 5 * N, s));
   PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
-  local.neighbor_pairs = c->npairs;
-  if (stats) *stats = local;
+  c->h2d_pending = false;
+  gather_stats(c, stats);
   return st;
 }
 

@@ -12,6 +12,22 @@ template <> struct V4<double> { using t = double4_32a; };
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Persistent work loop: the CTA takes work items from the counter *queue (which
+// starts at zero) until `total` have been handed out; every thread of the CTA
+// calls f(item) for the same items, so f may use __syncthreads.
+template <class F>
+__device__ __forceinline__ void for_each_item(int *queue, int total, F &&f) {
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= total) return;
+    f(item);
+  }
+}
+
 // wrap an integer index into [0, n)
 __device__ __forceinline__ int wrapi(int i, int n) {
   i %= n;

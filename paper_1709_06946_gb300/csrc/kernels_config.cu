@@ -64,13 +64,6 @@ __global__ void k_scan_add(int *out, int64_t n, const int *offs) {
   }
 }
 
-struct BinArgs {
-  int N;
-  double L, h, cs;
-  int Ng, P, nc;
-  int T[3], nt[3];
-};
-
 __device__ __forceinline__ double wrap_coord(double x, double L) {
   x = fmod(x, L);
   if (x < 0) x += L;
@@ -83,46 +76,52 @@ __device__ __forceinline__ int support_start(double x, double h, int P) {
   return (P & 1) ? (int)rint(q) - (P - 1) / 2 : (int)floor(q) - P / 2 + 1;
 }
 
-__global__ void k_bin(BinArgs b, const double *pos, double *posw, int *tile_key, int *tile_cnt, int *bad) {
-  int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= b.N) return;
+// Wraps particle u (user order) of its suspension into [0, L) and counts it in
+// the spreading tile that holds the first grid index of its support.
+__global__ void k_bin(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
+                      int P, const double *pos, double *posw, int *tile_key, int *tile_cnt, int *bad) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= Ntot) return;
+  const SysDev &b = sys[find_sys(p0, nsys, u)];
   int iw[3];
   for (int d = 0; d < 3; ++d) {
-    double x = pos[3 * (int64_t)u + d];
+    double x = pos[3 * u + d];
     if (!isfinite(x)) {
       atomicOr(bad, 1);
       x = 0.0;
     }
     x = wrap_coord(x, b.L);
-    posw[3 * (int64_t)u + d] = x;
-    iw[d] = wrapi(support_start(x, b.h, b.P), b.Ng);
+    posw[3 * u + d] = x;
+    iw[d] = wrapi(support_start(x, b.h, P), b.Ng);
   }
-  int tk = ((iw[2] / b.T[2]) * b.nt[1] + iw[1] / b.T[1]) * b.nt[0] + iw[0] / b.T[0];
+  int tk = b.tile0 + ((iw[2] / b.T[2]) * b.nt[1] + iw[1] / b.T[1]) * b.nt[0] + iw[0] / b.T[0];
   tile_key[u] = tk;
   atomicAdd(&tile_cnt[tk], 1);
 }
 
-__global__ void k_scatter(int N, const int *key, const int *start, int *cur, int *perm, int *inv) {
-  int u = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_scatter(int64_t N, const int *key, const int *start, int *cur, int *perm, int *inv) {
+  int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= N) return;
   int k = key[u];
   int i = start[k] + atomicAdd(&cur[k], 1);
-  perm[i] = u;
+  perm[i] = (int)u;
   inv[u] = i;
 }
 
 template <typename T>
-__global__ void k_derive(BinArgs b, const int *perm, const double *posw, int4 *sp_i0,
-                         typename V4<T>::t *sp_d0, void *rs, int *cell_key, int *cell_cnt) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= b.N) return;
+__global__ void k_derive(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
+                         int P, const int *perm, const double *posw, int4 *sp_i0, typename V4<T>::t *sp_d0,
+                         void *rs, int *cell_key, int *cell_cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  const SysDev &b = sys[find_sys(p0, nsys, i)];
   int u = perm[i];
   double x[3];
   int iw[3], c[3];
   T d0[3];
   for (int d = 0; d < 3; ++d) {
     x[d] = posw[3 * (int64_t)u + d];
-    int i0 = support_start(x[d], b.h, b.P);
+    int i0 = support_start(x[d], b.h, P);
     iw[d] = wrapi(i0, b.Ng);
     d0[d] = (T)(i0 * b.h - x[d]);
     c[d] = min((int)(x[d] / b.cs), b.nc - 1);
@@ -141,23 +140,17 @@ __global__ void k_derive(BinArgs b, const int *perm, const double *posw, int4 *s
   } else {
     ((double4_32a *)rs)[i] = make_double4_32a(x[0], x[1], x[2], 0.0);
   }
-  int ck = (c[2] * b.nc + c[1]) * b.nc + c[0];
+  int ck = b.cell0 + (c[2] * b.nc + c[1]) * b.nc + c[0];
   cell_key[i] = ck;
   atomicAdd(&cell_cnt[ck], 1);
 }
 
-__global__ void k_cell_scatter(int N, const int *cell_key, const int *start, int *cur, int *list) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_cell_scatter(int64_t N, const int *cell_key, const int *start, int *cur, int *list) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int ck = cell_key[i];
-  list[start[ck] + atomicAdd(&cur[ck], 1)] = i;
+  list[start[ck] + atomicAdd(&cur[ck], 1)] = (int)i;
 }
-
-struct NbrArgs {
-  int N, nc;
-  float csf, Lf, rc2f;
-  double L, rc2;
-};
 
 __device__ __forceinline__ void unpack_cell(float w, int c[3]) {
   int p = __float_as_int(w);
@@ -166,8 +159,8 @@ __device__ __forceinline__ void unpack_cell(float w, int c[3]) {
   c[2] = (p >> 20) & 1023;
 }
 
-// Separation x_i - x_j (minimum image) for the two position representations.
-__device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const float4 &pj, const NbrArgs &a) {
+// Separation x_i - x_j (minimum image) from cell-relative FP32 offsets.
+__device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const float4 &pj, const SysDev &a) {
   int cj[3];
   unpack_cell(pj.w, cj);
   int dc[3];
@@ -188,13 +181,17 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
 }
 
 // Neighbour list in one pass: particle i writes the indices of its neighbours
-// (r < r_cut, minimum image) into its own slots and records their number; the
-// largest count and the total are accumulated for the host's capacity check.
+// (r < r_cut, minimum image within its own suspension) into its own slots and
+// records their number; per suspension the total and the largest count are
+// accumulated for the host's capacity check.
 template <typename T>
-__global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const int *cell_list, int *cnt, int *list,
-                      int slots, unsigned long long *tot) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.N) return;
+__global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
+                      float rc2f, double rc2, const void *rs, const int *cell_start, const int *cell_list, int *cnt,
+                      int *list, unsigned long long *tot) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  const int si = find_sys(p0, nsys, i);
+  const SysDev &a = sys[si];
   int ci[3];
   float4 pf;
   double4_32a pd;
@@ -203,20 +200,21 @@ __global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const in
     unpack_cell(pf.w, ci);
   } else {
     pd = ((const double4_32a *)rs)[i];
-    ci[0] = min((int)(pd.x / (a.L / a.nc)), a.nc - 1);
-    ci[1] = min((int)(pd.y / (a.L / a.nc)), a.nc - 1);
-    ci[2] = min((int)(pd.z / (a.L / a.nc)), a.nc - 1);
+    ci[0] = min((int)(pd.x / a.cs), a.nc - 1);
+    ci[1] = min((int)(pd.y / a.cs), a.nc - 1);
+    ci[2] = min((int)(pd.z / a.cs), a.nc - 1);
   }
   // 5-cell stencil per dimension, or every cell once when there are fewer than 5
   int lo = a.nc >= 5 ? -2 : 0, hi = a.nc >= 5 ? 2 : a.nc - 1;
   int n = 0;
-  int *mine = list + (size_t)i * slots;
+  const int slots = a.slots;
+  int *mine = list + a.nbr0 + (i - a.p0) * slots;
   for (int dz = lo; dz <= hi; ++dz)
     for (int dy = lo; dy <= hi; ++dy)
       for (int dx = lo; dx <= hi; ++dx) {
         int cz = a.nc >= 5 ? wrapi(ci[2] + dz, a.nc) : dz, cy = a.nc >= 5 ? wrapi(ci[1] + dy, a.nc) : dy;
         int cx = a.nc >= 5 ? wrapi(ci[0] + dx, a.nc) : dx;
-        int c = (cz * a.nc + cy) * a.nc + cx;
+        int c = a.cell0 + (cz * a.nc + cy) * a.nc + cx;
         int e = cell_start[c + 1];
         for (int k = cell_start[c]; k < e; ++k) {
           int j = cell_list[k];
@@ -224,14 +222,14 @@ __global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const in
           bool in;
           if (sizeof(T) == 4) {
             float3 r = sep(pf, ci, ((const float4 *)rs)[j], a);
-            in = r.x * r.x + r.y * r.y + r.z * r.z < a.rc2f;
+            in = r.x * r.x + r.y * r.y + r.z * r.z < rc2f;
           } else {
             double4_32a q = ((const double4_32a *)rs)[j];
             double rx = pd.x - q.x, ry = pd.y - q.y, rz = pd.z - q.z;
             rx -= a.L * rint(rx / a.L);
             ry -= a.L * rint(ry / a.L);
             rz -= a.L * rint(rz / a.L);
-            in = rx * rx + ry * ry + rz * rz < a.rc2;
+            in = rx * rx + ry * ry + rz * rz < rc2;
           }
           if (in) {
             if (n < slots) mine[n] = j;
@@ -240,8 +238,8 @@ __global__ void k_nbr(NbrArgs a, const void *rs, const int *cell_start, const in
         }
       }
   cnt[i] = n;
-  atomicAdd(&tot[0], (unsigned long long)n);
-  atomicMax(&tot[1], (unsigned long long)n);
+  atomicAdd(&tot[2 * si], (unsigned long long)n);
+  atomicMax(&tot[2 * si + 1], (unsigned long long)n);
 }
 
 void *alloc_dev(pse_ctx *c, size_t bytes) {
@@ -295,83 +293,87 @@ int64_t scan_tmp_ints(int64_t n1) {
   return tot + 16;
 }
 
+// Slot layout of the neighbour list: per suspension `slots` entries per particle.
+int64_t layout_neighbours(pse_ctx *c) {
+  int64_t off = 0;
+  for (int q = 0; q < c->nsys; ++q) {
+    c->hs[q].nbr0 = off;
+    off += (int64_t)c->hs[q].slots * c->hs[q].N;
+  }
+  return off;
+}
+
 // Builds the sorted configuration for positions d_pos (device, user order, FP64).
 pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_SETUP, s);
   c->nlaunch += 6;  // bin, scatter, derive, cell scatter, neighbour count and fill (+ scans)
   const Params &p = c->p;
-  int N = (int)p.N;
-  BinArgs b;
-  b.N = N;
-  b.L = p.L;
-  b.h = p.h;
-  b.cs = p.cs;
-  b.Ng = p.Ng;
-  b.P = p.P;
-  b.nc = p.nc;
-  for (int d = 0; d < 3; ++d) {
-    b.T[d] = p.tile[d];
-    b.nt[d] = p.ntile[d];
-  }
+  const int64_t N = p.N;
+  const int ns = c->nsys;
   unsigned nb = (unsigned)ceil_div(N, 256);
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_start, 0, sizeof(int) * (c->ntiles + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_cur, 0, sizeof(int) * (c->ntiles + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->ncells + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cur, 0, sizeof(int) * (c->ncells + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-  k_bin<<<nb, 256, 0, s>>>(b, d_pos, c->d_posw, c->d_tile_key, c->d_tile_start, c->d_flag);
+  k_bin<<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, d_pos, c->d_posw, c->d_tile_key, c->d_tile_start,
+                           c->d_flag);
   PSE_TRY(exclusive_scan(c, c->d_tile_start, c->ntiles + 1, s));
   k_scatter<<<nb, 256, 0, s>>>(N, c->d_tile_key, c->d_tile_start, c->d_tile_cur, c->d_perm, c->d_inv);
   if (c->prec == PSE_MIXED)
-    k_derive<float><<<nb, 256, 0, s>>>(b, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0, (float4 *)c->d_sp_d0,
-                                       c->d_rs, c->d_cell_key, c->d_cell_start);
+    k_derive<float><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0,
+                                       (float4 *)c->d_sp_d0, c->d_rs, c->d_cell_key, c->d_cell_start);
   else
-    k_derive<double><<<nb, 256, 0, s>>>(b, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0, (double4_32a *)c->d_sp_d0,
-                                        c->d_rs, c->d_cell_key, c->d_cell_start);
+    k_derive<double><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0,
+                                        (double4_32a *)c->d_sp_d0, c->d_rs, c->d_cell_key, c->d_cell_start);
   PSE_TRY(exclusive_scan(c, c->d_cell_start, c->ncells + 1, s));
   k_cell_scatter<<<nb, 256, 0, s>>>(N, c->d_cell_key, c->d_cell_start, c->d_cell_cur, c->d_cell_list);
-  NbrArgs a;
-  a.N = N;
-  a.nc = p.nc;
-  a.csf = (float)p.cs;
-  a.Lf = (float)p.L;
-  a.L = p.L;
-  a.rc2 = p.rcut * p.rcut;
-  a.rc2f = (float)a.rc2;
+  const double rc2 = p.rcut * p.rcut;
   unsigned nb128 = (unsigned)ceil_div(N, 128);
   for (int attempt = 0; attempt < 2; ++attempt) {
-    PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long), s));
+    PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long) * ns, s));
     if (c->prec == PSE_MIXED)
-      k_nbr<float><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr,
-                                         c->nbr_slots, c->d_nbr_tot);
+      k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
+                                         c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot);
     else
-      k_nbr<double><<<nb128, 128, 0, s>>>(a, c->d_rs, c->d_cell_start, c->d_cell_list, c->d_nbr_start, c->d_nbr,
-                                          c->nbr_slots, c->d_nbr_tot);
-    unsigned long long tm[2];
+      k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
+                                          c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot);
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    PSE_CUDA_TRY(c, cudaMemcpyAsync(tm, c->d_nbr_tot, sizeof(tm), cudaMemcpyDeviceToHost, s));
+    PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_nbr_tot, c->d_nbr_tot, 2 * sizeof(unsigned long long) * ns,
+                                    cudaMemcpyDeviceToHost, s));
     PSE_CUDA_TRY(c, cudaGetLastError());
     PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
     if (c->h_pinned_int[1]) {
       c->err = "non-finite particle position";
       return PSE_ERR_NONFINITE;
     }
-    c->npairs = (int64_t)tm[0];
-    if ((int64_t)tm[1] <= c->nbr_slots) break;
-    // a particle has more neighbours than slots: enlarge and rebuild once
-    int slots = (int)((tm[1] + 15) / 8 * 8);
-    if ((double)slots * N > 2.0e9) {
+    bool grow = false;
+    c->npairs = 0;
+    c->npairs_sys.assign(ns, 0);
+    for (int q = 0; q < ns; ++q) {
+      c->npairs_sys[q] = (int64_t)c->h_nbr_tot[2 * q];
+      c->npairs += c->npairs_sys[q];
+      int64_t mx = (int64_t)c->h_nbr_tot[2 * q + 1];
+      if (mx > c->hs[q].slots) {
+        c->hs[q].slots = (int)((mx + 15) / 8 * 8);  // a particle has more neighbours than slots
+        grow = true;
+      }
+    }
+    if (!grow) break;
+    // enlarge the list and rebuild once
+    int64_t cap = layout_neighbours(c);
+    if ((double)cap > 2.0e9) {
       c->err = "neighbour list exceeds 2^31 entries";
       return PSE_ERR_INVALID_ARG;
     }
-    void *q = alloc_dev(c, sizeof(int) * (size_t)slots * N);
+    void *q = alloc_dev(c, sizeof(int) * (size_t)cap);
     if (!q) {
       c->err = "cannot allocate neighbour list";
       return PSE_ERR_OOM;
     }
     c->d_nbr = (int *)q;  // the old list stays in c->allocs and is freed at destroy
-    c->nbr_slots = slots;
-    c->nbr_cap = (int64_t)slots * N;
+    c->nbr_cap = cap;
+    PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_sys, c->hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice, s));
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;

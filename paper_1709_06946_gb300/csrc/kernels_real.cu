@@ -2,11 +2,15 @@
 // over neighbours closer than r_cut of the 8x8 real-space block (Eqs. MUFr-MDCr)
 // applied to [F; S], plus the real-space self term (App. A, Case 3).
 //
-// One thread per particle, neighbour list in CSR form, sorted particle order so
-// that neighbours' records are close in memory.  The seven scalar functions
+// G lanes per particle walk its slotted neighbour list; particles are in sorted
+// order (by suspension, then spreading tile) so that neighbours' records are
+// close in memory.  A persistent grid takes blocks of particles from a work
+// counter; particles of suspensions marked inactive are skipped.  The seven scalar functions
 // come from a table on r: linear interpolation in FP32 (mixed form), cubic
 // Lagrange interpolation in FP64 with one-sided stencils at the r = 2a node
 // where the functions have a kink.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "pse_internal.cuh"
 
@@ -14,9 +18,8 @@ namespace pse {
 namespace {
 
 struct RealArgs {
-  int N, nc, len, k2, slots;
-  float csf, Lf;
-  double L;
+  int64_t Ntot;
+  int nsys, len, k2;
   double inv_dr, self_uf, self_es;
 };
 
@@ -31,7 +34,7 @@ template <> struct Pos<float> {
     c[1] = (q >> 10) & 1023;
     c[2] = (q >> 20) & 1023;
   }
-  __device__ void sep(const void *rs, int j, const RealArgs &a, float d[3]) const {
+  __device__ void sep(const void *rs, int j, const SysDev &a, float d[3]) const {
     float4 o = ((const float4 *)rs)[j];
     int q = __float_as_int(o.w);
     int cj[3] = {q & 1023, (q >> 10) & 1023, (q >> 20) & 1023};
@@ -48,7 +51,7 @@ template <> struct Pos<float> {
 template <> struct Pos<double> {
   double4_32a p;
   __device__ void load(const void *rs, int i) { p = ((const double4_32a *)rs)[i]; }
-  __device__ void sep(const void *rs, int j, const RealArgs &a, double d[3]) const {
+  __device__ void sep(const void *rs, int j, const SysDev &a, double d[3]) const {
     double4_32a o = ((const double4_32a *)rs)[j];
     d[0] = p.x - o.x;
     d[1] = p.y - o.y;
@@ -92,117 +95,130 @@ __device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, dou
 // the neighbours' records are fetched in parallel) and the partial sums are
 // reduced with shuffles; the first lane of the group adds the self term.
 template <typename T, int MODE, int G>
-__global__ void __launch_bounds__(256) k_real(RealArgs a, const void *rs, const int *__restrict__ nstart,
-                                              const int *__restrict__ nbr, const T *__restrict__ vin,
-                                              T *__restrict__ vout, const T *__restrict__ tab) {
+__global__ void __launch_bounds__(256) k_real(RealArgs a, const SysDev *__restrict__ sys,
+                                              const int64_t *__restrict__ p0, const int *__restrict__ active,
+                                              int *queue, int nitems, const void *rs,
+                                              const int *__restrict__ nstart, const int *__restrict__ nbr,
+                                              const T *__restrict__ vin, T *__restrict__ vout,
+                                              const T *__restrict__ tab) {
   constexpr bool HAS_F = MODE != M_SE, WANT_U = MODE != M_SE, WANT_E = MODE != M_FSU;
   using T4 = typename V4<T>::t;
-  const int gid = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G);
-  const int sub = threadIdx.x % G;
-  const bool active = gid < a.N;
-  const int i = active ? gid : a.N - 1;
-  Pos<T> pi;
-  pi.load(rs, i);
-  const T4 *v4 = (const T4 *)vin;
-  T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
-  const int64_t k0 = (int64_t)i * a.slots;
-  const int64_t e = active ? k0 + nstart[i] : 0;
-  for (int64_t k = (active ? k0 : 0) + sub; k < e; k += G) {
-    int j = nbr[k];
-    T d[3];
-    pi.sep(rs, j, a, d);
-    T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    T r = sqrt(r2), ir = (T)1 / r;
-    T rh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
-    T f[7];
-    lookup(tab, a, r, f);
-    T4 q0 = v4[2 * j], q1 = v4[2 * j + 1];
-    T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
-    T v[3];
-    Smul(s, rh, v);
-    T q = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
-    if (WANT_U) {
-      T c = f[3] * q;
+  for_each_item(queue, nitems, [&](int item) {
+    const int64_t gid = ((int64_t)item * 256 + threadIdx.x) / G;
+    const int sub = threadIdx.x % G;
+    const int64_t i = gid < a.Ntot ? gid : a.Ntot - 1;
+    const int si = find_sys(p0, a.nsys, i);
+    const bool live = gid < a.Ntot && active[si];
+    const SysDev &sd = sys[si];
+    Pos<T> pi;
+    pi.load(rs, (int)i);
+    const T4 *v4 = (const T4 *)vin;
+    T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
+    const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots;
+    const int64_t e = live ? k0 + nstart[i] : 0;
+    for (int64_t k = (live ? k0 : 0) + sub; k < e; k += G) {
+      int j = nbr[k];
+      T d[3];
+      pi.sep(rs, j, sd, d);
+      T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      T r = sqrt(r2), ir = (T)1 / r;
+      T rh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+      T f[7];
+      lookup(tab, a, r, f);
+      T4 q0 = v4[2 * j], q1 = v4[2 * j + 1];
+      T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
+      T v[3];
+      Smul(s, rh, v);
+      T q = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+      if (WANT_U) {
+        T c = f[3] * q;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) U[m] += f[2] * v[m] + c * rh[m];
-      if (HAS_F) {
-        T F[3] = {q0.x, q0.y, q0.z};
-        T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
-        T cf = (f[1] - f[0]) * rf;
+        for (int m = 0; m < 3; ++m) U[m] += f[2] * v[m] + c * rh[m];
+        if (HAS_F) {
+          T F[3] = {q0.x, q0.y, q0.z};
+          T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
+          T cf = (f[1] - f[0]) * rf;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) U[m] += f[0] * F[m] + cf * rh[m];
+          for (int m = 0; m < 3; ++m) U[m] += f[0] * F[m] + cf * rh[m];
+        }
+      }
+      if (WANT_E) {
+        T sy[5], yr[5];
+        symY(v, rh, sy);
+        symY(rh, rh, yr);  // = 2 y(rh)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) E[m] += f[4] * s[m] + f[5] * sy[m] + (T)0.5 * f[6] * q * yr[m];
+        if (HAS_F) {
+          T F[3] = {q0.x, q0.y, q0.z};
+          T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
+          T sf[5];
+          symY(F, rh, sf);
+#pragma unroll
+          for (int m = 0; m < 5; ++m) E[m] += (T)(-0.5) * f[2] * sf[m] - (T)0.5 * f[3] * rf * yr[m];
+        }
       }
     }
-    if (WANT_E) {
-      T sy[5], yr[5];
-      symY(v, rh, sy);
-      symY(rh, rh, yr);  // = 2 y(rh)
 #pragma unroll
-      for (int m = 0; m < 5; ++m) E[m] += f[4] * s[m] + f[5] * sy[m] + (T)0.5 * f[6] * q * yr[m];
-      if (HAS_F) {
-        T F[3] = {q0.x, q0.y, q0.z};
-        T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
-        T sf[5];
-        symY(F, rh, sf);
+    for (int o = G / 2; o > 0; o >>= 1) {
 #pragma unroll
-        for (int m = 0; m < 5; ++m) E[m] += (T)(-0.5) * f[2] * sf[m] - (T)0.5 * f[3] * rf * yr[m];
+      for (int m = 0; m < 3; ++m) U[m] += __shfl_xor_sync(0xffffffffu, U[m], o, G);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) E[m] += __shfl_xor_sync(0xffffffffu, E[m], o, G);
+    }
+    if (live && sub == 0) {
+      T4 s0 = v4[2 * i], s1 = v4[2 * i + 1];
+      if (WANT_U && HAS_F) {
+        U[0] += (T)a.self_uf * s0.x;
+        U[1] += (T)a.self_uf * s0.y;
+        U[2] += (T)a.self_uf * s0.z;
       }
+      if (WANT_E) {
+        E[0] += (T)a.self_es * s0.w;
+        E[1] += (T)a.self_es * s1.x;
+        E[2] += (T)a.self_es * s1.y;
+        E[3] += (T)a.self_es * s1.z;
+        E[4] += (T)a.self_es * s1.w;
+      }
+      T4 o0, o1;
+      o0.x = U[0];
+      o0.y = U[1];
+      o0.z = U[2];
+      o0.w = E[0];
+      o1.x = E[1];
+      o1.y = E[2];
+      o1.z = E[3];
+      o1.w = E[4];
+      T4 *o4 = (T4 *)vout;
+      o4[2 * i] = o0;
+      o4[2 * i + 1] = o1;
     }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-#pragma unroll
-    for (int m = 0; m < 3; ++m) U[m] += __shfl_xor_sync(0xffffffffu, U[m], o, G);
-#pragma unroll
-    for (int m = 0; m < 5; ++m) E[m] += __shfl_xor_sync(0xffffffffu, E[m], o, G);
-  }
-  if (active && sub == 0) {
-    T4 s0 = v4[2 * i], s1 = v4[2 * i + 1];
-    if (WANT_U && HAS_F) {
-      U[0] += (T)a.self_uf * s0.x;
-      U[1] += (T)a.self_uf * s0.y;
-      U[2] += (T)a.self_uf * s0.z;
-    }
-    if (WANT_E) {
-      E[0] += (T)a.self_es * s0.w;
-      E[1] += (T)a.self_es * s1.x;
-      E[2] += (T)a.self_es * s1.y;
-      E[3] += (T)a.self_es * s1.z;
-      E[4] += (T)a.self_es * s1.w;
-    }
-    T4 o0, o1;
-    o0.x = U[0];
-    o0.y = U[1];
-    o0.z = U[2];
-    o0.w = E[0];
-    o1.x = E[1];
-    o1.y = E[2];
-    o1.z = E[3];
-    o1.w = E[4];
-    T4 *o4 = (T4 *)vout;
-    o4[2 * i] = o0;
-    o4[2 * i + 1] = o1;
-  }
+  });
+}
+
+template <typename T, int MODE, int G>
+void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, cudaStream_t s) {
+  auto kern = k_real<T, MODE, G>;
+  static std::atomic<int> per_sm{0};
+  const int64_t items = ceil_div(a.Ntot * G, 256);
+  unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
+  int *q = next_queue(c, s);
+  kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_rs, c->d_nbr_start, c->d_nbr,
+                            (const T *)vin, (T *)vout, (const T *)c->d_table);
 }
 
 template <typename T, int G>
 void launch_real_g(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int mode, cudaStream_t s) {
-  unsigned nb = (unsigned)ceil_div((int64_t)a.N * G, 256);
-  const T *tab = (const T *)c->d_table;
-  if (mode == M_FULL)
-    k_real<T, M_FULL, G><<<nb, 256, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
-  else if (mode == M_SE)
-    k_real<T, M_SE, G><<<nb, 256, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
-  else
-    k_real<T, M_FSU, G><<<nb, 256, 0, s>>>(a, c->d_rs, c->d_nbr_start, c->d_nbr, (const T *)vin, (T *)vout, tab);
+  if (mode == M_FULL) launch_real_m<T, M_FULL, G>(c, a, vin, vout, s);
+  else if (mode == M_SE) launch_real_m<T, M_SE, G>(c, a, vin, vout, s);
+  else launch_real_m<T, M_FSU, G>(c, a, vin, vout, s);
 }
 
 template <typename T>
 void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int mode, cudaStream_t s) {
-  // lanes per particle from the mean neighbour count of the current list
+  // lanes per particle from the mean neighbour count of the current lists
   int g = c->opt.real_lanes;
   if (g <= 0) {
-    double mean = a.N > 0 ? (double)c->npairs / a.N : 0.0;
+    double mean = a.Ntot > 0 ? (double)c->npairs / a.Ntot : 0.0;
     g = mean >= 64.0 ? 8 : (mean >= 24.0 ? 4 : 1);
   }
   switch (g) {
@@ -216,19 +232,16 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
 
 }  // namespace
 
-// vout = M_r vin for the current configuration (sorted order, [N][8]).
+// vout = M_r vin for the current configuration (sorted order, [N][8]); rows of
+// inactive suspensions are left untouched.
 pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_REAL, s);
   c->nlaunch += 1;
   RealArgs a;
-  a.N = (int)c->p.N;
-  a.nc = c->p.nc;
+  a.Ntot = c->p.N;
+  a.nsys = c->nsys;
   a.len = c->table_len;
   a.k2 = c->table_k2;
-  a.slots = c->nbr_slots;
-  a.csf = (float)c->p.cs;
-  a.Lf = (float)c->p.L;
-  a.L = c->p.L;
   a.inv_dr = 1.0 / c->table_dr;
   a.self_uf = c->self_uf;
   a.self_es = c->self_es;

@@ -4,6 +4,11 @@
 //
 // Inner products in the mixed form: each thread sums its FP32 products over a
 // short stretch of the vector, the cross-thread and cross-block sums are FP64.
+// Inner products and combinations are per suspension: every block covers one
+// chunk of one suspension's vector, results and coefficients live at
+// d_coef[s * COEF_STRIDE + ...], and suspensions marked inactive are skipped.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "pse_internal.cuh"
 
@@ -13,8 +18,8 @@ namespace {
 constexpr int DOT_NT = 256, DOT_ROWS = 8;
 
 template <typename T>
-__global__ void k_gather_in(int N, const int *perm, const T *F, const T *S, T *out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_gather_in(int64_t N, const int *perm, const T *F, const T *S, T *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int u = perm[i];
   T *o = out + 8 * (size_t)i;
@@ -23,8 +28,8 @@ __global__ void k_gather_in(int N, const int *perm, const T *F, const T *S, T *o
 }
 
 template <typename T>
-__global__ void k_scatter_out(int N, const int *perm, const T *in, T *U, T *E, T scale) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_scatter_out(int64_t N, const int *perm, const T *in, T *U, T *E, T scale) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int u = perm[i];
   const T *v = in + 8 * (size_t)i;
@@ -35,40 +40,67 @@ __global__ void k_scatter_out(int N, const int *perm, const T *in, T *U, T *E, T
 }
 
 template <typename T>
-__global__ void k_gather8(int N, const int *perm, const T *in, T *out) {
+__global__ void k_gather8(int64_t N, const int *perm, const T *in, T *out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 8 * (int64_t)N) return;
-  int i = (int)(e >> 3), c = (int)(e & 7);
+  if (e >= 8 * N) return;
+  int64_t i = e >> 3;
+  int c = (int)(e & 7);
   out[e] = in[8 * (size_t)perm[i] + c];
 }
 
 template <typename T>
-__global__ void k_scatter8(int N, const int *perm, const T *in, T *out, T scale) {
+__global__ void k_scatter8(int64_t N, const int *perm, const T *in, T *out, T scale) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 8 * (int64_t)N) return;
-  int i = (int)(e >> 3), c = (int)(e & 7);
+  if (e >= 8 * N) return;
+  int64_t i = e >> 3;
+  int c = (int)(e & 7);
   out[8 * (size_t)perm[i] + c] = scale * in[e];
 }
 
 template <typename T>
-__global__ void k_philox_w1(int N, const int *perm, uint64_t seed, uint64_t counter, T *out) {
+__global__ void k_philox_w1(int64_t N, const int *perm, uint64_t seed, uint64_t counter, T *out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 8 * (int64_t)N) return;
-  int i = (int)(e >> 3), c = (int)(e & 7);
+  if (e >= 8 * N) return;
+  int64_t i = e >> 3;
+  int c = (int)(e & 7);
   T z0, z1;
   normal_pair<T>(seed, counter, 1u, 8ull * (uint64_t)perm[i] + (uint64_t)c, z0, z1);
   out[e] = z0;
 }
 
-// partial[b][r] = sum over this block's share of rows[r] . w   (r < nrows <= DOT_ROWS)
+// The chunked vector kernels: block b covers VEC_CHUNK elements of the [N][8]
+// vectors of one suspension (blocks of suspension s start at blk0[s]).
+struct Chunk {
+  int s;
+  int64_t beg, end;
+};
+__device__ __forceinline__ Chunk chunk_of(const SysDev *sys, const int *blk0, int nsys) {
+  Chunk ch;
+  ch.s = find_sys(blk0, nsys, blockIdx.x);
+  const SysDev &q = sys[ch.s];
+  ch.beg = 8 * q.p0 + (int64_t)(blockIdx.x - q.blk0) * VEC_CHUNK;
+  int64_t lim = 8 * (q.p0 + q.N);
+  ch.end = ch.beg + VEC_CHUNK < lim ? ch.beg + VEC_CHUNK : lim;
+  return ch;
+}
+
+struct VecArgs {
+  const SysDev *sys;
+  const int *blk0, *active;
+  int nsys;
+};
+
+// partial[b][r] = sum over block b's chunk of rows[r] . w   (r < nrows <= DOT_ROWS)
 template <typename T>
-__global__ void k_multidot(const T *__restrict__ rows, int64_t stride, int nrows, int64_t n, const T *__restrict__ w,
-                           double *partial) {
+__global__ void k_multidot(VecArgs va, const T *__restrict__ rows, int64_t stride, int nrows,
+                           const T *__restrict__ w, double *partial) {
   __shared__ double red[DOT_ROWS][DOT_NT / 32];
+  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
+  if (!va.active[ch.s]) return;
   T acc[DOT_ROWS];
 #pragma unroll
   for (int r = 0; r < DOT_ROWS; ++r) acc[r] = 0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
     T we = w[e];
 #pragma unroll
     for (int r = 0; r < DOT_ROWS; ++r)
@@ -84,47 +116,59 @@ __global__ void k_multidot(const T *__restrict__ rows, int64_t stride, int nrows
   }
   __syncthreads();
   if (threadIdx.x < DOT_ROWS) {
-    double s = 0;
-    for (int k = 0; k < DOT_NT / 32; ++k) s += red[threadIdx.x][k];
-    partial[(size_t)blockIdx.x * DOT_ROWS + threadIdx.x] = s;
+    double sum = 0;
+    for (int k = 0; k < DOT_NT / 32; ++k) sum += red[threadIdx.x][k];
+    partial[(size_t)blockIdx.x * DOT_ROWS + threadIdx.x] = sum;
   }
 }
 
-__global__ void k_dot_final(const double *partial, int nblocks, int nrows, double *out) {
+// out[s * COEF_STRIDE + r] = sum of the partials of suspension s (one block per suspension).
+__global__ void k_dot_final(VecArgs va, const double *partial, int nrows, double *out) {
+  const int s = blockIdx.x;
+  if (!va.active[s]) return;
   int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (r >= nrows) return;
-  double s = 0;
-  for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * DOT_ROWS + r];
+  const int b0 = va.blk0[s], b1 = va.blk0[s + 1];
+  double sum = 0;
+  for (int b = b0 + lane; b < b1; b += 32) sum += partial[(size_t)b * DOT_ROWS + r];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[r] = s;
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) out[(size_t)s * COEF_STRIDE + r] = sum;
 }
 
-// w[e] = (SET ? 0 : w[e]) + sgn * sum_r coef[r] rows[r][e]
+// w[e] = (SET ? 0 : w[e]) + sgn * sum_r coef[s][r] rows[r][e], r < nrows (or nrows_s[s])
 template <typename T, bool SET>
-__global__ void k_combine(T *w, const T *__restrict__ rows, int64_t stride, int nrows, int64_t n,
-                          const double *__restrict__ coef, T sgn) {
+__global__ void k_combine(VecArgs va, T *w, const T *__restrict__ rows, int64_t stride, int nrows,
+                          const int *__restrict__ nrows_s, const double *__restrict__ coef, T sgn) {
   __shared__ T cs[128];
-  for (int r = threadIdx.x; r < nrows && r < 128; r += blockDim.x) cs[r] = (T)coef[r];
+  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
+  if (!va.active[ch.s]) return;
+  const int nr = nrows_s ? min(nrows, nrows_s[ch.s]) : nrows;
+  const double *cf = coef + (size_t)ch.s * COEF_STRIDE;
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) cs[r] = (T)cf[r];
   __syncthreads();
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    T s = 0;
-    for (int r = 0; r < nrows; ++r) s += cs[r] * rows[r * stride + e];
-    w[e] = SET ? sgn * s : w[e] + sgn * s;
+  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
+    T sum = 0;
+    for (int r = 0; r < nr; ++r) sum += cs[r] * rows[r * stride + e];
+    w[e] = SET ? sgn * sum : w[e] + sgn * sum;
   }
 }
 
+// dst = f * src with f = a, or f = coef[s][0] per suspension when coef is given
 template <typename T>
-__global__ void k_vscale(T *dst, const T *src, T a, int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = a * src[e];
+__global__ void k_vscale(VecArgs va, T *dst, const T *src, T a, const double *__restrict__ coef) {
+  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
+  if (!va.active[ch.s]) return;
+  const T f = coef ? (T)coef[(size_t)ch.s * COEF_STRIDE] : a;
+  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) dst[e] = f * src[e];
 }
 
 template <typename T>
-__global__ void k_zero_slots(T *v, int N, int slot0, int nslot) {
+__global__ void k_zero_slots(T *v, int64_t N, int slot0, int nslot) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)N * nslot) return;
-  int i = (int)(e / nslot), c = (int)(e % nslot);
+  if (e >= N * nslot) return;
+  int64_t i = e / nslot;
+  int c = (int)(e % nslot);
   v[8 * (size_t)i + slot0 + c] = 0;
 }
 
@@ -136,19 +180,24 @@ __device__ __forceinline__ double wrapL(double x, double L) {
 }
 
 template <typename T>
-__global__ void k_midpoint(int N, double L, const double *x0, const T *B, double fac, double *xo) {
+__global__ void k_midpoint(VecArgs va, const int64_t *__restrict__ p0, int64_t N, const double *x0, const T *B,
+                           double fac, double *xo) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 3 * (int64_t)N) return;
-  int u = (int)(e / 3), d = (int)(e % 3);
+  if (e >= 3 * N) return;
+  int64_t u = e / 3;
+  int d = (int)(e % 3);
+  const double L = va.sys[find_sys(p0, va.nsys, u)].L;
   xo[e] = wrapL(x0[e] + fac * (double)B[8 * (size_t)u + d], L);
 }
 
 template <typename T>
-__global__ void k_final(int N, double L, const int *inv, const double *x0, const T *B, const T *Us, double dt,
-                        double *xo) {
+__global__ void k_final(VecArgs va, const int64_t *__restrict__ p0, int64_t N, const int *inv, const double *x0,
+                        const T *B, const T *Us, double dt, double *xo) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 3 * (int64_t)N) return;
-  int u = (int)(e / 3), d = (int)(e % 3);
+  if (e >= 3 * N) return;
+  int64_t u = e / 3;
+  int d = (int)(e % 3);
+  const double L = va.sys[find_sys(p0, va.nsys, u)].L;
   double U = (double)B[8 * (size_t)u + d] + (double)Us[8 * (size_t)inv[u] + d];
   xo[e] = wrapL(x0[e] + dt * U, L);
 }
@@ -162,7 +211,18 @@ __global__ void k_finite(const T *p, int64_t n, int *bad) {
     }
 }
 
+__global__ void k_clear(int *q) { *q = 0; }
+
 unsigned grid_for(int64_t n, int nt = 256) { return (unsigned)ceil_div(n, nt); }
+
+VecArgs vec_args(const pse_ctx *c) {
+  VecArgs v;
+  v.sys = c->d_sys;
+  v.blk0 = c->d_blk0;
+  v.active = c->d_active;
+  v.nsys = c->nsys;
+  return v;
+}
 
 }  // namespace
 
@@ -175,10 +235,16 @@ unsigned grid_for(int64_t n, int nt = 256) { return (unsigned)ceil_div(n, nt); }
     }                               \
   } while (0)
 
+int *next_queue(pse_ctx *c, cudaStream_t s) {
+  int *q = c->d_queue + (c->queue_slot++ & 63);
+  k_clear<<<1, 1, 0, s>>>(q);
+  return q;
+}
+
 pse_status gather_in(pse_ctx *c, const void *F, const void *S, void *vout, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
+  int64_t N = c->p.N;
   DISPATCH(c, (k_gather_in<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)F, (const float *)S, (float *)vout)),
            (k_gather_in<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)F, (const double *)S, (double *)vout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
@@ -188,7 +254,7 @@ pse_status gather_in(pse_ctx *c, const void *F, const void *S, void *vout, cudaS
 pse_status scatter_out(pse_ctx *c, const void *vin, void *U, void *E, double scale, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
+  int64_t N = c->p.N;
   DISPATCH(c, (k_scatter_out<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)vin, (float *)U, (float *)E, (float)scale)),
            (k_scatter_out<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)vin, (double *)U, (double *)E, scale)));
   PSE_CUDA_TRY(c, cudaGetLastError());
@@ -198,9 +264,9 @@ pse_status scatter_out(pse_ctx *c, const void *vin, void *U, void *E, double sca
 pse_status gather_user8(pse_ctx *c, const void *user8, void *vout, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
-  DISPATCH(c, (k_gather8<float><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const float *)user8, (float *)vout)),
-           (k_gather8<double><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const double *)user8, (double *)vout)));
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_gather8<float><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, (const float *)user8, (float *)vout)),
+           (k_gather8<double><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, (const double *)user8, (double *)vout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -208,9 +274,9 @@ pse_status gather_user8(pse_ctx *c, const void *user8, void *vout, cudaStream_t 
 pse_status scatter_user8(pse_ctx *c, const void *vin, void *user8, double scale, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
-  DISPATCH(c, (k_scatter8<float><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const float *)vin, (float *)user8, (float)scale)),
-           (k_scatter8<double><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, (const double *)vin, (double *)user8, scale)));
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_scatter8<float><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, (const float *)vin, (float *)user8, (float)scale)),
+           (k_scatter8<double><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, (const double *)vin, (double *)user8, scale)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -218,66 +284,72 @@ pse_status scatter_user8(pse_ctx *c, const void *vin, void *user8, double scale,
 pse_status philox_w1(pse_ctx *c, uint64_t seed, uint64_t counter, void *vout, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
-  DISPATCH(c, (k_philox_w1<float><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, seed, counter, (float *)vout)),
-           (k_philox_w1<double><<<grid_for(8 * (int64_t)N), 256, 0, s>>>(N, c->d_perm, seed, counter, (double *)vout)));
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_philox_w1<float><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, seed, counter, (float *)vout)),
+           (k_philox_w1<double><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, seed, counter, (double *)vout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
 
-// d_out[r] = rows[r] . w for r < nrows (rows contiguous with stride n).
-pse_status multidot(pse_ctx *c, const void *rows, int nrows, int64_t n, const void *w, double *d_out, cudaStream_t s) {
+// coef[s][off + r] = rows[r] . w over suspension s, for r < nrows (rows of length 8N, contiguous).
+pse_status multidot(pse_ctx *c, const void *rows, int nrows, const void *w, int off, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
-  int nb = c->dots_blocks;
-  double *partial = c->d_dots;
+  const int64_t n = 8 * c->p.N;
+  const unsigned nb = (unsigned)c->nvblk;
+  VecArgs va = vec_args(c);
   for (int r0 = 0; r0 < nrows; r0 += DOT_ROWS) {
     int nr = std::min(DOT_ROWS, nrows - r0);
-    DISPATCH(c, (k_multidot<float><<<nb, DOT_NT, 0, s>>>((const float *)rows + (size_t)r0 * n, n, nr, n, (const float *)w, partial)),
-             (k_multidot<double><<<nb, DOT_NT, 0, s>>>((const double *)rows + (size_t)r0 * n, n, nr, n, (const double *)w, partial)));
-    k_dot_final<<<1, 32 * DOT_ROWS, 0, s>>>(partial, nb, nr, d_out + r0);
+    DISPATCH(c, (k_multidot<float><<<nb, DOT_NT, 0, s>>>(va, (const float *)rows + (size_t)r0 * n, n, nr, (const float *)w, c->d_dots)),
+             (k_multidot<double><<<nb, DOT_NT, 0, s>>>(va, (const double *)rows + (size_t)r0 * n, n, nr, (const double *)w, c->d_dots)));
+    k_dot_final<<<c->nsys, 32 * DOT_ROWS, 0, s>>>(va, c->d_dots, nr, c->d_coef + off + r0);
     c->nlaunch += 2;
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
 
-pse_status combine_sub(pse_ctx *c, void *w, const void *rows, int nrows, int64_t n, const double *d_coef, cudaStream_t s) {
+// w -= sum_r coef[s][off + r] rows[r]  (r < nrows)
+pse_status combine_sub(pse_ctx *c, void *w, const void *rows, int nrows, int off, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
-  unsigned nb = std::min<unsigned>(grid_for(n), 4096);
+  const int64_t n = 8 * c->p.N;
+  const unsigned nb = (unsigned)c->nvblk;
+  VecArgs va = vec_args(c);
   for (int r0 = 0; r0 < nrows; r0 += 128) {
     int nr = std::min(128, nrows - r0);
     c->nlaunch += 1;
-    DISPATCH(c, (k_combine<float, false><<<nb, 256, 0, s>>>((float *)w, (const float *)rows + (size_t)r0 * n, n, nr, n, d_coef + r0, -1.0f)),
-             (k_combine<double, false><<<nb, 256, 0, s>>>((double *)w, (const double *)rows + (size_t)r0 * n, n, nr, n, d_coef + r0, -1.0)));
+    DISPATCH(c, (k_combine<float, false><<<nb, 256, 0, s>>>(va, (float *)w, (const float *)rows + (size_t)r0 * n, n, nr, nullptr, c->d_coef + off + r0, -1.0f)),
+             (k_combine<double, false><<<nb, 256, 0, s>>>(va, (double *)w, (const double *)rows + (size_t)r0 * n, n, nr, nullptr, c->d_coef + off + r0, -1.0)));
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
 
-pse_status combine_set(pse_ctx *c, void *y, const void *rows, int nrows, int64_t n, const double *d_coef, cudaStream_t s) {
+// y = sum_r coef[s][off + r] rows[r]  (r < d_nrows[s] <= maxrows <= 128)
+pse_status combine_set(pse_ctx *c, void *y, const void *rows, const int *d_nrows, int maxrows, int off,
+                       cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
-  unsigned nb = std::min<unsigned>(grid_for(n), 4096);
-  for (int r0 = 0; r0 < nrows; r0 += 128) {
-    int nr = std::min(128, nrows - r0);
-    c->nlaunch += 1;
-    if (r0 == 0) {
-      DISPATCH(c, (k_combine<float, true><<<nb, 256, 0, s>>>((float *)y, (const float *)rows, n, nr, n, d_coef, 1.0f)),
-               (k_combine<double, true><<<nb, 256, 0, s>>>((double *)y, (const double *)rows, n, nr, n, d_coef, 1.0)));
-    } else {
-      DISPATCH(c, (k_combine<float, false><<<nb, 256, 0, s>>>((float *)y, (const float *)rows + (size_t)r0 * n, n, nr, n, d_coef + r0, 1.0f)),
-               (k_combine<double, false><<<nb, 256, 0, s>>>((double *)y, (const double *)rows + (size_t)r0 * n, n, nr, n, d_coef + r0, 1.0)));
-    }
+  const int64_t n = 8 * c->p.N;
+  const unsigned nb = (unsigned)c->nvblk;
+  VecArgs va = vec_args(c);
+  if (maxrows > 128) {
+    c->err = "too many Krylov vectors";
+    return PSE_ERR_INVALID_ARG;
   }
+  c->nlaunch += 1;
+  DISPATCH(c, (k_combine<float, true><<<nb, 256, 0, s>>>(va, (float *)y, (const float *)rows, n, maxrows, d_nrows, c->d_coef + off, 1.0f)),
+           (k_combine<double, true><<<nb, 256, 0, s>>>(va, (double *)y, (const double *)rows, n, maxrows, d_nrows, c->d_coef + off, 1.0)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
 
-pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int64_t n, cudaStream_t s) {
+pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int off, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  unsigned nb = std::min<unsigned>(grid_for(n), 4096);
-  DISPATCH(c, (k_vscale<float><<<nb, 256, 0, s>>>((float *)dst, (const float *)src, (float)a, n)),
-           (k_vscale<double><<<nb, 256, 0, s>>>((double *)dst, (const double *)src, a, n)));
+  const unsigned nb = (unsigned)c->nvblk;
+  VecArgs va = vec_args(c);
+  const double *cf = off >= 0 ? c->d_coef + off : nullptr;
+  DISPATCH(c, (k_vscale<float><<<nb, 256, 0, s>>>(va, (float *)dst, (const float *)src, (float)a, cf)),
+           (k_vscale<double><<<nb, 256, 0, s>>>(va, (double *)dst, (const double *)src, a, cf)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -285,9 +357,9 @@ pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int64_t n, c
 pse_status vzero_slots(pse_ctx *c, void *v, int slot0, int nslot, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
-  DISPATCH(c, (k_zero_slots<float><<<grid_for((int64_t)N * nslot), 256, 0, s>>>((float *)v, N, slot0, nslot)),
-           (k_zero_slots<double><<<grid_for((int64_t)N * nslot), 256, 0, s>>>((double *)v, N, slot0, nslot)));
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_zero_slots<float><<<grid_for(N * nslot), 256, 0, s>>>((float *)v, N, slot0, nslot)),
+           (k_zero_slots<double><<<grid_for(N * nslot), 256, 0, s>>>((double *)v, N, slot0, nslot)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -295,9 +367,10 @@ pse_status vzero_slots(pse_ctx *c, void *v, int slot0, int nslot, cudaStream_t s
 pse_status midpoint(pse_ctx *c, const double *x0, const void *B_user, double fac, double *xout, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
-  DISPATCH(c, (k_midpoint<float><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, x0, (const float *)B_user, fac, xout)),
-           (k_midpoint<double><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, x0, (const double *)B_user, fac, xout)));
+  int64_t N = c->p.N;
+  VecArgs va = vec_args(c);
+  DISPATCH(c, (k_midpoint<float><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, x0, (const float *)B_user, fac, xout)),
+           (k_midpoint<double><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, x0, (const double *)B_user, fac, xout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -306,9 +379,10 @@ pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const 
                         double *xout, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
-  int N = (int)c->p.N;
-  DISPATCH(c, (k_final<float><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, c->d_inv, x0, (const float *)B_user, (const float *)U_sorted, dt, xout)),
-           (k_final<double><<<grid_for(3 * (int64_t)N), 256, 0, s>>>(N, c->p.L, c->d_inv, x0, (const double *)B_user, (const double *)U_sorted, dt, xout)));
+  int64_t N = c->p.N;
+  VecArgs va = vec_args(c);
+  DISPATCH(c, (k_final<float><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, c->d_inv, x0, (const float *)B_user, (const float *)U_sorted, dt, xout)),
+           (k_final<double><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, c->d_inv, x0, (const double *)B_user, (const double *)U_sorted, dt, xout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

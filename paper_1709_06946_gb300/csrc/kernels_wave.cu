@@ -3,8 +3,12 @@
 //   spread (Q) -> R2C FFT -> per-k scaling (P^+ B P with the Gaussian
 //   deconvolution) -> C2R FFT -> interpolate (sigma Q^T).
 //
-// Spreading: one CTA owns one output tile of the grid and accumulates it in
-// shared memory; it visits the particles of the 2x2x2 bins whose Gaussian
+// A handle may hold several suspensions: their half spectra are concatenated
+// (one thread per half-spectrum point of any suspension), and the transforms run
+// as one batched cuFFT plan per group of suspensions with the same grid size.
+//
+// Spreading: a CTA owns one output tile of the grid at a time and accumulates it
+// in shared memory; it visits the particles of the 2x2x2 bins whose Gaussian
 // supports can reach the tile (bins hold particles by the grid index where their
 // support starts), so every grid value is written exactly once with coalesced
 // stores and no global atomics or zeroing pass.  Interpolation mirrors it: the
@@ -19,10 +23,14 @@
 namespace pse {
 namespace {
 
+// Launch-wide arguments of the per-k kernels; per-suspension values come from SysDev.
 struct ScaleArgs {
-  int Ng, nkx;
-  double kfac, a, q4, eta_g, cscale;
-  size_t cstride;
+  int nsys;
+  int64_t nk_tot;
+  double a, q4;
+  const SysDev *sys;
+  const int64_t *k0;   // nsys + 1 prefix of half-spectrum points
+  const int *active;
 };
 
 template <typename T>
@@ -50,7 +58,7 @@ __device__ __forceinline__ void shape(T x, T &s0, T &s1) {
   }
 }
 
-__device__ __forceinline__ bool kvector(const ScaleArgs &s, size_t idx, int &ix, int &iy, int &iz) {
+__device__ __forceinline__ bool kvector(const SysDev &s, size_t idx, int &ix, int &iy, int &iz) {
   ix = (int)(idx % s.nkx);
   iy = (int)((idx / s.nkx) % s.Ng);
   iz = (int)(idx / ((size_t)s.nkx * s.Ng));
@@ -88,10 +96,15 @@ __device__ __forceinline__ void project_out(typename Cx<T>::t *g, size_t idx, si
 }
 
 template <typename T, int MODE>
-__global__ void k_scale(ScaleArgs s, typename Cx<T>::t *g, size_t nk) {
+__global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
   using C2 = typename Cx<T>::t;
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nk) return;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= sa.nk_tot) return;
+  const int sidx = find_sys(sa.k0, sa.nsys, gidx);
+  if (!sa.active[sidx]) return;
+  const SysDev &s = sa.sys[sidx];
+  const size_t idx = (size_t)(gidx - s.k0);
+  C2 *g = g_all + s.cgrid0;
   constexpr bool HF = MODE != M_SE, WU = MODE != M_SE, WE = MODE != M_FSU;
   constexpr int sIn = HF ? 3 : 0, uOut = 0, eOut = (MODE == M_SE) ? 0 : 3;
   int ix, iy, iz;
@@ -112,9 +125,9 @@ __global__ void k_scale(ScaleArgs s, typename Cx<T>::t *g, size_t nk) {
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
   T s0, s1;
-  shape<T>(kk * (T)s.a, s0, s1);
-  T u = k2 * (T)s.q4;
-  T c = (T)s.cscale * ((T)1 + u) * exp(-((T)1 - (T)s.eta_g) * u) / k2;
+  shape<T>(kk * (T)sa.a, s0, s1);
+  T u = k2 * (T)sa.q4;
+  T c = (T)s.c_apply * ((T)1 + u) * exp(-((T)1 - (T)s.eta_g) * u) / k2;
   T fr[3] = {0, 0, 0}, fi[3] = {0, 0, 0};
   if (HF) {
 #pragma unroll
@@ -154,11 +167,16 @@ __global__ void k_scale(ScaleArgs s, typename Cx<T>::t *g, size_t nk) {
 // Wave-space noise: dW2 on the half spectrum (Hermitian partners on kx = 0),
 // u = sigma e^{eta_g k^2/8xi^2} sqrt(H/(eta V k^2)) (I - kk) dW2, then P^+.
 template <typename T, bool EXT>
-__global__ void k_noise(ScaleArgs s, const T *__restrict__ w2, uint64_t seed, uint64_t counter,
-                        typename Cx<T>::t *g, size_t nk) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nk) return;
+__global__ void k_noise(ScaleArgs sa, const T *__restrict__ w2, uint64_t seed, uint64_t counter,
+                        typename Cx<T>::t *g_all) {
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= sa.nk_tot) return;
+  const int sidx = find_sys(sa.k0, sa.nsys, gidx);
+  if (!sa.active[sidx]) return;
+  const SysDev &s = sa.sys[sidx];
+  const size_t idx = (size_t)(gidx - s.k0), nk = (size_t)s.Ng * s.Ng * s.nkx;
   using C2 = typename Cx<T>::t;
+  C2 *g = g_all + s.cgrid0;
   int ix, iy, iz;
   bool live = kvector(s, idx, ix, iy, iz);
   const size_t cs = s.cstride;
@@ -178,7 +196,7 @@ __global__ void k_noise(ScaleArgs s, const T *__restrict__ w2, uint64_t seed, ui
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     T re, im;
-    size_t n = (size_t)m * nk + src;
+    size_t n = 3 * (size_t)s.k0 + (size_t)m * nk + src;  // normals of suspension s follow those of 0..s-1
     if (EXT) {
       re = w2[2 * n];
       im = w2[2 * n + 1];
@@ -192,9 +210,9 @@ __global__ void k_noise(ScaleArgs s, const T *__restrict__ w2, uint64_t seed, ui
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
   T s0, s1;
-  shape<T>(kk * (T)s.a, s0, s1);
-  T u = k2 * (T)s.q4;
-  T c = (T)s.cscale * sqrt(((T)1 + u) / k2) * exp(-(T)0.5 * ((T)1 - (T)s.eta_g) * u);
+  shape<T>(kk * (T)sa.a, s0, s1);
+  T u = k2 * (T)sa.q4;
+  T c = (T)s.c_noise * sqrt(((T)1 + u) / k2) * exp(-(T)0.5 * ((T)1 - (T)s.eta_g) * u);
   T kh[3] = {k[0] * ik, k[1] * ik, k[2] * ik};
   T pr = kh[0] * dr[0] + kh[1] * dr[1] + kh[2] * dr[2], pi = kh[0] * di[0] + kh[1] * di[1] + kh[2] * di[2];
   T ur[3], ui[3];
@@ -206,48 +224,39 @@ __global__ void k_noise(ScaleArgs s, const T *__restrict__ w2, uint64_t seed, ui
   project_out<T, true, true>(g, idx, cs, 0, 3, k, s0, s1, ur, ui);
 }
 
-WaveArgs wave_args(const pse_ctx *c) {
-  const Params &p = c->p;
-  WaveArgs a;
-  a.N = (int)p.N;
-  a.Ng = p.Ng;
-  a.P = p.P;
-  for (int d = 0; d < 3; ++d) {
-    a.T[d] = p.tile[d];
-    a.nt[d] = p.ntile[d];
-  }
-  a.h = p.h;
-  a.alpha = 2.0 * p.xi * p.xi / p.eta_g;
-  a.pref = std::pow(2.0 * p.xi * p.xi / (M_PI * p.eta_g), 1.5);
-  return a;
-}
-
-ScaleArgs scale_args(const pse_ctx *c, double cscale) {
-  const Params &p = c->p;
+ScaleArgs scale_args(const pse_ctx *c) {
   ScaleArgs s;
-  s.Ng = p.Ng;
-  s.nkx = p.nkx;
-  s.kfac = 2.0 * M_PI / p.L;
-  s.a = p.a;
-  s.q4 = 1.0 / (4.0 * p.xi * p.xi);
-  s.eta_g = p.eta_g;
-  s.cscale = cscale;
-  s.cstride = (size_t)p.Ng * p.Ng * p.nkx;
+  s.nsys = c->nsys;
+  s.nk_tot = c->nk_tot;
+  s.a = c->p.a;
+  s.q4 = 1.0 / (4.0 * c->p.xi * c->p.xi);
+  s.sys = c->d_sys;
+  s.k0 = c->d_k0;
+  s.active = c->d_active;
   return s;
 }
 
+// One batched transform per grid-size group over the leading `comps` components
+// of every suspension in the group.
 template <typename T>
-pse_status fft(pse_ctx *c, bool forward, int batch, cudaStream_t s) {
+pse_status fft(pse_ctx *c, bool forward, int comps, cudaStream_t s) {
   StageTimer timer(c, PSE_STAGE_FFT, s);
-  c->nfft += 1;
-  cufftHandle plan = forward ? c->plan_r2c[batch] : c->plan_c2r[batch];
-  PSE_CUFFT_TRY(c, cufftSetStream(plan, s));
-  if (sizeof(T) == 4) {
-    if (forward) PSE_CUFFT_TRY(c, cufftExecR2C(plan, (cufftReal *)c->d_grid, (cufftComplex *)c->d_cgrid));
-    else PSE_CUFFT_TRY(c, cufftExecC2R(plan, (cufftComplex *)c->d_cgrid, (cufftReal *)c->d_grid));
-  } else {
-    if (forward) PSE_CUFFT_TRY(c, cufftExecD2Z(plan, (cufftDoubleReal *)c->d_grid, (cufftDoubleComplex *)c->d_cgrid));
-    else PSE_CUFFT_TRY(c, cufftExecZ2D(plan, (cufftDoubleComplex *)c->d_cgrid, (cufftDoubleReal *)c->d_grid));
+  for (FftGroup &g : c->groups) {
+    bool any = false;
+    for (int q : g.members) any = any || c->h_active[q];
+    if (!any) continue;
+    c->nfft += 1;
+    cufftHandle plan = forward ? g.r2c[comps] : g.c2r[comps];
+    PSE_CUFFT_TRY(c, cufftSetStream(plan, s));
+    T *rg = (T *)c->d_grid + g.grid0;
+    typename Cx<T>::t *cg = (typename Cx<T>::t *)c->d_cgrid + g.cgrid0;
+    if (sizeof(T) == 4) {
+      if (forward) PSE_CUFFT_TRY(c, cufftExecR2C(plan, (cufftReal *)rg, (cufftComplex *)cg));
+      else PSE_CUFFT_TRY(c, cufftExecC2R(plan, (cufftComplex *)cg, (cufftReal *)rg));
+    } else {
+      if (forward) PSE_CUFFT_TRY(c, cufftExecD2Z(plan, (cufftDoubleReal *)rg, (cufftDoubleComplex *)cg));
+      else PSE_CUFFT_TRY(c, cufftExecZ2D(plan, (cufftDoubleComplex *)cg, (cufftDoubleReal *)rg));
+    }
   }
   return PSE_OK;
 }
@@ -255,32 +264,30 @@ pse_status fft(pse_ctx *c, bool forward, int batch, cudaStream_t s) {
 template <typename T>
 pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s) {
   WaveArgs a = wave_args(c);
-  const Params &p = c->p;
-  if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout, 0, sizeof(T) * 8 * (size_t)p.N, s));
+  if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout, 0, sizeof(T) * 8 * (size_t)c->p.N, s));
   int cin = mode == M_SE ? 5 : 8, cout = mode == M_FULL ? 8 : (mode == M_SE ? 5 : 3);
   {
     StageTimer timer(c, PSE_STAGE_SPREAD, s);
-    c->nlaunch += 1;
+    c->nlaunch += 2;  // counter reset + kernel
     spread_launch(c, a, vin, mode, s);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, true, cin, s));
-  ScaleArgs sa = scale_args(c, p.sigma() * p.sigma() / (p.V() * p.eta));
-  size_t nk = (size_t)p.Ng * p.Ng * p.nkx;
-  unsigned nb = (unsigned)ceil_div((int64_t)nk, 256);
+  ScaleArgs sa = scale_args(c);
+  unsigned nb = (unsigned)ceil_div(c->nk_tot, 256);
   using C2 = typename Cx<T>::t;
   {
     StageTimer timer(c, PSE_STAGE_SCALE, s);
     c->nlaunch += 1;
-    if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
-    else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
-    else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid, nk);
+    if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, false, cout, s));
   {
     StageTimer timer(c, PSE_STAGE_INTERP, s);
-    c->nlaunch += 1;
+    c->nlaunch += 2;
     interp_launch(c, a, vout, mode, s);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
@@ -289,23 +296,21 @@ pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool 
 
 template <typename T>
 pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t counter, void *vout, cudaStream_t s) {
-  const Params &p = c->p;
   WaveArgs a = wave_args(c);
-  ScaleArgs sa = scale_args(c, p.sigma() / std::sqrt(p.eta * p.V()));
-  size_t nk = (size_t)p.Ng * p.Ng * p.nkx;
-  unsigned nb = (unsigned)ceil_div((int64_t)nk, 256);
+  ScaleArgs sa = scale_args(c);
+  unsigned nb = (unsigned)ceil_div(c->nk_tot, 256);
   using C2 = typename Cx<T>::t;
   {
     StageTimer timer(c, PSE_STAGE_NOISE, s);
     c->nlaunch += 1;
-    if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, (C2 *)c->d_cgrid, nk);
-    else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, (C2 *)c->d_cgrid, nk);
+    if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, (C2 *)c->d_cgrid);
+    else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, (C2 *)c->d_cgrid);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, false, 8, s));
   {
     StageTimer timer(c, PSE_STAGE_INTERP, s);
-    c->nlaunch += 1;
+    c->nlaunch += 2;
     interp_launch(c, a, vout, M_FULL, s);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
@@ -313,6 +318,17 @@ pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t coun
 }
 
 }  // namespace
+
+WaveArgs wave_args(const pse_ctx *c) {
+  WaveArgs a;
+  a.P = c->p.P;
+  a.nsys = c->nsys;
+  a.ntiles = (int)c->ntiles;
+  a.sys = c->d_sys;
+  a.tile0 = c->d_tile0;
+  a.active = c->d_active;
+  return a;
+}
 
 pse_status wave_apply(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s) {
   return c->prec == PSE_MIXED ? wave_apply_t<float>(c, vin, vout, mode, add, s)

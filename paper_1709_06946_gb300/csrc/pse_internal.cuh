@@ -4,7 +4,9 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -56,26 +58,89 @@ bool tridiag_eigen(int n, std::vector<double> &d, std::vector<double> e, std::ve
 
 }  // namespace pse
 
+namespace pse {
+// Per-suspension constants of a handle (device copy in pse_ctx::d_sys).  A
+// handle holds nsys >= 1 independent suspensions; their particles, spreading
+// tiles, cells, half-spectrum points and vector blocks are concatenated, and
+// every kernel finds the suspension of its work item from the prefix tables
+// (d_p0, d_tile0, d_k0, d_blk0).
+struct SysDev {
+  int64_t p0;              // first particle (same range in user and sorted order)
+  int64_t nbr0;            // first neighbour slot
+  int64_t k0;              // first half-spectrum point of the concatenated spectra
+  int64_t grid0, gstride;  // real grid component c at grid0 + c * gstride (reals)
+  int64_t cgrid0, cstride; // half spectrum component c at cgrid0 + c * cstride (complex)
+  int N, Ng, nkx, nc, slots, tile0, cell0, blk0;
+  int T[3], nt[3];
+  double L, h, cs;
+  float Lf, csf;
+  double alpha, pref;      // spreading Gaussian exp(-alpha r^2) and its prefactor
+  double kfac, eta_g;      // 2 pi / L, Gaussian width
+  double c_apply, c_noise; // sigma^2/(V eta) and sigma/sqrt(eta V)
+};
+
+// Index s with start[s] <= x < start[s + 1] (start has n + 1 entries).
+template <typename I>
+__host__ __device__ __forceinline__ int find_sys(const I *start, int n, int64_t x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)start[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One cuFFT group: the suspensions with the same grid size, whose grids are
+// stored as [component][suspension][Ng^3] so that any leading set of
+// components of the whole group is one strided batch.
+struct FftGroup {
+  int Ng = 0, nsys = 0;
+  std::vector<int> members;           // suspensions of the group, in slot order
+  int64_t grid0 = 0, cgrid0 = 0;
+  cufftHandle r2c[9] = {0}, c2r[9] = {0};  // indexed by components per suspension
+  bool ok[2][9] = {{false}};
+};
+
+constexpr int VEC_CHUNK = 4096;    // vector elements per block of the chunked vector kernels
+constexpr int COEF_STRIDE = 512;   // doubles of Krylov coefficients per suspension
+}  // namespace pse
+
 // ---------------------------------------------------------------------------
 // Device-side state of a handle.
 struct pse_ctx {
-  pse::Params p;
+  pse::Params p;           // shared parameters; p.N = total particles (per-suspension values in ps)
   int prec;                // pse_precision
   size_t ts;               // sizeof real type (4 or 8)
   pse_options opt;
   int lanczos_max, krylov_max;
   double lanczos_tol, krylov_tol;
   std::string err;
-  int device = 0;
+  int device = 0, nsm = 0;
   int64_t dev_bytes = 0;
   std::vector<void *> allocs;
+
+  // suspensions
+  int nsys = 1;
+  std::vector<pse::Params> ps;     // per suspension (N, L, Ng, cells, tiles)
+  std::vector<pse::SysDev> hs;     // host copy of d_sys
+  pse::SysDev *d_sys = nullptr;
+  int64_t *d_p0 = nullptr, *d_k0 = nullptr;  // nsys + 1 prefix tables
+  int *d_tile0 = nullptr, *d_blk0 = nullptr; // nsys + 1 prefix tables
+  int *d_active = nullptr;                   // per suspension: 1 = take part in the next kernels
+  std::vector<int> h_active;
+  std::vector<pse::FftGroup> groups;
+  int64_t nk_tot = 0, nvblk = 0;             // half-spectrum points, vector blocks
+  std::vector<pse_stats> sys_stats;          // per suspension, last call
+  int *d_queue = nullptr;                    // work counters of the persistent kernels
+  int queue_slot = 0;
 
   // real-space table (device, real type), self terms
   void *d_table = nullptr;
   int table_len = 0, table_k2 = 0;
   double table_dr = 0, self_uf = 0, self_es = 0;
 
-  // configuration state (sorted order = by spreading tile)
+  // configuration state (sorted order = by suspension, then spreading tile)
   double *d_posw = nullptr;     // wrapped positions, user order, N x 3
   int *d_tile_key = nullptr, *d_cell_key = nullptr;
   int *d_perm = nullptr, *d_inv = nullptr;   // sorted -> user, user -> sorted
@@ -83,40 +148,39 @@ struct pse_ctx {
   int *d_cell_start = nullptr, *d_cell_cur = nullptr;   // ncells + 1
   int *d_cell_list = nullptr;
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
-  int *d_nbr = nullptr;         // neighbour slots: particle i owns [i*nbr_slots, (i+1)*nbr_slots)
-  int nbr_slots = 0;            // slots per particle
+  int *d_nbr = nullptr;         // neighbour slots: particle i of suspension s owns slots*(i-p0) + nbr0 ...
   int64_t nbr_cap = 0, npairs = 0;
-  unsigned long long *d_nbr_tot = nullptr;  // total pairs and maximum count
+  std::vector<int64_t> npairs_sys;
+  unsigned long long *d_nbr_tot = nullptr;  // per suspension: total pairs and maximum count
+  unsigned long long *h_nbr_tot = nullptr;  // pinned copy
   void *d_sp_i0 = nullptr;      // int4 per particle: wrapped support start
   void *d_sp_d0 = nullptr;      // real4: i0*h - x per dimension
   void *d_rs = nullptr;         // float4 (cell offset + packed cell) or double4_32a positions
   int *d_scan_tmp = nullptr;    // block sums for scans
   int64_t ntiles = 0, ncells = 0;
   int *d_flag = nullptr;        // device status word
-  int *h_pinned_int = nullptr;  // host pinned scratch
+  int *h_pinned_int = nullptr;  // host pinned scratch: 8 words, then active and row-count staging (2 x nsys)
 
   // grids
-  void *d_grid = nullptr;       // 8 x Ng^3 real
-  void *d_cgrid = nullptr;      // 8 x Ng^2 (Ng/2+1) complex
+  void *d_grid = nullptr;       // real grids of all suspensions (FftGroup layout)
+  void *d_cgrid = nullptr;      // half spectra, same layout
   void *d_fft_work = nullptr;
-  cufftHandle plan_r2c[9] = {0}, plan_c2r[9] = {0};  // indexed by batch size
-  bool plan_ok[9] = {false};
+  int64_t grid_elems = 0, cgrid_elems = 0;
 
   // particle vectors, sorted order, [N][8] real
   void *d_v[6] = {nullptr};
   void *d_B = nullptr;          // Brownian velocities, user order [N][8]
   void *d_basis = nullptr;      // Krylov basis (max+1) x 8N
-  double *d_dots = nullptr;     // partial / final dot products
-  double *d_coef = nullptr;     // coefficient vectors for combinations
-  double *h_dots = nullptr;     // pinned
-  int dots_blocks = 0;
+  double *d_dots = nullptr;     // per-block partial dot products
+  double *d_coef = nullptr;     // per suspension COEF_STRIDE doubles: dots and combination coefficients
+  double *h_dots = nullptr;     // pinned, nsys x COEF_STRIDE (device-to-host)
+  double *h_wbuf = nullptr;     // pinned, nsys x COEF_STRIDE (host-to-device)
+  bool h2d_pending = false;     // a host-to-device copy from pinned staging may still be queued
 
   double *d_pos0 = nullptr, *d_posh = nullptr;  // FP64 positions, user order
-  void *d_stage[4] = {nullptr}; // staging for host arrays
-  size_t stage_bytes[4] = {0};
-
-  cudaStream_t side = nullptr;  // second stream for the real-space sum
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void *d_stage[6] = {nullptr}; // staging for host arrays
+  size_t stage_bytes[6] = {0};
+  int *d_nrows = nullptr;       // per suspension: vectors in the final Krylov combination
 
   // profiling
   bool prof_on = false;
@@ -195,17 +259,41 @@ pse_status scatter_out(pse_ctx *c, const void *vin, void *U, void *E, double sca
 pse_status gather_user8(pse_ctx *c, const void *user8, void *vout, cudaStream_t s);
 pse_status scatter_user8(pse_ctx *c, const void *vin, void *user8, double scale, cudaStream_t s);
 pse_status philox_w1(pse_ctx *c, uint64_t seed, uint64_t counter, void *vout, cudaStream_t s);
-pse_status multidot(pse_ctx *c, const void *rows, int nrows, int64_t n, const void *w,
-                    double *d_out, cudaStream_t s);
-pse_status combine_sub(pse_ctx *c, void *w, const void *rows, int nrows, int64_t n,
-                       const double *d_coef, cudaStream_t s);
-pse_status combine_set(pse_ctx *c, void *y, const void *rows, int nrows, int64_t n,
-                       const double *d_coef, cudaStream_t s);
-pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int64_t n, cudaStream_t s);
+// Per-suspension Krylov helpers over [N][8] vectors; coefficients and results
+// live at d_coef + s * COEF_STRIDE + off for suspension s, and suspensions
+// with d_active[s] == 0 are skipped.
+pse_status multidot(pse_ctx *c, const void *rows, int nrows, const void *w, int off, cudaStream_t s);
+pse_status combine_sub(pse_ctx *c, void *w, const void *rows, int nrows, int off, cudaStream_t s);
+pse_status combine_set(pse_ctx *c, void *y, const void *rows, const int *d_nrows, int maxrows, int off,
+                       cudaStream_t s);
+// dst = a * src (a uniform) or dst = coef[s][off] * src per suspension when off >= 0.
+pse_status vscale(pse_ctx *c, void *dst, const void *src, double a, int off, cudaStream_t s);
 pse_status vzero_slots(pse_ctx *c, void *v, int slot0, int nslot, cudaStream_t s);
 pse_status midpoint(pse_ctx *c, const double *x0, const void *B_user, double fac, double *xout,
                     cudaStream_t s);
 pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const void *U_sorted,
                         double dt, double *xout, cudaStream_t s);
 pse_status check_finite(pse_ctx *c, const void *ptr, int64_t n, bool dbl, int *bad, cudaStream_t s);
+// Uploads h_active to d_active (api.cu).
+pse_status upload_active(pse_ctx *c, cudaStream_t s);
+// Work counter for the next persistent launch (cleared on stream s).
+int *next_queue(pse_ctx *c, cudaStream_t s);
+// Resident CTAs of a persistent kernel: SMs x blocks per SM (queried once into
+// per_sm, 0 on entry), at most `items`.
+template <typename K>
+unsigned persistent_grid(pse_ctx *c, K kern, int threads, size_t smem, int64_t items, std::atomic<int> &per_sm) {
+  int v = per_sm.load(std::memory_order_relaxed);
+  if (v <= 0) {
+    int q = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, kern, threads, smem) != cudaSuccess || q < 1) {
+      cudaGetLastError();
+      q = 1;
+    }
+    per_sm.store(q, std::memory_order_relaxed);
+    v = q;
+  }
+  int64_t g = (int64_t)v * c->nsm;
+  if (g > items) g = items;
+  return (unsigned)(g < 1 ? 1 : g);
+}
 }  // namespace pse

@@ -64,6 +64,18 @@ int next_grid(double x) {
   return n;
 }
 
+bool smooth23(int n) {
+  for (int f : {2, 3})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+// smallest even 2^i 3^j >= n
+int ladder_grid(int n) {
+  while (n % 2 || !smooth23(n)) ++n;
+  return n;
+}
+
 int pick_tile(int Ng, int minsize, int cap, bool prefer8) {
   int best = -1;
   for (int d = 1; d <= Ng; ++d) {
@@ -205,6 +217,7 @@ int choose_params(Params &p, const pse_options &opt, std::string &err) {
       if (eg < 1.0) break;
       p.Ng = next_grid(p.Ng + 1);
     }
+    if (opt.grid_ladder) p.Ng = ladder_grid(p.Ng);  // a finer grid only lowers the NUFFT error
   }
   p.h = p.L / p.Ng;
   p.eta_g = (p.h * p.P * p.xi / p.m) * (p.h * p.P * p.xi / p.m);

@@ -1,7 +1,7 @@
 // Spreading / interpolation kernels shared by wave_spread.cu and wave_interp.cu.
 //
-// Both kernels run one CTA per grid tile (Tx x Ty x Tz points) and keep the
-// tile in shared memory as [z][y][x][component] with the components padded to
+// Both kernels are persistent: each CTA takes grid tiles (Tx x Ty x Tz points)
+// of any suspension from a work counter and keeps the tile in shared memory as [z][y][x][component] with the components padded to
 // CP = 4 or 8 so that one lane moves four components with one vector access.
 // The CTA walks the particles of the 2x2x2 bins whose Gaussian supports can
 // reach the tile (bins hold particles by the grid index where their support
@@ -21,10 +21,12 @@ template <typename T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
 template <> struct Cx<double> { using t = double2; };
 
+// Launch-wide arguments; the per-suspension ones come from SysDev.
 struct WaveArgs {
-  int N, Ng, P;
-  int T[3], nt[3];
-  double h, alpha, pref;
+  int P, nsys, ntiles;
+  const SysDev *sys;
+  const int *tile0;   // nsys + 1 prefix of tiles
+  const int *active;
 };
 
 constexpr int WAVE_THREADS = 512;
@@ -46,7 +48,7 @@ __host__ __device__ inline size_t wave_smem(const int T3[3]) {
          (size_t)LIST_CAP * (sizeof(int4) + 4 * sizeof(T) + CP * sizeof(T) + 3 * WMAX * sizeof(T));
 }
 
-__device__ __forceinline__ void tile_of(const WaveArgs &a, int tile, int t[3], int t0[3]) {
+__device__ __forceinline__ void tile_of(const SysDev &a, int tile, int t[3], int t0[3]) {
   t[0] = tile % a.nt[0];
   t[1] = (tile / a.nt[0]) % a.nt[1];
   t[2] = tile / (a.nt[0] * a.nt[1]);
@@ -54,7 +56,7 @@ __device__ __forceinline__ void tile_of(const WaveArgs &a, int tile, int t[3], i
 }
 
 // The (up to) 8 source bins of a tile and the running offsets of their ranges.
-__device__ __forceinline__ int tile_bins(const WaveArgs &a, const int t[3], const int *tile_start, int beg[8],
+__device__ __forceinline__ int tile_bins(const SysDev &a, const int t[3], const int *tile_start, int beg[8],
                                          int cum[9]) {
   int nb = 0;
   int nz = a.nt[2] > 1 ? 2 : 1, ny = a.nt[1] > 1 ? 2 : 1, nx = a.nt[0] > 1 ? 2 : 1;
@@ -63,7 +65,7 @@ __device__ __forceinline__ int tile_bins(const WaveArgs &a, const int t[3], cons
     for (int by = 0; by < ny; ++by)
       for (int bx = 0; bx < nx; ++bx) {
         int z = wrapi(t[2] - bz, a.nt[2]), y = wrapi(t[1] - by, a.nt[1]), x = wrapi(t[0] - bx, a.nt[0]);
-        int b = (z * a.nt[1] + y) * a.nt[0] + x;
+        int b = a.tile0 + (z * a.nt[1] + y) * a.nt[0] + x;
         beg[nb] = tile_start[b];
         cum[nb + 1] = cum[nb] + (tile_start[b + 1] - tile_start[b]);
         ++nb;
@@ -76,12 +78,13 @@ __device__ __forceinline__ int tile_bins(const WaveArgs &a, const int t[3], cons
 // given, and the 3 x P one-dimensional Gaussian weights when P <= WMAX);
 // returns the number of entries (after a barrier).
 template <typename T, int C, int SLOT0>
-__device__ __forceinline__ int build_list(const WaveArgs &a, const int t0[3], int nb, const int beg[8], const int cum[9],
+__device__ __forceinline__ int build_list(const SysDev &a, int P, const int t0[3], int nb, const int beg[8],
+                                          const int cum[9],
                                           int c0, const int4 *__restrict__ sp_i0,
                                           const typename V4<T>::t *__restrict__ sp_d0, const T *__restrict__ vin,
                                           int4 *s_meta, typename V4<T>::t *s_d0, T *s_m, T *s_w, int *s_count) {
   constexpr int CP = CPad<C>::v;
-  const int Ng = a.Ng, P = a.P;
+  const int Ng = a.Ng;
   for (int q = threadIdx.x; q < LIST_CAP; q += blockDim.x) {
     int v = c0 + q;
     if (v >= cum[nb]) break;
@@ -118,12 +121,54 @@ __device__ __forceinline__ int build_list(const WaveArgs &a, const int t0[3], in
 }
 
 // launchers (wave_spread.cu / wave_interp.cu)
+WaveArgs wave_args(const pse_ctx *c);
 void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 
+// Largest shared memory of a spreading/interpolation CTA over the suspensions.
+template <typename T, int C>
+inline size_t wave_smem_max(const pse_ctx *c) {
+  size_t m = 0;
+  for (const SysDev &q : c->hs) {
+    size_t v = wave_smem<T, C>(q.T);
+    if (v > m) m = v;
+  }
+  return m;
+}
+
+// Persistent grid of a wave kernel for a given shared-memory size (occupancy
+// looked up once per kernel and size; handles on several threads share the cache).
+struct OccCache {
+  std::mutex mu;
+  size_t smem[8] = {0};
+  int per_sm[8] = {0};
+};
+
 template <typename K>
-inline void set_smem(K kern) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+inline unsigned wave_grid(pse_ctx *c, K kern, size_t smem, int items, OccCache &oc) {
+  std::atomic<int> v{0};
+  {
+    std::lock_guard<std::mutex> g(oc.mu);
+    for (int k = 0; k < 8; ++k)
+      if (oc.per_sm[k] > 0 && oc.smem[k] == smem) v.store(oc.per_sm[k]);
+  }
+  const bool known = v.load() > 0;
+  unsigned grid = persistent_grid(c, kern, WAVE_THREADS, smem, items, v);
+  if (!known) {
+    std::lock_guard<std::mutex> g(oc.mu);
+    for (int k = 0; k < 8; ++k)
+      if (oc.per_sm[k] <= 0) {
+        oc.smem[k] = smem;
+        oc.per_sm[k] = v.load();
+        break;
+      }
+  }
+  return grid;
+}
+
+template <typename K>
+inline void set_smem(K kern, std::once_flag &once) {
+  std::call_once(once, [&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
 }
 
 }  // namespace pse

@@ -1,6 +1,7 @@
 // Gaussian interpolation sigma Q^T (Sec. 2.3.2, Eq. WSops2).
 //
-// One CTA per grid tile: the tile is staged in shared memory ([z][y][x][comp],
+// Persistent CTAs take grid tiles (of any suspension) from a work counter: the
+// tile is staged in shared memory ([z][y][x][comp],
 // one coalesced pass over the component-major grids), then each warp takes a
 // particle overlapping the tile; lanes map to (x, y, component-half) items of
 // its footprint, loop over z in registers, and the partial sums are reduced
@@ -17,149 +18,154 @@ __device__ __forceinline__ void add_out(T *dst, T v) {
 }
 
 template <typename T, int C, int SLOT0, int PT>
-__global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs a, const int4 *__restrict__ sp_i0,
+__global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
                                                          const typename V4<T>::t *__restrict__ sp_d0,
                                                          const int *__restrict__ tile_start,
-                                                         const T *__restrict__ grid, T *__restrict__ vout) {
+                                                         const T *__restrict__ grid_all, T *__restrict__ vout) {
   constexpr int CP = CPad<C>::v, H = CP / 4;
   constexpr int NPASS = PT > 0 ? (PT * PT * H + 31) / 32 : 1;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int s_count;
-  const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
-  const int npts = Tz * Ty * RX;
-  T4 *tile = (T4 *)smem_raw;
-  int4 *s_meta = (int4 *)(tile + (size_t)npts * H);
-  T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
-  T *s_m = (T *)(s_d0 + LIST_CAP);
-  T *s_w = s_m + LIST_CAP * CP;
-  int t[3], t0[3], beg[8], cum[9];
-  tile_of(a, blockIdx.x, t, t0);
-  const int Ng = a.Ng;
-  const size_t n3 = (size_t)Ng * Ng * Ng;
-  const int tv = Tx * Ty * Tz;
-  for (int q = threadIdx.x; q < tv; q += blockDim.x) {
-    int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
-    size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
-    T *dst = (T *)(tile + ((size_t)(z * Ty + y) * RX + x) * H);
+  for_each_item(queue, wa.ntiles, [&](int item) {
+    const int si = find_sys(wa.tile0, wa.nsys, item);
+    if (!wa.active[si]) return;
+    const SysDev &a = wa.sys[si];
+    const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
+    const int npts = Tz * Ty * RX;
+    T4 *tile = (T4 *)smem_raw;
+    int4 *s_meta = (int4 *)(tile + (size_t)npts * H);
+    T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
+    T *s_m = (T *)(s_d0 + LIST_CAP);
+    T *s_w = s_m + LIST_CAP * CP;
+    int t[3], t0[3], beg[8], cum[9];
+    tile_of(a, item - a.tile0, t, t0);
+    const int Ng = a.Ng;
+    const T *grid = grid_all + a.grid0;
+    const int tv = Tx * Ty * Tz;
+    for (int q = threadIdx.x; q < tv; q += blockDim.x) {
+      int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
+      size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
+      T *dst = (T *)(tile + ((size_t)(z * Ty + y) * RX + x) * H);
 #pragma unroll
-    for (int c = 0; c < CP; ++c) dst[c] = c < C ? grid[c * n3 + g] : (T)0;
-  }
-  const int nb = tile_bins(a, t, tile_start, beg, cum);
-  const int P = PT > 0 ? PT : a.P, nitem = P * P * H;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
-  const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
-  const size_t zstride = (size_t)Ty * RX * H;
-  int pjx[NPASS], pjy[NPASS];
-  bool pok[NPASS];
-#pragma unroll
-  for (int ps = 0; ps < NPASS; ++ps) {
-    int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
-    pok[ps] = it < nitem;
-    pjx[ps] = pok[ps] ? q % P : 0;
-    pjy[ps] = pok[ps] ? q / P : 0;
-  }
-  for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();  // also orders the tile staging before the first use
-    const int n = build_list<T, C, SLOT0>(a, t0, nb, beg, cum, c0, sp_i0, sp_d0, (const T *)nullptr, s_meta, s_d0,
-                                          s_m, s_w, &s_count);
-    for (int e = warp; e < n; e += WAVE_WARPS) {
-      const int4 m4 = s_meta[e];
-      T4 acc;
-      acc.x = acc.y = acc.z = acc.w = (T)0;
-      if (PT > 0) {
-        const T *w = s_w + e * 3 * WMAX;
-        T wz[PT > 0 ? PT : 1];
-        int lzs[PT > 0 ? PT : 1];
-#pragma unroll
-        for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
-          int lz = m4.w + jz;
-          if (lz >= Ng) lz -= Ng;
-          lzs[jz] = lz < Tz ? lz : -1;
-          wz[jz] = w[2 * WMAX + jz];
-        }
-#pragma unroll
-        for (int ps = 0; ps < NPASS; ++ps) {
-          int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
-          if (lx >= Ng) lx -= Ng;
-          if (ly >= Ng) ly -= Ng;
-          if (pok[ps] && lx < Tx && ly < Ty) {
-            const T wxy = w[pjx[ps]] * w[WMAX + pjy[ps]];
-            const T4 *col = tile + ((size_t)ly * RX + lx) * H + hh;
-#pragma unroll
-            for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
-              if (lzs[jz] >= 0) {
-                const T wt = wxy * wz[jz];
-                const T4 v = col[lzs[jz] * zstride];
-                acc.x += wt * v.x;
-                acc.y += wt * v.y;
-                acc.z += wt * v.z;
-                acc.w += wt * v.w;
-              }
-            }
-          }
-        }
-      } else {  // any support size: weights on the fly
-        const T4 d0 = s_d0[e];
-        for (int base = 0; base < nitem; base += 32) {
-          const int it = base + lane;
-          const int q = H == 2 ? (it >> 1) : it;
-          const int jx = q % P, jy = q / P;
-          int lx = m4.y + jx, ly = m4.z + jy;
-          if (lx >= Ng) lx -= Ng;
-          if (ly >= Ng) ly -= Ng;
-          if (it < nitem && lx < Tx && ly < Ty) {
-            const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-            const T wxy = exp(-alpha * (dx * dx + dy * dy));
-            const T4 *col = tile + ((size_t)ly * RX + lx) * H + hh;
-            for (int jz = 0; jz < P; ++jz) {
-              int lz = m4.w + jz;
-              if (lz >= Ng) lz -= Ng;
-              if (lz < Tz) {
-                const T dz = d0.z + (T)jz * hs;
-                const T wt = wxy * exp(-alpha * dz * dz);
-                const T4 v = col[lz * zstride];
-                acc.x += wt * v.x;
-                acc.y += wt * v.y;
-                acc.z += wt * v.z;
-                acc.w += wt * v.w;
-              }
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int o = (H == 2 ? 2 : 1); o < 32; o <<= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
-      }
-      if (lane < H) {
-        T *o = vout + 8 * (size_t)m4.x + SLOT0 + 4 * lane;
-        const T vals[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (4 * lane + c < C) add_out(o + c, pref * vals[c]);
-      }
+      for (int c = 0; c < CP; ++c) dst[c] = c < C ? grid[c * a.gstride + g] : (T)0;
     }
-    __syncthreads();
-  }
+    const int nb = tile_bins(a, t, tile_start, beg, cum);
+    const int P = PT > 0 ? PT : wa.P, nitem = P * P * H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
+    const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
+    const size_t zstride = (size_t)Ty * RX * H;
+    int pjx[NPASS], pjy[NPASS];
+    bool pok[NPASS];
+#pragma unroll
+    for (int ps = 0; ps < NPASS; ++ps) {
+      int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
+      pok[ps] = it < nitem;
+      pjx[ps] = pok[ps] ? q % P : 0;
+      pjy[ps] = pok[ps] ? q / P : 0;
+    }
+    for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
+      if (threadIdx.x == 0) s_count = 0;
+      __syncthreads();  // also orders the tile staging before the first use
+      const int n = build_list<T, C, SLOT0>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, (const T *)nullptr, s_meta,
+                                            s_d0, s_m, s_w, &s_count);
+      for (int e = warp; e < n; e += WAVE_WARPS) {
+        const int4 m4 = s_meta[e];
+        T4 acc;
+        acc.x = acc.y = acc.z = acc.w = (T)0;
+        if (PT > 0) {
+          const T *w = s_w + e * 3 * WMAX;
+          T wz[PT > 0 ? PT : 1];
+          int lzs[PT > 0 ? PT : 1];
+#pragma unroll
+          for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
+            int lz = m4.w + jz;
+            if (lz >= Ng) lz -= Ng;
+            lzs[jz] = lz < Tz ? lz : -1;
+            wz[jz] = w[2 * WMAX + jz];
+          }
+#pragma unroll
+          for (int ps = 0; ps < NPASS; ++ps) {
+            int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
+            if (lx >= Ng) lx -= Ng;
+            if (ly >= Ng) ly -= Ng;
+            if (pok[ps] && lx < Tx && ly < Ty) {
+              const T wxy = w[pjx[ps]] * w[WMAX + pjy[ps]];
+              const T4 *col = tile + ((size_t)ly * RX + lx) * H + hh;
+#pragma unroll
+              for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
+                if (lzs[jz] >= 0) {
+                  const T wt = wxy * wz[jz];
+                  const T4 v = col[lzs[jz] * zstride];
+                  acc.x += wt * v.x;
+                  acc.y += wt * v.y;
+                  acc.z += wt * v.z;
+                  acc.w += wt * v.w;
+                }
+              }
+            }
+          }
+        } else {  // any support size: weights on the fly
+          const T4 d0 = s_d0[e];
+          for (int base = 0; base < nitem; base += 32) {
+            const int it = base + lane;
+            const int q = H == 2 ? (it >> 1) : it;
+            const int jx = q % P, jy = q / P;
+            int lx = m4.y + jx, ly = m4.z + jy;
+            if (lx >= Ng) lx -= Ng;
+            if (ly >= Ng) ly -= Ng;
+            if (it < nitem && lx < Tx && ly < Ty) {
+              const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
+              const T wxy = exp(-alpha * (dx * dx + dy * dy));
+              const T4 *col = tile + ((size_t)ly * RX + lx) * H + hh;
+              for (int jz = 0; jz < P; ++jz) {
+                int lz = m4.w + jz;
+                if (lz >= Ng) lz -= Ng;
+                if (lz < Tz) {
+                  const T dz = d0.z + (T)jz * hs;
+                  const T wt = wxy * exp(-alpha * dz * dz);
+                  const T4 v = col[lz * zstride];
+                  acc.x += wt * v.x;
+                  acc.y += wt * v.y;
+                  acc.z += wt * v.z;
+                  acc.w += wt * v.w;
+                }
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int o = (H == 2 ? 2 : 1); o < 32; o <<= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+          acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+          acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+        }
+        if (lane < H) {
+          T *o = vout + 8 * (size_t)m4.x + SLOT0 + 4 * lane;
+          const T vals[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (4 * lane + c < C) add_out(o + c, pref * vals[c]);
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();  // the staged tile is no longer read when the next item overwrites it
+  });
 }
 
 template <typename T, int C, int SLOT0, int PT>
 void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
-  static bool init = false;
+  static std::once_flag once;
+  static OccCache occ;
   auto kern = k_interp<T, C, SLOT0, PT>;
-  if (!init) {
-    set_smem(kern);
-    init = true;
-  }
-  size_t sm = wave_smem<T, C>(a.T);
-  kern<<<(unsigned)c->ntiles, WAVE_THREADS, sm, s>>>(a, (const int4 *)c->d_sp_i0,
-                                                      (const typename V4<T>::t *)c->d_sp_d0, c->d_tile_start,
-                                                      (const T *)c->d_grid, (T *)vout);
+  set_smem(kern, once);
+  size_t sm = wave_smem_max<T, C>(c);
+  unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ);
+  int *q = next_queue(c, s);
+  kern<<<grid, WAVE_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
+                                      c->d_tile_start, (const T *)c->d_grid, (T *)vout);
 }
 
 template <typename T, int C, int SLOT0>

@@ -1,6 +1,7 @@
 // Gaussian spreading Q (Sec. 2.3.2, Eq. WSops2).
 //
-// One CTA per output tile.  Warp w owns the tile's z-planes w, w + 8, ...; for
+// Persistent CTAs take output tiles (of any suspension) from a work counter.
+// Warp w owns the tile's z-planes w, w + 16, ...; for
 // every particle overlapping the tile it adds the particle's P x P footprint in
 // its plane to the shared tile with plain vector read-modify-writes (lanes map
 // to distinct (x, y, component-half) items, and no other warp touches the
@@ -13,135 +14,141 @@ namespace pse {
 namespace {
 
 template <typename T, int C, int SLOT0, int PT>
-__global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs a, const int4 *__restrict__ sp_i0,
+__global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
                                                          const typename V4<T>::t *__restrict__ sp_d0,
                                                          const T *__restrict__ vin, const int *__restrict__ tile_start,
-                                                         T *__restrict__ grid) {
+                                                         T *__restrict__ grid_all) {
   constexpr int CP = CPad<C>::v, H = CP / 4;
   constexpr int NPASS = PT > 0 ? (PT * PT * H + 31) / 32 : 1;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int s_count;
-  const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
-  const int npts = Tz * Ty * RX;
-  T4 *acc = (T4 *)smem_raw;
-  int4 *s_meta = (int4 *)(acc + (size_t)npts * H);
-  T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
-  T *s_m = (T *)(s_d0 + LIST_CAP);
-  T *s_w = s_m + LIST_CAP * CP;
-  T4 zero;
-  zero.x = zero.y = zero.z = zero.w = (T)0;
-  for (int q = threadIdx.x; q < npts * H; q += blockDim.x) acc[q] = zero;
-  int t[3], t0[3], beg[8], cum[9];
-  tile_of(a, blockIdx.x, t, t0);
-  const int nb = tile_bins(a, t, tile_start, beg, cum);
-  const int P = PT > 0 ? PT : a.P, Ng = a.Ng, nitem = P * P * H;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
-  const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
-  // this lane's (x, y) footprint item in every pass (fixed for the whole kernel)
-  int pjx[NPASS], pjy[NPASS];
-  bool pok[NPASS];
+  for_each_item(queue, wa.ntiles, [&](int item) {
+    const int si = find_sys(wa.tile0, wa.nsys, item);
+    if (!wa.active[si]) return;
+    const SysDev &a = wa.sys[si];
+    const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
+    const int npts = Tz * Ty * RX;
+    T4 *acc = (T4 *)smem_raw;
+    int4 *s_meta = (int4 *)(acc + (size_t)npts * H);
+    T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
+    T *s_m = (T *)(s_d0 + LIST_CAP);
+    T *s_w = s_m + LIST_CAP * CP;
+    T4 zero;
+    zero.x = zero.y = zero.z = zero.w = (T)0;
+    for (int q = threadIdx.x; q < npts * H; q += blockDim.x) acc[q] = zero;
+    __syncthreads();  // cleared before any update or (for a tile with no particles) the read-out
+    int t[3], t0[3], beg[8], cum[9];
+    tile_of(a, item - a.tile0, t, t0);
+    const int nb = tile_bins(a, t, tile_start, beg, cum);
+    const int P = PT > 0 ? PT : wa.P, Ng = a.Ng, nitem = P * P * H;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
+    const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
+    // this lane's (x, y) footprint item in every pass (fixed for the whole tile)
+    int pjx[NPASS], pjy[NPASS];
+    bool pok[NPASS];
 #pragma unroll
-  for (int ps = 0; ps < NPASS; ++ps) {
-    int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
-    pok[ps] = it < nitem;
-    pjx[ps] = pok[ps] ? q % P : 0;
-    pjy[ps] = pok[ps] ? q / P : 0;
-  }
-  for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
-    if (threadIdx.x == 0) s_count = 0;
-    __syncthreads();
-    const int n = build_list<T, C, SLOT0>(a, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m, s_w,
-                                          &s_count);
-    for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
-      // the warp finds the particles whose support crosses its plane 32 list entries at a time
-      for (int base = 0; base < n; base += 32) {
-        int jzl = P;
-        if (base + lane < n) {
-          jzl = lz - s_meta[base + lane].w;
-          if (jzl < 0) jzl += Ng;
-        }
-        unsigned hits = __ballot_sync(0xffffffffu, jzl < P);
-        while (hits) {
-          const int b = __ffs(hits) - 1;
-          hits &= hits - 1;
-          const int e = base + b;
-          const int jz = __shfl_sync(0xffffffffu, jzl, b);
-          const int4 m4 = s_meta[e];
-          const T4 mv = ((const T4 *)s_m)[e * H + hh];
-          T4 *plane = acc + (size_t)lz * Ty * RX * H;
-          if (PT > 0) {
-            const T *w = s_w + e * 3 * WMAX;
-            const T wz = pref * w[2 * WMAX + jz];
-#pragma unroll
-            for (int ps = 0; ps < NPASS; ++ps) {
-              int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
-              if (lx >= Ng) lx -= Ng;
-              if (ly >= Ng) ly -= Ng;
-              if (pok[ps] && lx < Tx && ly < Ty) {
-                const T wt = w[pjx[ps]] * w[WMAX + pjy[ps]] * wz;
-                T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
-                T4 v = *p;
-                v.x += wt * mv.x;
-                v.y += wt * mv.y;
-                v.z += wt * mv.z;
-                v.w += wt * mv.w;
-                *p = v;
-              }
-            }
-          } else {  // any support size: weights on the fly
-            const T4 d0 = s_d0[e];
-            const T dz = d0.z + (T)jz * hs;
-            const T wz = pref * exp(-alpha * dz * dz);
-            for (int ib = 0; ib < nitem; ib += 32) {
-              const int it = ib + lane;
-              const int q = H == 2 ? (it >> 1) : it;
-              const int jx = q % P, jy = q / P;
-              int lx = m4.y + jx, ly = m4.z + jy;
-              if (lx >= Ng) lx -= Ng;
-              if (ly >= Ng) ly -= Ng;
-              if (it < nitem && lx < Tx && ly < Ty) {
-                const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-                const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
-                T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
-                T4 v = *p;
-                v.x += wt * mv.x;
-                v.y += wt * mv.y;
-                v.z += wt * mv.z;
-                v.w += wt * mv.w;
-                *p = v;
-              }
-            }
+    for (int ps = 0; ps < NPASS; ++ps) {
+      int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
+      pok[ps] = it < nitem;
+      pjx[ps] = pok[ps] ? q % P : 0;
+      pjy[ps] = pok[ps] ? q / P : 0;
+    }
+    for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
+      if (threadIdx.x == 0) s_count = 0;
+      __syncthreads();
+      const int n = build_list<T, C, SLOT0>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m, s_w,
+                                            &s_count);
+      for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
+        // the warp finds the particles whose support crosses its plane 32 list entries at a time
+        for (int base = 0; base < n; base += 32) {
+          int jzl = P;
+          if (base + lane < n) {
+            jzl = lz - s_meta[base + lane].w;
+            if (jzl < 0) jzl += Ng;
           }
-          __syncwarp();  // the next particle may update the same points from other lanes
+          unsigned hits = __ballot_sync(0xffffffffu, jzl < P);
+          while (hits) {
+            const int b = __ffs(hits) - 1;
+            hits &= hits - 1;
+            const int e = base + b;
+            const int jz = __shfl_sync(0xffffffffu, jzl, b);
+            const int4 m4 = s_meta[e];
+            const T4 mv = ((const T4 *)s_m)[e * H + hh];
+            T4 *plane = acc + (size_t)lz * Ty * RX * H;
+            if (PT > 0) {
+              const T *w = s_w + e * 3 * WMAX;
+              const T wz = pref * w[2 * WMAX + jz];
+#pragma unroll
+              for (int ps = 0; ps < NPASS; ++ps) {
+                int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
+                if (lx >= Ng) lx -= Ng;
+                if (ly >= Ng) ly -= Ng;
+                if (pok[ps] && lx < Tx && ly < Ty) {
+                  const T wt = w[pjx[ps]] * w[WMAX + pjy[ps]] * wz;
+                  T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
+                  T4 v = *p;
+                  v.x += wt * mv.x;
+                  v.y += wt * mv.y;
+                  v.z += wt * mv.z;
+                  v.w += wt * mv.w;
+                  *p = v;
+                }
+              }
+            } else {  // any support size: weights on the fly
+              const T4 d0 = s_d0[e];
+              const T dz = d0.z + (T)jz * hs;
+              const T wz = pref * exp(-alpha * dz * dz);
+              for (int ib = 0; ib < nitem; ib += 32) {
+                const int it = ib + lane;
+                const int q = H == 2 ? (it >> 1) : it;
+                const int jx = q % P, jy = q / P;
+                int lx = m4.y + jx, ly = m4.z + jy;
+                if (lx >= Ng) lx -= Ng;
+                if (ly >= Ng) ly -= Ng;
+                if (it < nitem && lx < Tx && ly < Ty) {
+                  const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
+                  const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
+                  T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
+                  T4 v = *p;
+                  v.x += wt * mv.x;
+                  v.y += wt * mv.y;
+                  v.z += wt * mv.z;
+                  v.w += wt * mv.w;
+                  *p = v;
+                }
+              }
+            }
+            __syncwarp();  // the next particle may update the same points from other lanes
+          }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  const size_t n3 = (size_t)Ng * Ng * Ng;
-  const int tv = Tx * Ty * Tz;
-  for (int q = threadIdx.x; q < tv; q += blockDim.x) {
-    int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
-    size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
-    const T *src = (const T *)(acc + ((size_t)(z * Ty + y) * RX + x) * H);
+    T *grid = grid_all + a.grid0;
+    const int tv = Tx * Ty * Tz;
+    for (int q = threadIdx.x; q < tv; q += blockDim.x) {
+      int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
+      size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
+      const T *src = (const T *)(acc + ((size_t)(z * Ty + y) * RX + x) * H);
 #pragma unroll
-    for (int c = 0; c < C; ++c) grid[c * n3 + g] = src[c];
-  }
+      for (int c = 0; c < C; ++c) grid[c * a.gstride + g] = src[c];
+    }
+    __syncthreads();  // the tile is read out before the next item clears it
+  });
 }
 
 template <typename T, int C, int SLOT0, int PT>
 void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
-  static bool init = false;
+  static std::once_flag once;
+  static OccCache occ;
   auto kern = k_spread<T, C, SLOT0, PT>;
-  if (!init) {
-    set_smem(kern);
-    init = true;
-  }
-  size_t sm = wave_smem<T, C>(a.T);
-  kern<<<(unsigned)c->ntiles, WAVE_THREADS, sm, s>>>(a, (const int4 *)c->d_sp_i0,
-                                                      (const typename V4<T>::t *)c->d_sp_d0, (const T *)vin,
-                                                      c->d_tile_start, (T *)c->d_grid);
+  set_smem(kern, once);
+  size_t sm = wave_smem_max<T, C>(c);
+  unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ);
+  int *q = next_queue(c, s);
+  kern<<<grid, WAVE_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
+                                      (const T *)vin, c->d_tile_start, (T *)c->d_grid);
 }
 
 template <typename T, int C, int SLOT0>

@@ -6,8 +6,10 @@ stresslets, and standard-normal noise arrays in the layouts of the C ABI.
 Both the oracle side and the CUDA side of a test receive the same arrays.
 
 Workload recipe: a = eta = kT = 1, box L = (4 pi N / (3 phi))^{1/3},
-positions by RSA (valid for phi <= 0.35), forces and stresslet components
-(orthonormal basis) i.i.d. N(0, 1) from numpy's PCG64 with the given seed.
+positions by RSA for phi <= 0.35 and, above (RSA jams near phi = 0.38), by
+overlap removal from uniform centres followed by hard-sphere Monte Carlo
+sweeps; forces and stresslet components (orthonormal basis) i.i.d. N(0, 1)
+from numpy's PCG64 with the given seed.
 """
 import ctypes
 import math
@@ -38,6 +40,9 @@ def _load():
         lib.pse_rsa.restype = ctypes.c_int64
         lib.pse_rsa.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                 ctypes.c_int64, ctypes.c_void_p]
+        lib.pse_pack.restype = ctypes.c_int64
+        lib.pse_pack.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -55,6 +60,21 @@ def rsa_positions(N, phi, seed=1, a=1.0, L=None):
     if got != N:
         raise RuntimeError('RSA placed %d of %d spheres (phi too high for RSA?)' % (got, N))
     return pos, L
+
+
+def packed_positions(N, phi, seed=1, a=1.0, sweeps=100):
+    """Hard-sphere centres at densities RSA cannot reach: overlap removal from
+    uniform centres, then `sweeps` Monte Carlo sweeps.  Returns (pos, L)."""
+    L = box_length(N, phi, a)
+    pos = np.empty((N, 3), dtype=np.float64)
+    if _load().pse_pack(N, L, a, seed, sweeps, 20000, pos.ctypes.data) != 0:
+        raise RuntimeError('could not remove the overlaps at phi = %g' % phi)
+    return pos, L
+
+
+def hard_sphere_positions(N, phi, seed=1, a=1.0):
+    """RSA for phi <= 0.35, packed_positions above."""
+    return rsa_positions(N, phi, seed, a) if phi <= 0.35 else packed_positions(N, phi, seed, a)
 
 
 def random_positions(N, L, seed=1):

@@ -23,7 +23,7 @@ def lib():
 
 def test_exports_every_header_symbol(lib):
     hdr = open(os.path.join(ROOT, 'include', 'pse.h')).read()
-    names = set(re.findall(r'^(?:pse_status|void|const char)\s*\*?\s*(pse_[a-z_0-9]+)\s*\(', hdr, re.M))
+    names = set(re.findall(r'^(?:pse_status|void|const char|int32_t)\s*\*?\s*(pse_[a-z_0-9]+)\s*\(', hdr, re.M))
     assert len(names) >= 12
     for n in names:
         assert hasattr(lib, n), n
@@ -103,3 +103,50 @@ def test_tridiagonal_square_root(lib):
         T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
         w, Q = np.linalg.eigh(T)
         assert np.abs(c - Q @ (np.sqrt(w) * Q[0])).max() < 1e-13
+
+
+def test_batch_arguments_checked_on_host(lib):
+    """Batch creation checks every suspension before touching the device and
+    names the one that fails; the memory estimate needs no device."""
+    h = ctypes.c_void_p()
+    o = pkg.binding.Options()
+    lib.pse_default_options(ctypes.byref(o))
+    N = np.array([100, 10, 50], dtype=np.int64)
+    L = np.array([16.2, 9.0, 20.0])
+    assert lib.pse_create_batch(ctypes.byref(h), 3, N.ctypes.data, L.ctypes.data, 1.0, 1.0, 1.0, 0.5, 1e-3, 0,
+                                ctypes.byref(o)) == 1
+    assert b'suspension 1' in lib.pse_last_error(None)
+    assert lib.pse_create_batch(ctypes.byref(h), 0, N.ctypes.data, L.ctypes.data, 1.0, 1.0, 1.0, 0.5, 1e-3, 0,
+                                ctypes.byref(o)) == 1
+    assert lib.pse_num_systems(None) == 0
+
+
+def test_memory_estimate(lib):
+    est = pkg.binding.estimate_bytes
+    one = est(100000, 80.0, xi=0.5, tol=1e-3)
+    assert one > 100000 * 8 * 4 * 100          # at least the Krylov basis
+    assert est(200000, 100.8, xi=0.5, tol=1e-3) > 1.8 * one
+    assert est(100000, 80.0, xi=0.5, tol=1e-3, precision='fp64') > 1.5 * one   # reals double, indices do not
+    both = est([100000, 100000], [80.0, 80.0], xi=0.5, tol=1e-3)
+    assert abs(both - 2 * one) < 0.05 * one
+    with pytest.raises(pkg.PSEError):
+        est([100, 10], [16.2, 9.0])
+
+
+def test_grid_ladder_rounds_to_three_smooth(lib):
+    """With grid_ladder the grid is the next even 2^i 3^j size at or above the rule's grid."""
+    h = ctypes.c_void_p()
+    for L in (20.0, 37.0, 61.0, 118.0):
+        b0 = pkg.binding.estimate_bytes(1000, L, xi=0.5)
+        b1 = pkg.binding.estimate_bytes(1000, L, xi=0.5, grid_ladder=1)
+        assert b1 >= b0
+
+
+def test_server_needs_a_device(lib):
+    """Without a GPU the server refuses to start (CUDA error), it does not crash."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip('a device is present')
+    srv = ctypes.c_void_p()
+    assert lib.pse_server_create(ctypes.byref(srv), 2, 1 << 30) == 3
+    assert lib.pse_server_create(ctypes.byref(srv), 0, 1 << 30) == 1
