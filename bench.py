@@ -10,7 +10,19 @@ final product and position update (no work skipped).  Inputs (grids 0.9 GB,
 Krylov basis, particle data) exceed the 129 MB L2 between steps.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on the host cores instead (a bounded sample of the same workload).
+on the host cores instead (a bounded sample of the same workload).  The default
+line also carries a short serving measurement (`serving`: Poisson arrivals of
+mobility / sample / step requests through the serving loop).
+
+Other workloads (their own JSON line each):
+  --workload batch256  256 independent suspensions (N log-uniform in [500, 20000],
+                       phi uniform in [0.05, 0.45]) advanced by one batched
+                       constrained step per iteration;
+  --workload serve     the serving stream: Poisson arrivals of mobility / sample /
+                       step requests, N log-uniform in [1000, 200000], phi in
+                       {0.1, 0.25, 0.4}, eps in {1e-3, 1e-4}, state resident,
+                       admission by device-memory footprint; the arrival rate is
+                       swept until the completion rate saturates.
 """
 import argparse
 import json
@@ -45,6 +57,13 @@ def parse():
     ap.add_argument('--e2e-steps', type=int, default=3)
     ap.add_argument('--cpu-N', type=int, default=1000)
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--workload', default='step', choices=['step', 'batch256', 'serve'])
+    ap.add_argument('--serve-seconds', type=float, default=12.0, help='per arrival rate')
+    ap.add_argument('--serve-slots', type=int, default=4)
+    ap.add_argument('--serve-pool', type=int, default=8, help='distinct resident suspensions')
+    ap.add_argument('--serve-rates', default='', help='comma-separated arrival rates (req/s)')
+    ap.add_argument('--no-serving', action='store_true', help='omit the serving block of the default line')
+    ap.add_argument('--compare-sequential', action='store_true', help='batch256: also time one handle per suspension')
     return ap.parse_args()
 
 
@@ -309,14 +328,198 @@ def run_ours(args, world, rank, local, pg):
         result['fp64'] = {'steps_per_s': 1.0 / t64, 'ms_per_step': 1000.0 * t64,
                           'mixed_speedup': t64 / (elapsed / args.steps)}
         h64.close()
+    if rank == 0 and world == 1 and not args.no_serving:
+        res, desc = serving_measure(pkg, args, [8.0], 6, 200000, 10.0)
+        r = res[0]
+        result['serving'] = {'p50_ms': r['p50_ms'], 'p99_ms': r['p99_ms'], 'req_per_s': r['req_per_s'],
+                             'offered_rate': r['offered_rate'], 'requests': r['requests'],
+                             'peak_running': r['peak_running'], 'stream': desc}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result['cpu_baseline'] = cpu_baseline(args)
     if rank == 0:
         print(json.dumps(result), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving
+def serve_pool(M, seed, nmax=200000):
+    """M distinct suspensions of the serving stream (N log-uniform in [1000, nmax],
+    phi in {0.1, 0.25, 0.4}, eps in {1e-3, 1e-4}), with positions and moments."""
+    import pse_inputs
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k in range(M):
+        N = int(round(math.exp(rng.uniform(math.log(1000), math.log(nmax)))))
+        phi = float(rng.choice([0.1, 0.25, 0.4]))
+        tol = float(rng.choice([1e-3, 1e-4]))
+        pos, L = pse_inputs.hard_sphere_positions(N, phi, seed=1000 + k)
+        F, S = pse_inputs.moments(N, seed=2000 + k)
+        pool.append({'N': N, 'phi': phi, 'tol': tol, 'L': L, 'pos': pos, 'F': F.astype(np.float32),
+                     'S': S.astype(np.float32)})
+    return pool
+
+
+def serve_at_rate(pkg, srv, pool, rate, seconds, xi, dt, seed):
+    """Poisson arrivals at `rate` req/s for `seconds`; kinds and suspensions uniform."""
+    rng = np.random.default_rng(seed)
+    kinds = ['mobility', 'sample', 'step']
+    srv.reset_stats()
+    tickets = []
+    t_end = time.perf_counter() + seconds
+    t_next = time.perf_counter()
+    n = 0
+    while True:
+        t_next += rng.exponential(1.0 / rate)
+        if t_next > t_end:
+            break
+        d = t_next - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        q = pool[int(rng.integers(len(pool)))]
+        kind = kinds[int(rng.integers(3))]
+        if kind == 'mobility':
+            t, _ = srv.submit('mobility', q['pos'], q['L'], xi=xi, tol=q['tol'], F=q['F'], S=q['S'])
+        elif kind == 'sample':
+            t, _ = srv.submit('sample', q['pos'], q['L'], xi=xi, tol=q['tol'], dt=dt, seed=n)
+        else:
+            t, _ = srv.submit('step', q['pos'].copy(), q['L'], xi=xi, tol=q['tol'], dt=dt, seed=n, counter=n)
+        tickets.append(t)
+        n += 1
+    for t in tickets:
+        srv.wait(t)
+    st = srv.stats()
+    return {'offered_rate': rate, 'requests': len(tickets), 'req_per_s': st['requests_per_s'],
+            'p50_ms': st['p50_ms'], 'p99_ms': st['p99_ms'], 'wait_p50_ms': st['wait_p50_ms'],
+            'wait_p99_ms': st['wait_p99_ms'], 'service_p50_ms': st['service_p50_ms'],
+            'peak_running': st['peak_running'], 'peak_resident_gb': st['peak_resident_bytes'] / 1e9,
+            'handles_created': st['handles_created'], 'handles_evicted': st['handles_evicted']}
+
+
+def serving_measure(pkg, args, rates, pool_size, nmax, seconds):
+    pool = serve_pool(pool_size, seed=77, nmax=nmax)
+    budget = int(0.8 * 280e9)
+    srv = pkg.Server(slots=args.serve_slots, budget_bytes=budget)
+    # make every suspension resident once (tables, plans, grids); not timed
+    warm = [srv.submit('mobility', q['pos'], q['L'], xi=args.xi, tol=q['tol'], F=q['F'], S=q['S'])[0] for q in pool]
+    for t in warm:
+        srv.wait(t)
+    out = []
+    for k, r in enumerate(rates):
+        res = serve_at_rate(pkg, srv, pool, r, seconds, args.xi, args.dt, seed=k)
+        out.append(res)
+        if res['req_per_s'] < 0.8 * r:          # saturated: completions no longer track arrivals
+            break
+    srv.close()
+    desc = ('%d resident suspensions, N log-uniform in [1000, %d] (N = %s), phi in {0.1, 0.25, 0.4}, '
+            'eps in {1e-3, 1e-4}, kinds mobility/sample/step uniform, %d slots, budget %.0f GB'
+            % (pool_size, nmax, sorted(q['N'] for q in pool), args.serve_slots, budget / 1e9))
+    return out, desc
+
+
+def run_serve(args):
+    import paper_1709_06946_gb300 as pkg
+    pkg.load()
+    rates = [float(r) for r in args.serve_rates.split(',')] if args.serve_rates else [2, 5, 10, 20, 40, 80, 160]
+    clocks = ClockSampler(0)
+    clocks.start()
+    res, desc = serving_measure(pkg, args, rates, max(args.serve_pool, 1), 200000, args.serve_seconds)
+    clk = clocks.stop()
+    best = max(res, key=lambda r: r['req_per_s'])
+    line = {'metric': 'served requests/s and p50/p99 latency (mobility/sample/step stream)',
+            'value': best['req_per_s'], 'unit': 'requests/s', 'n_gpus': 1, 'steps': len(res), 'warmup': 1,
+            'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
+            'config': {'workload': 'serving stream: ' + desc, 'seconds_per_rate': args.serve_seconds},
+            'p50_ms': best['p50_ms'], 'p99_ms': best['p99_ms'], 'sweep': res, 'clocks': clk}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- batch of suspensions
+def batch_suspensions(n, seed):
+    import pse_inputs
+    rng = np.random.default_rng(seed)
+    Ns, phis, pos, Ls = [], [], [], []
+    for k in range(n):
+        N = int(round(math.exp(rng.uniform(math.log(500), math.log(20000)))))
+        phi = float(rng.uniform(0.05, 0.45))
+        x, L = pse_inputs.hard_sphere_positions(N, phi, seed=5000 + k)
+        Ns.append(N)
+        phis.append(phi)
+        pos.append(x)
+        Ls.append(L)
+    return Ns, phis, pos, Ls
+
+
+def run_batch(args):
+    import torch
+    import paper_1709_06946_gb300 as pkg
+    pkg.load()
+    dev = torch.device('cuda', 0)
+    nsys = 256
+    Ns, phis, pos, Ls = batch_suspensions(nsys, seed=4)
+    h = pkg.PSE(Ns, Ls, xi=args.xi, tol=args.tol, precision='mixed', grid_ladder=1)
+    x = torch.tensor(np.concatenate(pos), device=dev, dtype=torch.float64)
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        h.step(x, args.dt, seed=11, step=k)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    h.set_profiling(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    iters = []
+    ev0.record(stream)
+    for k in range(args.steps):
+        _, st = h.step(x, args.dt, seed=11, step=args.warmup + k)
+        iters.append([(h.system_stats(s)['lanczos_iters'], h.system_stats(s)['krylov_iters']) for s in range(nsys)])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    clk = clocks.stop()
+    prof = h.profile()
+    grids = sorted({h.system_info(s)['Ng'] for s in range(nsys)})
+    it = np.array(iters)
+    value = args.steps / elapsed
+    line = {'metric': 'batched constrained steps/s (256 suspensions, one handle)', 'value': value,
+            'unit': 'batch steps/s', 'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup,
+            'ms_per_step': 1000.0 * elapsed / args.steps, 'higher_is_better': True, 'scaling': 'weak',
+            'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
+            'config': {'workload': '256 suspensions, N log-uniform in [500, 20000] (total %d), phi uniform in '
+                                   '[0.05, 0.45], eps=%g, xi=%g, grids rounded to 2^i 3^j (%d FFT groups)'
+                                   % (sum(Ns), args.tol, args.xi, len(grids)),
+                       'total_N': int(sum(Ns)), 'grids': grids},
+            'suspension_steps_per_s': nsys * value, 'ptps': sum(Ns) * value,
+            'iterations': {'lanczos_min': int(it[..., 0].min()), 'lanczos_max': int(it[..., 0].max()),
+                           'krylov_min': int(it[..., 1].min()), 'krylov_max': int(it[..., 1].max())},
+            'stage_ms_per_step': {k: v / args.steps for k, v in prof['ms'].items()},
+            'gpu_launches_per_step': prof['launches'] / args.steps, 'fft_execs_per_step': prof['fft_execs'] / args.steps,
+            'clocks': clk}
+    h.set_profiling(False)
+    h.close()
+    if args.compare_sequential:
+        hs = [pkg.PSE(Ns[s], Ls[s], xi=args.xi, tol=args.tol, precision='mixed') for s in range(nsys)]
+        xs = [torch.tensor(pos[s], device=dev, dtype=torch.float64) for s in range(nsys)]
+        for s in range(nsys):
+            hs[s].step(xs[s], args.dt, seed=11, step=0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for s in range(nsys):
+            hs[s].step(xs[s], args.dt, seed=11, step=1)
+        torch.cuda.synchronize(dev)
+        tseq = time.perf_counter() - t0
+        line['sequential_handles'] = {'s_per_round': tseq, 'batch_speedup': tseq / (elapsed / args.steps)}
+        for hh in hs:
+            hh.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload != 'step':
+        if args.impl == 'reference':
+            print(json.dumps({'impl': 'reference', 'unavailable': 'the oracle arm covers the N=1M step workload only'}))
+            return
+        run_batch(args) if args.workload == 'batch256' else run_serve(args)
+        return
     world, rank, local, pg = dist_setup(args)
     if args.impl == 'reference':
         run_reference(args, world, rank, pg)

@@ -320,6 +320,26 @@ pse_status pse_server_reset_stats(pse_server *srv);
  * frees every resident handle. */
 pse_status pse_server_destroy(pse_server *srv);
 
+/* Autotuner (no counterpart in the paper).  Times, on the configuration pos and
+ * the handle's own stream, `reps` calls of each candidate: lanes per particle of
+ * the pair sum (1, 4, 8, 16, 32; the S -> E plus the full product) and spreading
+ * tile caps (x, y, z) in {16,8,16}, {8,8,16}, {16,16,16}, {8,16,16}, {16,8,32},
+ * {8,8,32}, {32,8,16} (the S -> E wave product; each suspension's tile is the
+ * largest shape within the caps that divides its grid and fits shared memory),
+ * and keeps the fastest of each.  Waits for the device.  The choice persists for
+ * the handle's later calls; out (may be NULL) reports it and every timing. */
+typedef struct pse_tuning {
+  int32_t real_lanes;
+  int32_t tile[3];            /* chosen tile of suspension 0 */
+  double best_real_ms, best_wave_ms;
+  int32_t n_lanes, n_tiles;   /* candidates timed */
+  double real_ms[8];          /* per lanes candidate 1, 4, 8, 16, 32 */
+  int32_t tiles[8][3];        /* distinct tile candidates (suspension 0) */
+  double wave_ms[8];
+} pse_tuning;
+
+pse_status pse_autotune(pse_handle h, const double *pos, int32_t reps, pse_tuning *out, pse_stream stream);
+
 /* Enables (1) or disables (0) stage timing and resets the profile and the
  * launch counters.  Timing adds two event records per stage section. */
 pse_status pse_set_profiling(pse_handle h, int32_t enable);

@@ -87,6 +87,12 @@ class ServerStats(ctypes.Structure):
 
 REQ_KINDS = {'mobility': 0, 'sample': 1, 'step': 2}
 
+
+class Tuning(ctypes.Structure):
+    _fields_ = [('real_lanes', ctypes.c_int32), ('tile', ctypes.c_int32 * 3), ('best_real_ms', ctypes.c_double),
+                ('best_wave_ms', ctypes.c_double), ('n_lanes', ctypes.c_int32), ('n_tiles', ctypes.c_int32),
+                ('real_ms', ctypes.c_double * 8), ('tiles', (ctypes.c_int32 * 3) * 8), ('wave_ms', ctypes.c_double * 8)]
+
 # (name, restype, argtypes) of every symbol declared in include/pse.h
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -118,6 +124,7 @@ SIGNATURES = [
     ('pse_server_get_stats', ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     ('pse_server_reset_stats', ctypes.c_int, [_P]),
     ('pse_server_destroy', ctypes.c_int, [_P]),
+    ('pse_autotune', ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(Tuning), _P]),
     ('pse_set_profiling', ctypes.c_int, [_P, ctypes.c_int32]),
     ('pse_get_profile', ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     ('pse_stage_name', ctypes.c_char_p, [ctypes.c_int32]),
@@ -341,6 +348,16 @@ class PSE:
         d = stats.as_dict()
         d['status'] = st
         return S, d
+
+    def autotune(self, pos, reps=3):
+        """Times the pair-sum lanes and spreading-tile candidates on `pos` and keeps the fastest."""
+        t = Tuning()
+        self._check(self._lib.pse_autotune(self._h, _ptr(pos), int(reps), ctypes.byref(t), _stream(pos)))
+        self.info = self.get_info()
+        lanes = [1, 4, 8, 16, 32][:t.n_lanes]
+        return {'real_lanes': t.real_lanes, 'tile': tuple(t.tile), 'best_real_ms': t.best_real_ms,
+                'best_wave_ms': t.best_wave_ms, 'real_ms': dict(zip(lanes, list(t.real_ms)[:t.n_lanes])),
+                'wave_ms': {tuple(t.tiles[k]): t.wave_ms[k] for k in range(t.n_tiles)}}
 
     def set_profiling(self, enable=True):
         self._check(self._lib.pse_set_profiling(self._h, 1 if enable else 0))

@@ -693,7 +693,9 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_sp_d0 = A(4 * ts * N);
   c->d_rs = A(4 * ts * N);
   int64_t big = std::max<int64_t>(std::max<int64_t>(c->ntiles, c->ncells), N) + 1;
-  c->d_scan_tmp = (int *)A(sizeof(int) * (size_t)scan_tmp_ints(big));
+  c->scan_cap = scan_tmp_ints(big);
+  c->tile_cap = c->ntiles;
+  c->d_scan_tmp = (int *)A(sizeof(int) * (size_t)c->scan_cap);
   c->d_flag = (int *)A(sizeof(int) * 4);
   c->d_grid = A(ts * (size_t)c->grid_elems);
   c->d_cgrid = A(2 * ts * (size_t)c->cgrid_elems);
@@ -802,6 +804,136 @@ void destroy_impl(pse_ctx *c) {
   if (c->h_pinned_int) cudaFreeHost(c->h_pinned_int);
   if (c->h_nbr_tot) cudaFreeHost(c->h_nbr_tot);
   c->allocs.clear();
+}
+
+// Re-tiles every suspension with the tile caps (x, y, z); the tile arrays grow if needed.
+pse_status retile(pse_ctx *c, const int caps[3]) {
+  std::vector<Params> ps = c->ps;
+  std::vector<int> tile0(c->nsys + 1, 0);
+  for (int q = 0; q < c->nsys; ++q) {
+    std::string e;
+    if (choose_tile(ps[q], caps, c->opt.tile, e)) {
+      c->err = e;
+      return PSE_ERR_INVALID_ARG;
+    }
+    tile0[q + 1] = tile0[q] + ps[q].ntile[0] * ps[q].ntile[1] * ps[q].ntile[2];
+  }
+  const int64_t nt = tile0[c->nsys];
+  if (nt > c->tile_cap) {
+    void *a = dalloc(c, sizeof(int) * (size_t)(nt + 1)), *b = dalloc(c, sizeof(int) * (size_t)(nt + 1));
+    if (!a || !b) {
+      c->err = "cannot allocate tile arrays";
+      return PSE_ERR_OOM;
+    }
+    c->d_tile_start = (int *)a;
+    c->d_tile_cur = (int *)b;
+    c->tile_cap = nt;
+  }
+  int64_t need = scan_tmp_ints(std::max<int64_t>(std::max<int64_t>(nt, c->ncells), c->p.N) + 1);
+  if (need > c->scan_cap) {
+    void *q = dalloc(c, sizeof(int) * (size_t)need);
+    if (!q) {
+      c->err = "cannot allocate scan scratch";
+      return PSE_ERR_OOM;
+    }
+    c->d_scan_tmp = (int *)q;
+    c->scan_cap = need;
+  }
+  c->ps = ps;
+  for (int q = 0; q < c->nsys; ++q) {
+    for (int d = 0; d < 3; ++d) {
+      c->hs[q].T[d] = ps[q].tile[d];
+      c->hs[q].nt[d] = ps[q].ntile[d];
+    }
+    c->hs[q].tile0 = tile0[q];
+  }
+  c->ntiles = nt;
+  for (int d = 0; d < 3; ++d) {
+    c->p.tile[d] = ps[0].tile[d];
+    c->p.ntile[d] = ps[0].ntile[d];
+  }
+  PSE_CUDA_TRY(c, cudaDeviceSynchronize());
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_sys, c->hs.data(), sizeof(SysDev) * c->nsys, cudaMemcpyHostToDevice));
+  PSE_CUDA_TRY(c, cudaMemcpy(c->d_tile0, tile0.data(), sizeof(int) * (c->nsys + 1), cudaMemcpyHostToDevice));
+  return PSE_OK;
+}
+
+// Mean device time (ms) of `reps` calls of f on stream s after one untimed call.
+template <typename F>
+pse_status time_ms(pse_ctx *c, cudaStream_t s, int reps, F &&f, double *ms) {
+  PSE_TRY(f());
+  cudaEvent_t a, b;
+  PSE_CUDA_TRY(c, cudaEventCreate(&a));
+  PSE_CUDA_TRY(c, cudaEventCreate(&b));
+  PSE_CUDA_TRY(c, cudaEventRecord(a, s));
+  for (int k = 0; k < reps; ++k) PSE_TRY(f());
+  PSE_CUDA_TRY(c, cudaEventRecord(b, s));
+  PSE_CUDA_TRY(c, cudaEventSynchronize(b));
+  float t = 0.f;
+  PSE_CUDA_TRY(c, cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t / reps;
+  return PSE_OK;
+}
+
+pse_status autotune_impl(pse_ctx *c, const double *pos, int reps, pse_tuning *out, cudaStream_t s) {
+  void *dpos;
+  PSE_TRY(set_all_active(c, s));
+  PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * c->p.N, true, s, &dpos));
+  PSE_TRY(setup_config(c, (const double *)dpos, s));
+  PSE_TRY(philox_w1(c, 1, 1, c->d_v[0], s));  // any dense vector will do
+  pse_tuning t{};
+  // lanes per particle of the pair sum: the S -> E product of the GMRES loop plus the full product
+  const int lanes[5] = {1, 4, 8, 16, 32};
+  double best = INFINITY;
+  int bestg = c->opt.real_lanes;
+  for (int g : lanes) {
+    c->opt.real_lanes = g;
+    double ms = 0;
+    PSE_TRY(time_ms(c, s, reps, [&] {
+      pse_status a = real_apply(c, c->d_v[0], c->d_v[1], M_SE, s);
+      return a != PSE_OK ? a : real_apply(c, c->d_v[0], c->d_v[2], M_FULL, s);
+    }, &ms));
+    t.real_ms[t.n_lanes++] = ms;
+    if (ms < best) {
+      best = ms;
+      bestg = g;
+    }
+  }
+  c->opt.real_lanes = bestg;
+  t.real_lanes = bestg;
+  // spreading / interpolation tiles: candidate caps, timed on the S -> E wave product
+  const int cand[][3] = {{16, 8, 16}, {8, 8, 16}, {16, 16, 16}, {8, 16, 16}, {16, 8, 32}, {8, 8, 32}, {32, 8, 16}};
+  std::vector<std::vector<int>> seen;
+  double bw = INFINITY;
+  int bi = 0;
+  for (int k = 0; k < (int)(sizeof(cand) / sizeof(cand[0])); ++k) {
+    PSE_TRY(retile(c, cand[k]));
+    std::vector<int> sig;
+    for (const Params &q : c->ps) sig.insert(sig.end(), q.tile, q.tile + 3);
+    if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+    seen.push_back(sig);
+    PSE_TRY(setup_config(c, (const double *)dpos, s));
+    double ms = 0;
+    PSE_TRY(time_ms(c, s, reps, [&] { return wave_apply(c, c->d_v[0], c->d_v[1], M_SE, false, s); }, &ms));
+    if (t.n_tiles < 8) {
+      for (int d = 0; d < 3; ++d) t.tiles[t.n_tiles][d] = c->ps[0].tile[d];
+      t.wave_ms[t.n_tiles++] = ms;
+    }
+    if (ms < bw) {
+      bw = ms;
+      bi = k;
+    }
+  }
+  PSE_TRY(retile(c, cand[bi]));
+  PSE_TRY(setup_config(c, (const double *)dpos, s));
+  for (int d = 0; d < 3; ++d) t.tile[d] = c->ps[0].tile[d];
+  t.best_real_ms = best;
+  t.best_wave_ms = bw;
+  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (out) *out = t;
+  return PSE_OK;
 }
 
 pse_ctx *new_ctx(pse_precision prec, const pse_options &o, double a, double eta, double kT, double xi, double tol) {
@@ -1017,6 +1149,11 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
                                       const void *w2, void *S_out, pse_stats *stats, pse_stream stream) {
   if (!h || !w1 || !w2) return PSE_ERR_INVALID_ARG;
   return step_impl(h, pos, FP, dt, w1, w2, 0, 0, S_out, stats, (cudaStream_t)stream);
+}
+
+pse_status pse_autotune(pse_handle h, const double *pos, int32_t reps, pse_tuning *out, pse_stream stream) {
+  if (!h || !pos || reps < 1 || reps > 100) return PSE_ERR_INVALID_ARG;
+  return autotune_impl(h, pos, reps, out, (cudaStream_t)stream);
 }
 
 pse_status pse_set_profiling(pse_handle h, int32_t enable) {

@@ -32,6 +32,8 @@ struct Params {
 
 // Host-side parameter rules (Sec. 2.3.1 real-space cutoff, Eq. bound support size).
 int choose_params(Params &p, const pse_options &opt, std::string &err);
+// Spreading tile within caps (fixed[d] > 0 overrides dimension d); sets tile and ntile.
+int choose_tile(Params &p, const int caps[3], const int fixed[3], std::string &err);
 
 // Real-space scalar functions tabulated on r = i * dr, i = 0 .. len-1 (dr divides 2a).
 // Per node 8 values: fperp, fpar, gS, gR, kS, kX, kR, 0 (see tables.cpp for meaning).
@@ -158,6 +160,7 @@ struct pse_ctx {
   void *d_rs = nullptr;         // float4 (cell offset + packed cell) or double4_32a positions
   int *d_scan_tmp = nullptr;    // block sums for scans
   int64_t ntiles = 0, ncells = 0;
+  int64_t tile_cap = 0, scan_cap = 0;  // allocated tile-array and scan-scratch capacities
   int *d_flag = nullptr;        // device status word
   int *h_pinned_int = nullptr;  // host pinned scratch: 8 words, then active and row-count staging (2 x nsys)
 
