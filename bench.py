@@ -64,7 +64,25 @@ def parse():
     ap.add_argument('--serve-rates', default='', help='comma-separated arrival rates (req/s)')
     ap.add_argument('--no-serving', action='store_true', help='omit the serving block of the default line')
     ap.add_argument('--compare-sequential', action='store_true', help='batch256: also time one handle per suspension')
+    ap.add_argument('--graph', type=int, default=1, help='1: time the graph-captured step (default)')
+    ap.add_argument('--profile-steps', type=int, default=3, help='host-launched steps timed per stage')
+    ap.add_argument('--no-accuracy', action='store_true', help='omit the mixed-vs-FP64 error per output')
     return ap.parse_args()
+
+
+def max_over_ranks(x, pg, device):
+    """Largest x over the ranks (x itself on one process)."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world, steps, elapsed_max):
+    """Whole-job rate of independent replicas: the steps of all ranks over the slowest rank's time."""
+    return world * steps / elapsed_max
 
 
 def dist_setup(args):
@@ -187,6 +205,44 @@ def run_reference(args, world, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+def accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64):
+    """Relative L2 error of the mixed form against the all-FP64 form on the same
+    seeded inputs and the same external noise: mobility U and E, Brownian U^B and
+    E^B, one constrained step's displacement and stresslets; GMRES residuals."""
+    hm = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed')
+    N, Ng = args.N, hm.info['Ng']
+    g = torch.Generator(device=dev).manual_seed(3)
+    F = torch.randn((N, 3), generator=g, device=dev, dtype=torch.float64)
+    S = torch.randn((N, 5), generator=g, device=dev, dtype=torch.float64)
+    w1 = torch.randn((N, 8), generator=g, device=dev, dtype=torch.float64)
+    w2 = torch.randn((6 * Ng * Ng * (Ng // 2 + 1),), generator=g, device=dev, dtype=torch.float64)
+    x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+
+    def rel(a, b):
+        return float(torch.linalg.norm(a.double() - b) / torch.linalg.norm(b))
+    out = {}
+    U64, E64 = h64.mobility(x, F, S)
+    U32, E32 = hm.mobility(x, F.float(), S.float())
+    out['mobility_U'], out['mobility_E'] = rel(U32, U64), rel(E32, E64)
+    U64, E64, _ = h64.brownian(x, args.dt, w1=w1, w2=w2)
+    U32, E32, _ = hm.brownian(x, args.dt, w1=w1.float(), w2=w2.float())
+    out['brownian_U'], out['brownian_E'] = rel(U32, U64), rel(E32, E64)
+    x64, x32 = x.clone(), x.clone()
+    S64, st64 = h64.step(x64, args.dt, w1=w1, w2=w2, want_S=True)
+    S32, st32 = hm.step(x32, args.dt, w1=w1.float(), w2=w2.float(), want_S=True)
+    d64 = x64 - x
+    d32 = x32 - x
+    d64 -= L * torch.round(d64 / L)
+    d32 -= L * torch.round(d32 / L)
+    out['step_displacement'] = rel(d32, d64)
+    out['step_stresslet'] = rel(S32, S64)
+    out['gmres_relres'] = {'mixed': st32['krylov_relres'], 'fp64': st64['krylov_relres'],
+                           'iterations_mixed': st32['krylov_iters'], 'iterations_fp64': st64['krylov_iters']}
+    out['note'] = 'relative L2 over all particles, N=%d, same positions, moments and external noise' % N
+    hm.close()
+    return out
+
+
 def real_flops_per_pair():
     # FP32 operations of the pair kernel per neighbour, counted from its formulas (FMA = 2):
     # full 8->8 product (Lanczos), S->E (GMRES), [F;S]->U (final velocity).
@@ -202,19 +258,18 @@ def run_ours(args, world, rank, local, pg):
     dev = torch.device('cuda', local)
     torch.cuda.set_device(dev)
     pos_np, L = pse_inputs.rsa_positions(args.N, args.phi, seed=1 + rank)
-    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed')
+    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', use_graph=args.graph)
     inf = h.info
     x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
     stream = torch.cuda.current_stream(dev)
-    st_last = {}
     for k in range(args.warmup):
-        _, st_last = h.step(x, args.dt, seed=1234 + rank, step=k)
+        h.step(x, args.dt, seed=1234 + rank, step=k)
     torch.cuda.synchronize(dev)
+    graph_used = h.graph_ready()
     if pg is not None:
         pg.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    h.set_profiling(True)
     torch.cuda.synchronize(dev)
     if pg is not None:
         pg.barrier()
@@ -232,26 +287,37 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize(dev)
     if pg is not None:
         pg.barrier()
-    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1000.0, pg, dev)
     clk = clocks.stop()
+    value = replica_rate(world, args.steps, elapsed)
+
+    # per-stage device times: the same steps launched from the host with stage events
+    # (a captured graph cannot hold the events); also gives the kernel count per step
+    KP = max(1, args.profile_steps)
+    h.set_profiling(True)
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    piters = []
+    pe0.record(stream)
+    for k in range(KP):
+        _, st = h.step(x, args.dt, seed=1234 + rank, step=args.warmup + args.steps + k)
+        piters.append((st['lanczos_iters'], st['krylov_iters'], st['neighbor_pairs']))
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof_elapsed = pe0.elapsed_time(pe1) / 1000.0
     prof = h.profile()
     h.set_profiling(False)
-    if pg is not None:
-        t = torch.tensor([elapsed], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * args.steps / elapsed
 
     # roofline of the dominant stage (device time per stage from CUDA events on the launching stream)
     peaks = measured_peaks()
     stage_ms = prof['ms']
-    Li = sum(i[0] for i in iters)
-    Ki = sum(i[1] for i in iters)
-    npairs = float(np.mean([i[2] for i in iters]))
+    Li = sum(i[0] for i in piters)
+    Ki = sum(i[1] for i in piters)
+    npairs = float(np.mean([i[2] for i in piters]))
     Ng, N = inf['Ng'], args.N
     n3 = Ng ** 3
     nkh = Ng * Ng * (Ng // 2 + 1)
-    K = args.steps
+    K = KP
     # per step: GMRES products (5 -> 5) Ki/K times, one final [F;S] -> U product, one noise pass
     spread_comps = [5] * Ki + [8] * K
     interp_comps = [5] * Ki + [3] * K + [8] * K
@@ -291,13 +357,23 @@ def run_ours(args, world, rank, local, pg):
                          'parallelism': 'replicas' if world > 1 else 'single GPU',
                          'l2': 'inputs larger than L2 (FFT grids %.2f GB)' % (8 * n3 * 4 * 2 / 1e9)},
               'ptps': value * args.N / world,
-              'iterations': {'lanczos_mean': Li / K, 'krylov_mean': Ki / K, 'neighbor_pairs': npairs},
+              'iterations': {'lanczos_mean': float(np.mean([i[0] for i in iters])),
+                             'krylov_mean': float(np.mean([i[1] for i in iters])),
+                             'neighbor_pairs': float(np.mean([i[2] for i in iters]))},
               'latency_ms': {'p50': float(np.percentile(lat, 50)), 'p99': float(np.percentile(lat, 99)),
                              'note': 'per constrained-step call (single stream, no serving loop)'},
+              'execution': {'graph': bool(graph_used[0]), 'graph_error': graph_used[1],
+                            'host_launched_steps_per_s': KP / prof_elapsed,
+                            'note': 'value: steps captured as one CUDA graph (Krylov loops as conditional while '
+                                    'nodes); stage times and roofline: the same steps launched from the host with '
+                                    'stage events'},
               'stage_ms_per_step': {k: v / K for k, v in stage_ms.items()},
               'wave_stage_hbm': wave_rates,
-              'roofline': roof, 'clocks': clk, 'gpu_launches': int(prof['launches']),
-              'fft_execs': int(prof['fft_execs'])}
+              'roofline': roof, 'clocks': clk,
+              'gpu_launches': int(round(prof['launches'] / K * args.steps)),
+              'gpu_launches_note': 'kernels of this library per step (counted on the host-launched path) x timed '
+                                   'steps; cuFFT kernels excluded',
+              'fft_execs': int(round(prof['fft_execs'] / K * args.steps))}
 
     # end-to-end through the C ABI with host arrays (H2D positions in, D2H positions out, every step)
     pos_host = np.ascontiguousarray(pos_np.copy())
@@ -305,11 +381,7 @@ def run_ours(args, world, rank, local, pg):
     t0 = time.perf_counter()
     for k in range(args.e2e_steps):
         h.step(pos_host, args.dt, seed=7, step=1 + k)
-    e2e_t = (time.perf_counter() - t0) / max(1, args.e2e_steps)
-    if pg is not None:
-        t = torch.tensor([e2e_t], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks((time.perf_counter() - t0) / max(1, args.e2e_steps), pg, dev)
     result['e2e'] = {'value': world / e2e_t, 'unit': 'steps/s', 'h2d_bytes_per_step': 24 * args.N,
                      'd2h_bytes_per_step': 24 * args.N}
     h.close()
@@ -327,6 +399,8 @@ def run_ours(args, world, rank, local, pg):
         t64 = (time.perf_counter() - t0) / args.fp64_steps
         result['fp64'] = {'steps_per_s': 1.0 / t64, 'ms_per_step': 1000.0 * t64,
                           'mixed_speedup': t64 / (elapsed / args.steps)}
+        if not args.no_accuracy:
+            result['accuracy'] = accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64)
         h64.close()
     if rank == 0 and world == 1 and not args.no_serving:
         res, desc = serving_measure(pkg, args, [8.0], 6, 200000, 10.0)
@@ -387,7 +461,8 @@ def serve_at_rate(pkg, srv, pool, rate, seconds, xi, dt, seed):
     for t in tickets:
         srv.wait(t)
     st = srv.stats()
-    return {'offered_rate': rate, 'requests': len(tickets), 'req_per_s': st['requests_per_s'],
+    return {'offered_rate': rate, 'arrival_rate': len(tickets) / seconds, 'requests': len(tickets),
+            'req_per_s': st['requests_per_s'],
             'p50_ms': st['p50_ms'], 'p99_ms': st['p99_ms'], 'wait_p50_ms': st['wait_p50_ms'],
             'wait_p99_ms': st['wait_p99_ms'], 'service_p50_ms': st['service_p50_ms'],
             'peak_running': st['peak_running'], 'peak_resident_gb': st['peak_resident_bytes'] / 1e9,
@@ -406,7 +481,7 @@ def serving_measure(pkg, args, rates, pool_size, nmax, seconds):
     for k, r in enumerate(rates):
         res = serve_at_rate(pkg, srv, pool, r, seconds, args.xi, args.dt, seed=k)
         out.append(res)
-        if res['req_per_s'] < 0.8 * r:          # saturated: completions no longer track arrivals
+        if res['req_per_s'] < 0.85 * res['arrival_rate']:   # saturated: completions no longer track arrivals
             break
     srv.close()
     desc = ('%d resident suspensions, N log-uniform in [1000, %d] (N = %s), phi in {0.1, 0.25, 0.4}, '

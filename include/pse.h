@@ -93,7 +93,10 @@ typedef struct pse_options {
   int32_t real_lanes;      /* lanes sharing one particle in the pair sum (1,4,8,16,32); 0 = auto */
   int32_t grid_ladder;     /* 1: round the rule's grid up to an even 3-smooth size (2^i 3^j), so that
                               a batch has few distinct grids and therefore few FFT groups; 0 = off */
-  int32_t reserved[6];
+  int32_t use_graph;       /* 1: pse_constrained_step runs as one CUDA graph (captured on first use and
+                              again when dt, the presence of a force or the layout changes), with the
+                              Krylov loops as conditional while nodes; 0 = launches from the host */
+  int32_t reserved[5];
 } pse_options;
 
 typedef struct pse_info {
@@ -184,6 +187,14 @@ pse_status pse_get_info(pse_handle h, pse_info *out);
 
 /* Number of suspensions of a handle (0 for NULL). */
 int32_t pse_num_systems(pse_handle h);
+
+/* 1 if use_graph is on and the step graph has been captured (after a first
+ * pse_constrained_step), else 0. */
+int32_t pse_graph_ready(pse_handle h);
+
+/* Why graph capture was given up for this handle (steps then launch from the
+ * host), or "" if it was not. */
+const char *pse_graph_error(pse_handle h);
 
 /* Parameters of suspension s. */
 pse_status pse_get_system_info(pse_handle h, int32_t s, pse_info *out);
@@ -319,6 +330,13 @@ pse_status pse_server_reset_stats(pse_server *srv);
 /* Stops the workers after their current requests (queued ones are dropped) and
  * frees every resident handle. */
 pse_status pse_server_destroy(pse_server *srv);
+
+/* Pairwise hard-sphere repulsion as a harmonic overlap force (the paper's
+ * hard-sphere repulsion is not specified; read here as this force):
+ * F_i = sum_j k (2a - r_ij) (x_i - x_j)/r_ij over pairs closer than contact,
+ * minimum image, into F (N x 3 in the handle's precision, user order).  Uses
+ * the handle's cell and neighbour lists (r_cut >= 2a). */
+pse_status pse_overlap_force(pse_handle h, const double *pos, double kspring, void *F, pse_stream stream);
 
 /* Autotuner (no counterpart in the paper).  Times, on the configuration pos and
  * the handle's own stream, `reps` calls of each candidate: lanes per particle of

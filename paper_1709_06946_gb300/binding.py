@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
                 ('lanczos_tol', ctypes.c_double), ('lanczos_maxiter', ctypes.c_int32),
                 ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
                 ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('grid_ladder', ctypes.c_int32),
-                ('reserved', ctypes.c_int32 * 6)]
+                ('use_graph', ctypes.c_int32), ('reserved', ctypes.c_int32 * 5)]
 
 
 class Info(ctypes.Structure):
@@ -108,6 +108,8 @@ SIGNATURES = [
     ('pse_destroy', ctypes.c_int, [_P]),
     ('pse_get_info', ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     ('pse_num_systems', ctypes.c_int32, [_P]),
+    ('pse_graph_ready', ctypes.c_int32, [_P]),
+    ('pse_graph_error', ctypes.c_char_p, [_P]),
     ('pse_get_system_info', ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Info)]),
     ('pse_get_system_stats', ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Stats)]),
     ('pse_mobility_apply', ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -124,6 +126,7 @@ SIGNATURES = [
     ('pse_server_get_stats', ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     ('pse_server_reset_stats', ctypes.c_int, [_P]),
     ('pse_server_destroy', ctypes.c_int, [_P]),
+    ('pse_overlap_force', ctypes.c_int, [_P, _P, _D, _P, _P]),
     ('pse_autotune', ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(Tuning), _P]),
     ('pse_set_profiling', ctypes.c_int, [_P, ctypes.c_int32]),
     ('pse_get_profile', ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
@@ -204,7 +207,7 @@ def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
 
 
 def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
-             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=0):
+             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=0, use_graph=0):
     o = Options()
     load().pse_default_options(ctypes.byref(o))
     o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
@@ -214,6 +217,7 @@ def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxit
     o.table_points = int(table_points)
     o.real_lanes = int(real_lanes)
     o.grid_ladder = int(grid_ladder)
+    o.use_graph = int(use_graph)
     for d in range(3):
         o.tile[d] = int(tile[d])
     return o
@@ -268,6 +272,10 @@ class PSE:
         self.nsys = int(lib.pse_num_systems(h))
         self.offsets = np.concatenate([[0], np.cumsum(self.Ns)]).astype(np.int64)
         self.info = self.get_info()
+
+    def graph_ready(self):
+        """(captured, reason capture was given up or '')."""
+        return bool(self._lib.pse_graph_ready(self._h)), self._lib.pse_graph_error(self._h).decode()
 
     def system_info(self, s):
         """Parameters of suspension s (grid, cells, tiles, ...)."""
@@ -348,6 +356,12 @@ class PSE:
         d = stats.as_dict()
         d['status'] = st
         return S, d
+
+    def overlap_force(self, pos, k):
+        """Harmonic overlap repulsion k (2a - r) rh summed over pairs closer than contact."""
+        F = self._like(pos, (self.N, 3), self.dtype)
+        self._check(self._lib.pse_overlap_force(self._h, _ptr(pos), float(k), _ptr(F), _stream(pos)))
+        return F
 
     def autotune(self, pos, reps=3):
         """Times the pair-sum lanes and spreading-tile candidates on `pos` and keeps the fastest."""

@@ -118,284 +118,112 @@ pse_status staging_ready(pse_ctx *c, cudaStream_t s) {
   return PSE_OK;
 }
 
-pse_status upload_active(pse_ctx *c, cudaStream_t s) {
-  PSE_TRY(staging_ready(c, s));
-  std::copy(c->h_active.begin(), c->h_active.end(), c->h_pinned_int + 8);
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_active, c->h_pinned_int + 8, sizeof(int) * c->nsys, cudaMemcpyHostToDevice, s));
-  c->h2d_pending = true;
-  return PSE_OK;
-}
 
 }  // namespace pse
 
 namespace {
 
-// Per-suspension coefficient block (COEF_STRIDE doubles): first and second
-// Gram-Schmidt projections, |w|^2, a scale factor, the constants +1 and -1, and
-// the coefficients of the final Krylov combination.
-constexpr int CO_H1 = 0, CO_H2 = 128, CO_NRM = 256, CO_FAC = 257, CO_ONE = 258, CO_MONE = 259, CO_Y = 384;
-
 pse_status set_all_active(pse_ctx *c, cudaStream_t s) {
-  bool all = true;
-  for (int v : c->h_active) all = all && v;
-  if (all) return PSE_OK;
   std::fill(c->h_active.begin(), c->h_active.end(), 1);
-  return upload_active(c, s);
-}
-
-// h[s * count + k] = coefficient (off + k) of suspension s (waits on the stream).
-pse_status read_coef(pse_ctx *c, int off, int count, std::vector<double> &h, cudaStream_t s) {
-  PSE_CUDA_TRY(c, cudaMemcpy2DAsync(c->h_dots, sizeof(double) * count, c->d_coef + off, sizeof(double) * COEF_STRIDE,
-                                    sizeof(double) * count, c->nsys, cudaMemcpyDeviceToHost, s));
-  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
-  c->h2d_pending = false;
-  h.assign(c->h_dots, c->h_dots + (size_t)count * c->nsys);
+  kd_all_active(c, s);
+  PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
 
-// Coefficients (off .. off + count) of every suspension from h[s * count + k].
-pse_status write_coef(pse_ctx *c, int off, int count, const std::vector<double> &h, cudaStream_t s) {
-  PSE_TRY(staging_ready(c, s));
-  std::memcpy(c->h_wbuf, h.data(), sizeof(double) * count * c->nsys);
-  PSE_CUDA_TRY(c, cudaMemcpy2DAsync(c->d_coef + off, sizeof(double) * COEF_STRIDE, c->h_wbuf, sizeof(double) * count,
-                                    sizeof(double) * count, c->nsys, cudaMemcpyHostToDevice, s));
-  c->h2d_pending = true;
-  return PSE_OK;
-}
-
-pse_status write_nrows(pse_ctx *c, const std::vector<int> &nr, cudaStream_t s) {
-  PSE_TRY(staging_ready(c, s));
-  int *h = c->h_pinned_int + 8 + c->nsys;
-  std::copy(nr.begin(), nr.end(), h);
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_nrows, h, sizeof(int) * c->nsys, cudaMemcpyHostToDevice, s));
-  c->h2d_pending = true;
-  return PSE_OK;
-}
-
-void *row(pse_ctx *c, int r) { return (char *)c->d_basis + (size_t)r * 8 * c->p.N * c->ts; }
-
-// Orthogonalise w against rows 0..j of the basis twice (classical Gram-Schmidt,
-// FP64 coefficients) for every active suspension; h[s * (j+1) + i] receives the
-// summed coefficients and nrm2[s] = |w|^2.
-pse_status cgs2(pse_ctx *c, void *w, int j, std::vector<double> &h, std::vector<double> &nrm2, cudaStream_t s) {
-  PSE_TRY(multidot(c, c->d_basis, j + 1, w, CO_H1, s));
-  PSE_TRY(combine_sub(c, w, c->d_basis, j + 1, CO_H1, s));
-  PSE_TRY(multidot(c, c->d_basis, j + 1, w, CO_H2, s));
-  PSE_TRY(combine_sub(c, w, c->d_basis, j + 1, CO_H2, s));
-  PSE_TRY(multidot(c, w, 1, w, CO_NRM, s));
-  std::vector<double> buf;
-  PSE_TRY(read_coef(c, 0, CO_NRM + 1, buf, s));
-  const int ns = c->nsys;
-  h.assign((size_t)ns * (j + 1), 0.0);
-  nrm2.assign(ns, 0.0);
-  for (int q = 0; q < ns; ++q) {
-    const double *b = buf.data() + (size_t)q * (CO_NRM + 1);
-    for (int i = 0; i <= j; ++i) h[(size_t)q * (j + 1) + i] = b[CO_H1 + i] + b[CO_H2 + i];
-    nrm2[q] = b[CO_NRM];
+// Runs `body` (one Krylov iteration, launched on the stream it is given) until
+// the control kernels clear the loop flag, at most `cap` times.  Outside a
+// capture this is a host loop that reads the flag (and the active set) after
+// every iteration; while the step is being captured it becomes a conditional
+// while node whose body graph is captured from a second stream, so the whole
+// loop runs on the device.
+template <typename Body>
+pse_status krylov_loop(pse_ctx *c, int cap, cudaStream_t s, Body &&body) {
+  if (!c->capturing) {
+    for (int j = 0; j < cap; ++j) {
+      PSE_TRY(body(s));
+      kd_loop_end(c, cap, 0, 0, s);
+      PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_flag, c->kd.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_flag + 1, c->d_active, sizeof(int) * c->nsys, cudaMemcpyDeviceToHost, s));
+      PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+      c->h2d_pending = false;
+      std::copy(c->h_flag + 1, c->h_flag + 1 + c->nsys, c->h_active.begin());
+      if (!c->h_flag[0]) break;
+    }
+    return PSE_OK;
   }
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  cudaGraphConditionalHandle h;
+  PSE_CUDA_TRY(c, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  PSE_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  kd_loop_begin(c, h, 1, s);
+  PSE_CUDA_TRY(c, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  PSE_CUDA_TRY(c, cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  PSE_CUDA_TRY(c, cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body_g = np.conditional.phGraph_out[0];
+  PSE_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(c->cap_stream, body_g, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeRelaxed));
+  pse_status st = body(c->cap_stream);
+  kd_loop_end(c, cap, h, 1, c->cap_stream);
+  cudaGraph_t out_g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &out_g);
+  PSE_TRY(st);
+  PSE_CUDA_TRY(c, e);
   return PSE_OK;
+}
+
+// Orthogonalise w against basis rows 0..j (j = the device iteration counter)
+// twice (classical Gram-Schmidt, FP64 coefficients), then |w|^2.
+pse_status cgs2(pse_ctx *c, void *w, cudaStream_t s) {
+  PSE_TRY(multidot_rows(c, c->d_basis, 1, w, CO_H1, s));
+  PSE_TRY(combine_sub_rows(c, w, c->d_basis, 1, CO_H1, s));
+  PSE_TRY(multidot_rows(c, c->d_basis, 1, w, CO_H2, s));
+  PSE_TRY(combine_sub_rows(c, w, c->d_basis, 1, CO_H2, s));
+  return multidot(c, w, 1, w, CO_NRM, s);
 }
 
 // y = M_r^{1/2} z by Lanczos with full reorthogonalisation (Sec. 3.2), per
-// suspension, with the stopping rule |c_m - [c_{m-1}; 0]| / |c_m| <= tol
-// (tol = 0: fixed maxiter steps).
-pse_status lanczos(pse_ctx *c, const void *z, void *y, void *w, double tol, int maxiter, cudaStream_t s) {
-  const int ns = c->nsys;
-  struct St {
-    std::vector<double> alpha, beta, cvec, cprev;
-    double b0 = 0, err = INFINITY;
-    int it = 0;
-  };
-  std::vector<St> st(ns);
+// suspension, stopping rule and tridiagonal square root on the device.
+pse_status lanczos(pse_ctx *c, const void *z, void *y, void *w, cudaStream_t s) {
+  const int cap = c->lanczos_max;
   PSE_TRY(set_all_active(c, s));
   PSE_TRY(multidot(c, z, 1, z, CO_NRM, s));
-  std::vector<double> nrm, fac(ns, 0.0);
-  PSE_TRY(read_coef(c, CO_NRM, 1, nrm, s));
-  for (int q = 0; q < ns; ++q) {
-    st[q].b0 = std::sqrt(std::max(nrm[q], 0.0));
-    c->h_active[q] = st[q].b0 > 0.0;
-    fac[q] = st[q].b0 > 0.0 ? 1.0 / st[q].b0 : 0.0;
-  }
-  PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
-  PSE_TRY(upload_active(c, s));
-  PSE_TRY(vscale(c, row(c, 0), z, 0.0, CO_FAC, s));
-  for (int j = 0; j < maxiter; ++j) {
-    bool any = false;
-    for (int v : c->h_active) any = any || v;
-    if (!any) break;
-    PSE_TRY(real_apply(c, row(c, j), w, M_FULL, s));
-    std::vector<double> h, n2;
-    PSE_TRY(cgs2(c, w, j, h, n2, s));
-    for (int q = 0; q < ns; ++q) {
-      if (!c->h_active[q]) continue;
-      St &L = st[q];
-      L.it = j + 1;
-      L.alpha.push_back(h[(size_t)q * (j + 1) + j]);
-      double bj = std::sqrt(std::max(n2[q], 0.0));
-      int m = j + 1;
-      L.cvec.assign(m, 0.0);
-      if (j == 0) {
-        L.cvec[0] = std::sqrt(std::max(L.alpha[0], 0.0));
-      } else {
-        std::vector<double> d(L.alpha), e(L.beta), Z;
-        if (!tridiag_eigen(m, d, e, Z)) {
-          c->err = "tridiagonal eigen-solver failed";
-          return PSE_ERR_NOT_CONVERGED;
-        }
-        for (int i = 0; i < m; ++i) {
-          double sum = 0;
-          for (int k = 0; k < m; ++k) sum += Z[(size_t)i * m + k] * std::sqrt(std::max(d[k], 0.0)) * Z[k];
-          L.cvec[i] = sum;
-        }
-      }
-      bool stop = false;
-      if (!L.cprev.empty()) {
-        double num = 0, den = 0;
-        for (int i = 0; i < m; ++i) {
-          double dv = L.cvec[i] - (i < m - 1 ? L.cprev[i] : 0.0);
-          num += dv * dv;
-          den += L.cvec[i] * L.cvec[i];
-        }
-        L.err = std::sqrt(num / den);
-        if (tol > 0 && L.err <= tol) stop = true;
-      }
-      if (!stop) {
-        L.cprev = L.cvec;
-        if (bj == 0.0 || j == maxiter - 1) stop = true;
-      }
-      if (stop) {
-        c->h_active[q] = 0;
-      } else {
-        L.beta.push_back(bj);
-        fac[q] = 1.0 / bj;
-      }
-    }
-    any = false;
-    for (int v : c->h_active) any = any || v;
-    if (!any) break;
-    PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
-    PSE_TRY(upload_active(c, s));
-    PSE_TRY(vscale(c, row(c, j + 1), w, 0.0, CO_FAC, s));
-  }
-  int maxit = 0;
-  std::vector<double> coef((size_t)ns * 128, 0.0);
-  std::vector<int> nr(ns, 0);
-  for (int q = 0; q < ns; ++q) {
-    nr[q] = st[q].it;
-    maxit = std::max(maxit, st[q].it);
-    for (int i = 0; i < st[q].it; ++i) coef[(size_t)q * 128 + i] = st[q].b0 * st[q].cvec[i];
-  }
-  PSE_TRY(write_coef(c, CO_Y, 128, coef, s));
-  PSE_TRY(write_nrows(c, nr, s));
+  kd_lz_start(c, s);
+  PSE_TRY(vscale_row(c, c->d_basis, 0, z, c->d_vin, CO_FAC, s));
+  PSE_TRY(krylov_loop(c, cap, s, [&](cudaStream_t t) {
+    PSE_TRY(real_apply(c, c->d_vin, w, M_FULL, t));
+    PSE_TRY(cgs2(c, w, t));
+    kd_lz_step(c, t);
+    return vscale_row(c, c->d_basis, 1, w, c->d_vin, CO_FAC, t);
+  }));
   PSE_TRY(set_all_active(c, s));
-  PSE_TRY(combine_set(c, y, c->d_basis, c->d_nrows, std::max(maxit, 1), CO_Y, s));
-  bool capped = false;
-  for (int q = 0; q < ns; ++q) {
-    pse_stats &o = c->sys_stats[q];
-    o.lanczos_iters = st[q].it;
-    o.lanczos_change = std::isfinite(st[q].err) ? st[q].err : 0.0;
-    capped = capped || (tol > 0 && !(st[q].err <= tol) && st[q].it == maxiter);
-  }
-  return capped ? PSE_ERR_NOT_CONVERGED : PSE_OK;
+  return combine_set(c, y, c->d_basis, c->d_nrows, cap, CO_Y, s);
 }
 
 // Unrestarted GMRES (x0 = 0) for M_ES x = b at the current configuration, per
 // suspension; stops at |r|/|b| <= tol.  b and x hold the stresslet in slots 3..7.
-pse_status gmres(pse_ctx *c, const void *b, void *x, void *w, double tol, int maxiter, cudaStream_t s) {
-  const int ns = c->nsys, M = maxiter;
-  struct St {
-    std::vector<double> H, cs, sn, g;
-    double beta = 0, rel = 0;
-    int it = 0;
-  };
-  std::vector<St> st(ns);
+pse_status gmres(pse_ctx *c, const void *b, void *x, void *w, cudaStream_t s) {
+  const int cap = c->krylov_max;
   PSE_TRY(set_all_active(c, s));
   PSE_TRY(multidot(c, b, 1, b, CO_NRM, s));
-  std::vector<double> nrm, fac(ns, 0.0);
-  PSE_TRY(read_coef(c, CO_NRM, 1, nrm, s));
-  for (int q = 0; q < ns; ++q) {
-    St &G = st[q];
-    G.beta = std::sqrt(std::max(nrm[q], 0.0));
-    c->h_active[q] = G.beta > 0.0;
-    fac[q] = G.beta > 0.0 ? 1.0 / G.beta : 0.0;
-    G.rel = G.beta > 0.0 ? 1.0 : 0.0;
-    if (G.beta > 0.0) {
-      G.H.assign((size_t)(M + 1) * M, 0.0);
-      G.cs.assign(M, 0.0);
-      G.sn.assign(M, 0.0);
-      G.g.assign(M + 1, 0.0);
-      G.g[0] = G.beta;
-    }
-  }
-  PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
-  PSE_TRY(upload_active(c, s));
-  PSE_TRY(vscale(c, row(c, 0), b, 0.0, CO_FAC, s));
-  for (int j = 0; j < M; ++j) {
-    bool any = false;
-    for (int v : c->h_active) any = any || v;
-    if (!any) break;
-    PSE_TRY(mobility(c, row(c, j), w, M_SE, PSE_PART_ALL, s));
-    std::vector<double> h, n2;
-    PSE_TRY(cgs2(c, w, j, h, n2, s));
-    for (int q = 0; q < ns; ++q) {
-      if (!c->h_active[q]) continue;
-      St &G = st[q];
-      std::vector<double> &H = G.H;
-      G.it = j + 1;
-      for (int i = 0; i <= j; ++i) H[(size_t)i * M + j] = h[(size_t)q * (j + 1) + i];
-      double hn = std::sqrt(std::max(n2[q], 0.0));
-      H[(size_t)(j + 1) * M + j] = hn;
-      for (int i = 0; i < j; ++i) {  // previous rotations
-        double a = H[(size_t)i * M + j], bb = H[(size_t)(i + 1) * M + j];
-        H[(size_t)i * M + j] = G.cs[i] * a + G.sn[i] * bb;
-        H[(size_t)(i + 1) * M + j] = -G.sn[i] * a + G.cs[i] * bb;
-      }
-      double a = H[(size_t)j * M + j], bb = H[(size_t)(j + 1) * M + j];
-      double r = std::hypot(a, bb);
-      G.cs[j] = r == 0 ? 1.0 : a / r;
-      G.sn[j] = r == 0 ? 0.0 : bb / r;
-      H[(size_t)j * M + j] = r;
-      H[(size_t)(j + 1) * M + j] = 0.0;
-      G.g[j + 1] = -G.sn[j] * G.g[j];
-      G.g[j] = G.cs[j] * G.g[j];
-      G.rel = std::fabs(G.g[j + 1]) / G.beta;
-      if (G.rel <= tol || hn == 0.0 || j == M - 1) {
-        c->h_active[q] = 0;
-      } else {
-        fac[q] = 1.0 / hn;
-      }
-    }
-    any = false;
-    for (int v : c->h_active) any = any || v;
-    if (!any) break;
-    PSE_TRY(write_coef(c, CO_FAC, 1, fac, s));
-    PSE_TRY(upload_active(c, s));
-    PSE_TRY(vscale(c, row(c, j + 1), w, 0.0, CO_FAC, s));
-  }
-  int maxit = 0;
-  std::vector<double> coef((size_t)ns * 128, 0.0);
-  std::vector<int> nr(ns, 0);
-  for (int q = 0; q < ns; ++q) {
-    St &G = st[q];
-    nr[q] = G.it;
-    maxit = std::max(maxit, G.it);
-    for (int i = G.it - 1; i >= 0; --i) {
-      double sum = G.g[i];
-      for (int k = i + 1; k < G.it; ++k) sum -= G.H[(size_t)i * M + k] * coef[(size_t)q * 128 + k];
-      coef[(size_t)q * 128 + i] = sum / G.H[(size_t)i * M + i];
-    }
-  }
-  PSE_TRY(write_coef(c, CO_Y, 128, coef, s));
-  PSE_TRY(write_nrows(c, nr, s));
+  kd_gm_start(c, s);
+  PSE_TRY(vscale_row(c, c->d_basis, 0, b, c->d_vin, CO_FAC, s));
+  PSE_TRY(krylov_loop(c, cap, s, [&](cudaStream_t t) {
+    PSE_TRY(mobility(c, c->d_vin, w, M_SE, PSE_PART_ALL, t));
+    PSE_TRY(cgs2(c, w, t));
+    kd_gm_step(c, t);
+    return vscale_row(c, c->d_basis, 1, w, c->d_vin, CO_FAC, t);
+  }));
   PSE_TRY(set_all_active(c, s));
-  PSE_TRY(combine_set(c, x, c->d_basis, c->d_nrows, std::max(maxit, 1), CO_Y, s));
-  bool capped = false;
-  for (int q = 0; q < ns; ++q) {
-    c->sys_stats[q].krylov_iters = st[q].it;
-    c->sys_stats[q].krylov_relres = st[q].rel;
-    capped = capped || (!(st[q].rel <= tol) && st[q].it == M);
-  }
-  return capped ? PSE_ERR_NOT_CONVERGED : PSE_OK;
+  return combine_set(c, x, c->d_basis, c->d_nrows, cap, CO_Y, s);
 }
 
 // Unscaled Brownian slip [M_r^{1/2} w1 + M_w^{1/2} dW2] in sorted order into out.
@@ -403,18 +231,15 @@ pse_status sample_sorted(pse_ctx *c, const void *d_w1, const void *d_w2, uint64_
                          cudaStream_t s) {
   if (d_w1) PSE_TRY(gather_user8(c, d_w1, c->d_v[0], s));
   else PSE_TRY(philox_w1(c, seed, counter, c->d_v[0], s));
-  pse_status ls = lanczos(c, c->d_v[0], out, c->d_v[1], c->lanczos_tol, c->lanczos_max, s);
-  if (ls != PSE_OK && ls != PSE_ERR_NOT_CONVERGED) return ls;
-  PSE_TRY(set_all_active(c, s));
-  PSE_TRY(wave_noise(c, d_w2, seed, counter, out, s));
-  return ls;
+  PSE_TRY(lanczos(c, c->d_v[0], out, c->d_v[1], s));
+  return wave_noise(c, d_w2, seed, counter, out, s);
 }
 
 pse_status check_inputs(pse_ctx *c, const void *p, int64_t n, bool dbl, cudaStream_t s) {
   if (!p) return PSE_OK;
-  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
-  PSE_TRY(check_finite(c, p, n, dbl, c->d_flag, s));
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 2, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag + 2, 0, sizeof(int), s));
+  PSE_TRY(check_finite(c, p, n, dbl, c->d_flag + 2, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 2, c->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
   c->h2d_pending = false;
   if (c->h_pinned_int[2]) {
@@ -422,6 +247,36 @@ pse_status check_inputs(pse_ctx *c, const void *p, int64_t n, bool dbl, cudaStre
     return PSE_ERR_NONFINITE;
   }
   return PSE_OK;
+}
+
+// Per-suspension iteration counts and residuals of the last Lanczos / GMRES run
+// (read from the device after the stream has been synchronised); returns
+// NOT_CONVERGED if a cap was reached.
+pse_status read_krylov_stats(pse_ctx *c, bool lz, bool gm, cudaStream_t s) {
+  const int ns = c->nsys;
+  std::vector<int> it(2 * ns);
+  std::vector<double> r(2 * ns);
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(it.data(), c->kd.l_it, sizeof(int) * 2 * ns, cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(r.data(), c->kd.l_err, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(r.data() + ns, c->kd.g_rel, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
+  std::vector<int> gi(2 * ns);
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(gi.data(), c->kd.g_it, sizeof(int) * 2 * ns, cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  bool capped = false;
+  for (int q = 0; q < ns; ++q) {
+    pse_stats &o = c->sys_stats[q];
+    if (lz) {
+      o.lanczos_iters = it[q];
+      o.lanczos_change = std::isfinite(r[q]) ? r[q] : 0.0;
+      capped = capped || it[ns + q];
+    }
+    if (gm) {
+      o.krylov_iters = gi[q];
+      o.krylov_relres = r[ns + q];
+      capped = capped || gi[ns + q];
+    }
+  }
+  return capped ? PSE_ERR_NOT_CONVERGED : PSE_OK;
 }
 
 // Aggregate of the per-suspension statistics (largest iteration counts and
@@ -446,28 +301,16 @@ void reset_stats(pse_ctx *c) {
 
 size_t w2_bytes(const pse_ctx *c) { return c->ts * 6 * (size_t)c->nk_tot; }
 
-pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const void *w1, const void *w2, uint64_t seed,
-                     uint64_t stepno, void *S_out, pse_stats *st, cudaStream_t s) {
+// The constrained mid-point step (Sec. 3.4, App. B) from x_k in d_pos0 to
+// x_{k+1} in d_posout; S in d_v[5].  Same launches eagerly and under capture.
+pse_status step_body(pse_ctx *c, const void *dFP, double dt, const void *dw1, const void *dw2, uint64_t seed,
+                     uint64_t stepno, cudaStream_t s) {
   const Params &p = c->p;
-  int64_t N = p.N;
-  size_t vb = c->ts * 8 * N;
-  if (!(dt > 0) || !pos) {
-    c->err = "dt must be > 0 and pos non-NULL";
-    return PSE_ERR_INVALID_ARG;
-  }
-  reset_stats(c);
-  PSE_TRY(set_all_active(c, s));
-  void *dpos, *dFP, *dw1, *dw2;
-  PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
-  PSE_TRY(stage(c, 1, FP, c->ts * 3 * N, true, s, &dFP));
-  PSE_TRY(stage(c, 2, w1, vb, true, s, &dw1));
-  PSE_TRY(stage(c, 3, w2, w2_bytes(c), true, s, &dw2));
-  PSE_TRY(check_inputs(c, dFP, 3 * N, c->prec == PSE_FP64, s));
+  const int64_t N = p.N;
+  const size_t vb = c->ts * 8 * N;
   // 1. Brownian slip at x_k (unconstrained), user order, scaled by sqrt(2kT/dt)
-  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_pos0, dpos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
   PSE_TRY(setup_config(c, c->d_pos0, s));
-  pse_status sst = sample_sorted(c, dw1, dw2, seed, stepno, c->d_v[2], s);
-  if (sst != PSE_OK && sst != PSE_ERR_NOT_CONVERGED) return sst;
+  PSE_TRY(sample_sorted(c, dw1, dw2, seed, stepno, c->d_v[2], s));
   PSE_TRY(scatter_user8(c, c->d_v[2], c->d_B, std::sqrt(2.0 * p.kT / dt), s));
   // 2. x_{k+1/2} = x_k + dt/2 U^B
   PSE_TRY(midpoint(c, c->d_pos0, c->d_B, 0.5 * dt, c->d_posh, s));
@@ -481,8 +324,7 @@ pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const v
     PSE_TRY(combine_sub(c, c->d_v[2], c->d_v[4], 1, CO_ONE, s));
   }
   PSE_TRY(vzero_slots(c, c->d_v[2], 0, 3, s));
-  pse_status gst = gmres(c, c->d_v[2], c->d_v[5], c->d_v[1], c->krylov_tol, c->krylov_max, s);
-  if (gst != PSE_OK && gst != PSE_ERR_NOT_CONVERGED) return gst;
+  PSE_TRY(gmres(c, c->d_v[2], c->d_v[5], c->d_v[1], s));
   PSE_TRY(vzero_slots(c, c->d_v[5], 0, 3, s));
   // 4. U = U^B + M_UF F^P + M_US S;  x_{k+1} = x_k + dt U
   if (dFP) {
@@ -492,18 +334,158 @@ pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const v
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_v[3], c->d_v[5], vb, cudaMemcpyDeviceToDevice, s));
   }
   PSE_TRY(mobility(c, c->d_v[3], c->d_v[4], M_FSU, PSE_PART_ALL, s));
-  PSE_TRY(final_update(c, c->d_pos0, c->d_B, c->d_v[4], dt, (double *)dpos, s));
+  return final_update(c, c->d_pos0, c->d_B, c->d_v[4], dt, c->d_posout, s);
+}
+
+// Captures step_body (in-kernel noise read from d_rng, force from d_stage[1] when
+// given) as a CUDA graph with the Krylov loops as conditional while nodes.
+pse_status capture_step(pse_ctx *c, const void *dFP, double dt) {
+  // captured on the handle's own stream (the caller's may be the legacy default
+  // stream, which cannot be captured); the graph is launched on the caller's stream
+  if (!c->g_stream) PSE_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->g_stream, cudaStreamNonBlocking));
+  cudaStream_t s = c->g_stream;
+  if (c->g_exec) {
+    cudaGraphExecDestroy(c->g_exec);
+    c->g_exec = nullptr;
+  }
+  if (c->g_graph) {
+    cudaGraphDestroy(c->g_graph);
+    c->g_graph = nullptr;
+  }
+  if (!c->cap_stream) PSE_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const bool prof = c->prof_on;
+  c->prof_on = false;  // stage events cannot live inside conditional bodies
+  PSE_CUDA_TRY(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  c->capturing = true;
+  std::fill(c->h_active.begin(), c->h_active.end(), 1);
+  pse_status st = PSE_OK;
+  cudaError_t e = cudaMemsetAsync(c->d_flag, 0, sizeof(int) * 4, s);
+  if (e == cudaSuccess && dFP) st = check_finite(c, dFP, 3 * c->p.N, c->prec == PSE_FP64, c->d_flag + 2, s);
+  if (e == cudaSuccess && st == PSE_OK) st = step_body(c, dFP, dt, nullptr, nullptr, 0, 0, s);
+  c->capturing = false;
+  c->prof_on = prof;
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess || st != PSE_OK || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st == PSE_OK) {
+      c->err = std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+      st = PSE_ERR_CUDA;
+    }
+    return st;
+  }
+  c->g_graph = g;
+  PSE_CUDA_TRY(c, cudaGraphInstantiate(&c->g_exec, g, 0));
+  c->g_dt = dt;
+  c->g_force = dFP ? 1 : 0;
+  c->g_version = c->layout_version;
+  return PSE_OK;
+}
+
+// After a graph step: non-finite inputs, neighbour-list overflow (the list grows
+// and the step is repeated eagerly), per-suspension pair counts.
+pse_status graph_checks(pse_ctx *c, bool *redo, cudaStream_t s) {
+  const int ns = c->nsys;
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int, c->d_flag, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_nbr_tot, c->d_nbr_tot, 2 * sizeof(unsigned long long) * ns,
+                                  cudaMemcpyDeviceToHost, s));
+  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  c->h2d_pending = false;
+  *redo = false;
+  if (c->h_pinned_int[0]) {
+    c->err = "non-finite particle position";
+    return PSE_ERR_NONFINITE;
+  }
+  if (c->h_pinned_int[2]) {
+    c->err = "non-finite input";
+    return PSE_ERR_NONFINITE;
+  }
+  c->npairs = 0;
+  c->npairs_sys.assign(ns, 0);
+  for (int q = 0; q < ns; ++q) {
+    c->npairs_sys[q] = (int64_t)c->h_nbr_tot[2 * q];
+    c->npairs += c->npairs_sys[q];
+  }
+  *redo = c->h_pinned_int[1] != 0;  // a list overflowed in one of the two builds
+  return PSE_OK;
+}
+
+pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const void *w1, const void *w2, uint64_t seed,
+                     uint64_t stepno, void *S_out, pse_stats *st, cudaStream_t s) {
+  const Params &p = c->p;
+  int64_t N = p.N;
+  size_t vb = c->ts * 8 * N;
+  if (!(dt > 0) || !pos) {
+    c->err = "dt must be > 0 and pos non-NULL";
+    return PSE_ERR_INVALID_ARG;
+  }
+  reset_stats(c);
+  PSE_TRY(set_all_active(c, s));
+  void *dpos, *dFP, *dw1, *dw2;
+  PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
+  PSE_TRY(stage(c, 2, w1, vb, true, s, &dw1));
+  PSE_TRY(stage(c, 3, w2, w2_bytes(c), true, s, &dw2));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_pos0, dpos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  const bool graph = c->opt.use_graph != 0 && !w1 && !w2 && !c->prof_on;
+  bool done = false;
+  if (graph) {
+    // the force always comes from the same buffer so that the captured graph can read it
+    dFP = nullptr;
+    if (FP) {
+      if (c->stage_bytes[1] < c->ts * 3 * N) {
+        void *q = dalloc(c, c->ts * 3 * N);
+        if (!q) {
+          c->err = "cannot allocate staging buffer";
+          return PSE_ERR_OOM;
+        }
+        c->d_stage[1] = q;
+        c->stage_bytes[1] = c->ts * 3 * N;
+      }
+      dFP = c->d_stage[1];
+      PSE_CUDA_TRY(c, cudaMemcpyAsync(dFP, FP, c->ts * 3 * N, cudaMemcpyDefault, s));
+    }
+    if (!c->g_exec || c->g_dt != dt || c->g_force != (dFP ? 1 : 0) || c->g_version != c->layout_version) {
+      PSE_CUDA_TRY(c, cudaStreamSynchronize(s));  // inputs staged on s are complete before capture
+      pse_status cs = capture_step(c, dFP, dt);
+      if (cs != PSE_OK) {  // fall back to host-launched steps for this handle
+        cudaGetLastError();
+        c->graph_error = c->err;
+        c->opt.use_graph = 0;
+        PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+        return step_impl(c, pos, FP, dt, w1, w2, seed, stepno, S_out, st, s);
+      }
+    }
+    PSE_TRY(staging_ready(c, s));
+    c->h_rng[0] = seed;
+    c->h_rng[1] = stepno;
+    PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_rng, c->h_rng, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    c->h2d_pending = true;
+    PSE_CUDA_TRY(c, cudaGraphLaunch(c->g_exec, s));
+    c->nlaunch += 1;
+    bool redo = false;
+    PSE_TRY(graph_checks(c, &redo, s));
+    if (redo) ++c->layout_version;  // the eager rerun below grows the lists; recapture next time
+    done = !redo;
+  }
+  if (!done) {
+    PSE_TRY(stage(c, 1, FP, c->ts * 3 * N, true, s, &dFP));
+    PSE_TRY(check_inputs(c, dFP, 3 * N, c->prec == PSE_FP64, s));
+    PSE_TRY(step_body(c, dFP, dt, dw1, dw2, seed, stepno, s));
+  }
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(dpos, c->d_posout, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
   PSE_TRY(unstage(c, pos, dpos, sizeof(double) * 3 * N, s));
   if (S_out) {
     void *dS;
-    PSE_TRY(stage(c, 1, S_out, c->ts * 5 * N, false, s, &dS));
+    PSE_TRY(stage(c, 4, S_out, c->ts * 5 * N, false, s, &dS));
     PSE_TRY(scatter_out(c, c->d_v[5], nullptr, dS, 1.0, s));
     PSE_TRY(unstage(c, S_out, dS, c->ts * 5 * N, s));
   }
   PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
   c->h2d_pending = false;
+  pse_status ks = read_krylov_stats(c, true, true, s);
   gather_stats(c, st);
-  return (sst == PSE_ERR_NOT_CONVERGED || gst == PSE_ERR_NOT_CONVERGED) ? PSE_ERR_NOT_CONVERGED : PSE_OK;
+  return ks;
 }
 
 // Device memory of a handle before it is created (the admission estimate of a
@@ -531,7 +513,10 @@ int64_t estimate_bytes(const pse_ctx *c) {
   b += (int64_t)ts * 8 * n3;                               // cuFFT work area (upper bound)
   b += (int64_t)ts * 8 * Nt * (7 + rows);                 // vectors and Krylov basis
   b += Nt * 48;                                            // FP64 positions (x_k, x_{k+1/2})
-  b += vblk * 64 + (int64_t)c->nsys * (COEF_STRIDE * 8 + 256);
+  b += vblk * 8 * MAX_ROWS + (int64_t)c->nsys * (COEF_STRIDE * 8 + 256);
+  const int64_t L = c->lanczos_max, M = c->krylov_max;
+  b += (int64_t)c->nsys * 8 * (6 * L + L * L + (M + 1) * M + 3 * M + 8);  // Krylov control state
+  b += (int64_t)ts * 8 * Nt + 24 * Nt;                                    // current Krylov vector, output positions
   return b;
 }
 
@@ -603,6 +588,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
     double mean = 4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * p.N / p.V();
     d.slots = (int)std::min<double>(std::max<int64_t>(p.N, 8), std::ceil((1.4 * mean + 24) / 8.0) * 8.0);
     d.slots = std::max(d.slots, 8);
+    c->npairs_est += (int64_t)(mean * p.N);
     d.tile0 = tile0[q];
     d.cell0 = (int)cell_tot;
     d.k0 = k0[q];
@@ -669,6 +655,8 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_blk0 = (int *)A(sizeof(int) * (ns + 1));
   c->d_active = (int *)A(sizeof(int) * ns);
   c->d_nrows = (int *)A(sizeof(int) * ns);
+  c->kd.active = c->d_active;
+  c->kd.nrows = c->d_nrows;
   c->d_queue = (int *)A(sizeof(int) * 64);
   c->d_table = A(ts * 8 * (size_t)t.len);
   c->d_posw = (double *)A(sizeof(double) * 3 * N);
@@ -702,8 +690,40 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   for (int i = 0; i < 6; ++i) c->d_v[i] = A(ts * 8 * N);
   c->d_B = A(ts * 8 * N);
   c->d_basis = A(ts * 8 * N * (size_t)(std::max(c->lanczos_max, c->krylov_max) + 1));
-  c->d_dots = (double *)A(sizeof(double) * 8 * (size_t)c->nvblk);
+  c->d_dots = (double *)A(sizeof(double) * MAX_ROWS * (size_t)c->nvblk);
+  c->d_vin = A(ts * 8 * N);
+  c->d_posout = (double *)A(sizeof(double) * 3 * N);
+  c->d_rng = (uint64_t *)A(2 * sizeof(uint64_t));
+  {  // Krylov control state
+    KDev &k = c->kd;
+    const int L = c->lanczos_max, M = c->krylov_max;
+    k.nsys = ns;
+    k.lmax = L;
+    k.gmax = M;
+    k.ltol = c->lanczos_tol;
+    k.gtol = c->krylov_tol;
+    k.iter = (int *)A(sizeof(int) * 4);
+    k.flag = k.iter + 2;
+    k.l_it = (int *)A(sizeof(int) * 2 * ns);   // l_it then l_capped (read back together)
+    k.l_capped = k.l_it + ns;
+    k.g_it = (int *)A(sizeof(int) * 2 * ns);   // g_it then g_capped
+    k.g_capped = k.g_it + ns;
+    k.l_alpha = (double *)A(sizeof(double) * ns * (size_t)L);
+    k.l_beta = (double *)A(sizeof(double) * ns * (size_t)L);
+    k.l_cprev = (double *)A(sizeof(double) * ns * (size_t)L);
+    k.l_c = (double *)A(sizeof(double) * ns * (size_t)L);
+    k.l_work = (double *)A(sizeof(double) * ns * (size_t)(2 * L + L * L));
+    k.l_b0 = (double *)A(sizeof(double) * ns);
+    k.l_err = (double *)A(sizeof(double) * ns);
+    k.g_H = (double *)A(sizeof(double) * ns * (size_t)(M + 1) * M);
+    k.g_cs = (double *)A(sizeof(double) * ns * (size_t)M);
+    k.g_sn = (double *)A(sizeof(double) * ns * (size_t)M);
+    k.g_g = (double *)A(sizeof(double) * ns * (size_t)(M + 1));
+    k.g_beta = (double *)A(sizeof(double) * ns);
+    k.g_rel = (double *)A(sizeof(double) * ns);
+  }
   c->d_coef = (double *)A(sizeof(double) * COEF_STRIDE * (size_t)ns);
+  c->kd.coef = c->d_coef;
   c->d_pos0 = (double *)A(sizeof(double) * 3 * N);
   c->d_posh = (double *)A(sizeof(double) * 3 * N);
   if (fail) {
@@ -714,6 +734,11 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_wbuf, sizeof(double) * COEF_STRIDE * (size_t)ns));
   PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_pinned_int, sizeof(int) * (8 + 2 * (size_t)ns)));
   PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_nbr_tot, 2 * sizeof(unsigned long long) * ns));
+  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_flag, sizeof(int) * (1 + (size_t)ns)));
+  PSE_CUDA_TRY(c, cudaMallocHost((void **)&c->h_rng, 2 * sizeof(uint64_t)));
+  PSE_CUDA_TRY(c, cudaMemset(c->kd.iter, 0, sizeof(int) * 4));
+  PSE_CUDA_TRY(c, cudaMemset(c->kd.l_it, 0, sizeof(int) * 2 * ns));
+  PSE_CUDA_TRY(c, cudaMemset(c->kd.g_it, 0, sizeof(int) * 2 * ns));
   PSE_CUDA_TRY(c, cudaMemcpy(c->d_sys, c->hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice));
   PSE_CUDA_TRY(c, cudaMemcpy(c->d_p0, p0.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
   PSE_CUDA_TRY(c, cudaMemcpy(c->d_k0, k0.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice));
@@ -798,11 +823,21 @@ void destroy_impl(pse_ctx *c) {
       if (g.ok[1][b]) cufftDestroy(g.c2r[b]);
     }
   c->groups.clear();
+  if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
+  if (c->g_graph) cudaGraphDestroy(c->g_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->g_stream) cudaStreamDestroy(c->g_stream);
+  c->g_stream = nullptr;
+  c->g_exec = nullptr;
+  c->g_graph = nullptr;
+  c->cap_stream = nullptr;
   for (void *q : c->allocs) cudaFree(q);
   if (c->h_dots) cudaFreeHost(c->h_dots);
   if (c->h_wbuf) cudaFreeHost(c->h_wbuf);
   if (c->h_pinned_int) cudaFreeHost(c->h_pinned_int);
   if (c->h_nbr_tot) cudaFreeHost(c->h_nbr_tot);
+  if (c->h_flag) cudaFreeHost(c->h_flag);
+  if (c->h_rng) cudaFreeHost(c->h_rng);
   c->allocs.clear();
 }
 
@@ -928,6 +963,7 @@ pse_status autotune_impl(pse_ctx *c, const double *pos, int reps, pse_tuning *ou
   }
   PSE_TRY(retile(c, cand[bi]));
   PSE_TRY(setup_config(c, (const double *)dpos, s));
+  ++c->layout_version;  // a captured step graph holds the old tiles and lanes
   for (int d = 0; d < 3; ++d) t.tile[d] = c->ps[0].tile[d];
   t.best_real_ms = best;
   t.best_wave_ms = bw;
@@ -1063,6 +1099,10 @@ pse_status pse_get_info(pse_handle h, pse_info *o) {
 
 int32_t pse_num_systems(pse_handle h) { return h ? h->nsys : 0; }
 
+int32_t pse_graph_ready(pse_handle h) { return h && h->opt.use_graph && h->g_exec ? 1 : 0; }
+
+const char *pse_graph_error(pse_handle h) { return h ? h->graph_error.c_str() : ""; }
+
 pse_status pse_get_system_info(pse_handle h, int32_t s, pse_info *o) {
   if (!h || !o || s < 0 || s >= h->nsys) return PSE_ERR_INVALID_ARG;
   fill_info(h, h->ps[s], h->dev_bytes, o);
@@ -1128,13 +1168,13 @@ pse_status pse_brownian_sample(pse_handle h, const double *pos, double dt, uint6
   PSE_TRY(stage(c, 4, EB, c->ts * 5 * N, false, s, &dE));
   PSE_TRY(check_inputs(c, dw1, 8 * N, c->prec == PSE_FP64, s));
   PSE_TRY(setup_config(c, (const double *)dpos, s));
-  pse_status st = sample_sorted(c, dw1, dw2, seed, counter, c->d_v[2], s);
-  if (st != PSE_OK && st != PSE_ERR_NOT_CONVERGED) return st;
+  PSE_TRY(sample_sorted(c, dw1, dw2, seed, counter, c->d_v[2], s));
   PSE_TRY(scatter_out(c, c->d_v[2], dU, dE, std::sqrt(2.0 * p.kT / dt), s));
   PSE_TRY(unstage(c, UB, dU, c->ts * 3 * N, s));
   PSE_TRY(unstage(c, EB, dE, c->ts * 5 * N, s));
   PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
   c->h2d_pending = false;
+  pse_status st = read_krylov_stats(c, true, false, s);
   gather_stats(c, stats);
   return st;
 }
@@ -1149,6 +1189,25 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
                                       const void *w2, void *S_out, pse_stats *stats, pse_stream stream) {
   if (!h || !w1 || !w2) return PSE_ERR_INVALID_ARG;
   return step_impl(h, pos, FP, dt, w1, w2, 0, 0, S_out, stats, (cudaStream_t)stream);
+}
+
+pse_status pse_overlap_force(pse_handle h, const double *pos, double kspring, void *F, pse_stream stream) {
+  if (!h || !pos || !F || !(kspring >= 0)) return PSE_ERR_INVALID_ARG;
+  pse_ctx *c = h;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = c->p.N;
+  if (c->p.rcut < 2.0 * c->p.a) {
+    c->err = "r_cut below contact: the neighbour lists cannot hold the overlapping pairs";
+    return PSE_ERR_INVALID_ARG;
+  }
+  void *dpos, *dF;
+  PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
+  PSE_TRY(stage(c, 4, F, c->ts * 3 * N, false, s, &dF));
+  PSE_TRY(setup_config(c, (const double *)dpos, s));
+  PSE_TRY(overlap_force(c, kspring, dF, s));
+  PSE_TRY(unstage(c, F, dF, c->ts * 3 * N, s));
+  if (F != dF) PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  return PSE_OK;
 }
 
 pse_status pse_autotune(pse_handle h, const double *pos, int32_t reps, pse_tuning *out, pse_stream stream) {

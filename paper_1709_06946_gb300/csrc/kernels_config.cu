@@ -187,7 +187,7 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
 template <typename T>
 __global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
                       float rc2f, double rc2, const void *rs, const int *cell_start, const int *cell_list, int *cnt,
-                      int *list, unsigned long long *tot) {
+                      int *list, unsigned long long *tot, int *ovf) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Ntot) return;
   const int si = find_sys(p0, nsys, i);
@@ -238,6 +238,7 @@ __global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict_
         }
       }
   cnt[i] = n;
+  if (n > slots) atomicOr(ovf, 1);
   atomicAdd(&tot[2 * si], (unsigned long long)n);
   atomicMax(&tot[2 * si + 1], (unsigned long long)n);
 }
@@ -315,7 +316,7 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_cur, 0, sizeof(int) * (c->ntiles + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->ncells + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cur, 0, sizeof(int) * (c->ncells + 1), s));
-  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));
+  if (!c->capturing) PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));  // a graph clears it once
   k_bin<<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, d_pos, c->d_posw, c->d_tile_key, c->d_tile_start,
                            c->d_flag);
   PSE_TRY(exclusive_scan(c, c->d_tile_start, c->ntiles + 1, s));
@@ -334,10 +335,11 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
     PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long) * ns, s));
     if (c->prec == PSE_MIXED)
       k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
-                                         c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot);
+                                         c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot, c->d_flag + 1);
     else
       k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
-                                          c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot);
+                                          c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot, c->d_flag + 1);
+    if (c->capturing) return PSE_OK;  // the graph's caller checks the flags and the totals afterwards
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_nbr_tot, c->d_nbr_tot, 2 * sizeof(unsigned long long) * ns,
                                     cudaMemcpyDeviceToHost, s));
@@ -373,6 +375,7 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
     }
     c->d_nbr = (int *)q;  // the old list stays in c->allocs and is freed at destroy
     c->nbr_cap = cap;
+    ++c->layout_version;
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_sys, c->hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice, s));
   }
   PSE_CUDA_TRY(c, cudaGetLastError());

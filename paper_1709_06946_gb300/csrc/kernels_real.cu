@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_real(RealArgs a, const SysDev *__restri
     const T4 *v4 = (const T4 *)vin;
     T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
     const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots;
-    const int64_t e = live ? k0 + nstart[i] : 0;
+    const int64_t e = live ? k0 + min(nstart[i], sd.slots) : 0;  // an overflowed list is flagged and redone
     for (int64_t k = (live ? k0 : 0) + sub; k < e; k += G) {
       int j = nbr[k];
       T d[3];
@@ -218,7 +218,8 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
   // lanes per particle from the mean neighbour count of the current lists
   int g = c->opt.real_lanes;
   if (g <= 0) {
-    double mean = a.Ntot > 0 ? (double)c->npairs / a.Ntot : 0.0;
+    const int64_t pairs = c->npairs > 0 ? c->npairs : c->npairs_est;  // before the first list: the estimate
+    double mean = a.Ntot > 0 ? (double)pairs / a.Ntot : 0.0;
     g = mean >= 64.0 ? 8 : (mean >= 24.0 ? 4 : 1);
   }
   switch (g) {
@@ -230,7 +231,46 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
   }
 }
 
+// Harmonic overlap repulsion F_i = sum_j k (2a - r_ij) rh_ij over neighbours
+// closer than 2a, written in user order (one thread per particle).
+template <typename T>
+__global__ void k_overlap(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
+                          double contact, double kspring, const void *rs, const int *__restrict__ nstart,
+                          const int *__restrict__ nbr, const int *__restrict__ perm, T *F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  const SysDev &sd = sys[find_sys(p0, nsys, i)];
+  Pos<T> pi;
+  pi.load(rs, (int)i);
+  double f[3] = {0, 0, 0};
+  const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots, e = k0 + min(nstart[i], sd.slots);
+  for (int64_t k = k0; k < e; ++k) {
+    T d[3];
+    pi.sep(rs, nbr[k], sd, d);
+    double r = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+    if (r >= contact || r == 0.0) continue;
+    double c = kspring * (contact - r) / r;
+    for (int m = 0; m < 3; ++m) f[m] += c * (double)d[m];
+  }
+  const int64_t u = perm[i];
+  for (int m = 0; m < 3; ++m) F[3 * u + m] = (T)f[m];
+}
+
 }  // namespace
+
+pse_status overlap_force(pse_ctx *c, double kspring, void *F, cudaStream_t s) {
+  c->nlaunch += 1;
+  const int64_t N = c->p.N;
+  const unsigned nb = (unsigned)ceil_div(N, 256);
+  if (c->prec == PSE_MIXED)
+    k_overlap<float><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, c->nsys, N, 2.0 * c->p.a, kspring, c->d_rs,
+                                        c->d_nbr_start, c->d_nbr, c->d_perm, (float *)F);
+  else
+    k_overlap<double><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, c->nsys, N, 2.0 * c->p.a, kspring, c->d_rs,
+                                         c->d_nbr_start, c->d_nbr, c->d_perm, (double *)F);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
 
 // vout = M_r vin for the current configuration (sorted order, [N][8]); rows of
 // inactive suspensions are left untouched.

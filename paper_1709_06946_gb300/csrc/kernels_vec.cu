@@ -57,10 +57,15 @@ __global__ void k_scatter8(int64_t N, const int *perm, const T *in, T *out, T sc
   out[8 * (size_t)perm[i] + c] = scale * in[e];
 }
 
+// (seed, counter) come from rng[0..2) when rng is given (a captured graph reads them at launch)
 template <typename T>
-__global__ void k_philox_w1(int64_t N, const int *perm, uint64_t seed, uint64_t counter, T *out) {
+__global__ void k_philox_w1(int64_t N, const int *perm, uint64_t seed, uint64_t counter, const uint64_t *rng, T *out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 8 * N) return;
+  if (rng) {
+    seed = rng[0];
+    counter = rng[1];
+  }
   int64_t i = e >> 3;
   int c = (int)(e & 7);
   T z0, z1;
@@ -139,11 +144,13 @@ __global__ void k_dot_final(VecArgs va, const double *partial, int nrows, double
 // w[e] = (SET ? 0 : w[e]) + sgn * sum_r coef[s][r] rows[r][e], r < nrows (or nrows_s[s])
 template <typename T, bool SET>
 __global__ void k_combine(VecArgs va, T *w, const T *__restrict__ rows, int64_t stride, int nrows,
-                          const int *__restrict__ nrows_s, const double *__restrict__ coef, T sgn) {
-  __shared__ T cs[128];
+                          const int *__restrict__ nrows_s, const double *__restrict__ coef, T sgn,
+                          const int *__restrict__ nrows_dev = nullptr, int add = 0) {
+  __shared__ T cs[MAX_ROWS];
   const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
   if (!va.active[ch.s]) return;
-  const int nr = nrows_s ? min(nrows, nrows_s[ch.s]) : nrows;
+  int nr = nrows_dev ? min(*nrows_dev + add, MAX_ROWS) : nrows;
+  if (nrows_s) nr = min(nr, nrows_s[ch.s]);
   const double *cf = coef + (size_t)ch.s * COEF_STRIDE;
   for (int r = threadIdx.x; r < nr; r += blockDim.x) cs[r] = (T)cf[r];
   __syncthreads();
@@ -151,6 +158,75 @@ __global__ void k_combine(VecArgs va, T *w, const T *__restrict__ rows, int64_t 
     T sum = 0;
     for (int r = 0; r < nr; ++r) sum += cs[r] * rows[r * stride + e];
     w[e] = SET ? sgn * sum : w[e] + sgn * sum;
+  }
+}
+
+// partial[b][r] = sum over block b's chunk of rows[r] . w for r < *nrows_dev + add
+// (at most MAX_ROWS), eight rows per pass over w.
+template <typename T>
+__global__ void k_multidot_rows(VecArgs va, const T *__restrict__ rows, int64_t stride, const int *nrows_dev, int add,
+                                const T *__restrict__ w, double *partial) {
+  __shared__ double red[DOT_ROWS][DOT_NT / 32];
+  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
+  if (!va.active[ch.s]) return;
+  const int nrows = min(*nrows_dev + add, MAX_ROWS);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r0 = 0; r0 < nrows; r0 += DOT_ROWS) {
+    const int nr = min(DOT_ROWS, nrows - r0);
+    T acc[DOT_ROWS];
+#pragma unroll
+    for (int r = 0; r < DOT_ROWS; ++r) acc[r] = 0;
+    for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
+      T we = w[e];
+#pragma unroll
+      for (int r = 0; r < DOT_ROWS; ++r)
+        if (r < nr) acc[r] += rows[(r0 + r) * stride + e] * we;
+    }
+#pragma unroll
+    for (int r = 0; r < DOT_ROWS; ++r) {
+      double v = (double)acc[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[r][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      double sum = 0;
+      for (int k = 0; k < DOT_NT / 32; ++k) sum += red[threadIdx.x][k];
+      partial[(size_t)blockIdx.x * MAX_ROWS + r0 + threadIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+// out[s * COEF_STRIDE + r] = sum of suspension s's partials, r < *nrows_dev + add (one block per suspension).
+__global__ void k_dot_final_rows(VecArgs va, const double *partial, const int *nrows_dev, int add, double *out) {
+  const int s = blockIdx.x;
+  if (!va.active[s]) return;
+  const int nrows = min(*nrows_dev + add, MAX_ROWS);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int b0 = va.blk0[s], b1 = va.blk0[s + 1];
+  for (int r = wid; r < nrows; r += nw) {
+    double sum = 0;
+    for (int b = b0 + lane; b < b1; b += 32) sum += partial[(size_t)b * MAX_ROWS + r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) out[(size_t)s * COEF_STRIDE + r] = sum;
+  }
+}
+
+// basis row *iter + delta (and vin when given) = coef[s][0] * src
+template <typename T>
+__global__ void k_vscale_row(VecArgs va, T *basis, int64_t stride, const int *iter, int delta, const T *src, T *vin,
+                             const double *__restrict__ coef) {
+  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
+  if (!va.active[ch.s]) return;
+  const T f = (T)coef[(size_t)ch.s * COEF_STRIDE];
+  T *dst = basis + (int64_t)(*iter + delta) * stride;
+  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
+    const T v = f * src[e];
+    dst[e] = v;
+    if (vin) vin[e] = v;
   }
 }
 
@@ -285,8 +361,9 @@ pse_status philox_w1(pse_ctx *c, uint64_t seed, uint64_t counter, void *vout, cu
   StageTimer timer(c, PSE_STAGE_VECTOR, s);
   c->nlaunch += 1;
   int64_t N = c->p.N;
-  DISPATCH(c, (k_philox_w1<float><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, seed, counter, (float *)vout)),
-           (k_philox_w1<double><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, seed, counter, (double *)vout)));
+  const uint64_t *rng = c->capturing ? c->d_rng : nullptr;
+  DISPATCH(c, (k_philox_w1<float><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, seed, counter, rng, (float *)vout)),
+           (k_philox_w1<double><<<grid_for(8 * N), 256, 0, s>>>(N, c->d_perm, seed, counter, rng, (double *)vout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -304,6 +381,40 @@ pse_status multidot(pse_ctx *c, const void *rows, int nrows, const void *w, int 
     k_dot_final<<<c->nsys, 32 * DOT_ROWS, 0, s>>>(va, c->d_dots, nr, c->d_coef + off + r0);
     c->nlaunch += 2;
   }
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status multidot_rows(pse_ctx *c, const void *rows, int add, const void *w, int off, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  const int64_t n = 8 * c->p.N;
+  VecArgs va = vec_args(c);
+  c->nlaunch += 2;
+  DISPATCH(c, (k_multidot_rows<float><<<(unsigned)c->nvblk, DOT_NT, 0, s>>>(va, (const float *)rows, n, c->kd.iter, add, (const float *)w, c->d_dots)),
+           (k_multidot_rows<double><<<(unsigned)c->nvblk, DOT_NT, 0, s>>>(va, (const double *)rows, n, c->kd.iter, add, (const double *)w, c->d_dots)));
+  k_dot_final_rows<<<c->nsys, 256, 0, s>>>(va, c->d_dots, c->kd.iter, add, c->d_coef + off);
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status combine_sub_rows(pse_ctx *c, void *w, const void *rows, int add, int off, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  const int64_t n = 8 * c->p.N;
+  VecArgs va = vec_args(c);
+  c->nlaunch += 1;
+  DISPATCH(c, (k_combine<float, false><<<(unsigned)c->nvblk, 256, 0, s>>>(va, (float *)w, (const float *)rows, n, 0, nullptr, c->d_coef + off, -1.0f, c->kd.iter, add)),
+           (k_combine<double, false><<<(unsigned)c->nvblk, 256, 0, s>>>(va, (double *)w, (const double *)rows, n, 0, nullptr, c->d_coef + off, -1.0, c->kd.iter, add)));
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status vscale_row(pse_ctx *c, void *basis, int delta, const void *src, void *vin, int off, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  const int64_t n = 8 * c->p.N;
+  VecArgs va = vec_args(c);
+  c->nlaunch += 1;
+  DISPATCH(c, (k_vscale_row<float><<<(unsigned)c->nvblk, 256, 0, s>>>(va, (float *)basis, n, c->kd.iter, delta, (const float *)src, (float *)vin, c->d_coef + off)),
+           (k_vscale_row<double><<<(unsigned)c->nvblk, 256, 0, s>>>(va, (double *)basis, n, c->kd.iter, delta, (const double *)src, (double *)vin, c->d_coef + off)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -331,7 +442,7 @@ pse_status combine_set(pse_ctx *c, void *y, const void *rows, const int *d_nrows
   const int64_t n = 8 * c->p.N;
   const unsigned nb = (unsigned)c->nvblk;
   VecArgs va = vec_args(c);
-  if (maxrows > 128) {
+  if (maxrows > MAX_ROWS) {
     c->err = "too many Krylov vectors";
     return PSE_ERR_INVALID_ARG;
   }

@@ -168,9 +168,13 @@ __global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
 // u = sigma e^{eta_g k^2/8xi^2} sqrt(H/(eta V k^2)) (I - kk) dW2, then P^+.
 template <typename T, bool EXT>
 __global__ void k_noise(ScaleArgs sa, const T *__restrict__ w2, uint64_t seed, uint64_t counter,
-                        typename Cx<T>::t *g_all) {
+                        const uint64_t *rng, typename Cx<T>::t *g_all) {
   const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gidx >= sa.nk_tot) return;
+  if (rng) {  // a captured graph reads (seed, counter) at launch
+    seed = rng[0];
+    counter = rng[1];
+  }
   const int sidx = find_sys(sa.k0, sa.nsys, gidx);
   if (!sa.active[sidx]) return;
   const SysDev &s = sa.sys[sidx];
@@ -303,8 +307,9 @@ pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t coun
   {
     StageTimer timer(c, PSE_STAGE_NOISE, s);
     c->nlaunch += 1;
-    if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, (C2 *)c->d_cgrid);
-    else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, (C2 *)c->d_cgrid);
+    const uint64_t *rng = c->capturing ? c->d_rng : nullptr;
+    if (w2) k_noise<T, true><<<nb, 256, 0, s>>>(sa, (const T *)w2, seed, counter, nullptr, (C2 *)c->d_cgrid);
+    else k_noise<T, false><<<nb, 256, 0, s>>>(sa, nullptr, seed, counter, rng, (C2 *)c->d_cgrid);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, false, 8, s));

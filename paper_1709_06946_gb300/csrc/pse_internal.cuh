@@ -106,6 +106,26 @@ struct FftGroup {
 
 constexpr int VEC_CHUNK = 4096;    // vector elements per block of the chunked vector kernels
 constexpr int COEF_STRIDE = 512;   // doubles of Krylov coefficients per suspension
+constexpr int MAX_ROWS = 128;      // Krylov vectors per dot-product / combination launch
+// Per-suspension coefficient block (COEF_STRIDE doubles): first and second
+// Gram-Schmidt projections, |w|^2, a scale factor, the constants +1 and -1, and
+// the coefficients of the final Krylov combination.
+constexpr int CO_H1 = 0, CO_H2 = 128, CO_NRM = 256, CO_FAC = 257, CO_ONE = 258, CO_MONE = 259, CO_Y = 384;
+
+// Device state of the per-suspension Krylov iterations; the control kernels
+// (krylov_dev.cu) take the FP64 scalar steps of Lanczos (tridiagonal square
+// root, stopping rule) and GMRES (Givens rotations, back substitution) on the
+// device, so that an iteration needs no host round trip.
+struct KDev {
+  int nsys, lmax, gmax;
+  double ltol, gtol;
+  double *coef;
+  int *active, *nrows, *iter, *flag;   // flag[0]: continue the loop
+  double *l_alpha, *l_beta, *l_cprev, *l_c, *l_work, *l_b0, *l_err;
+  int *l_it, *l_capped;
+  double *g_H, *g_cs, *g_sn, *g_g, *g_beta, *g_rel;
+  int *g_it, *g_capped;
+};
 }  // namespace pse
 
 // ---------------------------------------------------------------------------
@@ -151,7 +171,7 @@ struct pse_ctx {
   int *d_cell_list = nullptr;
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
   int *d_nbr = nullptr;         // neighbour slots: particle i of suspension s owns slots*(i-p0) + nbr0 ...
-  int64_t nbr_cap = 0, npairs = 0;
+  int64_t nbr_cap = 0, npairs = 0, npairs_est = 0;  // last list's pairs; estimate from the densities
   std::vector<int64_t> npairs_sys;
   unsigned long long *d_nbr_tot = nullptr;  // per suspension: total pairs and maximum count
   unsigned long long *h_nbr_tot = nullptr;  // pinned copy
@@ -184,6 +204,18 @@ struct pse_ctx {
   void *d_stage[6] = {nullptr}; // staging for host arrays
   size_t stage_bytes[6] = {0};
   int *d_nrows = nullptr;       // per suspension: vectors in the final Krylov combination
+  pse::KDev kd{};               // Krylov control state (device arrays)
+  int *h_flag = nullptr;        // pinned copy of kd.flag and kd.active
+  void *d_vin = nullptr;        // current Krylov vector, input of the products
+  double *d_posout = nullptr;   // FP64 positions after a step (user order)
+  bool capturing = false;       // a CUDA graph of the step is being captured
+  cudaStream_t cap_stream = nullptr, g_stream = nullptr;  // capture streams of the loop bodies / the step
+  cudaGraphExec_t g_exec = nullptr;
+  cudaGraph_t g_graph = nullptr;
+  double g_dt = 0;
+  int g_force = -1, g_version = -1, layout_version = 0;
+  uint64_t *d_rng = nullptr, *h_rng = nullptr;  // (seed, counter) read by the noise kernels in a graph
+  std::string graph_error;      // why graph capture was given up, if it was
 
   // profiling
   bool prof_on = false;
@@ -249,6 +281,8 @@ namespace pse {
 struct Scan;
 pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s);
 pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStream_t s);
+// Harmonic overlap force of the current configuration into F (user order, N x 3).
+pse_status overlap_force(pse_ctx *c, double kspring, void *F, cudaStream_t s);
 pse_status wave_apply(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s);
 pse_status wave_noise(pse_ctx *c, const void *w2, uint64_t seed, uint64_t counter, void *vout,
                       cudaStream_t s);
@@ -277,8 +311,19 @@ pse_status midpoint(pse_ctx *c, const double *x0, const void *B_user, double fac
 pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const void *U_sorted,
                         double dt, double *xout, cudaStream_t s);
 pse_status check_finite(pse_ctx *c, const void *ptr, int64_t n, bool dbl, int *bad, cudaStream_t s);
-// Uploads h_active to d_active (api.cu).
-pse_status upload_active(pse_ctx *c, cudaStream_t s);
+// Krylov control kernels (krylov_dev.cu); handle = 0 and graph = 0 outside a graph.
+void kd_lz_start(pse_ctx *c, cudaStream_t s);
+void kd_lz_step(pse_ctx *c, cudaStream_t s);
+void kd_gm_start(pse_ctx *c, cudaStream_t s);
+void kd_gm_step(pse_ctx *c, cudaStream_t s);
+void kd_loop_begin(pse_ctx *c, cudaGraphConditionalHandle h, int graph, cudaStream_t s);
+void kd_loop_end(pse_ctx *c, int cap, cudaGraphConditionalHandle h, int graph, cudaStream_t s);
+void kd_all_active(pse_ctx *c, cudaStream_t s);
+// Rows 0 .. *kd.iter + add - 1 of the basis: dot products into coef[s][off + r] and w -= sum coef rows.
+pse_status multidot_rows(pse_ctx *c, const void *rows, int add, const void *w, int off, cudaStream_t s);
+pse_status combine_sub_rows(pse_ctx *c, void *w, const void *rows, int add, int off, cudaStream_t s);
+// Row *kd.iter + delta of the basis (and vin, if given) = coef[s][off] * src.
+pse_status vscale_row(pse_ctx *c, void *basis, int delta, const void *src, void *vin, int off, cudaStream_t s);
 // Work counter for the next persistent launch (cleared on stream s).
 int *next_queue(pse_ctx *c, cudaStream_t s);
 // Resident CTAs of a persistent kernel: SMs x blocks per SM (queried once into

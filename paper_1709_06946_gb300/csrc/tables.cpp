@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "krylov_math.cuh"
 #include "pse_internal.cuh"
 
 namespace pse {
@@ -364,56 +365,8 @@ void fill_real_table_f32(const Params &p, int points_per_2a, int len, float *out
 
 bool tridiag_eigen(int n, std::vector<double> &d, std::vector<double> e, std::vector<double> &Z) {
   Z.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
   e.resize(n, 0.0);
-  if (n > 0) e[n - 1] = 0.0;
-  const double eps = 2.220446049250313e-16;
-  for (int l = 0; l < n; ++l) {
-    for (int iter = 0;; ++iter) {
-      int m = l;
-      for (; m < n - 1; ++m) {
-        double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) <= eps * dd) break;
-      }
-      if (m == l) break;
-      if (iter > 100) return false;
-      // shift from the leading 2x2 block (eigenvalue of it closest to d[l])
-      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double rr = std::hypot(g, 1.0);
-      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? rr : -rr));
-      double s = 1.0, c = 1.0, pp = 0.0;
-      int i = m - 1;
-      bool deflated = false;
-      for (; i >= l; --i) {
-        double f = s * e[i], b = c * e[i];
-        rr = std::hypot(f, g);
-        e[i + 1] = rr;
-        if (rr == 0.0) {  // underflow: split the problem
-          d[i + 1] -= pp;
-          e[m] = 0.0;
-          deflated = true;
-          break;
-        }
-        s = f / rr;
-        c = g / rr;
-        g = d[i + 1] - pp;
-        rr = (d[i] - g) * s + 2.0 * c * b;
-        pp = s * rr;
-        d[i + 1] = g + pp;
-        g = c * rr - b;
-        for (int k = 0; k < n; ++k) {  // rotate columns i, i+1 of Z
-          double zf = Z[(size_t)k * n + i + 1];
-          Z[(size_t)k * n + i + 1] = s * Z[(size_t)k * n + i] + c * zf;
-          Z[(size_t)k * n + i] = c * Z[(size_t)k * n + i] - s * zf;
-        }
-      }
-      if (deflated) continue;
-      d[l] -= pp;
-      e[l] = g;
-      e[m] = 0.0;
-    }
-  }
-  return true;
+  return tql_eigen(n, d.data(), e.data(), Z.data());
 }
 
 }  // namespace pse
