@@ -493,7 +493,8 @@ def serving_measure(pkg, args, rates, pool_size, nmax, seconds):
 def run_serve(args):
     import paper_1709_06946_gb300 as pkg
     pkg.load()
-    rates = [float(r) for r in args.serve_rates.split(',')] if args.serve_rates else [2, 5, 10, 20, 40, 80, 160]
+    rates = ([float(r) for r in args.serve_rates.split(',')] if args.serve_rates
+             else [2, 5, 10, 20, 40, 80, 160, 320, 640, 1280])
     clocks = ClockSampler(0)
     clocks.start()
     res, desc = serving_measure(pkg, args, rates, max(args.serve_pool, 1), 200000, args.serve_seconds)

@@ -341,8 +341,8 @@ pse_status pse_overlap_force(pse_handle h, const double *pos, double kspring, vo
 /* Autotuner (no counterpart in the paper).  Times, on the configuration pos and
  * the handle's own stream, `reps` calls of each candidate: lanes per particle of
  * the pair sum (1, 4, 8, 16, 32; the S -> E plus the full product) and spreading
- * tile caps (x, y, z) in {16,8,16}, {8,8,16}, {16,16,16}, {8,16,16}, {16,8,32},
- * {8,8,32}, {32,8,16} (the S -> E wave product; each suspension's tile is the
+ * tile caps (x, y, z) in {16,16,16}, {16,8,16}, {8,8,16}, {8,16,16}, {16,16,32},
+ * {16,8,32}, {32,8,16} (the S -> E wave product; each suspension's tile is the
  * largest shape within the caps that divides its grid and fits shared memory),
  * and keeps the fastest of each.  Waits for the device.  The choice persists for
  * the handle's later calls; out (may be NULL) reports it and every timing. */

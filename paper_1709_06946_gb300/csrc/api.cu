@@ -939,7 +939,7 @@ pse_status autotune_impl(pse_ctx *c, const double *pos, int reps, pse_tuning *ou
   c->opt.real_lanes = bestg;
   t.real_lanes = bestg;
   // spreading / interpolation tiles: candidate caps, timed on the S -> E wave product
-  const int cand[][3] = {{16, 8, 16}, {8, 8, 16}, {16, 16, 16}, {8, 16, 16}, {16, 8, 32}, {8, 8, 32}, {32, 8, 16}};
+  const int cand[][3] = {{16, 16, 16}, {16, 8, 16}, {8, 8, 16}, {8, 16, 16}, {16, 16, 32}, {16, 8, 32}, {32, 8, 16}};
   std::vector<std::vector<int>> seen;
   double bw = INFINITY;
   int bi = 0;

@@ -94,8 +94,10 @@ __device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, dou
 // G lanes share one particle: they walk its neighbour list with stride G (so
 // the neighbours' records are fetched in parallel) and the partial sums are
 // reduced with shuffles; the first lane of the group adds the self term.
+// FP32: at most 64 registers so that four 256-thread CTAs fit an SM (the full
+// 8 -> 8 product would otherwise take 74 and leave room for three).
 template <typename T, int MODE, int G>
-__global__ void __launch_bounds__(256) k_real(RealArgs a, const SysDev *__restrict__ sys,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_real(RealArgs a, const SysDev *__restrict__ sys,
                                               const int64_t *__restrict__ p0, const int *__restrict__ active,
                                               int *queue, int nitems, const void *rs,
                                               const int *__restrict__ nstart, const int *__restrict__ nbr,

@@ -1,8 +1,11 @@
 // Spreading / interpolation kernels shared by wave_spread.cu and wave_interp.cu.
 //
 // Both kernels are persistent: each CTA takes grid tiles (Tx x Ty x Tz points)
-// of any suspension from a work counter and keeps the tile in shared memory as [z][y][x][component] with the components padded to
-// CP = 4 or 8 so that one lane moves four components with one vector access.
+// of any suspension from a work counter and keeps the tile in shared memory,
+// points in [z][y][x] order, components split into a vector array (components
+// 0..3, one 16-byte access) and, for 5 or 8 components, a second array
+// (component 4 alone, or components 4..7): one lane updates all components of
+// one point with two accesses and no padding.
 // The CTA walks the particles of the 2x2x2 bins whose Gaussian supports can
 // reach the tile (bins hold particles by the grid index where their support
 // starts) in chunks: the particles that overlap the tile are compacted into a
@@ -40,12 +43,90 @@ __host__ __device__ inline int tile_rx(int Tx) { return Tx + ((Tx & 3) == 0 ? 2 
 
 template <int C> struct CPad { static constexpr int v = C <= 4 ? 4 : 8; };
 
+// Tile storage for C components: a[i] holds components 0..3 of point i, b the
+// rest (one real for C = 5, a second vector for C = 8, nothing for C <= 4).
+template <typename T, int C>
+struct TileL {
+  using T4 = typename V4<T>::t;
+  static constexpr int EXTRA = C == 5 ? 1 : (C == 8 ? 4 : 0);  // reals per point in b
+  // rounded up to 64 bytes so that the particle list after the tile stays aligned
+  // (5 components take 20 or 40 bytes per point)
+  __host__ __device__ static size_t bytes(size_t npts) {
+    size_t b = npts * (sizeof(T4) + (EXTRA == 4 ? sizeof(T4) : EXTRA * sizeof(T)));
+    return (b + 63) / 64 * 64;
+  }
+  T4 *a;
+  void *b;
+  __device__ void init(void *base, int npts) {
+    a = (T4 *)base;
+    b = (void *)(a + npts);
+  }
+  __device__ __forceinline__ void load(int i, T v[C]) const {
+    const T4 x = a[i];
+    v[0] = x.x;
+    if (C > 1) v[1] = x.y;
+    if (C > 2) v[2] = x.z;
+    if (C > 3) v[3] = x.w;
+    if (EXTRA == 1) v[4] = ((const T *)b)[i];
+    if (EXTRA == 4) {
+      const T4 y = ((const T4 *)b)[i];
+      v[4] = y.x;
+      v[5] = y.y;
+      v[6] = y.z;
+      v[7] = y.w;
+    }
+  }
+  __device__ __forceinline__ void store(int i, const T v[C]) const {
+    T4 x;
+    x.x = v[0];
+    x.y = C > 1 ? v[1] : (T)0;
+    x.z = C > 2 ? v[2] : (T)0;
+    x.w = C > 3 ? v[3] : (T)0;
+    a[i] = x;
+    if (EXTRA == 1) ((T *)b)[i] = v[4];
+    if (EXTRA == 4) {
+      T4 y;
+      y.x = v[4];
+      y.y = v[5];
+      y.z = v[6];
+      y.w = v[7];
+      ((T4 *)b)[i] = y;
+    }
+  }
+};
+
 // shared memory of a spreading/interpolation CTA (tile + particle list)
 template <typename T, int C>
 __host__ __device__ inline size_t wave_smem(const int T3[3]) {
   constexpr int CP = CPad<C>::v;
-  return (size_t)T3[2] * T3[1] * tile_rx(T3[0]) * CP * sizeof(T) +
+  return TileL<T, C>::bytes((size_t)T3[2] * T3[1] * tile_rx(T3[0])) +
          (size_t)LIST_CAP * (sizeof(int4) + 4 * sizeof(T) + CP * sizeof(T) + 3 * WMAX * sizeof(T));
+}
+
+// Sum of v[0..8) over the warp in 9 shuffles: each exchange halves the
+// components a lane keeps, so lane l ends with the total of component
+// 4 b4 + 2 b3 + b2 (b_k = bit k of l), the same in the four lanes l, l^1, l^2, l^3.
+template <typename T>
+__device__ __forceinline__ T warp_reduce8(const T v[8], int lane) {
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+  T k4[4], k2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const T keep = b4 ? v[i + 4] : v[i], send = b4 ? v[i] : v[i + 4];
+    k4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const T keep = b3 ? k4[i + 2] : k4[i], send = b3 ? k4[i] : k4[i + 2];
+    k2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  T k1 = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? k2[0] : k2[1], 4);
+  k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+  k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+  return k1;
+}
+__device__ __forceinline__ int reduce8_component(int lane) {
+  return 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
 }
 
 __device__ __forceinline__ void tile_of(const SysDev &a, int tile, int t[3], int t0[3]) {
@@ -166,9 +247,22 @@ inline unsigned wave_grid(pse_ctx *c, K kern, size_t smem, int items, OccCache &
   return grid;
 }
 
+// Allows the kernel the device's opt-in shared memory per block minus its own
+// static shared memory.
 template <typename K>
 inline void set_smem(K kern, std::once_flag &once) {
-  std::call_once(once, [&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); });
+  std::call_once(once, [&] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    cudaGetLastError();
+  });
 }
 
 }  // namespace pse

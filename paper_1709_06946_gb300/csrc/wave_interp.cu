@@ -22,8 +22,8 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
                                                          const typename V4<T>::t *__restrict__ sp_d0,
                                                          const int *__restrict__ tile_start,
                                                          const T *__restrict__ grid_all, T *__restrict__ vout) {
-  constexpr int CP = CPad<C>::v, H = CP / 4;
-  constexpr int NPASS = PT > 0 ? (PT * PT * H + 31) / 32 : 1;
+  constexpr int CP = CPad<C>::v;
+  constexpr int NPASS = PT > 0 ? (PT * PT + 31) / 32 : 1;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int s_count;
@@ -33,8 +33,9 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
     const SysDev &a = wa.sys[si];
     const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
     const int npts = Tz * Ty * RX;
-    T4 *tile = (T4 *)smem_raw;
-    int4 *s_meta = (int4 *)(tile + (size_t)npts * H);
+    TileL<T, C> tl;
+    tl.init(smem_raw, npts);
+    int4 *s_meta = (int4 *)(smem_raw + TileL<T, C>::bytes(npts));
     T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
     T *s_m = (T *)(s_d0 + LIST_CAP);
     T *s_w = s_m + LIST_CAP * CP;
@@ -46,23 +47,24 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
     for (int q = threadIdx.x; q < tv; q += blockDim.x) {
       int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
       size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
-      T *dst = (T *)(tile + ((size_t)(z * Ty + y) * RX + x) * H);
+      T v[C];
 #pragma unroll
-      for (int c = 0; c < CP; ++c) dst[c] = c < C ? grid[c * a.gstride + g] : (T)0;
+      for (int c = 0; c < C; ++c) v[c] = grid[c * a.gstride + g];
+      tl.store((z * Ty + y) * RX + x, v);
     }
     const int nb = tile_bins(a, t, tile_start, beg, cum);
-    const int P = PT > 0 ? PT : wa.P, nitem = P * P * H;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
+    const int P = PT > 0 ? PT : wa.P, nitem = P * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
-    const size_t zstride = (size_t)Ty * RX * H;
+    const int zstride = Ty * RX;
     int pjx[NPASS], pjy[NPASS];
     bool pok[NPASS];
 #pragma unroll
     for (int ps = 0; ps < NPASS; ++ps) {
-      int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
+      int it = ps * 32 + lane;
       pok[ps] = it < nitem;
-      pjx[ps] = pok[ps] ? q % P : 0;
-      pjy[ps] = pok[ps] ? q / P : 0;
+      pjx[ps] = pok[ps] ? it % P : 0;
+      pjy[ps] = pok[ps] ? it / P : 0;
     }
     for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
       if (threadIdx.x == 0) s_count = 0;
@@ -71,8 +73,9 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
                                             s_d0, s_m, s_w, &s_count);
       for (int e = warp; e < n; e += WAVE_WARPS) {
         const int4 m4 = s_meta[e];
-        T4 acc;
-        acc.x = acc.y = acc.z = acc.w = (T)0;
+        T acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = (T)0;
         if (PT > 0) {
           const T *w = s_w + e * 3 * WMAX;
           T wz[PT > 0 ? PT : 1];
@@ -91,16 +94,15 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
             if (ly >= Ng) ly -= Ng;
             if (pok[ps] && lx < Tx && ly < Ty) {
               const T wxy = w[pjx[ps]] * w[WMAX + pjy[ps]];
-              const T4 *col = tile + ((size_t)ly * RX + lx) * H + hh;
+              const int col = ly * RX + lx;
 #pragma unroll
               for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
                 if (lzs[jz] >= 0) {
                   const T wt = wxy * wz[jz];
-                  const T4 v = col[lzs[jz] * zstride];
-                  acc.x += wt * v.x;
-                  acc.y += wt * v.y;
-                  acc.z += wt * v.z;
-                  acc.w += wt * v.w;
+                  T v[C];
+                  tl.load(col + lzs[jz] * zstride, v);
+#pragma unroll
+                  for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
                 }
               }
             }
@@ -109,45 +111,32 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
           const T4 d0 = s_d0[e];
           for (int base = 0; base < nitem; base += 32) {
             const int it = base + lane;
-            const int q = H == 2 ? (it >> 1) : it;
-            const int jx = q % P, jy = q / P;
+            const int jx = it % P, jy = it / P;
             int lx = m4.y + jx, ly = m4.z + jy;
             if (lx >= Ng) lx -= Ng;
             if (ly >= Ng) ly -= Ng;
             if (it < nitem && lx < Tx && ly < Ty) {
               const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
               const T wxy = exp(-alpha * (dx * dx + dy * dy));
-              const T4 *col = tile + ((size_t)ly * RX + lx) * H + hh;
+              const int col = ly * RX + lx;
               for (int jz = 0; jz < P; ++jz) {
                 int lz = m4.w + jz;
                 if (lz >= Ng) lz -= Ng;
                 if (lz < Tz) {
                   const T dz = d0.z + (T)jz * hs;
                   const T wt = wxy * exp(-alpha * dz * dz);
-                  const T4 v = col[lz * zstride];
-                  acc.x += wt * v.x;
-                  acc.y += wt * v.y;
-                  acc.z += wt * v.z;
-                  acc.w += wt * v.w;
+                  T v[C];
+                  tl.load(col + lz * zstride, v);
+#pragma unroll
+                  for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
                 }
               }
             }
           }
         }
-#pragma unroll
-        for (int o = (H == 2 ? 2 : 1); o < 32; o <<= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-          acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
-          acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
-        }
-        if (lane < H) {
-          T *o = vout + 8 * (size_t)m4.x + SLOT0 + 4 * lane;
-          const T vals[4] = {acc.x, acc.y, acc.z, acc.w};
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (4 * lane + c < C) add_out(o + c, pref * vals[c]);
-        }
+        const T tot = warp_reduce8(acc, lane);
+        const int comp = reduce8_component(lane);
+        if ((lane & 3) == 0 && comp < C) add_out(vout + 8 * (size_t)m4.x + SLOT0 + comp, pref * tot);
       }
       __syncthreads();
     }

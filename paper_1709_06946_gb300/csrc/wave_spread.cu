@@ -3,9 +3,9 @@
 // Persistent CTAs take output tiles (of any suspension) from a work counter.
 // Warp w owns the tile's z-planes w, w + 16, ...; for
 // every particle overlapping the tile it adds the particle's P x P footprint in
-// its plane to the shared tile with plain vector read-modify-writes (lanes map
-// to distinct (x, y, component-half) items, and no other warp touches the
-// plane), so there are no atomics and the result is deterministic.  The tile is
+// its plane to the shared tile with plain read-modify-writes (each lane owns one
+// (x, y) point of the footprint and updates all its components; no other warp
+// touches the plane), so there are no atomics and the result is deterministic.  The tile is
 // then written once to the component-major grids with coalesced stores; no grid
 // zeroing pass is needed because the tiles cover the grid.
 #include "wave_common.cuh"
@@ -18,8 +18,8 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
                                                          const typename V4<T>::t *__restrict__ sp_d0,
                                                          const T *__restrict__ vin, const int *__restrict__ tile_start,
                                                          T *__restrict__ grid_all) {
-  constexpr int CP = CPad<C>::v, H = CP / 4;
-  constexpr int NPASS = PT > 0 ? (PT * PT * H + 31) / 32 : 1;
+  constexpr int CP = CPad<C>::v;
+  constexpr int NPASS = PT > 0 ? (PT * PT + 31) / 32 : 1;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int s_count;
@@ -29,30 +29,34 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
     const SysDev &a = wa.sys[si];
     const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
     const int npts = Tz * Ty * RX;
-    T4 *acc = (T4 *)smem_raw;
-    int4 *s_meta = (int4 *)(acc + (size_t)npts * H);
+    TileL<T, C> tl;
+    tl.init(smem_raw, npts);
+    int4 *s_meta = (int4 *)(smem_raw + TileL<T, C>::bytes(npts));
     T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
     T *s_m = (T *)(s_d0 + LIST_CAP);
     T *s_w = s_m + LIST_CAP * CP;
-    T4 zero;
-    zero.x = zero.y = zero.z = zero.w = (T)0;
-    for (int q = threadIdx.x; q < npts * H; q += blockDim.x) acc[q] = zero;
+    {
+      T zero[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) zero[c] = (T)0;
+      for (int q = threadIdx.x; q < npts; q += blockDim.x) tl.store(q, zero);
+    }
     __syncthreads();  // cleared before any update or (for a tile with no particles) the read-out
     int t[3], t0[3], beg[8], cum[9];
     tile_of(a, item - a.tile0, t, t0);
     const int nb = tile_bins(a, t, tile_start, beg, cum);
-    const int P = PT > 0 ? PT : wa.P, Ng = a.Ng, nitem = P * P * H;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, hh = H == 2 ? (lane & 1) : 0;
+    const int P = PT > 0 ? PT : wa.P, Ng = a.Ng, nitem = P * P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
-    // this lane's (x, y) footprint item in every pass (fixed for the whole tile)
+    // this lane's (x, y) footprint point in every pass (fixed for the whole tile)
     int pjx[NPASS], pjy[NPASS];
     bool pok[NPASS];
 #pragma unroll
     for (int ps = 0; ps < NPASS; ++ps) {
-      int it = ps * 32 + lane, q = H == 2 ? (it >> 1) : it;
+      int it = ps * 32 + lane;
       pok[ps] = it < nitem;
-      pjx[ps] = pok[ps] ? q % P : 0;
-      pjy[ps] = pok[ps] ? q / P : 0;
+      pjx[ps] = pok[ps] ? it % P : 0;
+      pjy[ps] = pok[ps] ? it / P : 0;
     }
     for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
       if (threadIdx.x == 0) s_count = 0;
@@ -60,6 +64,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
       const int n = build_list<T, C, SLOT0>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m, s_w,
                                             &s_count);
       for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
+        const int plane = lz * Ty * RX;
         // the warp finds the particles whose support crosses its plane 32 list entries at a time
         for (int base = 0; base < n; base += 32) {
           int jzl = P;
@@ -74,8 +79,9 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
             const int e = base + b;
             const int jz = __shfl_sync(0xffffffffu, jzl, b);
             const int4 m4 = s_meta[e];
-            const T4 mv = ((const T4 *)s_m)[e * H + hh];
-            T4 *plane = acc + (size_t)lz * Ty * RX * H;
+            T mv[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) mv[c] = s_m[e * CP + c];
             if (PT > 0) {
               const T *w = s_w + e * 3 * WMAX;
               const T wz = pref * w[2 * WMAX + jz];
@@ -86,13 +92,12 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
                 if (ly >= Ng) ly -= Ng;
                 if (pok[ps] && lx < Tx && ly < Ty) {
                   const T wt = w[pjx[ps]] * w[WMAX + pjy[ps]] * wz;
-                  T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
-                  T4 v = *p;
-                  v.x += wt * mv.x;
-                  v.y += wt * mv.y;
-                  v.z += wt * mv.z;
-                  v.w += wt * mv.w;
-                  *p = v;
+                  const int i = plane + ly * RX + lx;
+                  T v[C];
+                  tl.load(i, v);
+#pragma unroll
+                  for (int c = 0; c < C; ++c) v[c] += wt * mv[c];
+                  tl.store(i, v);
                 }
               }
             } else {  // any support size: weights on the fly
@@ -101,21 +106,19 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
               const T wz = pref * exp(-alpha * dz * dz);
               for (int ib = 0; ib < nitem; ib += 32) {
                 const int it = ib + lane;
-                const int q = H == 2 ? (it >> 1) : it;
-                const int jx = q % P, jy = q / P;
+                const int jx = it % P, jy = it / P;
                 int lx = m4.y + jx, ly = m4.z + jy;
                 if (lx >= Ng) lx -= Ng;
                 if (ly >= Ng) ly -= Ng;
                 if (it < nitem && lx < Tx && ly < Ty) {
                   const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
                   const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
-                  T4 *p = plane + ((size_t)ly * RX + lx) * H + hh;
-                  T4 v = *p;
-                  v.x += wt * mv.x;
-                  v.y += wt * mv.y;
-                  v.z += wt * mv.z;
-                  v.w += wt * mv.w;
-                  *p = v;
+                  const int i = plane + ly * RX + lx;
+                  T v[C];
+                  tl.load(i, v);
+#pragma unroll
+                  for (int c = 0; c < C; ++c) v[c] += wt * mv[c];
+                  tl.store(i, v);
                 }
               }
             }
@@ -130,9 +133,10 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
     for (int q = threadIdx.x; q < tv; q += blockDim.x) {
       int x = q % Tx, y = (q / Tx) % Ty, z = q / (Tx * Ty);
       size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
-      const T *src = (const T *)(acc + ((size_t)(z * Ty + y) * RX + x) * H);
+      T v[C];
+      tl.load((z * Ty + y) * RX + x, v);
 #pragma unroll
-      for (int c = 0; c < C; ++c) grid[c * a.gstride + g] = src[c];
+      for (int c = 0; c < C; ++c) grid[c * a.gstride + g] = v[c];
     }
     __syncthreads();  // the tile is read out before the next item clears it
   });
