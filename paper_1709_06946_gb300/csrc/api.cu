@@ -508,7 +508,7 @@ int64_t estimate_bytes(const pse_ctx *c) {
   b += (int64_t)ts * 8 * 2048 * 16;                 // table (upper bound)
   b += Nt * (24 + 4 * 6 + 16 + 8 * (int64_t)ts);   // positions, keys, perm/inv, cells, records
   b += nbr * 4 + (Nt + 1) * 4;
-  b += (ntile + ncell) * 16;
+  b += (ntile * (8 + 8 * SUB_BLOCKS) + ncell * 8);
   b += (int64_t)ts * 8 * n3 + 2 * (int64_t)ts * 8 * nk;   // grids and half spectra
   b += (int64_t)ts * 8 * n3;                               // cuFFT work area (upper bound)
   b += (int64_t)ts * 8 * Nt * (7 + rows);                 // vectors and Krylov basis
@@ -666,6 +666,8 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_inv = (int *)A(sizeof(int) * N);
   c->d_tile_start = (int *)A(sizeof(int) * (c->ntiles + 1));
   c->d_tile_cur = (int *)A(sizeof(int) * (c->ntiles + 1));
+  c->d_fine_start = (int *)A(sizeof(int) * (c->ntiles * SUB_BLOCKS + 1));
+  c->d_fine_cur = (int *)A(sizeof(int) * (c->ntiles * SUB_BLOCKS + 1));
   c->d_cell_start = (int *)A(sizeof(int) * (c->ncells + 1));
   c->d_cell_cur = (int *)A(sizeof(int) * (c->ncells + 1));
   c->d_cell_list = (int *)A(sizeof(int) * N);
@@ -680,7 +682,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_sp_i0 = A(sizeof(int4) * N);
   c->d_sp_d0 = A(4 * ts * N);
   c->d_rs = A(4 * ts * N);
-  int64_t big = std::max<int64_t>(std::max<int64_t>(c->ntiles, c->ncells), N) + 1;
+  int64_t big = std::max<int64_t>(std::max<int64_t>(c->ntiles * SUB_BLOCKS, c->ncells), N) + 1;
   c->scan_cap = scan_tmp_ints(big);
   c->tile_cap = c->ntiles;
   c->d_scan_tmp = (int *)A(sizeof(int) * (size_t)c->scan_cap);
@@ -856,15 +858,19 @@ pse_status retile(pse_ctx *c, const int caps[3]) {
   const int64_t nt = tile0[c->nsys];
   if (nt > c->tile_cap) {
     void *a = dalloc(c, sizeof(int) * (size_t)(nt + 1)), *b = dalloc(c, sizeof(int) * (size_t)(nt + 1));
-    if (!a || !b) {
+    void *fa = dalloc(c, sizeof(int) * (size_t)(nt * SUB_BLOCKS + 1));
+    void *fb = dalloc(c, sizeof(int) * (size_t)(nt * SUB_BLOCKS + 1));
+    if (!a || !b || !fa || !fb) {
       c->err = "cannot allocate tile arrays";
       return PSE_ERR_OOM;
     }
     c->d_tile_start = (int *)a;
     c->d_tile_cur = (int *)b;
+    c->d_fine_start = (int *)fa;
+    c->d_fine_cur = (int *)fb;
     c->tile_cap = nt;
   }
-  int64_t need = scan_tmp_ints(std::max<int64_t>(std::max<int64_t>(nt, c->ncells), c->p.N) + 1);
+  int64_t need = scan_tmp_ints(std::max<int64_t>(std::max<int64_t>(nt * SUB_BLOCKS, c->ncells), c->p.N) + 1);
   if (need > c->scan_cap) {
     void *q = dalloc(c, sizeof(int) * (size_t)need);
     if (!q) {

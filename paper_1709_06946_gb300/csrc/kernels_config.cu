@@ -77,7 +77,9 @@ __device__ __forceinline__ int support_start(double x, double h, int P) {
 }
 
 // Wraps particle u (user order) of its suspension into [0, L) and counts it in
-// the spreading tile that holds the first grid index of its support.
+// the spreading tile that holds the first grid index of its support, refined by
+// the 4 x 4 x 4 sub-block of the tile (so that the sorted order is spatially
+// coherent inside a tile: neighbours' records then lie close together).
 __global__ void k_bin(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
                       int P, const double *pos, double *posw, int *tile_key, int *tile_cnt, int *bad) {
   int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,8 +97,16 @@ __global__ void k_bin(const SysDev *__restrict__ sys, const int64_t *__restrict_
     iw[d] = wrapi(support_start(x, b.h, P), b.Ng);
   }
   int tk = b.tile0 + ((iw[2] / b.T[2]) * b.nt[1] + iw[1] / b.T[1]) * b.nt[0] + iw[0] / b.T[0];
+  int sub = (((iw[2] % b.T[2]) * 4 / b.T[2]) * 4 + (iw[1] % b.T[1]) * 4 / b.T[1]) * 4 + (iw[0] % b.T[0]) * 4 / b.T[0];
+  tk = tk * SUB_BLOCKS + sub;
   tile_key[u] = tk;
   atomicAdd(&tile_cnt[tk], 1);
+}
+
+// tile_start[t] = fine_start[t * SUB_BLOCKS] for t = 0 .. ntiles
+__global__ void k_tile_starts(int64_t ntiles, const int *fine_start, int *tile_start) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= ntiles) tile_start[t] = fine_start[t * SUB_BLOCKS];
 }
 
 __global__ void k_scatter(int64_t N, const int *key, const int *start, int *cur, int *perm, int *inv) {
@@ -312,15 +322,17 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   const int64_t N = p.N;
   const int ns = c->nsys;
   unsigned nb = (unsigned)ceil_div(N, 256);
-  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_start, 0, sizeof(int) * (c->ntiles + 1), s));
-  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_tile_cur, 0, sizeof(int) * (c->ntiles + 1), s));
+  const int64_t nfine = c->ntiles * SUB_BLOCKS;
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_fine_start, 0, sizeof(int) * (nfine + 1), s));
+  PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_fine_cur, 0, sizeof(int) * (nfine + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_start, 0, sizeof(int) * (c->ncells + 1), s));
   PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_cell_cur, 0, sizeof(int) * (c->ncells + 1), s));
   if (!c->capturing) PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_flag, 0, sizeof(int), s));  // a graph clears it once
-  k_bin<<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, d_pos, c->d_posw, c->d_tile_key, c->d_tile_start,
+  k_bin<<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, d_pos, c->d_posw, c->d_tile_key, c->d_fine_start,
                            c->d_flag);
-  PSE_TRY(exclusive_scan(c, c->d_tile_start, c->ntiles + 1, s));
-  k_scatter<<<nb, 256, 0, s>>>(N, c->d_tile_key, c->d_tile_start, c->d_tile_cur, c->d_perm, c->d_inv);
+  PSE_TRY(exclusive_scan(c, c->d_fine_start, nfine + 1, s));
+  k_scatter<<<nb, 256, 0, s>>>(N, c->d_tile_key, c->d_fine_start, c->d_fine_cur, c->d_perm, c->d_inv);
+  k_tile_starts<<<(unsigned)ceil_div(c->ntiles + 1, 256), 256, 0, s>>>(c->ntiles, c->d_fine_start, c->d_tile_start);
   if (c->prec == PSE_MIXED)
     k_derive<float><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0,
                                        (float4 *)c->d_sp_d0, c->d_rs, c->d_cell_key, c->d_cell_start);

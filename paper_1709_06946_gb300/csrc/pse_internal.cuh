@@ -107,6 +107,7 @@ struct FftGroup {
 constexpr int VEC_CHUNK = 4096;    // vector elements per block of the chunked vector kernels
 constexpr int COEF_STRIDE = 512;   // doubles of Krylov coefficients per suspension
 constexpr int MAX_ROWS = 128;      // Krylov vectors per dot-product / combination launch
+constexpr int SUB_BLOCKS = 64;     // 4 x 4 x 4 sub-blocks of a spreading tile in the sort key
 // Per-suspension coefficient block (COEF_STRIDE doubles): first and second
 // Gram-Schmidt projections, |w|^2, a scale factor, the constants +1 and -1, and
 // the coefficients of the final Krylov combination.
@@ -167,6 +168,7 @@ struct pse_ctx {
   int *d_tile_key = nullptr, *d_cell_key = nullptr;
   int *d_perm = nullptr, *d_inv = nullptr;   // sorted -> user, user -> sorted
   int *d_tile_start = nullptr, *d_tile_cur = nullptr;   // ntiles + 1
+  int *d_fine_start = nullptr, *d_fine_cur = nullptr;   // ntiles * SUB_BLOCKS + 1 (sort by tile and sub-block)
   int *d_cell_start = nullptr, *d_cell_cur = nullptr;   // ncells + 1
   int *d_cell_list = nullptr;
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)

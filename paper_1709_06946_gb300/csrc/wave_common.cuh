@@ -158,7 +158,25 @@ __device__ __forceinline__ int tile_bins(const SysDev &a, const int t[3], const 
 // the tile into the shared list (offsets, weight origins, moments when vin is
 // given, and the 3 x P one-dimensional Gaussian weights when P <= WMAX);
 // returns the number of entries (after a barrier).
-template <typename T, int C, int SLOT0>
+// Candidate order of the chunks: with SPREAD, candidate v of n is taken at
+// (v * stride) mod n for a stride coprime to n, so that every chunk samples the
+// whole tile (the sorted order is spatially coherent; a chunk of neighbouring
+// particles would cross only a few z planes and leave most plane-owning warps idle).
+__device__ __forceinline__ int spread_stride(int n) {
+  int st = 97;
+  for (;;) {  // the first odd stride from 97 that is coprime to n (a few steps at most)
+    int x = n, y = st;
+    while (y) {
+      int r = x % y;
+      x = y;
+      y = r;
+    }
+    if (x == 1 || n <= 1) return st;
+    st += 2;
+  }
+}
+
+template <typename T, int C, int SLOT0, bool SPREAD = false>
 __device__ __forceinline__ int build_list(const SysDev &a, int P, const int t0[3], int nb, const int beg[8],
                                           const int cum[9],
                                           int c0, const int4 *__restrict__ sp_i0,
@@ -166,9 +184,12 @@ __device__ __forceinline__ int build_list(const SysDev &a, int P, const int t0[3
                                           int4 *s_meta, typename V4<T>::t *s_d0, T *s_m, T *s_w, int *s_count) {
   constexpr int CP = CPad<C>::v;
   const int Ng = a.Ng;
+  const int total = cum[nb];
+  const int st = SPREAD ? spread_stride(total) : 1;
   for (int q = threadIdx.x; q < LIST_CAP; q += blockDim.x) {
     int v = c0 + q;
-    if (v >= cum[nb]) break;
+    if (v >= total) break;
+    if (SPREAD) v = (int)(((int64_t)v * st) % total);
     int b = 0;
     while (v >= cum[b + 1]) ++b;
     int k = beg[b] + (v - cum[b]);

@@ -61,22 +61,27 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
     for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
       if (threadIdx.x == 0) s_count = 0;
       __syncthreads();
-      const int n = build_list<T, C, SLOT0>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m, s_w,
-                                            &s_count);
+      const int n = build_list<T, C, SLOT0, true>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m,
+                                                  s_w, &s_count);
       for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
         const int plane = lz * Ty * RX;
-        // the warp finds the particles whose support crosses its plane 32 list entries at a time
-        for (int base = 0; base < n; base += 32) {
+        // the warp finds the particles whose support crosses its plane 32 list entries at a
+        // time; group g holds entries g, g + ng, g + 2 ng, ... so that particles taken one
+        // after the other lie far apart in the (spatially sorted) list and rarely update
+        // the same points back to back
+        const int ng = (n + 31) >> 5;
+        for (int g = 0; g < ng; ++g) {
+          const int mine = lane * ng + g;
           int jzl = P;
-          if (base + lane < n) {
-            jzl = lz - s_meta[base + lane].w;
+          if (mine < n) {
+            jzl = lz - s_meta[mine].w;
             if (jzl < 0) jzl += Ng;
           }
           unsigned hits = __ballot_sync(0xffffffffu, jzl < P);
           while (hits) {
             const int b = __ffs(hits) - 1;
             hits &= hits - 1;
-            const int e = base + b;
+            const int e = b * ng + g;
             const int jz = __shfl_sync(0xffffffffu, jzl, b);
             const int4 m4 = s_meta[e];
             T mv[C];
