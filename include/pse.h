@@ -340,7 +340,9 @@ pse_status pse_overlap_force(pse_handle h, const double *pos, double kspring, vo
 
 /* Autotuner (no counterpart in the paper).  Times, on the configuration pos and
  * the handle's own stream, `reps` calls of each candidate: lanes per particle of
- * the pair sum (1, 4, 8, 16, 32; the S -> E plus the full product) and spreading
+ * the pair sum (1, 4, 8, 16, 32; the S -> E plus the full product), then at the
+ * chosen lanes the pair sum with its table staged in shared memory by one
+ * 1024-thread CTA per SM (FP32, when the table fits), and spreading
  * tile caps (x, y, z) in {16,16,16}, {16,8,16}, {8,8,16}, {8,16,16}, {16,16,32},
  * {16,8,32}, {32,8,16} (the S -> E wave product; each suspension's tile is the
  * largest shape within the caps that divides its grid and fits shared memory),
@@ -348,6 +350,8 @@ pse_status pse_overlap_force(pse_handle h, const double *pos, double kspring, vo
  * the handle's later calls; out (may be NULL) reports it and every timing. */
 typedef struct pse_tuning {
   int32_t real_lanes;
+  int32_t real_smem_table;    /* 1: the pair sum reads its table from shared memory (FP32, if it fits) */
+  double real_smem_ms;        /* its time, when tried */
   int32_t tile[3];            /* chosen tile of suspension 0 */
   double best_real_ms, best_wave_ms;
   int32_t n_lanes, n_tiles;   /* candidates timed */

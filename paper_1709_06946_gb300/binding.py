@@ -89,7 +89,8 @@ REQ_KINDS = {'mobility': 0, 'sample': 1, 'step': 2}
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [('real_lanes', ctypes.c_int32), ('tile', ctypes.c_int32 * 3), ('best_real_ms', ctypes.c_double),
+    _fields_ = [('real_lanes', ctypes.c_int32), ('real_smem_table', ctypes.c_int32), ('real_smem_ms', ctypes.c_double),
+                ('tile', ctypes.c_int32 * 3), ('best_real_ms', ctypes.c_double),
                 ('best_wave_ms', ctypes.c_double), ('n_lanes', ctypes.c_int32), ('n_tiles', ctypes.c_int32),
                 ('real_ms', ctypes.c_double * 8), ('tiles', (ctypes.c_int32 * 3) * 8), ('wave_ms', ctypes.c_double * 8)]
 
@@ -369,7 +370,8 @@ class PSE:
         self._check(self._lib.pse_autotune(self._h, _ptr(pos), int(reps), ctypes.byref(t), _stream(pos)))
         self.info = self.get_info()
         lanes = [1, 4, 8, 16, 32][:t.n_lanes]
-        return {'real_lanes': t.real_lanes, 'tile': tuple(t.tile), 'best_real_ms': t.best_real_ms,
+        return {'real_lanes': t.real_lanes, 'real_smem_table': t.real_smem_table, 'real_smem_ms': t.real_smem_ms,
+                'tile': tuple(t.tile), 'best_real_ms': t.best_real_ms,
                 'best_wave_ms': t.best_wave_ms, 'real_ms': dict(zip(lanes, list(t.real_ms)[:t.n_lanes])),
                 'wave_ms': {tuple(t.tiles[k]): t.wave_ms[k] for k in range(t.n_tiles)}}
 

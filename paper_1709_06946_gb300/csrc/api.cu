@@ -507,7 +507,7 @@ int64_t estimate_bytes(const pse_ctx *c) {
   int64_t b = 0;
   b += (int64_t)ts * 8 * 2048 * 16;                 // table (upper bound)
   b += Nt * (24 + 4 * 6 + 16 + 8 * (int64_t)ts);   // positions, keys, perm/inv, cells, records
-  b += nbr * 4 + (Nt + 1) * 4;
+  b += nbr * 4 * (int64_t)ts + (Nt + 1) * 4;
   b += (ntile * (8 + 8 * SUB_BLOCKS) + ncell * 8);
   b += (int64_t)ts * 8 * n3 + 2 * (int64_t)ts * 8 * nk;   // grids and half spectra
   b += (int64_t)ts * 8 * n3;                               // cuFFT work area (upper bound)
@@ -557,6 +557,11 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   const int64_t N = c->p.N;
   PSE_CUDA_TRY(c, cudaGetDevice(&c->device));
   PSE_CUDA_TRY(c, cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
+  {
+    int optin = 0;
+    PSE_CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    c->smem_optin = optin > 4096 ? (size_t)optin - 4096 : 0;  // room for the kernel's static shared memory
+  }
   // per-suspension layout: particles, tiles, cells, half spectra, vector blocks
   c->hs.assign(ns, SysDev{});
   std::vector<int64_t> p0(ns + 1, 0), k0(ns + 1, 0);
@@ -677,7 +682,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
     c->err = "neighbour list exceeds 2^31 entries";
     return PSE_ERR_INVALID_ARG;
   }
-  c->d_nbr = (int *)A(sizeof(int) * (size_t)c->nbr_cap);
+  c->d_nbr_geo = A(4 * ts * (size_t)c->nbr_cap);
   c->d_nbr_tot = (unsigned long long *)A(2 * sizeof(unsigned long long) * ns);
   c->d_sp_i0 = A(sizeof(int4) * N);
   c->d_sp_d0 = A(4 * ts * N);
@@ -944,6 +949,23 @@ pse_status autotune_impl(pse_ctx *c, const double *pos, int reps, pse_tuning *ou
   }
   c->opt.real_lanes = bestg;
   t.real_lanes = bestg;
+  // the table in shared memory (FP32, when it fits), at the chosen lanes
+  t.real_smem_table = 0;
+  if (c->prec == PSE_MIXED && sizeof(float) * 8 * (size_t)c->table_len <= c->smem_optin) {
+    c->real_smem_table = 1;
+    double ms = 0;
+    PSE_TRY(time_ms(c, s, reps, [&] {
+      pse_status a = real_apply(c, c->d_v[0], c->d_v[1], M_SE, s);
+      return a != PSE_OK ? a : real_apply(c, c->d_v[0], c->d_v[2], M_FULL, s);
+    }, &ms));
+    t.real_smem_ms = ms;
+    if (ms < best) {
+      best = ms;
+      t.real_smem_table = 1;
+    } else {
+      c->real_smem_table = 0;
+    }
+  }
   // spreading / interpolation tiles: candidate caps, timed on the S -> E wave product
   const int cand[][3] = {{16, 16, 16}, {16, 8, 16}, {8, 8, 16}, {8, 16, 16}, {16, 16, 32}, {16, 8, 32}, {32, 8, 16}};
   std::vector<std::vector<int>> seen;

@@ -28,6 +28,15 @@ __device__ __forceinline__ void for_each_item(int *queue, int total, F &&f) {
   }
 }
 
+// A particle index carried in the fourth component of a separation record (the
+// bits of the index in FP32; the value, exactly, in FP64).
+template <typename T> __device__ __forceinline__ T index_as_real(int j);
+template <> __device__ __forceinline__ float index_as_real<float>(int j) { return __int_as_float(j); }
+template <> __device__ __forceinline__ double index_as_real<double>(int j) { return (double)j; }
+template <typename T> __device__ __forceinline__ int real_as_index(T x);
+template <> __device__ __forceinline__ int real_as_index<float>(float x) { return __float_as_int(x); }
+template <> __device__ __forceinline__ int real_as_index<double>(double x) { return (int)x; }
+
 // wrap an integer index into [0, n)
 __device__ __forceinline__ int wrapi(int i, int n) {
   i %= n;

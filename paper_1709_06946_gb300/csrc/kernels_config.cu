@@ -190,14 +190,14 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
   return r;
 }
 
-// Neighbour list in one pass: particle i writes the indices of its neighbours
-// (r < r_cut, minimum image within its own suspension) into its own slots and
-// records their number; per suspension the total and the largest count are
+// Neighbour list in one pass: particle i writes, for each neighbour j (r < r_cut,
+// minimum image within its own suspension), the separation x_i - x_j and j into
+// its own row of slots and records their number; per suspension the total and the largest count are
 // accumulated for the host's capacity check.
 template <typename T>
 __global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
                       float rc2f, double rc2, const void *rs, const int *cell_start, const int *cell_list, int *cnt,
-                      int *list, unsigned long long *tot, int *ovf) {
+                      typename V4<T>::t *geo, unsigned long long *tot, int *ovf) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Ntot) return;
   const int si = find_sys(p0, nsys, i);
@@ -218,7 +218,7 @@ __global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict_
   int lo = a.nc >= 5 ? -2 : 0, hi = a.nc >= 5 ? 2 : a.nc - 1;
   int n = 0;
   const int slots = a.slots;
-  int *mine = list + a.nbr0 + (i - a.p0) * slots;
+  typename V4<T>::t *mgeo = geo + a.nbr0 + (i - a.p0) * slots;
   for (int dz = lo; dz <= hi; ++dz)
     for (int dy = lo; dy <= hi; ++dy)
       for (int dx = lo; dx <= hi; ++dx) {
@@ -230,19 +230,36 @@ __global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict_
           int j = cell_list[k];
           if (j == i) continue;
           bool in;
+          T d[3], r2;
+          (void)r2;
           if (sizeof(T) == 4) {
             float3 r = sep(pf, ci, ((const float4 *)rs)[j], a);
-            in = r.x * r.x + r.y * r.y + r.z * r.z < rc2f;
+            d[0] = r.x;
+            d[1] = r.y;
+            d[2] = r.z;
+            r2 = (T)(r.x * r.x + r.y * r.y + r.z * r.z);
+            in = (float)r2 < rc2f;
           } else {
             double4_32a q = ((const double4_32a *)rs)[j];
             double rx = pd.x - q.x, ry = pd.y - q.y, rz = pd.z - q.z;
             rx -= a.L * rint(rx / a.L);
             ry -= a.L * rint(ry / a.L);
             rz -= a.L * rint(rz / a.L);
-            in = rx * rx + ry * ry + rz * rz < rc2;
+            d[0] = (T)rx;
+            d[1] = (T)ry;
+            d[2] = (T)rz;
+            r2 = (T)(rx * rx + ry * ry + rz * rz);
+            in = (double)r2 < rc2;
           }
           if (in) {
-            if (n < slots) mine[n] = j;
+            if (n < slots) {  // separation x_i - x_j and the neighbour's index in one record
+              typename V4<T>::t gg;
+              gg.x = d[0];
+              gg.y = d[1];
+              gg.z = d[2];
+              gg.w = index_as_real<T>(j);
+              mgeo[n] = gg;
+            }
             ++n;
           }
         }
@@ -347,10 +364,12 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
     PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long) * ns, s));
     if (c->prec == PSE_MIXED)
       k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
-                                         c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot, c->d_flag + 1);
+                                         c->d_cell_list, c->d_nbr_start, (float4 *)c->d_nbr_geo, c->d_nbr_tot,
+                                         c->d_flag + 1);
     else
       k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
-                                          c->d_cell_list, c->d_nbr_start, c->d_nbr, c->d_nbr_tot, c->d_flag + 1);
+                                          c->d_cell_list, c->d_nbr_start, (double4_32a *)c->d_nbr_geo, c->d_nbr_tot,
+                                          c->d_flag + 1);
     if (c->capturing) return PSE_OK;  // the graph's caller checks the flags and the totals afterwards
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_nbr_tot, c->d_nbr_tot, 2 * sizeof(unsigned long long) * ns,
@@ -380,12 +399,12 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
       c->err = "neighbour list exceeds 2^31 entries";
       return PSE_ERR_INVALID_ARG;
     }
-    void *q = alloc_dev(c, sizeof(int) * (size_t)cap);
-    if (!q) {
+    void *gq = alloc_dev(c, 4 * c->ts * (size_t)cap);
+    if (!gq) {
       c->err = "cannot allocate neighbour list";
       return PSE_ERR_OOM;
     }
-    c->d_nbr = (int *)q;  // the old list stays in c->allocs and is freed at destroy
+    c->d_nbr_geo = gq;  // the old list stays in c->allocs and is freed at destroy
     c->nbr_cap = cap;
     ++c->layout_version;
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_sys, c->hs.data(), sizeof(SysDev) * ns, cudaMemcpyHostToDevice, s));

@@ -60,12 +60,24 @@ template <> struct Pos<double> {
   }
 };
 
+template <bool SH = false>
 __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, float r, float f[7]) {
   float x = r * (float)a.inv_dr;
   int q = min((int)x, a.len - 2);
   float t = x - (float)q;
   const float4 *t4 = (const float4 *)tab;
-  float4 a0 = __ldg(t4 + 2 * q), a1 = __ldg(t4 + 2 * q + 1), b0 = __ldg(t4 + 2 * q + 2), b1 = __ldg(t4 + 2 * q + 3);
+  float4 a0, a1, b0, b1;
+  if (SH) {  // table staged in shared memory
+    a0 = t4[2 * q];
+    a1 = t4[2 * q + 1];
+    b0 = t4[2 * q + 2];
+    b1 = t4[2 * q + 3];
+  } else {
+    a0 = __ldg(t4 + 2 * q);
+    a1 = __ldg(t4 + 2 * q + 1);
+    b0 = __ldg(t4 + 2 * q + 2);
+    b1 = __ldg(t4 + 2 * q + 3);
+  }
   f[0] = fmaf(t, b0.x - a0.x, a0.x);
   f[1] = fmaf(t, b0.y - a0.y, a0.y);
   f[2] = fmaf(t, b0.z - a0.z, a0.z);
@@ -75,6 +87,7 @@ __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, floa
   f[6] = fmaf(t, b1.z - a1.z, a1.z);
 }
 
+template <bool SH = false>
 __device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, double r, double f[7]) {
   double x = r * a.inv_dr;
   int q = min((int)x, a.len - 2);
@@ -95,38 +108,50 @@ __device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, dou
 // the neighbours' records are fetched in parallel) and the partial sums are
 // reduced with shuffles; the first lane of the group adds the self term.
 // FP32: at most 64 registers so that four 256-thread CTAs fit an SM (the full
-// 8 -> 8 product would otherwise take 74 and leave room for three).
-template <typename T, int MODE, int G>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_real(RealArgs a, const SysDev *__restrict__ sys,
+// 8 -> 8 product would otherwise take 74 and leave room for three).  With
+// SHT (FP32 only) one 1024-thread CTA per SM first copies the table into shared
+// memory and the lookups leave L1 to the neighbours' records.
+template <typename T, int MODE, int G, bool SHT = false, int NT = SHT ? 1024 : 256>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real(RealArgs a,
+                                              const SysDev *__restrict__ sys,
                                               const int64_t *__restrict__ p0, const int *__restrict__ active,
                                               int *queue, int nitems, const void *rs,
-                                              const int *__restrict__ nstart, const int *__restrict__ nbr,
+                                              const int *__restrict__ nstart,
+                                              const typename V4<T>::t *__restrict__ geo,
                                               const T *__restrict__ vin, T *__restrict__ vout,
-                                              const T *__restrict__ tab) {
+                                              const T *__restrict__ gtab) {
+  extern __shared__ __align__(16) unsigned char tab_raw[];
+  const T *tab = gtab;
+  if (SHT) {
+    float4 *dst = (float4 *)tab_raw;
+    const float4 *src = (const float4 *)gtab;
+    for (int q = threadIdx.x; q < 2 * a.len; q += blockDim.x) dst[q] = src[q];
+    __syncthreads();
+    tab = (const T *)tab_raw;
+  }
   constexpr bool HAS_F = MODE != M_SE, WANT_U = MODE != M_SE, WANT_E = MODE != M_FSU;
   using T4 = typename V4<T>::t;
   for_each_item(queue, nitems, [&](int item) {
-    const int64_t gid = ((int64_t)item * 256 + threadIdx.x) / G;
+    const int64_t gid = ((int64_t)item * NT + threadIdx.x) / G;
     const int sub = threadIdx.x % G;
     const int64_t i = gid < a.Ntot ? gid : a.Ntot - 1;
     const int si = find_sys(p0, a.nsys, i);
     const bool live = gid < a.Ntot && active[si];
     const SysDev &sd = sys[si];
-    Pos<T> pi;
-    pi.load(rs, (int)i);
     const T4 *v4 = (const T4 *)vin;
     T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
+    // particle i's row of slots; an overflowed list is flagged and redone
     const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots;
-    const int64_t e = live ? k0 + min(nstart[i], sd.slots) : 0;  // an overflowed list is flagged and redone
-    for (int64_t k = (live ? k0 : 0) + sub; k < e; k += G) {
-      int j = nbr[k];
-      T d[3];
-      pi.sep(rs, j, sd, d);
-      T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      T r = sqrt(r2), ir = (T)1 / r;
-      T rh[3] = {d[0] * ir, d[1] * ir, d[2] * ir};
+    const int cnt = live ? min(nstart[i], sd.slots) : 0;
+    for (int n = sub; n < cnt; n += G) {
+      const int64_t k = k0 + n;
+      const T4 gg = geo[k];  // separation x_i - x_j and j, stored by the list build
+      const int j = real_as_index<T>(gg.w);
+      const T r2 = gg.x * gg.x + gg.y * gg.y + gg.z * gg.z;
+      const T ir = sizeof(T) == 4 ? (T)rsqrtf((float)r2) : (T)1 / sqrt(r2), r = r2 * ir;
+      T rh[3] = {gg.x * ir, gg.y * ir, gg.z * ir};
       T f[7];
-      lookup(tab, a, r, f);
+      lookup<SHT>(tab, a, r, f);
       T4 q0 = v4[2 * j], q1 = v4[2 * j + 1];
       T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
       T v[3];
@@ -199,13 +224,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_real(RealArgs a
 
 template <typename T, int MODE, int G>
 void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, cudaStream_t s) {
+  const size_t tab_bytes = sizeof(T) * 8 * (size_t)a.len;
+  if (sizeof(T) == 4 && c->real_smem_table && tab_bytes <= c->smem_optin) {
+    auto kern = k_real<T, MODE, G, true>;
+    static std::once_flag once;
+    std::call_once(once, [&] {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_optin);
+      cudaGetLastError();
+    });
+    static std::atomic<int> per_sm{0};
+    const int64_t items = ceil_div(a.Ntot * G, 1024);
+    unsigned grid = persistent_grid(c, kern, 1024, tab_bytes, items, per_sm);
+    int *q = next_queue(c, s);
+    kern<<<grid, 1024, tab_bytes, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_rs, c->d_nbr_start,
+                                       (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout,
+                                       (const T *)c->d_table);
+    return;
+  }
   auto kern = k_real<T, MODE, G>;
   static std::atomic<int> per_sm{0};
   const int64_t items = ceil_div(a.Ntot * G, 256);
   unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
   int *q = next_queue(c, s);
-  kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_rs, c->d_nbr_start, c->d_nbr,
-                            (const T *)vin, (T *)vout, (const T *)c->d_table);
+  kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_rs, c->d_nbr_start,
+                            (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout,
+                            (const T *)c->d_table);
 }
 
 template <typename T, int G>
@@ -234,25 +277,24 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
 }
 
 // Harmonic overlap repulsion F_i = sum_j k (2a - r_ij) rh_ij over neighbours
-// closer than 2a, written in user order (one thread per particle).
+// closer than 2a (from the list's separation records), written in user order.
 template <typename T>
 __global__ void k_overlap(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
-                          double contact, double kspring, const void *rs, const int *__restrict__ nstart,
-                          const int *__restrict__ nbr, const int *__restrict__ perm, T *F) {
+                          double contact, double kspring, const int *__restrict__ nstart,
+                          const typename V4<T>::t *__restrict__ geo, const int *__restrict__ perm, T *F) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Ntot) return;
   const SysDev &sd = sys[find_sys(p0, nsys, i)];
-  Pos<T> pi;
-  pi.load(rs, (int)i);
   double f[3] = {0, 0, 0};
-  const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots, e = k0 + min(nstart[i], sd.slots);
-  for (int64_t k = k0; k < e; ++k) {
-    T d[3];
-    pi.sep(rs, nbr[k], sd, d);
-    double r = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+  const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots;
+  const int cnt = min(nstart[i], sd.slots);
+  for (int n = 0; n < cnt; ++n) {
+    const typename V4<T>::t g = geo[k0 + n];
+    const double d[3] = {(double)g.x, (double)g.y, (double)g.z};
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (r >= contact || r == 0.0) continue;
     double c = kspring * (contact - r) / r;
-    for (int m = 0; m < 3; ++m) f[m] += c * (double)d[m];
+    for (int m = 0; m < 3; ++m) f[m] += c * d[m];
   }
   const int64_t u = perm[i];
   for (int m = 0; m < 3; ++m) F[3 * u + m] = (T)f[m];
@@ -265,11 +307,11 @@ pse_status overlap_force(pse_ctx *c, double kspring, void *F, cudaStream_t s) {
   const int64_t N = c->p.N;
   const unsigned nb = (unsigned)ceil_div(N, 256);
   if (c->prec == PSE_MIXED)
-    k_overlap<float><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, c->nsys, N, 2.0 * c->p.a, kspring, c->d_rs,
-                                        c->d_nbr_start, c->d_nbr, c->d_perm, (float *)F);
+    k_overlap<float><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, c->nsys, N, 2.0 * c->p.a, kspring, c->d_nbr_start,
+                                        (const float4 *)c->d_nbr_geo, c->d_perm, (float *)F);
   else
-    k_overlap<double><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, c->nsys, N, 2.0 * c->p.a, kspring, c->d_rs,
-                                         c->d_nbr_start, c->d_nbr, c->d_perm, (double *)F);
+    k_overlap<double><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, c->nsys, N, 2.0 * c->p.a, kspring, c->d_nbr_start,
+                                         (const double4_32a *)c->d_nbr_geo, c->d_perm, (double *)F);
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

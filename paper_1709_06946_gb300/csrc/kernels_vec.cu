@@ -95,23 +95,57 @@ struct VecArgs {
   int nsys;
 };
 
-// partial[b][r] = sum over block b's chunk of rows[r] . w   (r < nrows <= DOT_ROWS)
+// 16-byte vectors of the chunked kernels (a chunk holds a multiple of 8 elements
+// and starts 32-byte aligned): 4 floats or 2 doubles per access.
+template <typename T> struct V16;
+template <> struct V16<float> {
+  using t = float4;
+  static constexpr int n = 4;
+  static __device__ __forceinline__ void get(const float4 &v, float a[4]) {
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+  }
+  static __device__ __forceinline__ float4 put(const float a[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+};
+template <> struct V16<double> {
+  using t = double2;
+  static constexpr int n = 2;
+  static __device__ __forceinline__ void get(const double2 &v, double a[2]) {
+    a[0] = v.x;
+    a[1] = v.y;
+  }
+  static __device__ __forceinline__ double2 put(const double a[2]) { return make_double2(a[0], a[1]); }
+};
+
+// acc[r] += rows[r0 + r] . w over the block's chunk, r < nr <= DOT_ROWS
 template <typename T>
-__global__ void k_multidot(VecArgs va, const T *__restrict__ rows, int64_t stride, int nrows,
-                           const T *__restrict__ w, double *partial) {
-  __shared__ double red[DOT_ROWS][DOT_NT / 32];
-  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
-  if (!va.active[ch.s]) return;
-  T acc[DOT_ROWS];
+__device__ __forceinline__ void chunk_dots(const Chunk &ch, const T *__restrict__ rows, int64_t stride, int r0, int nr,
+                                           const T *__restrict__ w, T acc[DOT_ROWS]) {
+  using V = V16<T>;
+  using VT = typename V::t;
 #pragma unroll
   for (int r = 0; r < DOT_ROWS; ++r) acc[r] = 0;
-  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
-    T we = w[e];
+  for (int64_t e = ch.beg + (int64_t)threadIdx.x * V::n; e < ch.end; e += (int64_t)blockDim.x * V::n) {
+    T wv[V::n];
+    V::get(*(const VT *)(w + e), wv);
 #pragma unroll
     for (int r = 0; r < DOT_ROWS; ++r)
-      if (r < nrows) acc[r] += rows[r * stride + e] * we;
+      if (r < nr) {
+        T x[V::n];
+        V::get(*(const VT *)(rows + (r0 + r) * stride + e), x);
+#pragma unroll
+        for (int i = 0; i < V::n; ++i) acc[r] += x[i] * wv[i];
+      }
   }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+}
+
+// partial[b * pstride + r0 + r] = block sum of acc[r] (FP64 across threads), r < nr
+template <typename T>
+__device__ __forceinline__ void block_sums(const T acc[DOT_ROWS], int nr, double *partial, int pstride, int r0,
+                                           double red[DOT_ROWS][DOT_NT / 32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int r = 0; r < DOT_ROWS; ++r) {
     double v = (double)acc[r];
@@ -120,11 +154,24 @@ __global__ void k_multidot(VecArgs va, const T *__restrict__ rows, int64_t strid
     if (lane == 0) red[r][wid] = v;
   }
   __syncthreads();
-  if (threadIdx.x < DOT_ROWS) {
+  if (threadIdx.x < nr) {
     double sum = 0;
     for (int k = 0; k < DOT_NT / 32; ++k) sum += red[threadIdx.x][k];
-    partial[(size_t)blockIdx.x * DOT_ROWS + threadIdx.x] = sum;
+    partial[(size_t)blockIdx.x * pstride + r0 + threadIdx.x] = sum;
   }
+  __syncthreads();
+}
+
+// partial[b][r] = sum over block b's chunk of rows[r] . w   (r < nrows <= DOT_ROWS)
+template <typename T>
+__global__ void k_multidot(VecArgs va, const T *__restrict__ rows, int64_t stride, int nrows,
+                           const T *__restrict__ w, double *partial) {
+  __shared__ double red[DOT_ROWS][DOT_NT / 32];
+  const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
+  if (!va.active[ch.s]) return;
+  T acc[DOT_ROWS];
+  chunk_dots(ch, rows, stride, 0, nrows, w, acc);
+  block_sums(acc, nrows, partial, DOT_ROWS, 0, red);
 }
 
 // out[s * COEF_STRIDE + r] = sum of the partials of suspension s (one block per suspension).
@@ -146,6 +193,8 @@ template <typename T, bool SET>
 __global__ void k_combine(VecArgs va, T *w, const T *__restrict__ rows, int64_t stride, int nrows,
                           const int *__restrict__ nrows_s, const double *__restrict__ coef, T sgn,
                           const int *__restrict__ nrows_dev = nullptr, int add = 0) {
+  using V = V16<T>;
+  using VT = typename V::t;
   __shared__ T cs[MAX_ROWS];
   const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
   if (!va.active[ch.s]) return;
@@ -154,10 +203,26 @@ __global__ void k_combine(VecArgs va, T *w, const T *__restrict__ rows, int64_t 
   const double *cf = coef + (size_t)ch.s * COEF_STRIDE;
   for (int r = threadIdx.x; r < nr; r += blockDim.x) cs[r] = (T)cf[r];
   __syncthreads();
-  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
-    T sum = 0;
-    for (int r = 0; r < nr; ++r) sum += cs[r] * rows[r * stride + e];
-    w[e] = SET ? sgn * sum : w[e] + sgn * sum;
+  for (int64_t e = ch.beg + (int64_t)threadIdx.x * V::n; e < ch.end; e += (int64_t)blockDim.x * V::n) {
+    T sum[V::n];
+#pragma unroll
+    for (int i = 0; i < V::n; ++i) sum[i] = 0;
+    for (int r = 0; r < nr; ++r) {
+      T x[V::n];
+      V::get(*(const VT *)(rows + r * stride + e), x);
+#pragma unroll
+      for (int i = 0; i < V::n; ++i) sum[i] += cs[r] * x[i];
+    }
+    T out[V::n];
+    if (SET) {
+#pragma unroll
+      for (int i = 0; i < V::n; ++i) out[i] = sgn * sum[i];
+    } else {
+      V::get(*(const VT *)(w + e), out);
+#pragma unroll
+      for (int i = 0; i < V::n; ++i) out[i] += sgn * sum[i];
+    }
+    *(VT *)(w + e) = V::put(out);
   }
 }
 
@@ -170,32 +235,11 @@ __global__ void k_multidot_rows(VecArgs va, const T *__restrict__ rows, int64_t 
   const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
   if (!va.active[ch.s]) return;
   const int nrows = min(*nrows_dev + add, MAX_ROWS);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int r0 = 0; r0 < nrows; r0 += DOT_ROWS) {
     const int nr = min(DOT_ROWS, nrows - r0);
     T acc[DOT_ROWS];
-#pragma unroll
-    for (int r = 0; r < DOT_ROWS; ++r) acc[r] = 0;
-    for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
-      T we = w[e];
-#pragma unroll
-      for (int r = 0; r < DOT_ROWS; ++r)
-        if (r < nr) acc[r] += rows[(r0 + r) * stride + e] * we;
-    }
-#pragma unroll
-    for (int r = 0; r < DOT_ROWS; ++r) {
-      double v = (double)acc[r];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[r][wid] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < nr) {
-      double sum = 0;
-      for (int k = 0; k < DOT_NT / 32; ++k) sum += red[threadIdx.x][k];
-      partial[(size_t)blockIdx.x * MAX_ROWS + r0 + threadIdx.x] = sum;
-    }
-    __syncthreads();
+    chunk_dots(ch, rows, stride, r0, nr, w, acc);
+    block_sums(acc, nr, partial, MAX_ROWS, r0, red);
   }
 }
 
@@ -219,24 +263,37 @@ __global__ void k_dot_final_rows(VecArgs va, const double *partial, const int *n
 template <typename T>
 __global__ void k_vscale_row(VecArgs va, T *basis, int64_t stride, const int *iter, int delta, const T *src, T *vin,
                              const double *__restrict__ coef) {
+  using V = V16<T>;
+  using VT = typename V::t;
   const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
   if (!va.active[ch.s]) return;
   const T f = (T)coef[(size_t)ch.s * COEF_STRIDE];
   T *dst = basis + (int64_t)(*iter + delta) * stride;
-  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) {
-    const T v = f * src[e];
-    dst[e] = v;
-    if (vin) vin[e] = v;
+  for (int64_t e = ch.beg + (int64_t)threadIdx.x * V::n; e < ch.end; e += (int64_t)blockDim.x * V::n) {
+    T x[V::n];
+    V::get(*(const VT *)(src + e), x);
+#pragma unroll
+    for (int i = 0; i < V::n; ++i) x[i] *= f;
+    *(VT *)(dst + e) = V::put(x);
+    if (vin) *(VT *)(vin + e) = V::put(x);
   }
 }
 
 // dst = f * src with f = a, or f = coef[s][0] per suspension when coef is given
 template <typename T>
 __global__ void k_vscale(VecArgs va, T *dst, const T *src, T a, const double *__restrict__ coef) {
+  using V = V16<T>;
+  using VT = typename V::t;
   const Chunk ch = chunk_of(va.sys, va.blk0, va.nsys);
   if (!va.active[ch.s]) return;
   const T f = coef ? (T)coef[(size_t)ch.s * COEF_STRIDE] : a;
-  for (int64_t e = ch.beg + threadIdx.x; e < ch.end; e += blockDim.x) dst[e] = f * src[e];
+  for (int64_t e = ch.beg + (int64_t)threadIdx.x * V::n; e < ch.end; e += (int64_t)blockDim.x * V::n) {
+    T x[V::n];
+    V::get(*(const VT *)(src + e), x);
+#pragma unroll
+    for (int i = 0; i < V::n; ++i) x[i] *= f;
+    *(VT *)(dst + e) = V::put(x);
+  }
 }
 
 template <typename T>

@@ -140,6 +140,8 @@ struct pse_ctx {
   double lanczos_tol, krylov_tol;
   std::string err;
   int device = 0, nsm = 0;
+  size_t smem_optin = 0;        // largest dynamic shared memory a 1024-thread pair-sum CTA may take
+  int real_smem_table = 0;      // pair sum with the table staged in shared memory (autotuned)
   int64_t dev_bytes = 0;
   std::vector<void *> allocs;
 
@@ -172,7 +174,8 @@ struct pse_ctx {
   int *d_cell_start = nullptr, *d_cell_cur = nullptr;   // ncells + 1
   int *d_cell_list = nullptr;
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
-  int *d_nbr = nullptr;         // neighbour slots: particle i of suspension s owns slots*(i-p0) + nbr0 ...
+  void *d_nbr_geo = nullptr;    // neighbour slots, particle i of suspension s owning nbr0 + (i - p0) slots ...:
+                                // real4 (x_i - x_j, j) per neighbour, written by the list build
   int64_t nbr_cap = 0, npairs = 0, npairs_est = 0;  // last list's pairs; estimate from the densities
   std::vector<int64_t> npairs_sys;
   unsigned long long *d_nbr_tot = nullptr;  // per suspension: total pairs and maximum count

@@ -38,7 +38,9 @@ def test_autotune_keeps_results(pkg, prec):
     U0, E0 = h.mobility(x, Ft, St)
     t = h.autotune(x, reps=2)
     assert t['real_lanes'] in (1, 4, 8, 16, 32) and len(t['real_ms']) == 5 and len(t['wave_ms']) >= 2
-    assert t['best_real_ms'] == min(t['real_ms'].values())
+    tried = list(t['real_ms'].values()) + ([t['real_smem_ms']] if t['real_smem_ms'] > 0 else [])
+    assert t['best_real_ms'] == min(tried)
+    assert t['real_smem_table'] == (t['real_smem_ms'] > 0 and t['real_smem_ms'] < min(t['real_ms'].values()))
     assert t['best_wave_ms'] == min(t['wave_ms'].values())
     assert tuple(h.info['tile']) == t['tile'] and t['tile'] in t['wave_ms']
     U1, E1 = h.mobility(x, Ft, St)
