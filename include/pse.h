@@ -91,8 +91,9 @@ typedef struct pse_options {
   int32_t krylov_maxiter;  /* 0 = 50 */
   int32_t tile[3];         /* spreading/interpolation tile (x, y, z); 0 = auto */
   int32_t real_lanes;      /* lanes sharing one particle in the pair sum (1,4,8,16,32); 0 = auto */
-  int32_t grid_ladder;     /* 1: round the rule's grid up to an even 3-smooth size (2^i 3^j), so that
-                              a batch has few distinct grids and therefore few FFT groups; 0 = off */
+  int32_t grid_ladder;     /* 1 (default): round the rule's grid up to an even 2^i 3^j size (a finer grid
+                              only lowers the NUFFT error; cuFFT runs these sizes faster, and a batch then
+                              has few distinct grids and few FFT groups); 0: the 2,3,5,7-smooth rule */
   int32_t use_graph;       /* 1: pse_constrained_step runs as one CUDA graph (captured on first use and
                               again when dt, the presence of a force or the layout changes), with the
                               Krylov loops as conditional while nodes; 0 = launches from the host */

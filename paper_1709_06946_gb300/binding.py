@@ -208,7 +208,7 @@ def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
 
 
 def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
-             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=0, use_graph=0):
+             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=1, use_graph=0):
     o = Options()
     load().pse_default_options(ctypes.byref(o))
     o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT

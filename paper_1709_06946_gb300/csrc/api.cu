@@ -1083,6 +1083,7 @@ void pse_default_options(pse_options *o) {
   o->krylov_tol = -1.0;
   o->lanczos_maxiter = 100;
   o->krylov_maxiter = 50;
+  o->grid_ladder = 1;
 }
 
 pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT, double xi, double tol,

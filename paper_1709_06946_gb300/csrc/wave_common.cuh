@@ -247,7 +247,7 @@ struct OccCache {
 };
 
 template <typename K>
-inline unsigned wave_grid(pse_ctx *c, K kern, size_t smem, int items, OccCache &oc) {
+inline unsigned wave_grid(pse_ctx *c, K kern, size_t smem, int items, OccCache &oc, int threads = WAVE_THREADS) {
   std::atomic<int> v{0};
   {
     std::lock_guard<std::mutex> g(oc.mu);
@@ -255,7 +255,7 @@ inline unsigned wave_grid(pse_ctx *c, K kern, size_t smem, int items, OccCache &
       if (oc.per_sm[k] > 0 && oc.smem[k] == smem) v.store(oc.per_sm[k]);
   }
   const bool known = v.load() > 0;
-  unsigned grid = persistent_grid(c, kern, WAVE_THREADS, smem, items, v);
+  unsigned grid = persistent_grid(c, kern, threads, smem, items, v);
   if (!known) {
     std::lock_guard<std::mutex> g(oc.mu);
     for (int k = 0; k < 8; ++k)

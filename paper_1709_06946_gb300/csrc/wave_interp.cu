@@ -17,8 +17,10 @@ __device__ __forceinline__ void add_out(T *dst, T v) {
   atomicAdd(dst, v);
 }
 
-template <typename T, int C, int SLOT0, int PT>
-__global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
+// NT threads per CTA: 1024 for 8 components (whose tile leaves room for one CTA
+// per SM), 512 otherwise.
+template <typename T, int C, int SLOT0, int PT, int NT = (C == 8 ? 1024 : WAVE_THREADS)>
+__global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
                                                          const typename V4<T>::t *__restrict__ sp_d0,
                                                          const int *__restrict__ tile_start,
                                                          const T *__restrict__ grid_all, T *__restrict__ vout) {
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_interp(WaveArgs wa, int *queue
       __syncthreads();  // also orders the tile staging before the first use
       const int n = build_list<T, C, SLOT0>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, (const T *)nullptr, s_meta,
                                             s_d0, s_m, s_w, &s_count);
-      for (int e = warp; e < n; e += WAVE_WARPS) {
+      for (int e = warp; e < n; e += NT / 32) {
         const int4 m4 = s_meta[e];
         T acc[8];
 #pragma unroll
@@ -148,12 +150,13 @@ template <typename T, int C, int SLOT0, int PT>
 void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   static std::once_flag once;
   static OccCache occ;
-  auto kern = k_interp<T, C, SLOT0, PT>;
+  constexpr int NT = C == 8 ? 1024 : WAVE_THREADS;
+  auto kern = k_interp<T, C, SLOT0, PT, NT>;
   set_smem(kern, once);
   size_t sm = wave_smem_max<T, C>(c);
-  unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ);
+  unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ, NT);
   int *q = next_queue(c, s);
-  kern<<<grid, WAVE_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
+  kern<<<grid, NT, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
                                       c->d_tile_start, (const T *)c->d_grid, (T *)vout);
 }
 

@@ -34,7 +34,7 @@ def test_exports_every_header_symbol(lib):
 def test_default_options(lib):
     o = pkg.binding.Options()
     lib.pse_default_options(ctypes.byref(o))
-    assert o.rule == 0 and o.lanczos_maxiter == 100 and o.krylov_maxiter == 50
+    assert o.rule == 0 and o.lanczos_maxiter == 100 and o.krylov_maxiter == 50 and o.grid_ladder == 1
     assert o.lanczos_tol < 0 and o.krylov_tol < 0
 
 
@@ -137,7 +137,7 @@ def test_grid_ladder_rounds_to_three_smooth(lib):
     """With grid_ladder the grid is the next even 2^i 3^j size at or above the rule's grid."""
     h = ctypes.c_void_p()
     for L in (20.0, 37.0, 61.0, 118.0):
-        b0 = pkg.binding.estimate_bytes(1000, L, xi=0.5)
+        b0 = pkg.binding.estimate_bytes(1000, L, xi=0.5, grid_ladder=0)
         b1 = pkg.binding.estimate_bytes(1000, L, xi=0.5, grid_ladder=1)
         assert b1 >= b0
 
