@@ -25,7 +25,12 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
                                                          const int *__restrict__ tile_start,
                                                          const T *__restrict__ grid_all, T *__restrict__ vout) {
   constexpr int CP = CPad<C>::v;
-  constexpr int NPASS = PT > 0 ? (PT * PT + 31) / 32 : 1;
+  // footprint work split: NFULL passes in which each lane takes one whole (x, y)
+  // column (P points along z), then the REM leftover columns' REM * P points one
+  // per lane over NMINI passes (P = 6: one full pass and one of 24 points)
+  constexpr int PP = PT > 0 ? PT * PT : 1;
+  constexpr int NFULL = PP / 32, REM = PP % 32;
+  constexpr int NMINI = PT > 0 ? (REM * (PT > 0 ? PT : 1) + 31) / 32 : 0;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int s_count;
@@ -59,14 +64,24 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
     const int zstride = Ty * RX;
-    int pjx[NPASS], pjy[NPASS];
-    bool pok[NPASS];
+    // this lane's columns (full passes) and points (leftover passes)
+    int fjx[NFULL > 0 ? NFULL : 1], fjy[NFULL > 0 ? NFULL : 1];
+    int mjx[NMINI > 0 ? NMINI : 1], mjy[NMINI > 0 ? NMINI : 1], mjz[NMINI > 0 ? NMINI : 1];
+    bool mok[NMINI > 0 ? NMINI : 1];
 #pragma unroll
-    for (int ps = 0; ps < NPASS; ++ps) {
-      int it = ps * 32 + lane;
-      pok[ps] = it < nitem;
-      pjx[ps] = pok[ps] ? it % P : 0;
-      pjy[ps] = pok[ps] ? it / P : 0;
+    for (int ps = 0; ps < NFULL; ++ps) {
+      const int col = ps * 32 + lane;
+      fjx[ps] = col % P;
+      fjy[ps] = col / P;
+    }
+#pragma unroll
+    for (int ms = 0; ms < NMINI; ++ms) {
+      const int it = ms * 32 + lane;
+      mok[ms] = it < REM * P;
+      const int col = NFULL * 32 + (mok[ms] ? it / P : 0);
+      mjx[ms] = col % P;
+      mjy[ms] = col / P;
+      mjz[ms] = mok[ms] ? it % P : 0;
     }
     for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
       if (threadIdx.x == 0) s_count = 0;
@@ -90,12 +105,12 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
             wz[jz] = w[2 * WMAX + jz];
           }
 #pragma unroll
-          for (int ps = 0; ps < NPASS; ++ps) {
-            int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
+          for (int ps = 0; ps < NFULL; ++ps) {
+            int lx = m4.y + fjx[ps], ly = m4.z + fjy[ps];
             if (lx >= Ng) lx -= Ng;
             if (ly >= Ng) ly -= Ng;
-            if (pok[ps] && lx < Tx && ly < Ty) {
-              const T wxy = w[pjx[ps]] * w[WMAX + pjy[ps]];
+            if (lx < Tx && ly < Ty) {
+              const T wxy = w[fjx[ps]] * w[WMAX + fjy[ps]];
               const int col = ly * RX + lx;
 #pragma unroll
               for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
@@ -107,6 +122,21 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
                   for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
                 }
               }
+            }
+          }
+#pragma unroll
+          for (int ms = 0; ms < NMINI; ++ms) {
+            int lx = m4.y + mjx[ms], ly = m4.z + mjy[ms];
+            if (lx >= Ng) lx -= Ng;
+            if (ly >= Ng) ly -= Ng;
+            int lz = m4.w + mjz[ms];
+            if (lz >= Ng) lz -= Ng;
+            if (mok[ms] && lx < Tx && ly < Ty && lz < Tz) {
+              const T wt = w[mjx[ms]] * w[WMAX + mjy[ms]] * w[2 * WMAX + mjz[ms]];
+              T v[C];
+              tl.load((ly * RX + lx) + lz * zstride, v);
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
             }
           }
         } else {  // any support size: weights on the fly
