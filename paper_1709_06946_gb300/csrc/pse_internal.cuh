@@ -104,7 +104,7 @@ struct FftGroup {
   bool ok[2][9] = {{false}};
 };
 
-constexpr int VEC_CHUNK = 4096;    // vector elements per block of the chunked vector kernels
+constexpr int VEC_CHUNK = 16384;   // vector elements per block of the chunked vector kernels
 constexpr int COEF_STRIDE = 512;   // doubles of Krylov coefficients per suspension
 constexpr int MAX_ROWS = 128;      // Krylov vectors per dot-product / combination launch
 constexpr int SUB_BLOCKS = 64;     // 4 x 4 x 4 sub-blocks of a spreading tile in the sort key
