@@ -97,7 +97,8 @@ __global__ void k_bin(const SysDev *__restrict__ sys, const int64_t *__restrict_
     iw[d] = wrapi(support_start(x, b.h, P), b.Ng);
   }
   int tk = b.tile0 + ((iw[2] / b.T[2]) * b.nt[1] + iw[1] / b.T[1]) * b.nt[0] + iw[0] / b.T[0];
-  int sub = (((iw[2] % b.T[2]) * 4 / b.T[2]) * 4 + (iw[1] % b.T[1]) * 4 / b.T[1]) * 4 + (iw[0] % b.T[0]) * 4 / b.T[0];
+  int sub = (((iw[2] % b.T[2]) * SUB_SIDE / b.T[2]) * SUB_SIDE + (iw[1] % b.T[1]) * SUB_SIDE / b.T[1]) * SUB_SIDE +
+            (iw[0] % b.T[0]) * SUB_SIDE / b.T[0];
   tk = tk * SUB_BLOCKS + sub;
   tile_key[u] = tk;
   atomicAdd(&tile_cnt[tk], 1);

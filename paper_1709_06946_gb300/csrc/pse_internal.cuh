@@ -107,7 +107,8 @@ struct FftGroup {
 constexpr int VEC_CHUNK = 16384;   // vector elements per block of the chunked vector kernels
 constexpr int COEF_STRIDE = 512;   // doubles of Krylov coefficients per suspension
 constexpr int MAX_ROWS = 128;      // Krylov vectors per dot-product / combination launch
-constexpr int SUB_BLOCKS = 64;     // 4 x 4 x 4 sub-blocks of a spreading tile in the sort key
+constexpr int SUB_SIDE = 4;        // sub-blocks per tile side in the sort key
+constexpr int SUB_BLOCKS = SUB_SIDE * SUB_SIDE * SUB_SIDE;  // sub-blocks of a spreading tile
 // Per-suspension coefficient block (COEF_STRIDE doubles): first and second
 // Gram-Schmidt projections, |w|^2, a scale factor, the constants +1 and -1, and
 // the coefficients of the final Krylov combination.

@@ -77,6 +77,12 @@ int ladder_grid(int n) {
   return n;
 }
 
+// Padded row length (points) of a spreading tile; the kernels use the same rule.
+int tile_row(int Tx, int P) {
+  if (Tx >= 16) return Tx + (((P - Tx) % 8) + 8) % 8;
+  return Tx + ((Tx & 3) == 0 ? 2 : 0);
+}
+
 int pick_tile(int Ng, int minsize, int cap, bool prefer8) {
   int best = -1;
   for (int d = 1; d <= Ng; ++d) {
@@ -249,21 +255,23 @@ int choose_tile(Params &p, const int caps[3], const int fixed[3], std::string &e
   p.tile[1] = fixed[1] > 0 ? fixed[1] : pick_tile(p.Ng, mins, caps[1], false);
   p.tile[2] = fixed[2] > 0 ? fixed[2] : pick_tile(p.Ng, mins, caps[2], false);
   // shared memory of a spreading/interpolation CTA with 8 components (the
-  // largest): the tile (rows padded by 2 points when Tx is a multiple of 4) plus
-  // a 128-entry particle list; the 8-component kernels then run one CTA per SM
-  // and the 5-component ones (the GMRES loop) two
-  auto smem = [&]() {
-    int rx = p.tile[0] + ((p.tile[0] & 3) == 0 ? 2 : 0);
-    return (size_t)8 * p.tile[2] * p.tile[1] * rx * p.ts + (size_t)128 * (16 + 36 * p.ts);
-  };
+  // largest): the tile with its padded rows; the 8-component kernels then run
+  // one CTA per SM and the 5-component ones (the GMRES loop) two
+  auto smem = [&]() { return (size_t)8 * p.tile[2] * p.tile[1] * tile_row(p.tile[0], p.P) * p.ts; };
   const size_t budget = 200 * 1024;
-  while (smem() > budget && (fixed[0] <= 0 || fixed[1] <= 0 || fixed[2] <= 0)) {
-    int d = p.tile[0] >= p.tile[1] ? 0 : 1;  // keep the z planes; shrink x or y
-    if (p.tile[d] <= mins || fixed[d] > 0) d = 1 - d;
-    if (p.tile[d] <= mins || fixed[d] > 0) d = 2;
-    int nt = pick_tile(p.Ng, mins, p.tile[d] - 1, d == 0);
-    if (nt >= p.tile[d]) break;
-    p.tile[d] = nt;
+  while (smem() > budget) {  // shrink the larger of x and y first, z last
+    const int order[3] = {p.tile[0] >= p.tile[1] ? 0 : 1, p.tile[0] >= p.tile[1] ? 1 : 0, 2};
+    bool shrunk = false;
+    for (int d : order) {
+      if (fixed[d] > 0) continue;
+      const int nt = pick_tile(p.Ng, mins, p.tile[d] - 1, d == 0);
+      if (nt < p.tile[d]) {
+        p.tile[d] = nt;
+        shrunk = true;
+        break;
+      }
+    }
+    if (!shrunk) break;
   }
   if (smem() > 220 * 1024) {  // the opt-in limit is 227 KB less the kernels' static shared memory
     err = "spreading tile exceeds the shared-memory limit; choose a smaller tile";
@@ -272,6 +280,10 @@ int choose_tile(Params &p, const int caps[3], const int fixed[3], std::string &e
   for (int d = 0; d < 3; ++d) {
     if (p.Ng % p.tile[d] || (p.tile[d] < p.P - 1 && p.tile[d] != p.Ng)) {
       err = "tile sizes must divide Ng and be >= P-1";
+      return 1;
+    }
+    if (p.tile[d] > 256) {  // the kernels pack tile offsets into 10-bit fields
+      err = "tile sizes must be at most 256";
       return 1;
     }
     p.ntile[d] = p.Ng / p.tile[d];

@@ -6,11 +6,12 @@
 // 0..3, one 16-byte access) and, for 5 or 8 components, a second array
 // (component 4 alone, or components 4..7): one lane updates all components of
 // one point with two accesses and no padding.
-// The CTA walks the particles of the 2x2x2 bins whose Gaussian supports can
-// reach the tile (bins hold particles by the grid index where their support
-// starts) in chunks: the particles that overlap the tile are compacted into a
-// shared-memory list together with their offsets, weights' origins and
-// moments, then processed by the warps.
+// The particles that can reach a tile are those of the 2x2x2 bins below it
+// (bins hold particles by the grid index where their support starts); the warps
+// scan these candidates themselves, 32 at a time with a ballot, so there is no
+// shared particle list and no CTA barrier between the staging of a tile and its
+// read-out.  The 1D Gaussian weights of a particle are computed one per lane and
+// broadcast with shuffles.
 #pragma once
 
 #include <cmath>
@@ -34,12 +35,16 @@ struct WaveArgs {
 
 constexpr int WAVE_THREADS = 512;
 constexpr int WAVE_WARPS = WAVE_THREADS / 32;
-constexpr int LIST_CAP = 128;
-constexpr int WMAX = 8;   // weights kept in the list for supports up to WMAX points per side
 
-// padded row length (points) of the shared tile: keeps vector accesses of
-// neighbouring rows in different banks
-__host__ __device__ inline int tile_rx(int Tx) { return Tx + ((Tx & 3) == 0 ? 2 : 0); }
+// Padded row length (points) of the shared tile.  Rows of 16 points or more:
+// the smallest RX >= Tx with RX = P (mod 8); a warp that takes footprint point
+// (j mod P, j / P) in lane j then touches 16-byte slots RX (j / P) + j mod P = j
+// (mod 8), so each quarter warp of a 16-byte access hits 8 different bank
+// groups.  Shorter rows (where that padding would cost up to 7/8 of the tile):
+// 2 points of padding when Tx is a multiple of 4.
+__host__ __device__ constexpr int tile_rx(int Tx, int P) {
+  return Tx >= 16 ? Tx + (((P - Tx) % 8) + 8) % 8 : Tx + ((Tx & 3) == 0 ? 2 : 0);
+}
 
 template <int C> struct CPad { static constexpr int v = C <= 4 ? 4 : 8; };
 
@@ -95,12 +100,10 @@ struct TileL {
   }
 };
 
-// shared memory of a spreading/interpolation CTA (tile + particle list)
+// shared memory of a spreading/interpolation CTA (the tile)
 template <typename T, int C>
-__host__ __device__ inline size_t wave_smem(const int T3[3]) {
-  constexpr int CP = CPad<C>::v;
-  return TileL<T, C>::bytes((size_t)T3[2] * T3[1] * tile_rx(T3[0])) +
-         (size_t)LIST_CAP * (sizeof(int4) + 4 * sizeof(T) + CP * sizeof(T) + 3 * WMAX * sizeof(T));
+__host__ __device__ inline size_t wave_smem(const int T3[3], int P) {
+  return TileL<T, C>::bytes((size_t)T3[2] * T3[1] * tile_rx(T3[0], P));
 }
 
 // Sum of v[0..8) over the warp in 9 shuffles: each exchange halves the
@@ -154,72 +157,79 @@ __device__ __forceinline__ int tile_bins(const SysDev &a, const int t[3], const 
   return nb;
 }
 
-// Compacts the candidates [c0, c0 + LIST_CAP) of the tile's bins that overlap
-// the tile into the shared list (offsets, weight origins, moments when vin is
-// given, and the 3 x P one-dimensional Gaussian weights when P <= WMAX);
-// returns the number of entries (after a barrier).
-// Candidate order of the chunks: with SPREAD, candidate v of n is taken at
-// (v * stride) mod n for a stride coprime to n, so that every chunk samples the
-// whole tile (the sorted order is spatially coherent; a chunk of neighbouring
-// particles would cross only a few z planes and leave most plane-owning warps idle).
-__device__ __forceinline__ int spread_stride(int n) {
-  int st = 97;
-  for (;;) {  // the first odd stride from 97 that is coprime to n (a few steps at most)
-    int x = n, y = st;
-    while (y) {
-      int r = x % y;
-      x = y;
-      y = r;
+// Candidates of plane lz of a tile for a spreading warp: per source bin, only
+// the sub-block z-layers (particles are sorted by 4 x 4 x 4 sub-blocks of their
+// tile, z-layer major) whose support starts can reach the plane, i.e. whose
+// start z within its tile lies in [lz - P + 1, lz] (same z layer of tiles) or
+// [Tz + lz - P + 1, Tz + lz] (the layer below).  With one tile along z (where
+// supports wrap onto the same tile) every bin is taken whole.
+__device__ __forceinline__ int plane_bins(const SysDev &a, const int t[3], int lz, int P, const int *fine_start,
+                                          int beg[8], int cum[9]) {
+  int nb = 0;
+  const int nz = a.nt[2] > 1 ? 2 : 1, ny = a.nt[1] > 1 ? 2 : 1, nx = a.nt[0] > 1 ? 2 : 1, Tz = a.T[2];
+  cum[0] = 0;
+  for (int bz = 0; bz < nz; ++bz) {
+    int lo = 0, hi = SUB_SIDE - 1;
+    if (nz > 1) {
+      const int zlo = max(0, lz - P + 1 + bz * Tz), zhi = min(Tz - 1, lz + bz * Tz);
+      if (zlo > zhi) continue;
+      lo = zlo * SUB_SIDE / Tz;
+      hi = zhi * SUB_SIDE / Tz;
     }
-    if (x == 1 || n <= 1) return st;
-    st += 2;
+    const int z = wrapi(t[2] - bz, a.nt[2]);
+    for (int by = 0; by < ny; ++by)
+      for (int bx = 0; bx < nx; ++bx) {
+        const int y = wrapi(t[1] - by, a.nt[1]), x = wrapi(t[0] - bx, a.nt[0]);
+        const int64_t b = (int64_t)(a.tile0 + (z * a.nt[1] + y) * a.nt[0] + x) * SUB_BLOCKS;
+        beg[nb] = fine_start[b + lo * SUB_SIDE * SUB_SIDE];
+        cum[nb + 1] = cum[nb] + (fine_start[b + (hi + 1) * SUB_SIDE * SUB_SIDE] - beg[nb]);
+        ++nb;
+      }
   }
+  return nb;
 }
 
-template <typename T, int C, int SLOT0, bool SPREAD = false>
-__device__ __forceinline__ int build_list(const SysDev &a, int P, const int t0[3], int nb, const int beg[8],
-                                          const int cum[9],
-                                          int c0, const int4 *__restrict__ sp_i0,
-                                          const typename V4<T>::t *__restrict__ sp_d0, const T *__restrict__ vin,
-                                          int4 *s_meta, typename V4<T>::t *s_d0, T *s_m, T *s_w, int *s_count) {
-  constexpr int CP = CPad<C>::v;
+// Particle index of candidate v (0 <= v < cum[nb]) of the tile's bins.
+__device__ __forceinline__ int candidate(int v, int nb, const int beg[8], const int cum[9]) {
+  int b = 0;
+  while (b + 1 < nb && v >= cum[b + 1]) ++b;
+  return beg[b] + (v - cum[b]);
+}
+
+// Offsets (wrapped) of a support start from the tile origin; true if the P^3
+// support overlaps the tile.
+__device__ __forceinline__ bool overlaps(const SysDev &a, int P, const int t0[3], const int4 &i0, int &ox, int &oy,
+                                         int &oz) {
   const int Ng = a.Ng;
-  const int total = cum[nb];
-  const int st = SPREAD ? spread_stride(total) : 1;
-  for (int q = threadIdx.x; q < LIST_CAP; q += blockDim.x) {
-    int v = c0 + q;
-    if (v >= total) break;
-    if (SPREAD) v = (int)(((int64_t)v * st) % total);
-    int b = 0;
-    while (v >= cum[b + 1]) ++b;
-    int k = beg[b] + (v - cum[b]);
-    int4 i0 = sp_i0[k];
-    int ox = wrapi(i0.x - t0[0], Ng), oy = wrapi(i0.y - t0[1], Ng), oz = wrapi(i0.z - t0[2], Ng);
-    bool hit = (ox < a.T[0] || ox + P - 1 >= Ng) && (oy < a.T[1] || oy + P - 1 >= Ng) &&
-               (oz < a.T[2] || oz + P - 1 >= Ng);
-    if (hit) {
-      int e = atomicAdd(s_count, 1);
-      s_meta[e] = make_int4(k, ox, oy, oz);
-      typename V4<T>::t d0 = sp_d0[k];
-      s_d0[e] = d0;
-      if (vin) {
-#pragma unroll
-        for (int c = 0; c < CP; ++c) s_m[e * CP + c] = c < C ? vin[8 * (size_t)k + SLOT0 + c] : (T)0;
-      }
-      if (P <= WMAX) {
-        const T al = (T)a.alpha, hs = (T)a.h;
-        T *w = s_w + e * 3 * WMAX;
-        for (int j = 0; j < P; ++j) {
-          T dx = d0.x + (T)j * hs, dy = d0.y + (T)j * hs, dz = d0.z + (T)j * hs;
-          w[j] = exp(-al * dx * dx);
-          w[WMAX + j] = exp(-al * dy * dy);
-          w[2 * WMAX + j] = exp(-al * dz * dz);
-        }
-      }
-    }
-  }
-  __syncthreads();
-  return *s_count;
+  ox = i0.x - t0[0];  // in (-Ng, Ng): support starts and tile origins lie in [0, Ng)
+  oy = i0.y - t0[1];
+  oz = i0.z - t0[2];
+  ox += ox < 0 ? Ng : 0;
+  oy += oy < 0 ? Ng : 0;
+  oz += oz < 0 ? Ng : 0;
+  return (ox < a.T[0] || ox + P - 1 >= Ng) && (oy < a.T[1] || oy + P - 1 >= Ng) &&
+         (oz < a.T[2] || oz + P - 1 >= Ng);
+}
+
+// Signed offset of a support start from the tile origin (in (-P, T) for a
+// support that overlaps the tile when there are at least two tiles per side),
+// and the three packed into one int (10 bits each, biased by 512) for a shuffle.
+__device__ __forceinline__ int signed_offset(int o, int Ng, int P) { return o > Ng - P ? o - Ng : o; }
+__device__ __forceinline__ int pack_offsets(int x, int y, int z) { return (x + 512) | ((y + 512) << 10) | ((z + 512) << 20); }
+__device__ __forceinline__ void unpack_offsets(int p, int &x, int &y, int &z) {
+  x = (p & 1023) - 512;
+  y = ((p >> 10) & 1023) - 512;
+  z = ((p >> 20) & 1023) - 512;
+}
+
+// One 1D Gaussian weight per lane: lanes [0, P) along x, [P, 2P) along y,
+// [2P, 3P) along z (3P <= 32); exp(-alpha (d0 + j h)^2).
+template <typename T>
+__device__ __forceinline__ T lane_weight(int lane, int P, T alpha, T hs, const typename V4<T>::t &d0) {
+  if (lane >= 3 * P) return (T)0;
+  const int d = lane / P, j = lane - d * P;
+  const T o = (d == 0 ? d0.x : (d == 1 ? d0.y : d0.z)) + (T)j * hs;
+  return exp(-alpha * o * o);
 }
 
 // launchers (wave_spread.cu / wave_interp.cu)
@@ -232,11 +242,26 @@ template <typename T, int C>
 inline size_t wave_smem_max(const pse_ctx *c) {
   size_t m = 0;
   for (const SysDev &q : c->hs) {
-    size_t v = wave_smem<T, C>(q.T);
+    size_t v = wave_smem<T, C>(q.T, c->p.P);
     if (v > m) m = v;
   }
   return m;
 }
+
+// The kernels specialised for 16^3 tiles (mixed precision, P = 5, 6 or 8) are
+// taken when every suspension has that tile and at least two tiles per side (so
+// that a support crosses the periodic boundary into another tile, never back
+// into the same one, and offsets from the tile origin can be kept signed).
+constexpr int CUBE = 16;
+inline bool cubic_tiles(const pse_ctx *c) {
+  if (c->prec != PSE_MIXED || (c->p.P != 5 && c->p.P != 6 && c->p.P != 8) || c->hs.empty()) return false;
+  for (const SysDev &q : c->hs)
+    for (int d = 0; d < 3; ++d)
+      if (q.T[d] != CUBE || q.nt[d] < 2) return false;
+  return true;
+}
+void spread16_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
+void interp16_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 
 // Persistent grid of a wave kernel for a given shared-memory size (occupancy
 // looked up once per kernel and size; handles on several threads share the cache).

@@ -1,11 +1,12 @@
 // Gaussian interpolation sigma Q^T (Sec. 2.3.2, Eq. WSops2).
 //
 // Persistent CTAs take grid tiles (of any suspension) from a work counter: the
-// tile is staged in shared memory ([z][y][x][comp],
-// one coalesced pass over the component-major grids), then each warp takes a
-// particle overlapping the tile; lanes map to (x, y, component-half) items of
-// its footprint, loop over z in registers, and the partial sums are reduced
-// across the warp and added to the particle's outputs (a particle whose support
+// tile is staged in shared memory (one coalesced pass over the component-major
+// grids), then the warps scan the candidate particles 32 at a time (each warp its
+// own groups) and interpolate every one whose support overlaps the tile: each
+// lane takes whole (x, y) columns of the footprint and then leftover points,
+// the partial sums are reduced across the warp (9 shuffles for up to 8
+// components) and added to the particle's outputs (a particle whose support
 // straddles tiles receives one addition per tile).
 #include "wave_common.cuh"
 
@@ -19,33 +20,30 @@ __device__ __forceinline__ void add_out(T *dst, T v) {
 
 // NT threads per CTA: 1024 for 8 components (whose tile leaves room for one CTA
 // per SM), 512 otherwise.
-template <typename T, int C, int SLOT0, int PT, int NT = (C == 8 ? 1024 : WAVE_THREADS)>
+template <typename T, int C, int SLOT0, int PT, int NT>
 __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
-                                                         const typename V4<T>::t *__restrict__ sp_d0,
-                                                         const int *__restrict__ tile_start,
-                                                         const T *__restrict__ grid_all, T *__restrict__ vout) {
-  constexpr int CP = CPad<C>::v;
+                                               const typename V4<T>::t *__restrict__ sp_d0,
+                                               const int *__restrict__ tile_start, const T *__restrict__ grid_all,
+                                               T *__restrict__ vout) {
   // footprint work split: NFULL passes in which each lane takes one whole (x, y)
   // column (P points along z), then the REM leftover columns' REM * P points one
   // per lane over NMINI passes (P = 6: one full pass and one of 24 points)
   constexpr int PP = PT > 0 ? PT * PT : 1;
   constexpr int NFULL = PP / 32, REM = PP % 32;
   constexpr int NMINI = PT > 0 ? (REM * (PT > 0 ? PT : 1) + 31) / 32 : 0;
+  constexpr int PZ = PT > 0 ? PT : 1;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  __shared__ int s_count;
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
     if (!wa.active[si]) return;
     const SysDev &a = wa.sys[si];
-    const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
+    const int P = PT > 0 ? PT : wa.P;
+    const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2];
+    const int RX = tile_rx(Tx, P);
     const int npts = Tz * Ty * RX;
     TileL<T, C> tl;
     tl.init(smem_raw, npts);
-    int4 *s_meta = (int4 *)(smem_raw + TileL<T, C>::bytes(npts));
-    T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
-    T *s_m = (T *)(s_d0 + LIST_CAP);
-    T *s_w = s_m + LIST_CAP * CP;
     int t[3], t0[3], beg[8], cum[9];
     tile_of(a, item - a.tile0, t, t0);
     const int Ng = a.Ng;
@@ -59,8 +57,9 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
       for (int c = 0; c < C; ++c) v[c] = grid[c * a.gstride + g];
       tl.store((z * Ty + y) * RX + x, v);
     }
+    __syncthreads();
     const int nb = tile_bins(a, t, tile_start, beg, cum);
-    const int P = PT > 0 ? PT : wa.P, nitem = P * P;
+    const int total = cum[nb];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
     const int zstride = Ty * RX;
@@ -71,96 +70,109 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
 #pragma unroll
     for (int ps = 0; ps < NFULL; ++ps) {
       const int col = ps * 32 + lane;
-      fjx[ps] = col % P;
-      fjy[ps] = col / P;
+      fjx[ps] = col % PZ;
+      fjy[ps] = col / PZ;
     }
 #pragma unroll
     for (int ms = 0; ms < NMINI; ++ms) {
       const int it = ms * 32 + lane;
-      mok[ms] = it < REM * P;
-      const int col = NFULL * 32 + (mok[ms] ? it / P : 0);
-      mjx[ms] = col % P;
-      mjy[ms] = col / P;
-      mjz[ms] = mok[ms] ? it % P : 0;
+      mok[ms] = it < REM * PZ;
+      const int col = NFULL * 32 + (mok[ms] ? it / PZ : 0);
+      mjx[ms] = col % PZ;
+      mjy[ms] = col / PZ;
+      mjz[ms] = mok[ms] ? it % PZ : 0;
     }
-    for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
-      if (threadIdx.x == 0) s_count = 0;
-      __syncthreads();  // also orders the tile staging before the first use
-      const int n = build_list<T, C, SLOT0>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, (const T *)nullptr, s_meta,
-                                            s_d0, s_m, s_w, &s_count);
-      for (int e = warp; e < n; e += NT / 32) {
-        const int4 m4 = s_meta[e];
+    for (int base = warp * 32; base < total; base += (NT / 32) * 32) {
+      const int v = base + lane;
+      int k = 0, ox = 0, oy = 0, oz = 0;
+      bool hit = false;
+      if (v < total) {
+        k = candidate(v, nb, beg, cum);
+        hit = overlaps(a, P, t0, sp_i0[k], ox, oy, oz);
+      }
+      // signed offsets fit the packing for any grid (a hit's offset is in (-P, T))
+      const int pk = pack_offsets(signed_offset(ox, Ng, P), signed_offset(oy, Ng, P), signed_offset(oz, Ng, P));
+      unsigned mask = __ballot_sync(0xffffffffu, hit);
+      while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int ke = __shfl_sync(0xffffffffu, k, src);
+        int ex, ey, ez;
+        unpack_offsets(__shfl_sync(0xffffffffu, pk, src), ex, ey, ez);
+        ex += ex < 0 ? Ng : 0;  // back to offsets in [0, Ng)
+        ey += ey < 0 ? Ng : 0;
+        ez += ez < 0 ? Ng : 0;
+        const T4 d0 = sp_d0[ke];
         T acc[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = (T)0;
         if (PT > 0) {
-          const T *w = s_w + e * 3 * WMAX;
-          T wz[PT > 0 ? PT : 1];
-          int lzs[PT > 0 ? PT : 1];
+          const T wl = lane_weight(lane, PZ, alpha, hs, d0);
+          T wz[PZ];
+          int lzs[PZ];
 #pragma unroll
-          for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
-            int lz = m4.w + jz;
+          for (int jz = 0; jz < PZ; ++jz) {
+            wz[jz] = __shfl_sync(0xffffffffu, wl, 2 * PZ + jz);
+            int lz = ez + jz;
             if (lz >= Ng) lz -= Ng;
             lzs[jz] = lz < Tz ? lz : -1;
-            wz[jz] = w[2 * WMAX + jz];
           }
 #pragma unroll
           for (int ps = 0; ps < NFULL; ++ps) {
-            int lx = m4.y + fjx[ps], ly = m4.z + fjy[ps];
+            const T wxy = __shfl_sync(0xffffffffu, wl, fjx[ps]) * __shfl_sync(0xffffffffu, wl, PZ + fjy[ps]);
+            int lx = ex + fjx[ps], ly = ey + fjy[ps];
             if (lx >= Ng) lx -= Ng;
             if (ly >= Ng) ly -= Ng;
             if (lx < Tx && ly < Ty) {
-              const T wxy = w[fjx[ps]] * w[WMAX + fjy[ps]];
               const int col = ly * RX + lx;
 #pragma unroll
-              for (int jz = 0; jz < (PT > 0 ? PT : 1); ++jz) {
+              for (int jz = 0; jz < PZ; ++jz) {
                 if (lzs[jz] >= 0) {
                   const T wt = wxy * wz[jz];
-                  T v[C];
-                  tl.load(col + lzs[jz] * zstride, v);
+                  T vv[C];
+                  tl.load(col + lzs[jz] * zstride, vv);
 #pragma unroll
-                  for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
+                  for (int c = 0; c < C; ++c) acc[c] += wt * vv[c];
                 }
               }
             }
           }
 #pragma unroll
           for (int ms = 0; ms < NMINI; ++ms) {
-            int lx = m4.y + mjx[ms], ly = m4.z + mjy[ms];
+            const T wt = __shfl_sync(0xffffffffu, wl, mjx[ms]) * __shfl_sync(0xffffffffu, wl, PZ + mjy[ms]) *
+                         __shfl_sync(0xffffffffu, wl, 2 * PZ + mjz[ms]);
+            int lx = ex + mjx[ms], ly = ey + mjy[ms], lz = ez + mjz[ms];
             if (lx >= Ng) lx -= Ng;
             if (ly >= Ng) ly -= Ng;
-            int lz = m4.w + mjz[ms];
             if (lz >= Ng) lz -= Ng;
             if (mok[ms] && lx < Tx && ly < Ty && lz < Tz) {
-              const T wt = w[mjx[ms]] * w[WMAX + mjy[ms]] * w[2 * WMAX + mjz[ms]];
-              T v[C];
-              tl.load((ly * RX + lx) + lz * zstride, v);
+              T vv[C];
+              tl.load((ly * RX + lx) + lz * zstride, vv);
 #pragma unroll
-              for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
+              for (int c = 0; c < C; ++c) acc[c] += wt * vv[c];
             }
           }
         } else {  // any support size: weights on the fly
-          const T4 d0 = s_d0[e];
-          for (int base = 0; base < nitem; base += 32) {
-            const int it = base + lane;
+          for (int b0 = 0; b0 < P * P; b0 += 32) {
+            const int it = b0 + lane;
             const int jx = it % P, jy = it / P;
-            int lx = m4.y + jx, ly = m4.z + jy;
+            int lx = ex + jx, ly = ey + jy;
             if (lx >= Ng) lx -= Ng;
             if (ly >= Ng) ly -= Ng;
-            if (it < nitem && lx < Tx && ly < Ty) {
+            if (it < P * P && lx < Tx && ly < Ty) {
               const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
               const T wxy = exp(-alpha * (dx * dx + dy * dy));
               const int col = ly * RX + lx;
               for (int jz = 0; jz < P; ++jz) {
-                int lz = m4.w + jz;
+                int lz = ez + jz;
                 if (lz >= Ng) lz -= Ng;
                 if (lz < Tz) {
                   const T dz = d0.z + (T)jz * hs;
                   const T wt = wxy * exp(-alpha * dz * dz);
-                  T v[C];
-                  tl.load(col + lz * zstride, v);
+                  T vv[C];
+                  tl.load(col + lz * zstride, vv);
 #pragma unroll
-                  for (int c = 0; c < C; ++c) acc[c] += wt * v[c];
+                  for (int c = 0; c < C; ++c) acc[c] += wt * vv[c];
                 }
               }
             }
@@ -168,9 +180,8 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
         }
         const T tot = warp_reduce8(acc, lane);
         const int comp = reduce8_component(lane);
-        if ((lane & 3) == 0 && comp < C) add_out(vout + 8 * (size_t)m4.x + SLOT0 + comp, pref * tot);
+        if ((lane & 3) == 0 && comp < C) add_out(vout + 8 * (size_t)ke + SLOT0 + comp, pref * tot);
       }
-      __syncthreads();
     }
     __syncthreads();  // the staged tile is no longer read when the next item overwrites it
   });
@@ -187,7 +198,7 @@ void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ, NT);
   int *q = next_queue(c, s);
   kern<<<grid, NT, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
-                                      c->d_tile_start, (const T *)c->d_grid, (T *)vout);
+                            c->d_tile_start, (const T *)c->d_grid, (T *)vout);
 }
 
 template <typename T, int C, int SLOT0>
@@ -204,6 +215,7 @@ void interp_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
 
 // mode selects the interpolated components: M_FULL U,E (8), M_SE E (5), M_FSU U (3)
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
+  if (cubic_tiles(c)) return interp16_launch(c, a, vout, mode, s);
   if (c->prec == PSE_MIXED) {
     if (mode == M_FULL) interp_p<float, 8, 0>(c, a, vout, s);
     else if (mode == M_SE) interp_p<float, 5, 3>(c, a, vout, s);

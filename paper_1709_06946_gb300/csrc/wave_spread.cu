@@ -1,40 +1,66 @@
 // Gaussian spreading Q (Sec. 2.3.2, Eq. WSops2).
 //
 // Persistent CTAs take output tiles (of any suspension) from a work counter.
-// Warp w owns the tile's z-planes w, w + 16, ...; for
-// every particle overlapping the tile it adds the particle's P x P footprint in
-// its plane to the shared tile with plain read-modify-writes (each lane owns one
-// (x, y) point of the footprint and updates all its components; no other warp
-// touches the plane), so there are no atomics and the result is deterministic.  The tile is
-// then written once to the component-major grids with coalesced stores; no grid
-// zeroing pass is needed because the tiles cover the grid.
+// Warp w owns the tile's z-planes w, w + 16, ...: it scans the candidate
+// particles whose support can cross its plane 32 at a time (a ballot picks the
+// hits) and adds each hit's P x P footprint in the plane to the shared tile with
+// plain read-modify-writes (each lane owns one (x, y) point of the footprint and
+// updates all its components; no other warp touches the plane), so there are no
+// atomics, the result is deterministic, and the warps never wait for one another
+// between the clearing of a tile and its read-out.  The tile is then written
+// once to the component-major grids with coalesced stores; no grid zeroing pass
+// is needed because the tiles cover the grid.
 #include "wave_common.cuh"
 
 namespace pse {
 namespace {
 
+// moments [SLOT0, SLOT0 + C) of particle k (an 8-slot row), read by the whole warp
+template <typename T, int C, int SLOT0>
+__device__ __forceinline__ void load_moments(const T *__restrict__ vin, int k, T mv[C]) {
+  const T *row = vin + 8 * (size_t)k;
+  if (sizeof(T) == 4 && SLOT0 == 3 && C == 5) {
+    mv[0] = row[3];
+    const float4 q = *(const float4 *)(row + 4);
+    mv[1] = q.x;
+    mv[2] = q.y;
+    mv[3] = q.z;
+    mv[4] = q.w;
+  } else if (sizeof(T) == 4 && SLOT0 == 0 && C == 8) {
+    const float4 q = *(const float4 *)row, r = *(const float4 *)(row + 4);
+    mv[0] = q.x;
+    mv[1] = q.y;
+    mv[2] = q.z;
+    mv[3] = q.w;
+    mv[4] = r.x;
+    mv[5] = r.y;
+    mv[6] = r.z;
+    mv[7] = r.w;
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) mv[c] = row[SLOT0 + c];
+  }
+}
+
 template <typename T, int C, int SLOT0, int PT>
 __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
                                                          const typename V4<T>::t *__restrict__ sp_d0,
-                                                         const T *__restrict__ vin, const int *__restrict__ tile_start,
+                                                         const T *__restrict__ vin, const int *__restrict__ fine_start,
                                                          T *__restrict__ grid_all) {
-  constexpr int CP = CPad<C>::v;
   constexpr int NPASS = PT > 0 ? (PT * PT + 31) / 32 : 1;
+  constexpr int PZ = PT > 0 ? PT : 1;
   using T4 = typename V4<T>::t;
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  __shared__ int s_count;
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
     if (!wa.active[si]) return;
     const SysDev &a = wa.sys[si];
-    const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2], RX = tile_rx(Tx);
+    const int P = PT > 0 ? PT : wa.P, Ng = a.Ng, nitem = P * P;
+    const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2];
+    const int RX = tile_rx(Tx, P);
     const int npts = Tz * Ty * RX;
     TileL<T, C> tl;
     tl.init(smem_raw, npts);
-    int4 *s_meta = (int4 *)(smem_raw + TileL<T, C>::bytes(npts));
-    T4 *s_d0 = (T4 *)(s_meta + LIST_CAP);
-    T *s_m = (T *)(s_d0 + LIST_CAP);
-    T *s_w = s_m + LIST_CAP * CP;
     {
       T zero[C];
 #pragma unroll
@@ -44,8 +70,6 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
     __syncthreads();  // cleared before any update or (for a tile with no particles) the read-out
     int t[3], t0[3], beg[8], cum[9];
     tile_of(a, item - a.tile0, t, t0);
-    const int nb = tile_bins(a, t, tile_start, beg, cum);
-    const int P = PT > 0 ? PT : wa.P, Ng = a.Ng, nitem = P * P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
     // this lane's (x, y) footprint point in every pass (fixed for the whole tile)
@@ -58,81 +82,80 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
       pjx[ps] = pok[ps] ? it % P : 0;
       pjy[ps] = pok[ps] ? it / P : 0;
     }
-    for (int c0 = 0; c0 < cum[nb]; c0 += LIST_CAP) {
-      if (threadIdx.x == 0) s_count = 0;
-      __syncthreads();
-      const int n = build_list<T, C, SLOT0, true>(a, P, t0, nb, beg, cum, c0, sp_i0, sp_d0, vin, s_meta, s_d0, s_m,
-                                                  s_w, &s_count);
-      for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
-        const int plane = lz * Ty * RX;
-        // the warp finds the particles whose support crosses its plane 32 list entries at a
-        // time; group g holds entries g, g + ng, g + 2 ng, ... so that particles taken one
-        // after the other lie far apart in the (spatially sorted) list and rarely update
-        // the same points back to back
-        const int ng = (n + 31) >> 5;
-        for (int g = 0; g < ng; ++g) {
-          const int mine = lane * ng + g;
-          int jzl = P;
-          if (mine < n) {
-            jzl = lz - s_meta[mine].w;
-            if (jzl < 0) jzl += Ng;
-          }
-          unsigned hits = __ballot_sync(0xffffffffu, jzl < P);
-          while (hits) {
-            const int b = __ffs(hits) - 1;
-            hits &= hits - 1;
-            const int e = b * ng + g;
-            const int jz = __shfl_sync(0xffffffffu, jzl, b);
-            const int4 m4 = s_meta[e];
-            T mv[C];
-#pragma unroll
-            for (int c = 0; c < C; ++c) mv[c] = s_m[e * CP + c];
-            if (PT > 0) {
-              const T *w = s_w + e * 3 * WMAX;
-              const T wz = pref * w[2 * WMAX + jz];
-#pragma unroll
-              for (int ps = 0; ps < NPASS; ++ps) {
-                int lx = m4.y + pjx[ps], ly = m4.z + pjy[ps];
-                if (lx >= Ng) lx -= Ng;
-                if (ly >= Ng) ly -= Ng;
-                if (pok[ps] && lx < Tx && ly < Ty) {
-                  const T wt = w[pjx[ps]] * w[WMAX + pjy[ps]] * wz;
-                  const int i = plane + ly * RX + lx;
-                  T v[C];
-                  tl.load(i, v);
-#pragma unroll
-                  for (int c = 0; c < C; ++c) v[c] += wt * mv[c];
-                  tl.store(i, v);
-                }
-              }
-            } else {  // any support size: weights on the fly
-              const T4 d0 = s_d0[e];
-              const T dz = d0.z + (T)jz * hs;
-              const T wz = pref * exp(-alpha * dz * dz);
-              for (int ib = 0; ib < nitem; ib += 32) {
-                const int it = ib + lane;
-                const int jx = it % P, jy = it / P;
-                int lx = m4.y + jx, ly = m4.z + jy;
-                if (lx >= Ng) lx -= Ng;
-                if (ly >= Ng) ly -= Ng;
-                if (it < nitem && lx < Tx && ly < Ty) {
-                  const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-                  const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
-                  const int i = plane + ly * RX + lx;
-                  T v[C];
-                  tl.load(i, v);
-#pragma unroll
-                  for (int c = 0; c < C; ++c) v[c] += wt * mv[c];
-                  tl.store(i, v);
-                }
-              }
-            }
-            __syncwarp();  // the next particle may update the same points from other lanes
+    for (int lz = warp; lz < Tz; lz += WAVE_WARPS) {
+      const int plane = lz * Ty * RX;
+      const int nb = plane_bins(a, t, lz, P, fine_start, beg, cum);
+      const int total = cum[nb];
+      for (int base = 0; base < total; base += 32) {
+        const int v = base + lane;
+        int k = 0, ox = 0, oy = 0, jz = P;
+        if (v < total) {
+          k = candidate(v, nb, beg, cum);
+          int oz;
+          if (overlaps(a, P, t0, sp_i0[k], ox, oy, oz)) {
+            jz = lz - oz;
+            if (jz < 0) jz += Ng;
           }
         }
+        // signed offsets fit the packing for any grid (a hit's offset is in (-P, T))
+        const int pk = pack_offsets(signed_offset(ox, Ng, P), signed_offset(oy, Ng, P), jz < P ? jz : 0);
+        unsigned hits = __ballot_sync(0xffffffffu, jz < P);
+        while (hits) {
+          const int src = __ffs(hits) - 1;
+          hits &= hits - 1;
+          const int ke = __shfl_sync(0xffffffffu, k, src);
+          int ex, ey, ez;
+          unpack_offsets(__shfl_sync(0xffffffffu, pk, src), ex, ey, ez);
+          ex += ex < 0 ? Ng : 0;  // back to offsets in [0, Ng)
+          ey += ey < 0 ? Ng : 0;
+          const T4 d0 = sp_d0[ke];
+          T mv[C];
+          load_moments<T, C, SLOT0>(vin, ke, mv);
+          if (PT > 0) {
+            const T wl = lane_weight(lane, PZ, alpha, hs, d0);
+            const T wz = pref * __shfl_sync(0xffffffffu, wl, 2 * PZ + ez);
+#pragma unroll
+            for (int ps = 0; ps < NPASS; ++ps) {
+              const T wxy = __shfl_sync(0xffffffffu, wl, pjx[ps]) * __shfl_sync(0xffffffffu, wl, PZ + pjy[ps]);
+              int lx = ex + pjx[ps], ly = ey + pjy[ps];
+              if (lx >= Ng) lx -= Ng;
+              if (ly >= Ng) ly -= Ng;
+              if (pok[ps] && lx < Tx && ly < Ty) {
+                const T wt = wxy * wz;
+                const int i = plane + ly * RX + lx;
+                T vv[C];
+                tl.load(i, vv);
+#pragma unroll
+                for (int c = 0; c < C; ++c) vv[c] += wt * mv[c];
+                tl.store(i, vv);
+              }
+            }
+          } else {  // any support size: weights on the fly
+            const T dz = d0.z + (T)ez * hs;
+            const T wz = pref * exp(-alpha * dz * dz);
+            for (int ib = 0; ib < nitem; ib += 32) {
+              const int it = ib + lane;
+              const int jx = it % P, jy = it / P;
+              int lx = ex + jx, ly = ey + jy;
+              if (lx >= Ng) lx -= Ng;
+              if (ly >= Ng) ly -= Ng;
+              if (it < nitem && lx < Tx && ly < Ty) {
+                const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
+                const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
+                const int i = plane + ly * RX + lx;
+                T vv[C];
+                tl.load(i, vv);
+#pragma unroll
+                for (int c = 0; c < C; ++c) vv[c] += wt * mv[c];
+                tl.store(i, vv);
+              }
+            }
+          }
+          __syncwarp();  // the next particle may update the same points from other lanes
+        }
       }
-      __syncthreads();
     }
+    __syncthreads();
     T *grid = grid_all + a.grid0;
     const int tv = Tx * Ty * Tz;
     for (int q = threadIdx.x; q < tv; q += blockDim.x) {
@@ -157,7 +180,7 @@ void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t 
   unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ);
   int *q = next_queue(c, s);
   kern<<<grid, WAVE_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
-                                      (const T *)vin, c->d_tile_start, (T *)c->d_grid);
+                                      (const T *)vin, c->d_fine_start, (T *)c->d_grid);
 }
 
 template <typename T, int C, int SLOT0>
@@ -173,6 +196,7 @@ void spread_p(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
 }  // namespace
 
 void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s) {
+  if (cubic_tiles(c)) return spread16_launch(c, a, vin, mode, s);
   if (c->prec == PSE_MIXED) {
     if (mode == M_SE) spread_p<float, 5, 3>(c, a, vin, s);
     else spread_p<float, 8, 0>(c, a, vin, s);

@@ -90,6 +90,28 @@ def test_mobility_dense_many_tiles(pkg, prec):
     h.close()
 
 
+@pytest.mark.parametrize('tol,Ng', [(1e-2, 48), (1e-3, 48), (1e-4, 64)])
+def test_mobility_cubic_tiles(pkg, tol, Ng):
+    """Mixed precision with 16^3 spreading tiles (the kernels specialised for
+    them) against the oracle and against the general kernels (16 x 8 x 16
+    tiles); supports of several sizes."""
+    N, phi, xi = 3000, 0.3, 0.7
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=11)
+    F, S = pse_inputs.moments(N, seed=12)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng)
+    assert tuple(h.info['tile']) == (16, 16, 16) and h.info['Ng'] == Ng
+    hg = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, tile=(16, 8, 16))
+    assert hg.info['Ng'] == h.info['Ng'] and hg.info['P'] == h.info['P']
+    p = _oracle_params(h, N, L, xi, tol)
+    got = _mob(pkg, h, pos, F, S, 'mixed')
+    gen = _mob(pkg, hg, pos, F, S, 'mixed')
+    Uo, Eo = opse.mobility_apply(pos, F, S, p)
+    assert _rel(got, np.concatenate([Uo, Eo], 1)) < TOL['mixed']
+    assert _rel(got, gen) < 5e-6
+    h.close()
+    hg.close()
+
+
 @pytest.mark.parametrize('prec', ['fp64', 'mixed'])
 def test_edge_cases(pkg, prec):
     # single particle: only self terms and its periodic images (wave space)
