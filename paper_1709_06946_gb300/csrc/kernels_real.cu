@@ -60,6 +60,14 @@ template <> struct Pos<double> {
   }
 };
 
+// 32 bytes (8 floats) from 32-byte aligned read-only global memory in one
+// 256-bit load.
+__device__ __forceinline__ void ldg8(const float *p, float4 &lo, float4 &hi) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w)
+      : "l"(p));
+}
+
 template <bool SH = false>
 __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, float r, float f[7]) {
   float x = r * (float)a.inv_dr;
@@ -72,11 +80,9 @@ __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, floa
     a1 = t4[2 * q + 1];
     b0 = t4[2 * q + 2];
     b1 = t4[2 * q + 3];
-  } else {
-    a0 = __ldg(t4 + 2 * q);
-    a1 = __ldg(t4 + 2 * q + 1);
-    b0 = __ldg(t4 + 2 * q + 2);
-    b1 = __ldg(t4 + 2 * q + 3);
+  } else {  // entries are 8 floats (32 bytes): one 256-bit load each
+    ldg8(tab + 8 * q, a0, a1);
+    ldg8(tab + 8 * q + 8, b0, b1);
   }
   f[0] = fmaf(t, b0.x - a0.x, a0.x);
   f[1] = fmaf(t, b0.y - a0.y, a0.y);
@@ -152,7 +158,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
       T rh[3] = {gg.x * ir, gg.y * ir, gg.z * ir};
       T f[7];
       lookup<SHT>(tab, a, r, f);
-      T4 q0 = v4[2 * j], q1 = v4[2 * j + 1];
+      T4 q0, q1;
+      if constexpr (sizeof(T) == 4) ldg8((const float *)vin + 8 * (size_t)j, q0, q1);  // the 8 slots of row j
+      else q0 = v4[2 * j], q1 = v4[2 * j + 1];
       T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
       T v[3];
       Smul(s, rh, v);

@@ -66,11 +66,7 @@ __device__ __forceinline__ int soff(int i0, int t0, int Ng, int P) {
   return o > Ng - P ? o - Ng : o;
 }
 
-template <int C>
-struct Tile16 {
-  static constexpr int EXTRA = C == 5 ? 1 : (C == 8 ? 4 : 0);
-};
-
+// moments [SLOT0, SLOT0 + C) of particle k (an 8-slot row), read by the whole warp
 template <int C, int SLOT0>
 __device__ __forceinline__ void moments(const float *__restrict__ vin, int k, float mv[C]) {
   const float *row = vin + 8 * (size_t)k;
