@@ -506,7 +506,7 @@ int64_t estimate_bytes(const pse_ctx *c) {
   int rows = std::max(c->lanczos_max, c->krylov_max) + 1;
   int64_t b = 0;
   b += (int64_t)ts * 8 * 2048 * 16;                 // table (upper bound)
-  b += Nt * (24 + 4 * 6 + 16 + 8 * (int64_t)ts);   // positions, keys, perm/inv, cells, records
+  b += Nt * (24 + 4 * 6 + 16 + 12 * (int64_t)ts);  // positions, keys, perm/inv, cells, records (two orders)
   b += nbr * 4 * (int64_t)ts + (Nt + 1) * 4;
   b += (ntile * (8 + 8 * SUB_BLOCKS) + ncell * 8);
   b += (int64_t)ts * 8 * n3 + 2 * (int64_t)ts * 8 * nk;   // grids and half spectra
@@ -687,6 +687,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_sp_i0 = A(sizeof(int4) * N);
   c->d_sp_d0 = A(4 * ts * N);
   c->d_rs = A(4 * ts * N);
+  c->d_rs_cell = A(4 * ts * N);
   int64_t big = std::max<int64_t>(std::max<int64_t>(c->ntiles * SUB_BLOCKS, c->ncells), N) + 1;
   c->scan_cap = scan_tmp_ints(big);
   c->tile_cap = c->ntiles;

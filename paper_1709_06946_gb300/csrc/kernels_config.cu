@@ -156,11 +156,18 @@ __global__ void k_derive(const SysDev *__restrict__ sys, const int64_t *__restri
   atomicAdd(&cell_cnt[ck], 1);
 }
 
-__global__ void k_cell_scatter(int64_t N, const int *cell_key, const int *start, int *cur, int *list) {
+// Cell list: the particles of every cell, and a copy of their records (cell
+// offsets or positions) in the same order, so that the neighbour search reads
+// contiguous records.
+template <typename T>
+__global__ void k_cell_scatter(int64_t N, const int *cell_key, const int *start, int *cur, int *list,
+                               const typename V4<T>::t *rs, typename V4<T>::t *rs_cell) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int ck = cell_key[i];
-  list[start[ck] + atomicAdd(&cur[ck], 1)] = (int)i;
+  const int k = start[ck] + atomicAdd(&cur[ck], 1);
+  list[k] = (int)i;
+  rs_cell[k] = rs[i];
 }
 
 __device__ __forceinline__ void unpack_cell(float w, int c[3]) {
@@ -191,18 +198,26 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
   return r;
 }
 
-// Neighbour list in one pass: particle i writes, for each neighbour j (r < r_cut,
-// minimum image within its own suspension), the separation x_i - x_j and j into
-// its own row of slots and records their number; per suspension the total and the largest count are
-// accumulated for the host's capacity check.
+// Neighbour list in one pass, one thread per particle i: for each neighbour j
+// (r < r_cut, minimum image within its own suspension) the separation x_i - x_j
+// and j go into i's own row of slots, and the row's length into cnt[i]; per
+// suspension the total and the largest count are accumulated for the host's
+// capacity check.  The stencil is 5 x 5 x 5 cells (every cell once when there
+// are fewer than 5 per side); each of its 25 x runs of cells is one range of
+// the cell-ordered records, or two where it wraps, so a thread streams through
+// contiguous records.
 template <typename T>
-__global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0, int nsys, int64_t Ntot,
-                      float rc2f, double rc2, const void *rs, const int *cell_start, const int *cell_list, int *cnt,
-                      typename V4<T>::t *geo, unsigned long long *tot, int *ovf) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0,
+                                             int nsys, int64_t Ntot, float rc2f, double rc2, const void *rs,
+                                             const void *rs_cell, const int *__restrict__ cell_start,
+                                             const int *__restrict__ cell_list, int *cnt, typename V4<T>::t *geo,
+                                             unsigned long long *tot, int *ovf) {
+  using T4 = typename V4<T>::t;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Ntot) return;
   const int si = find_sys(p0, nsys, i);
   const SysDev &a = sys[si];
+  const int nc = a.nc, slots = a.slots;
   int ci[3];
   float4 pf;
   double4_32a pd;
@@ -211,64 +226,90 @@ __global__ void k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict_
     unpack_cell(pf.w, ci);
   } else {
     pd = ((const double4_32a *)rs)[i];
-    ci[0] = min((int)(pd.x / a.cs), a.nc - 1);
-    ci[1] = min((int)(pd.y / a.cs), a.nc - 1);
-    ci[2] = min((int)(pd.z / a.cs), a.nc - 1);
+    ci[0] = min((int)(pd.x / a.cs), nc - 1);
+    ci[1] = min((int)(pd.y / a.cs), nc - 1);
+    ci[2] = min((int)(pd.z / a.cs), nc - 1);
   }
-  // 5-cell stencil per dimension, or every cell once when there are fewer than 5
-  int lo = a.nc >= 5 ? -2 : 0, hi = a.nc >= 5 ? 2 : a.nc - 1;
+  const bool wide = nc >= 5;
+  const int span = wide ? 5 : nc;
+  const int x0 = wide ? ci[0] - 2 : 0, x1 = wide ? ci[0] + 2 : nc - 1;
+  T4 *mgeo = geo + a.nbr0 + (i - a.p0) * slots;
   int n = 0;
-  const int slots = a.slots;
-  typename V4<T>::t *mgeo = geo + a.nbr0 + (i - a.p0) * slots;
-  for (int dz = lo; dz <= hi; ++dz)
-    for (int dy = lo; dy <= hi; ++dy)
-      for (int dx = lo; dx <= hi; ++dx) {
-        int cz = a.nc >= 5 ? wrapi(ci[2] + dz, a.nc) : dz, cy = a.nc >= 5 ? wrapi(ci[1] + dy, a.nc) : dy;
-        int cx = a.nc >= 5 ? wrapi(ci[0] + dx, a.nc) : dx;
-        int c = a.cell0 + (cz * a.nc + cy) * a.nc + cx;
-        int e = cell_start[c + 1];
-        for (int k = cell_start[c]; k < e; ++k) {
-          int j = cell_list[k];
-          if (j == i) continue;
-          bool in;
-          T d[3], r2;
-          (void)r2;
+  for (int dz = 0; dz < span; ++dz)
+    for (int dy = 0; dy < span; ++dy) {
+      int cz = dz, cy = dy;
+      if (wide) {
+        cz += ci[2] - 2;
+        cy += ci[1] - 2;
+        cz += cz < 0 ? nc : (cz >= nc ? -nc : 0);
+        cy += cy < 0 ? nc : (cy >= nc ? -nc : 0);
+      }
+      const int rowc = a.cell0 + (cz * nc + cy) * nc;
+      int s1, e1, s2 = 0, e2 = 0;
+      if (x0 < 0) {  // cells [x0 + nc, nc) and [0, x1]
+        s1 = cell_start[rowc + x0 + nc];
+        e1 = cell_start[rowc + nc];
+        s2 = cell_start[rowc];
+        e2 = cell_start[rowc + x1 + 1];
+      } else if (x1 >= nc) {  // cells [x0, nc) and [0, x1 - nc]
+        s1 = cell_start[rowc + x0];
+        e1 = cell_start[rowc + nc];
+        s2 = cell_start[rowc];
+        e2 = cell_start[rowc + x1 - nc + 1];
+      } else {
+        s1 = cell_start[rowc + x0];
+        e1 = cell_start[rowc + x1 + 1];
+      }
+      for (int part = 0; part < 2; ++part) {
+        const int kb = part ? s2 : s1, ke = part ? e2 : e1;
+        for (int k = kb; k < ke; ++k) {
+          T4 rec;
+          bool hit;
           if (sizeof(T) == 4) {
-            float3 r = sep(pf, ci, ((const float4 *)rs)[j], a);
-            d[0] = r.x;
-            d[1] = r.y;
-            d[2] = r.z;
-            r2 = (T)(r.x * r.x + r.y * r.y + r.z * r.z);
-            in = (float)r2 < rc2f;
+            const float3 d = sep(pf, ci, ((const float4 *)rs_cell)[k], a);
+            rec.x = d.x;
+            rec.y = d.y;
+            rec.z = d.z;
+            hit = d.x * d.x + d.y * d.y + d.z * d.z < rc2f;
           } else {
-            double4_32a q = ((const double4_32a *)rs)[j];
-            double rx = pd.x - q.x, ry = pd.y - q.y, rz = pd.z - q.z;
+            const double4_32a qj = ((const double4_32a *)rs_cell)[k];
+            double rx = pd.x - qj.x, ry = pd.y - qj.y, rz = pd.z - qj.z;
             rx -= a.L * rint(rx / a.L);
             ry -= a.L * rint(ry / a.L);
             rz -= a.L * rint(rz / a.L);
-            d[0] = (T)rx;
-            d[1] = (T)ry;
-            d[2] = (T)rz;
-            r2 = (T)(rx * rx + ry * ry + rz * rz);
-            in = (double)r2 < rc2;
+            rec.x = (T)rx;
+            rec.y = (T)ry;
+            rec.z = (T)rz;
+            hit = rx * rx + ry * ry + rz * rz < rc2;
           }
-          if (in) {
-            if (n < slots) {  // separation x_i - x_j and the neighbour's index in one record
-              typename V4<T>::t gg;
-              gg.x = d[0];
-              gg.y = d[1];
-              gg.z = d[2];
-              gg.w = index_as_real<T>(j);
-              mgeo[n] = gg;
+          if (hit) {
+            const int j = cell_list[k];
+            if (j != (int)i) {
+              if (n < slots) {  // separation x_i - x_j and the neighbour's index in one record
+                rec.w = index_as_real<T>(j);
+                mgeo[n] = rec;
+              }
+              ++n;
             }
-            ++n;
           }
         }
       }
+    }
   cnt[i] = n;
   if (n > slots) atomicOr(ovf, 1);
-  atomicAdd(&tot[2 * si], (unsigned long long)n);
-  atomicMax(&tot[2 * si + 1], (unsigned long long)n);
+  // per-suspension totals: one atomic per warp when the warp's particles share a suspension
+  const unsigned act = __activemask();
+  const int leader = __ffs(act) - 1;
+  if (__all_sync(act, si == __shfl_sync(act, si, leader))) {
+    const unsigned sum = __reduce_add_sync(act, (unsigned)n), big = __reduce_max_sync(act, (unsigned)n);
+    if ((int)(threadIdx.x & 31) == leader) {
+      atomicAdd(&tot[2 * si], (unsigned long long)sum);
+      atomicMax(&tot[2 * si + 1], (unsigned long long)big);
+    }
+  } else {
+    atomicAdd(&tot[2 * si], (unsigned long long)n);
+    atomicMax(&tot[2 * si + 1], (unsigned long long)n);
+  }
 }
 
 void *alloc_dev(pse_ctx *c, size_t bytes) {
@@ -358,19 +399,24 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
     k_derive<double><<<nb, 256, 0, s>>>(c->d_sys, c->d_p0, ns, N, p.P, c->d_perm, c->d_posw, (int4 *)c->d_sp_i0,
                                         (double4_32a *)c->d_sp_d0, c->d_rs, c->d_cell_key, c->d_cell_start);
   PSE_TRY(exclusive_scan(c, c->d_cell_start, c->ncells + 1, s));
-  k_cell_scatter<<<nb, 256, 0, s>>>(N, c->d_cell_key, c->d_cell_start, c->d_cell_cur, c->d_cell_list);
+  if (c->prec == PSE_MIXED)
+    k_cell_scatter<float><<<nb, 256, 0, s>>>(N, c->d_cell_key, c->d_cell_start, c->d_cell_cur, c->d_cell_list,
+                                             (const float4 *)c->d_rs, (float4 *)c->d_rs_cell);
+  else
+    k_cell_scatter<double><<<nb, 256, 0, s>>>(N, c->d_cell_key, c->d_cell_start, c->d_cell_cur, c->d_cell_list,
+                                              (const double4_32a *)c->d_rs, (double4_32a *)c->d_rs_cell);
   const double rc2 = p.rcut * p.rcut;
-  unsigned nb128 = (unsigned)ceil_div(N, 128);
+  const unsigned nb128 = (unsigned)ceil_div(N, 128);
   for (int attempt = 0; attempt < 2; ++attempt) {
     PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long) * ns, s));
     if (c->prec == PSE_MIXED)
-      k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
-                                         c->d_cell_list, c->d_nbr_start, (float4 *)c->d_nbr_geo, c->d_nbr_tot,
-                                         c->d_flag + 1);
+      k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell,
+                                         c->d_cell_start, c->d_cell_list, c->d_nbr_start, (float4 *)c->d_nbr_geo,
+                                         c->d_nbr_tot, c->d_flag + 1);
     else
-      k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_cell_start,
-                                          c->d_cell_list, c->d_nbr_start, (double4_32a *)c->d_nbr_geo, c->d_nbr_tot,
-                                          c->d_flag + 1);
+      k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell,
+                                          c->d_cell_start, c->d_cell_list, c->d_nbr_start, (double4_32a *)c->d_nbr_geo,
+                                          c->d_nbr_tot, c->d_flag + 1);
     if (c->capturing) return PSE_OK;  // the graph's caller checks the flags and the totals afterwards
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_nbr_tot, c->d_nbr_tot, 2 * sizeof(unsigned long long) * ns,
