@@ -119,7 +119,9 @@ template <> struct V16<double> {
   static __device__ __forceinline__ double2 put(const double a[2]) { return make_double2(a[0], a[1]); }
 };
 
-// acc[r] += rows[r0 + r] . w over the block's chunk, r < nr <= DOT_ROWS
+// acc[r] += rows[r0 + r] . w over the block's chunk, r < nr <= DOT_ROWS; each
+// thread keeps VEC_UNROLL independent 16-byte loads per row in flight
+constexpr int VEC_UNROLL = 4;
 template <typename T>
 __device__ __forceinline__ void chunk_dots(const Chunk &ch, const T *__restrict__ rows, int64_t stride, int r0, int nr,
                                            const T *__restrict__ w, T acc[DOT_ROWS]) {
@@ -127,16 +129,34 @@ __device__ __forceinline__ void chunk_dots(const Chunk &ch, const T *__restrict_
   using VT = typename V::t;
 #pragma unroll
   for (int r = 0; r < DOT_ROWS; ++r) acc[r] = 0;
-  for (int64_t e = ch.beg + (int64_t)threadIdx.x * V::n; e < ch.end; e += (int64_t)blockDim.x * V::n) {
-    T wv[V::n];
-    V::get(*(const VT *)(w + e), wv);
+  const int64_t step = (int64_t)blockDim.x * V::n;
+  for (int64_t e0 = ch.beg + (int64_t)threadIdx.x * V::n; e0 < ch.end; e0 += VEC_UNROLL * step) {
+    T wv[VEC_UNROLL][V::n];
+#pragma unroll
+    for (int u = 0; u < VEC_UNROLL; ++u) {
+      const int64_t e = e0 + u * step;
+      if (e < ch.end) V::get(*(const VT *)(w + e), wv[u]);
+      else
+#pragma unroll
+        for (int i = 0; i < V::n; ++i) wv[u][i] = 0;
+    }
 #pragma unroll
     for (int r = 0; r < DOT_ROWS; ++r)
       if (r < nr) {
-        T x[V::n];
-        V::get(*(const VT *)(rows + (r0 + r) * stride + e), x);
+        const T *row = rows + (r0 + r) * stride;
+        T x[VEC_UNROLL][V::n];
 #pragma unroll
-        for (int i = 0; i < V::n; ++i) acc[r] += x[i] * wv[i];
+        for (int u = 0; u < VEC_UNROLL; ++u) {
+          const int64_t e = e0 + u * step;
+          if (e < ch.end) V::get(*(const VT *)(row + e), x[u]);
+          else
+#pragma unroll
+            for (int i = 0; i < V::n; ++i) x[u][i] = 0;
+        }
+#pragma unroll
+        for (int u = 0; u < VEC_UNROLL; ++u)
+#pragma unroll
+          for (int i = 0; i < V::n; ++i) acc[r] += x[u][i] * wv[u][i];
       }
   }
 }
@@ -148,10 +168,12 @@ __device__ __forceinline__ void block_sums(const T acc[DOT_ROWS], int nr, double
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int r = 0; r < DOT_ROWS; ++r) {
-    double v = (double)acc[r];
+    if (r < nr) {
+      double v = (double)acc[r];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[r][wid] = v;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[r][wid] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < nr) {
@@ -203,26 +225,44 @@ __global__ void k_combine(VecArgs va, T *w, const T *__restrict__ rows, int64_t 
   const double *cf = coef + (size_t)ch.s * COEF_STRIDE;
   for (int r = threadIdx.x; r < nr; r += blockDim.x) cs[r] = (T)cf[r];
   __syncthreads();
-  for (int64_t e = ch.beg + (int64_t)threadIdx.x * V::n; e < ch.end; e += (int64_t)blockDim.x * V::n) {
-    T sum[V::n];
+  const int64_t step = (int64_t)blockDim.x * V::n;
+  for (int64_t e0 = ch.beg + (int64_t)threadIdx.x * V::n; e0 < ch.end; e0 += VEC_UNROLL * step) {
+    T sum[VEC_UNROLL][V::n];
 #pragma unroll
-    for (int i = 0; i < V::n; ++i) sum[i] = 0;
+    for (int u = 0; u < VEC_UNROLL; ++u)
+#pragma unroll
+      for (int i = 0; i < V::n; ++i) sum[u][i] = 0;
     for (int r = 0; r < nr; ++r) {
-      T x[V::n];
-      V::get(*(const VT *)(rows + r * stride + e), x);
+      const T *row = rows + r * stride;
+      T x[VEC_UNROLL][V::n];
 #pragma unroll
-      for (int i = 0; i < V::n; ++i) sum[i] += cs[r] * x[i];
+      for (int u = 0; u < VEC_UNROLL; ++u) {
+        const int64_t e = e0 + u * step;
+        if (e < ch.end) V::get(*(const VT *)(row + e), x[u]);
+        else
+#pragma unroll
+          for (int i = 0; i < V::n; ++i) x[u][i] = 0;
+      }
+#pragma unroll
+      for (int u = 0; u < VEC_UNROLL; ++u)
+#pragma unroll
+        for (int i = 0; i < V::n; ++i) sum[u][i] += cs[r] * x[u][i];
     }
-    T out[V::n];
-    if (SET) {
 #pragma unroll
-      for (int i = 0; i < V::n; ++i) out[i] = sgn * sum[i];
-    } else {
-      V::get(*(const VT *)(w + e), out);
+    for (int u = 0; u < VEC_UNROLL; ++u) {
+      const int64_t e = e0 + u * step;
+      if (e >= ch.end) continue;
+      T out[V::n];
+      if (SET) {
 #pragma unroll
-      for (int i = 0; i < V::n; ++i) out[i] += sgn * sum[i];
+        for (int i = 0; i < V::n; ++i) out[i] = sgn * sum[u][i];
+      } else {
+        V::get(*(const VT *)(w + e), out);
+#pragma unroll
+        for (int i = 0; i < V::n; ++i) out[i] += sgn * sum[u][i];
+      }
+      *(VT *)(w + e) = V::put(out);
     }
-    *(VT *)(w + e) = V::put(out);
   }
 }
 
