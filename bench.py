@@ -246,9 +246,9 @@ def accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # first launch of each kernel on the benchmark workload (N = 1048576, phi = 0.3, eps = 1e-3,
 # xi = 0.5, N_g = 256, P = 6); reported only for that workload, and to be retaken whenever the
-# kernel changes: 5-component spread, 8-component interpolation, full-product pair sum.
+# kernel changes: 5-component spread and interpolation (16^3 tiles), full-product pair sum.
 NCU_TRAFFIC_WORKLOAD = (1048576, 0.3, 1e-3, 0.5, 256, 6)
-NCU_TRAFFIC = {'spread': 379.1e6, 'interp': 649.6e6, 'real': 1900.3e6}
+NCU_TRAFFIC = {'spread': 350.7e6, 'interp': 434.9e6, 'real': 1900.1e6}
 
 
 def real_flops_per_pair():
