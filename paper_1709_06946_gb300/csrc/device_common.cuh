@@ -86,10 +86,10 @@ __device__ __forceinline__ void normal_pair(uint64_t seed, uint64_t step, uint32
 // Y components of the symmetric tensor p q^T + q p^T.
 template <typename T>
 __device__ __forceinline__ void symY(const T p[3], const T q[3], T e[5]) {
-  const T r2 = (T)1.4142135623730951, r6 = (T)2.4494897427831781;
+  const T r2 = (T)1.4142135623730951, i2 = (T)0.70710678118654752, i6 = (T)0.40824829046386302;
   T xx = 2 * p[0] * q[0], yy = 2 * p[1] * q[1], zz = 2 * p[2] * q[2];
-  e[0] = (xx - yy) / r2;
-  e[1] = (xx + yy - 2 * zz) / r6;
+  e[0] = (xx - yy) * i2;  // products with 1/sqrt(2), 1/sqrt(6): no division in the pair loop
+  e[1] = (xx + yy - 2 * zz) * i6;
   e[2] = r2 * (p[0] * q[1] + p[1] * q[0]);
   e[3] = r2 * (p[0] * q[2] + p[2] * q[0]);
   e[4] = r2 * (p[1] * q[2] + p[2] * q[1]);
