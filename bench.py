@@ -253,8 +253,10 @@ NCU_TRAFFIC = {'spread': 350.7e6, 'interp': 434.9e6, 'real': 1900.1e6}
 
 def real_flops_per_pair():
     # FP32 operations of the pair kernel per neighbour, counted from its formulas (FMA = 2):
-    # full 8->8 product (Lanczos), S->E (GMRES), [F;S]->U (final velocity).
-    return {'full': 233, 'se': 150, 'fsu': 102}
+    # separation and 1/r 10, seven table interpolations 23, S r^ 26, r^.S r^ 5, r^.F 5,
+    # U terms 22, E terms 92 (two Y-basis products of 24 each); full 8->8 product
+    # (Lanczos), S->E (GMRES), [F;S]->U (final velocity).
+    return {'full': 183, 'se': 147, 'fsu': 91}
 
 
 def run_ours(args, world, rank, local, pg):

@@ -164,33 +164,28 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
       T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
       T v[3];
       Smul(s, rh, v);
-      T q = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+      const T q = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+      const T F[3] = {q0.x, q0.y, q0.z};
+      const T rf = HAS_F ? rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2] : (T)0;
+      // the terms of each output along the same direction are collected first:
+      // U = f2 v + f0 F + (f3 q + (f1 - f0) rf) rh;
+      // E = f4 s + Y(f5 v - f2 F / 2, rh) + (f6 q - f3 rf) / 2 Y(rh, rh)
+      // (Y(., rh) is linear in its first argument)
       if (WANT_U) {
         T c = f[3] * q;
+        if (HAS_F) c += (f[1] - f[0]) * rf;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) U[m] += f[2] * v[m] + c * rh[m];
-        if (HAS_F) {
-          T F[3] = {q0.x, q0.y, q0.z};
-          T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
-          T cf = (f[1] - f[0]) * rf;
-#pragma unroll
-          for (int m = 0; m < 3; ++m) U[m] += f[0] * F[m] + cf * rh[m];
-        }
+        for (int m = 0; m < 3; ++m) U[m] += f[2] * v[m] + c * rh[m] + (HAS_F ? f[0] * F[m] : (T)0);
       }
       if (WANT_E) {
-        T sy[5], yr[5];
-        symY(v, rh, sy);
+        T pv[3], sy[5], yr[5];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) pv[m] = f[5] * v[m] - (HAS_F ? (T)0.5 * f[2] * F[m] : (T)0);
+        symY(pv, rh, sy);
         symY(rh, rh, yr);  // = 2 y(rh)
+        const T cy = (T)0.5 * (f[6] * q - (HAS_F ? f[3] * rf : (T)0));
 #pragma unroll
-        for (int m = 0; m < 5; ++m) E[m] += f[4] * s[m] + f[5] * sy[m] + (T)0.5 * f[6] * q * yr[m];
-        if (HAS_F) {
-          T F[3] = {q0.x, q0.y, q0.z};
-          T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
-          T sf[5];
-          symY(F, rh, sf);
-#pragma unroll
-          for (int m = 0; m < 5; ++m) E[m] += (T)(-0.5) * f[2] * sf[m] - (T)0.5 * f[3] * rf * yr[m];
-        }
+        for (int m = 0; m < 5; ++m) E[m] += f[4] * s[m] + sy[m] + cy * yr[m];
       }
     }
 #pragma unroll
