@@ -110,8 +110,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread16(WaveArgs wa, int *que
   const int lane = threadIdx.x & 31, lz = threadIdx.x >> 5;
   Ranges &rg = s_rng[lz];
   // lane roles fixed for the whole kernel: footprint point of each pass (an
-  // invalid point gets x = 64, outside every tile) and the 1D Gaussian weight
-  // the lane computes (axis lane / P, index lane % P)
+  // invalid point gets x = 64, outside every tile)
   int jx[NPASS], jy[NPASS];
 #pragma unroll
   for (int ps = 0; ps < NPASS; ++ps) {
@@ -119,7 +118,6 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread16(WaveArgs wa, int *que
     jx[ps] = it < P * P ? it % P : 64;
     jy[ps] = it < P * P ? it / P : 0;
   }
-  const int waxis = lane / P, wj = lane % P;
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
     if (!wa.active[si]) return;
@@ -148,7 +146,6 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread16(WaveArgs wa, int *que
       publish_ranges(rg, lane, beg, len);
     }
     const float nal = -(float)a.alpha * LOG2E, hs = (float)a.h, pref = (float)a.pref;
-    const float wjh = (float)wj * hs;
     __syncthreads();  // tile cleared, ranges published
     const int total = rg.cum[8];
     for (int base = 0; base < total; base += 32) {
@@ -173,13 +170,15 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread16(WaveArgs wa, int *que
         const float4 d0 = sp_d0[ke];
         float mv[C];
         moments<C, SLOT0>(vin, ke, mv);
-        const float o = (waxis == 0 ? d0.x : (waxis == 1 ? d0.y : d0.z)) + wjh;
-        const float wl = exp2f(nal * o * o);
-        const float wz = pref * __shfl_sync(0xffffffffu, wl, 2 * P + ez);
+        // weights computed by each lane for its own point (no shuffles: the
+        // shared-memory pipe, not issue, limits this kernel)
+        const float oz = d0.z + (float)ez * hs;
+        const float wz = pref * exp2f(nal * oz * oz);
         const int pb = lz * ZS + ey * RX + ex;
 #pragma unroll
         for (int ps = 0; ps < NPASS; ++ps) {
-          const float wt = __shfl_sync(0xffffffffu, wl, jx[ps] & 31) * __shfl_sync(0xffffffffu, wl, P + jy[ps]) * wz;
+          const float ox = d0.x + (float)jx[ps] * hs, oy = d0.y + (float)jy[ps] * hs;
+          const float wt = exp2f(nal * (ox * ox + oy * oy)) * wz;
           if ((unsigned)((ex + jx[ps]) | (ey + jy[ps])) < (unsigned)TS) {
             const int i = pb + jy[ps] * RX + jx[ps];
             float vv[C];
