@@ -157,9 +157,17 @@ pse_status krylov_loop(pse_ctx *c, int cap, cudaStream_t s, Body &&body) {
   size_t nd = 0;
   cudaGraphConditionalHandle h;
   PSE_CUDA_TRY(c, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive || !g) {  // an earlier capture error invalidated the sequence
+    c->err = "stream capture is not active";
+    return PSE_ERR_CUDA;
+  }
   PSE_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, g, 0, 0));
   kd_loop_begin(c, h, 1, s);
   PSE_CUDA_TRY(c, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive || !g) {
+    c->err = "stream capture is not active";
+    return PSE_ERR_CUDA;
+  }
   cudaGraphNodeParams np{};
   np.type = cudaGraphNodeTypeConditional;
   np.conditional.handle = h;
