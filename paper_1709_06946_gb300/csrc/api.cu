@@ -528,6 +528,16 @@ int64_t estimate_bytes(const pse_ctx *c) {
   return b;
 }
 
+// Marks a suspension for the spreading / interpolation kernels specialised for
+// 16^3 tiles (mixed precision, P = 5, 6 or 8, at least two tiles per side) and
+// counts it in c->n_cubic.
+void set_cubic(pse_ctx *c, SysDev &d) {
+  bool ok = c->prec == PSE_MIXED && (c->p.P == 5 || c->p.P == 6 || c->p.P == 8);
+  for (int k = 0; k < 3; ++k) ok = ok && d.T[k] == CUBE_TILE && d.nt[k] >= 2;
+  d.cubic = ok ? 1 : 0;
+  c->n_cubic += d.cubic;
+}
+
 pse_status choose_group(pse_ctx *c, int nsys, const int64_t *N, const double *L, const pse_options &o) {
   c->nsys = nsys;
   c->ps.assign(nsys, c->p);
@@ -572,6 +582,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   }
   // per-suspension layout: particles, tiles, cells, half spectra, vector blocks
   c->hs.assign(ns, SysDev{});
+  c->n_cubic = 0;
   std::vector<int64_t> p0(ns + 1, 0), k0(ns + 1, 0);
   std::vector<int> tile0(ns + 1, 0), blk0(ns + 1, 0);
   int64_t cell_tot = 0;
@@ -587,6 +598,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
       d.T[k] = p.tile[k];
       d.nt[k] = p.ntile[k];
     }
+    set_cubic(c, d);
     d.L = p.L;
     d.h = p.h;
     d.cs = p.cs;
@@ -895,11 +907,13 @@ pse_status retile(pse_ctx *c, const int caps[3]) {
     c->scan_cap = need;
   }
   c->ps = ps;
+  c->n_cubic = 0;
   for (int q = 0; q < c->nsys; ++q) {
     for (int d = 0; d < 3; ++d) {
       c->hs[q].T[d] = ps[q].tile[d];
       c->hs[q].nt[d] = ps[q].ntile[d];
     }
+    set_cubic(c, c->hs[q]);
     c->hs[q].tile0 = tile0[q];
   }
   c->ntiles = nt;

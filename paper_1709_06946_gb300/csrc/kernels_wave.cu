@@ -327,6 +327,7 @@ pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t coun
 WaveArgs wave_args(const pse_ctx *c) {
   WaveArgs a;
   a.P = c->p.P;
+  a.want = -1;
   a.nsys = c->nsys;
   a.ntiles = (int)c->ntiles;
   a.sys = c->d_sys;

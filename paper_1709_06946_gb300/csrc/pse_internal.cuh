@@ -74,6 +74,7 @@ struct SysDev {
   int64_t cgrid0, cstride; // half spectrum component c at cgrid0 + c * cstride (complex)
   int N, Ng, nkx, nc, slots, tile0, cell0, blk0;
   int T[3], nt[3];
+  int cubic;               // 1: mixed precision, P in {5, 6, 8}, 16^3 tiles, >= 2 tiles per side
   double L, h, cs;
   float Lf, csf;
   double alpha, pref;      // spreading Gaussian exp(-alpha r^2) and its prefactor
@@ -107,6 +108,7 @@ struct FftGroup {
 constexpr int VEC_CHUNK = 16384;   // vector elements per block of the chunked vector kernels
 constexpr int COEF_STRIDE = 512;   // doubles of Krylov coefficients per suspension
 constexpr int MAX_ROWS = 128;      // Krylov vectors per dot-product / combination launch
+constexpr int CUBE_TILE = 16;      // tile side of the specialised spreading / interpolation kernels
 constexpr int SUB_SIDE = 4;        // sub-blocks per tile side in the sort key
 constexpr int SUB_BLOCKS = SUB_SIDE * SUB_SIDE * SUB_SIDE;  // sub-blocks of a spreading tile
 // Per-suspension coefficient block (COEF_STRIDE doubles): first and second
@@ -134,6 +136,7 @@ struct KDev {
 // Device-side state of a handle.
 struct pse_ctx {
   pse::Params p;           // shared parameters; p.N = total particles (per-suspension values in ps)
+  int n_cubic = 0;         // suspensions with SysDev::cubic set
   int prec;                // pse_precision
   size_t ts;               // sizeof real type (4 or 8)
   pse_options opt;

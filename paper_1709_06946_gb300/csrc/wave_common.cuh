@@ -28,6 +28,7 @@ template <> struct Cx<double> { using t = double2; };
 // Launch-wide arguments; the per-suspension ones come from SysDev.
 struct WaveArgs {
   int P, nsys, ntiles;
+  int want;            // -1: every suspension; 0 / 1: only those with SysDev::cubic = want
   const SysDev *sys;
   const int *tile0;   // nsys + 1 prefix of tiles
   const int *active;
@@ -237,28 +238,28 @@ WaveArgs wave_args(const pse_ctx *c);
 void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 
-// Largest shared memory of a spreading/interpolation CTA over the suspensions.
+// Largest shared memory of a spreading/interpolation CTA over the suspensions
+// of a launch (want as in WaveArgs).
 template <typename T, int C>
-inline size_t wave_smem_max(const pse_ctx *c) {
+inline size_t wave_smem_max(const pse_ctx *c, int want = -1) {
   size_t m = 0;
   for (const SysDev &q : c->hs) {
+    if (want >= 0 && q.cubic != want) continue;
     size_t v = wave_smem<T, C>(q.T, c->p.P);
     if (v > m) m = v;
   }
   return m;
 }
 
-// The kernels specialised for 16^3 tiles (mixed precision, P = 5, 6 or 8) are
-// taken when every suspension has that tile and at least two tiles per side (so
+// The kernels specialised for 16^3 tiles run the suspensions marked
+// SysDev::cubic (mixed precision, P = 5, 6 or 8, at least two tiles per side, so
 // that a support crosses the periodic boundary into another tile, never back
-// into the same one, and offsets from the tile origin can be kept signed).
-constexpr int CUBE = 16;
-inline bool cubic_tiles(const pse_ctx *c) {
-  if (c->prec != PSE_MIXED || (c->p.P != 5 && c->p.P != 6 && c->p.P != 8) || c->hs.empty()) return false;
-  for (const SysDev &q : c->hs)
-    for (int d = 0; d < 3; ++d)
-      if (q.T[d] != CUBE || q.nt[d] < 2) return false;
-  return true;
+// into the same one, and offsets from the tile origin can be kept signed); the
+// general kernels run the others.  WaveArgs::want selects the suspensions of a
+// launch: -1 all, 0 the unmarked ones, 1 the marked ones.
+constexpr int CUBE = CUBE_TILE;
+__device__ __forceinline__ bool wave_skip(const WaveArgs &wa, int si, const SysDev &a) {
+  return !wa.active[si] || (wa.want >= 0 && a.cubic != wa.want);
 }
 void spread16_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
 void interp16_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);

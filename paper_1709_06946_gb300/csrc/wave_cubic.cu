@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread16(WaveArgs wa, int *que
   }
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
-    if (!wa.active[si]) return;
     const SysDev &a = wa.sys[si];
+    if (wave_skip(wa, si, a)) return;
     const int Ng = a.Ng;
     {
       float4 *z4 = (float4 *)smem_raw;
@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(NT) k_interp16(WaveArgs wa, int *queue, const 
   const int waxis = lane / P, wj = lane % P;
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
-    if (!wa.active[si]) return;
     const SysDev &a = wa.sys[si];
+    if (wave_skip(wa, si, a)) return;
     const int Ng = a.Ng;
     int t[3], t0[3];
     tile_of(a, item - a.tile0, t, t0);

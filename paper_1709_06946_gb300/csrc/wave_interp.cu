@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
   extern __shared__ __align__(32) unsigned char smem_raw[];
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
-    if (!wa.active[si]) return;
     const SysDev &a = wa.sys[si];
+    if (wave_skip(wa, si, a)) return;
     const int P = PT > 0 ? PT : wa.P;
     const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2];
     const int RX = tile_rx(Tx, P);
@@ -194,7 +194,7 @@ void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   constexpr int NT = C == 8 ? 1024 : WAVE_THREADS;
   auto kern = k_interp<T, C, SLOT0, PT, NT>;
   set_smem(kern, once);
-  size_t sm = wave_smem_max<T, C>(c);
+  size_t sm = wave_smem_max<T, C>(c, a.want);
   unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ, NT);
   int *q = next_queue(c, s);
   kern<<<grid, NT, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
@@ -215,15 +215,23 @@ void interp_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
 
 // mode selects the interpolated components: M_FULL U,E (8), M_SE E (5), M_FSU U (3)
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
-  if (cubic_tiles(c)) return interp16_launch(c, a, vout, mode, s);
+  if (c->n_cubic == c->nsys) return interp16_launch(c, a, vout, mode, s);
+  WaveArgs ag = a;
+  if (c->n_cubic > 0) {  // both kinds of suspensions: one launch each
+    WaveArgs ac = a;
+    ac.want = 1;
+    ag.want = 0;
+    interp16_launch(c, ac, vout, mode, s);
+    c->nlaunch += 2;
+  }
   if (c->prec == PSE_MIXED) {
-    if (mode == M_FULL) interp_p<float, 8, 0>(c, a, vout, s);
-    else if (mode == M_SE) interp_p<float, 5, 3>(c, a, vout, s);
-    else interp_p<float, 3, 0>(c, a, vout, s);
+    if (mode == M_FULL) interp_p<float, 8, 0>(c, ag, vout, s);
+    else if (mode == M_SE) interp_p<float, 5, 3>(c, ag, vout, s);
+    else interp_p<float, 3, 0>(c, ag, vout, s);
   } else {
-    if (mode == M_FULL) interp_p<double, 8, 0>(c, a, vout, s);
-    else if (mode == M_SE) interp_p<double, 5, 3>(c, a, vout, s);
-    else interp_p<double, 3, 0>(c, a, vout, s);
+    if (mode == M_FULL) interp_p<double, 8, 0>(c, ag, vout, s);
+    else if (mode == M_SE) interp_p<double, 5, 3>(c, ag, vout, s);
+    else interp_p<double, 3, 0>(c, ag, vout, s);
   }
 }
 

@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
   extern __shared__ __align__(32) unsigned char smem_raw[];
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
-    if (!wa.active[si]) return;
     const SysDev &a = wa.sys[si];
+    if (wave_skip(wa, si, a)) return;
     const int P = PT > 0 ? PT : wa.P, Ng = a.Ng, nitem = P * P;
     const int Tx = a.T[0], Ty = a.T[1], Tz = a.T[2];
     const int RX = tile_rx(Tx, P);
@@ -176,7 +176,7 @@ void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t 
   static OccCache occ;
   auto kern = k_spread<T, C, SLOT0, PT>;
   set_smem(kern, once);
-  size_t sm = wave_smem_max<T, C>(c);
+  size_t sm = wave_smem_max<T, C>(c, a.want);
   unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ);
   int *q = next_queue(c, s);
   kern<<<grid, WAVE_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const typename V4<T>::t *)c->d_sp_d0,
@@ -196,13 +196,21 @@ void spread_p(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
 }  // namespace
 
 void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s) {
-  if (cubic_tiles(c)) return spread16_launch(c, a, vin, mode, s);
+  if (c->n_cubic == c->nsys) return spread16_launch(c, a, vin, mode, s);
+  WaveArgs ag = a;
+  if (c->n_cubic > 0) {  // both kinds of suspensions: one launch each
+    WaveArgs ac = a;
+    ac.want = 1;
+    ag.want = 0;
+    spread16_launch(c, ac, vin, mode, s);
+    c->nlaunch += 2;
+  }
   if (c->prec == PSE_MIXED) {
-    if (mode == M_SE) spread_p<float, 5, 3>(c, a, vin, s);
-    else spread_p<float, 8, 0>(c, a, vin, s);
+    if (mode == M_SE) spread_p<float, 5, 3>(c, ag, vin, s);
+    else spread_p<float, 8, 0>(c, ag, vin, s);
   } else {
-    if (mode == M_SE) spread_p<double, 5, 3>(c, a, vin, s);
-    else spread_p<double, 8, 0>(c, a, vin, s);
+    if (mode == M_SE) spread_p<double, 5, 3>(c, ag, vin, s);
+    else spread_p<double, 8, 0>(c, ag, vin, s);
   }
 }
 

@@ -163,6 +163,43 @@ def test_batch_step_matches_oracle(pkg, prec):
     h.close()
 
 
+def test_batch_mixes_tile_kinds(pkg):
+    """Mixed precision batch where one suspension has 16^3 spreading tiles (the
+    specialised kernels, parity with the oracle in test_gpu_parity) and the
+    others smaller grids (the general kernels): the small ones against the
+    oracle, the 16^3 one against a handle of its own."""
+    systems = [(5000, 0.3, 41), (300, 0.3, 42), (211, 0.15, 43)]
+    pos, Ls, F, S = [], [], [], []
+    for k, (N, phi, seed) in enumerate(systems):
+        x, L = pse_inputs.rsa_positions(N, phi, seed=seed)
+        f, s_ = pse_inputs.moments(N, seed=140 + k)
+        pos.append(x)
+        Ls.append(L)
+        F.append(f)
+        S.append(s_)
+    Ns = [n for n, _, _ in systems]
+    h = pkg.PSE(Ns, Ls, xi=XI, tol=EPS, precision='mixed')
+    infos = [h.system_info(s) for s in range(len(Ns))]
+    assert tuple(infos[0]['tile']) == (16, 16, 16) and infos[0]['Ng'] >= 32
+    assert any(tuple(i['tile']) != (16, 16, 16) or i['Ng'] < 32 for i in infos[1:])
+    f32 = torch.float32
+    U, E = h.mobility(_cuda(np.concatenate(pos), torch.float64), _cuda(np.concatenate(F), f32),
+                      _cuda(np.concatenate(S), f32))
+    got = np.concatenate([U.double().cpu().numpy(), E.double().cpu().numpy()], 1)
+    for s, part in enumerate(_split(h, got)):
+        if s == 0:
+            continue
+        p = _oracle_params(h, s, Ns[s], Ls[s])
+        Uo, Eo = opse.mobility_apply(pos[s], F[s], S[s], p)
+        assert _rel(part, np.concatenate([Uo, Eo], 1)) < TOL['mixed'], s
+    h1 = pkg.PSE(Ns[0], Ls[0], xi=XI, tol=EPS, precision='mixed')
+    U1, E1 = h1.mobility(_cuda(pos[0], torch.float64), _cuda(F[0], f32), _cuda(S[0], f32))
+    one = np.concatenate([U1.double().cpu().numpy(), E1.double().cpu().numpy()], 1)
+    assert _rel(_split(h, got)[0], one) < 1e-6
+    h.close()
+    h1.close()
+
+
 def test_batch_in_kernel_noise_uses_global_indices(pkg):
     """In-kernel noise of a batch equals external noise drawn by the oracle's
     Philox with suspension s's indices following those of suspensions 0..s-1."""

@@ -170,6 +170,24 @@ def test_brownian_sample_external_noise(pkg, prec):
     assert _rel(got, B) < TOL[prec]
 
 
+def test_long_lanczos_recurrence(pkg):
+    """60 Lanczos steps (FP64): the tridiagonal square root is taken by one warp
+    with the eigenvectors in shared memory up to 48 rows and by one thread
+    beyond; both against the oracle's Lanczos with the same fixed length."""
+    N, phi, xi, tol, dt = 200, 0.2, 0.6, 1e-3, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=29)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='fp64', lanczos_tol=0.0, lanczos_maxiter=60)
+    p = _oracle_params(h, N, L, xi, tol)
+    w1 = pse_inputs.lanczos_noise(N, seed=30)
+    w2 = pse_inputs.wave_noise(p.Ng, seed=31)
+    U, E, st = h.brownian(_cuda(pos, torch.float64), dt, w1=_cuda(w1, torch.float64), w2=_cuda(w2, torch.float64))
+    B, sto = opse.brownian_sample(pos, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=60)
+    assert st['lanczos_iters'] == 60 and sto['lanczos_iters'] == 60
+    got = np.concatenate([U.cpu().numpy(), E.cpu().numpy()], 1)
+    assert _rel(got, B) < TOL['fp64']
+    h.close()
+
+
 def test_in_kernel_noise_matches_published_generator(pkg):
     """In-kernel Philox4x32-10 noise equals the same stream generated by the oracle."""
     N, phi, xi, tol, dt = 150, 0.15, 0.6, 1e-3, 1e-2
