@@ -23,43 +23,6 @@ struct RealArgs {
   double inv_dr, self_uf, self_es;
 };
 
-template <typename T> struct Pos;
-template <> struct Pos<float> {
-  float4 p;
-  int c[3];
-  __device__ void load(const void *rs, int i) {
-    p = ((const float4 *)rs)[i];
-    int q = __float_as_int(p.w);
-    c[0] = q & 1023;
-    c[1] = (q >> 10) & 1023;
-    c[2] = (q >> 20) & 1023;
-  }
-  __device__ void sep(const void *rs, int j, const SysDev &a, float d[3]) const {
-    float4 o = ((const float4 *)rs)[j];
-    int q = __float_as_int(o.w);
-    int cj[3] = {q & 1023, (q >> 10) & 1023, (q >> 20) & 1023};
-    float po[3] = {p.x - o.x, p.y - o.y, p.z - o.z};
-    for (int k = 0; k < 3; ++k) {
-      int t = c[k] - cj[k];
-      if (t > a.nc / 2) t -= a.nc;
-      if (t < -(a.nc / 2)) t += a.nc;
-      d[k] = t * a.csf + po[k];
-      if (a.nc < 5) d[k] -= a.Lf * rintf(d[k] / a.Lf);
-    }
-  }
-};
-template <> struct Pos<double> {
-  double4_32a p;
-  __device__ void load(const void *rs, int i) { p = ((const double4_32a *)rs)[i]; }
-  __device__ void sep(const void *rs, int j, const SysDev &a, double d[3]) const {
-    double4_32a o = ((const double4_32a *)rs)[j];
-    d[0] = p.x - o.x;
-    d[1] = p.y - o.y;
-    d[2] = p.z - o.z;
-    for (int k = 0; k < 3; ++k) d[k] -= a.L * rint(d[k] / a.L);
-  }
-};
-
 // 32 bytes (8 floats) from 32-byte aligned read-only global memory in one
 // 256-bit load.
 __device__ __forceinline__ void ldg8(const float *p, float4 &lo, float4 &hi) {
@@ -121,7 +84,7 @@ template <typename T, int MODE, int G, bool SHT = false, int NT = SHT ? 1024 : 2
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real(RealArgs a,
                                               const SysDev *__restrict__ sys,
                                               const int64_t *__restrict__ p0, const int *__restrict__ active,
-                                              int *queue, int nitems, const void *rs,
+                                              int *queue, int nitems,
                                               const int *__restrict__ nstart,
                                               const typename V4<T>::t *__restrict__ geo,
                                               const T *__restrict__ vin, T *__restrict__ vout,
@@ -239,7 +202,7 @@ void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, c
     const int64_t items = ceil_div(a.Ntot * G, 1024);
     unsigned grid = persistent_grid(c, kern, 1024, tab_bytes, items, per_sm);
     int *q = next_queue(c, s);
-    kern<<<grid, 1024, tab_bytes, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_rs, c->d_nbr_start,
+    kern<<<grid, 1024, tab_bytes, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
                                        (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout,
                                        (const T *)c->d_table);
     return;
@@ -249,7 +212,7 @@ void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, c
   const int64_t items = ceil_div(a.Ntot * G, 256);
   unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
   int *q = next_queue(c, s);
-  kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_rs, c->d_nbr_start,
+  kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
                             (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout,
                             (const T *)c->d_table);
 }
