@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = 'Brownian steps/s, N=1M phi=0.3 eps=1e-3, mixed vs FP64; served p50/p99 latency'
 FP32_PEAK_TFLOPS_AT_MAX = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+SMEM_PEAK_GBS_AT_MAX = 152 * 128 * 2.070e9 / 1e9          # 152 SMs x 128 B/clk shared-memory bandwidth x 2.07 GHz
 
 
 def parse():
@@ -366,6 +367,17 @@ def run_ours(args, world, rank, local, pg):
                  'traffic_note': 'DRAM bytes per full-product launch (neighbour records, 16 B per ordered pair)',
                  'peak_note': 'derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz',
                  'flops_per_pair': fl}
+    # the ceiling that binds spreading and interpolation: each particle's P^3 footprint x C
+    # components in the shared tile, read and written (spread) or read (interpolation)
+    P3 = inf['P'] ** 3
+    smem_algo = {'spread': sum(N * P3 * c * 4 * 2 for c in spread_comps),
+                 'interp': sum(N * P3 * c * 4 for c in interp_comps)}
+    smem_rates = {k: {'GB/s': smem_algo[k] / (stage_ms[k] / 1000.0) / 1e9 if stage_ms[k] > 0 else None,
+                      'peak_GB/s': SMEM_PEAK_GBS_AT_MAX,
+                      'frac': (smem_algo[k] / (stage_ms[k] / 1000.0) / 1e9) / SMEM_PEAK_GBS_AT_MAX
+                      if stage_ms[k] > 0 else None,
+                      'note': 'shared-memory bytes of the footprint updates (N P^3 C x 4 B, x2 when read and '
+                              'written) against the derived 152 SMs x 128 B/clk x 2070 MHz'} for k in smem_algo}
     wave_rates = {k: {'GB/s': algo[k] / (stage_ms[k] / 1000.0) / 1e9 if stage_ms[k] > 0 else None,
                       'frac_of_measured_hbm': (algo[k] / (stage_ms[k] / 1000.0) / 1e9) / peaks.get('hbm_gbs', 6800.0)
                       if stage_ms[k] > 0 else None} for k in algo}
@@ -392,7 +404,7 @@ def run_ours(args, world, rank, local, pg):
                                     'nodes); stage times and roofline: the same steps launched from the host with '
                                     'stage events'},
               'stage_ms_per_step': {k: v / K for k, v in stage_ms.items()},
-              'wave_stage_hbm': wave_rates,
+              'wave_stage_hbm': wave_rates, 'wave_stage_smem': smem_rates,
               'roofline': roof, 'roofline_pair_sum': roof_real, 'clocks': clk,
               'gpu_launches': int(round(prof['launches'] / K * args.steps)),
               'gpu_launches_note': 'kernels of this library per step (counted on the host-launched path) x timed '
