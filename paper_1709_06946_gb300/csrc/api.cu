@@ -684,6 +684,10 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->kd.nrows = c->d_nrows;
   c->d_queue = (int *)A(sizeof(int) * 64);
   c->d_table = A(ts * 8 * (size_t)t.len);
+  if (c->prec == PSE_MIXED) {
+    c->d_table_e = A(sizeof(float) * 8 * (size_t)t.len);
+    c->d_table_u = A(sizeof(float) * 8 * (size_t)t.len);
+  }
   c->d_posw = (double *)A(sizeof(double) * 3 * N);
   c->d_tile_key = (int *)A(sizeof(int) * N);
   c->d_cell_key = (int *)A(sizeof(int) * N);
@@ -781,6 +785,21 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   if (c->prec == PSE_MIXED) {
     std::vector<float> f(t.v.begin(), t.v.end());
     PSE_CUDA_TRY(c, cudaMemcpy(c->d_table, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+    const size_t len = (size_t)t.len;
+    std::vector<float> fe(8 * len, 0.0f), fu(8 * len, 0.0f);
+    for (size_t q = 0; q < len; ++q) {
+      const size_t q1 = q + 1 < len ? q + 1 : q;
+      for (int k = 0; k < 3; ++k) {
+        fe[8 * q + k] = f[8 * q + 4 + k];
+        fe[8 * q + 3 + k] = f[8 * q1 + 4 + k];
+      }
+      for (int k = 0; k < 4; ++k) {
+        fu[8 * q + k] = f[8 * q + k];
+        fu[8 * q + 4 + k] = f[8 * q1 + k];
+      }
+    }
+    PSE_CUDA_TRY(c, cudaMemcpy(c->d_table_e, fe.data(), sizeof(float) * fe.size(), cudaMemcpyHostToDevice));
+    PSE_CUDA_TRY(c, cudaMemcpy(c->d_table_u, fu.data(), sizeof(float) * fu.size(), cudaMemcpyHostToDevice));
   } else {
     PSE_CUDA_TRY(c, cudaMemcpy(c->d_table, t.v.data(), sizeof(double) * t.v.size(), cudaMemcpyHostToDevice));
   }

@@ -31,13 +31,32 @@ __device__ __forceinline__ void ldg8(const float *p, float4 &lo, float4 &hi) {
       : "l"(p));
 }
 
-template <bool SH = false>
+// f[0..7) at r by linear interpolation.  The full product reads two 8-float
+// entries (q and q + 1); the partial products read one 8-float interval record
+// holding the values they need at both ends: f4..f6 (S -> E) or f0..f3
+// ([F; S] -> U); the other functions are left unset.
+template <bool SH = false, int MODE = M_FULL>
 __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, float r, float f[7]) {
   float x = r * (float)a.inv_dr;
   int q = min((int)x, a.len - 2);
   float t = x - (float)q;
   const float4 *t4 = (const float4 *)tab;
   float4 a0, a1, b0, b1;
+  if (!SH && MODE == M_SE) {
+    ldg8(tab + 8 * q, a0, a1);  // f4 f5 f6 at q, then at q + 1
+    f[4] = fmaf(t, a0.w - a0.x, a0.x);
+    f[5] = fmaf(t, a1.x - a0.y, a0.y);
+    f[6] = fmaf(t, a1.y - a0.z, a0.z);
+    return;
+  }
+  if (!SH && MODE == M_FSU) {
+    ldg8(tab + 8 * q, a0, a1);  // f0..f3 at q, then at q + 1
+    f[0] = fmaf(t, a1.x - a0.x, a0.x);
+    f[1] = fmaf(t, a1.y - a0.y, a0.y);
+    f[2] = fmaf(t, a1.z - a0.z, a0.z);
+    f[3] = fmaf(t, a1.w - a0.w, a0.w);
+    return;
+  }
   if (SH) {  // table staged in shared memory
     a0 = t4[2 * q];
     a1 = t4[2 * q + 1];
@@ -56,7 +75,7 @@ __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, floa
   f[6] = fmaf(t, b1.z - a1.z, a1.z);
 }
 
-template <bool SH = false>
+template <bool SH = false, int MODE = M_FULL>
 __device__ __forceinline__ void lookup(const double *tab, const RealArgs &a, double r, double f[7]) {
   double x = r * a.inv_dr;
   int q = min((int)x, a.len - 2);
@@ -120,7 +139,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
       const T ir = sizeof(T) == 4 ? (T)rsqrtf((float)r2) : (T)1 / sqrt(r2), r = r2 * ir;
       T rh[3] = {gg.x * ir, gg.y * ir, gg.z * ir};
       T f[7];
-      lookup<SHT>(tab, a, r, f);
+      lookup<SHT, MODE>(tab, a, r, f);
       T4 q0, q1;
       if constexpr (sizeof(T) == 4) ldg8((const float *)vin + 8 * (size_t)j, q0, q1);  // the 8 slots of row j
       else q0 = v4[2 * j], q1 = v4[2 * j + 1];
@@ -210,11 +229,13 @@ void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, c
   auto kern = k_real<T, MODE, G>;
   static std::atomic<int> per_sm{0};
   const int64_t items = ceil_div(a.Ntot * G, 256);
+  const void *tab = c->d_table;  // FP32 partial products: their interval table
+  if (sizeof(T) == 4 && MODE == M_SE) tab = c->d_table_e;
+  if (sizeof(T) == 4 && MODE == M_FSU) tab = c->d_table_u;
   unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
   int *q = next_queue(c, s);
   kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
-                            (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout,
-                            (const T *)c->d_table);
+                            (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout, (const T *)tab);
 }
 
 template <typename T, int G>

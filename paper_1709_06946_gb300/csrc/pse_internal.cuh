@@ -166,6 +166,9 @@ struct pse_ctx {
 
   // real-space table (device, real type), self terms
   void *d_table = nullptr;
+  // FP32 interval tables for the partial products: per interval q the values at
+  // q and q + 1 of f4..f6 (S -> E) or of f0..f3 ([F; S] -> U), 8 floats each
+  void *d_table_e = nullptr, *d_table_u = nullptr;
   int table_len = 0, table_k2 = 0;
   double table_dr = 0, self_uf = 0, self_es = 0;
 
