@@ -341,7 +341,7 @@ pse_status step_body(pse_ctx *c, const void *dFP, double dt, const void *dw1, co
   } else {
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_v[3], c->d_v[5], vb, cudaMemcpyDeviceToDevice, s));
   }
-  PSE_TRY(mobility(c, c->d_v[3], c->d_v[4], M_FSU, PSE_PART_ALL, s));
+  PSE_TRY(mobility(c, c->d_v[3], c->d_v[4], dFP ? M_FSU : M_SU, PSE_PART_ALL, s));
   return final_update(c, c->d_pos0, c->d_B, c->d_v[4], dt, c->d_posout, s);
 }
 
@@ -1206,7 +1206,7 @@ pse_status pse_mobility_apply_parts(pse_handle h, const double *pos, const void 
   PSE_TRY(setup_config(c, (const double *)dpos, s));
   PSE_TRY(gather_in(c, dF, dS, c->d_v[0], s));
   int mode = M_FULL;
-  if (!E) mode = M_FSU;
+  if (!E) mode = dF ? M_FSU : M_SU;
   else if (!dF && !U) mode = M_SE;
   PSE_TRY(mobility(c, c->d_v[0], c->d_v[1], mode, parts, s));
   PSE_TRY(scatter_out(c, c->d_v[1], dU, dE, 1.0, s));

@@ -49,7 +49,7 @@ __device__ __forceinline__ void lookup(const float *tab, const RealArgs &a, floa
     f[6] = fmaf(t, a1.y - a0.z, a0.z);
     return;
   }
-  if (!SH && MODE == M_FSU) {
+  if (!SH && (MODE == M_FSU || MODE == M_SU)) {
     ldg8(tab + 8 * q, a0, a1);  // f0..f3 at q, then at q + 1
     f[0] = fmaf(t, a1.x - a0.x, a0.x);
     f[1] = fmaf(t, a1.y - a0.y, a0.y);
@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
     __syncthreads();
     tab = (const T *)tab_raw;
   }
-  constexpr bool HAS_F = MODE != M_SE, WANT_U = MODE != M_SE, WANT_E = MODE != M_FSU;
+  constexpr bool HAS_F = MODE == M_FULL || MODE == M_FSU, WANT_U = MODE != M_SE;
+  constexpr bool WANT_E = MODE == M_FULL || MODE == M_SE;
   using T4 = typename V4<T>::t;
   for_each_item(queue, nitems, [&](int item) {
     const int64_t gid = ((int64_t)item * NT + threadIdx.x) / G;
@@ -231,7 +232,7 @@ void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, c
   const int64_t items = ceil_div(a.Ntot * G, 256);
   const void *tab = c->d_table;  // FP32 partial products: their interval table
   if (sizeof(T) == 4 && MODE == M_SE) tab = c->d_table_e;
-  if (sizeof(T) == 4 && MODE == M_FSU) tab = c->d_table_u;
+  if (sizeof(T) == 4 && (MODE == M_FSU || MODE == M_SU)) tab = c->d_table_u;
   unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
   int *q = next_queue(c, s);
   kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
@@ -242,6 +243,7 @@ template <typename T, int G>
 void launch_real_g(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int mode, cudaStream_t s) {
   if (mode == M_FULL) launch_real_m<T, M_FULL, G>(c, a, vin, vout, s);
   else if (mode == M_SE) launch_real_m<T, M_SE, G>(c, a, vin, vout, s);
+  else if (mode == M_SU) launch_real_m<T, M_SU, G>(c, a, vin, vout, s);
   else launch_real_m<T, M_FSU, G>(c, a, vin, vout, s);
 }
 

@@ -105,7 +105,7 @@ __global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
   const SysDev &s = sa.sys[sidx];
   const size_t idx = (size_t)(gidx - s.k0);
   C2 *g = g_all + s.cgrid0;
-  constexpr bool HF = MODE != M_SE, WU = MODE != M_SE, WE = MODE != M_FSU;
+  constexpr bool HF = MODE == M_FULL || MODE == M_FSU, WU = MODE != M_SE, WE = MODE == M_FULL || MODE == M_SE;
   constexpr int sIn = HF ? 3 : 0, uOut = 0, eOut = (MODE == M_SE) ? 0 : 3;
   int ix, iy, iz;
   bool live = kvector(s, idx, ix, iy, iz);
@@ -269,7 +269,7 @@ template <typename T>
 pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s) {
   WaveArgs a = wave_args(c);
   if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout, 0, sizeof(T) * 8 * (size_t)c->p.N, s));
-  int cin = mode == M_SE ? 5 : 8, cout = mode == M_FULL ? 8 : (mode == M_SE ? 5 : 3);
+  int cin = (mode == M_SE || mode == M_SU) ? 5 : 8, cout = mode == M_FULL ? 8 : (mode == M_SE ? 5 : 3);
   {
     StageTimer timer(c, PSE_STAGE_SPREAD, s);
     c->nlaunch += 2;  // counter reset + kernel
@@ -285,6 +285,7 @@ pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool 
     c->nlaunch += 1;
     if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
     else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    else if (mode == M_SU) k_scale<T, M_SU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
     else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());

@@ -300,7 +300,8 @@ pse_status wave_apply(pse_ctx *c, const void *vin, void *vout, int mode, bool ad
 pse_status wave_noise(pse_ctx *c, const void *w2, uint64_t seed, uint64_t counter, void *vout,
                       cudaStream_t s);
 // mode flags for real/wave products
-enum { M_FULL = 0, M_SE = 1, M_FSU = 2 };
+// M_SU: S -> U (the final velocity when there is no external force)
+enum { M_FULL = 0, M_SE = 1, M_FSU = 2, M_SU = 3 };
 pse_status mobility(pse_ctx *c, const void *vin, void *vout, int mode, int parts, cudaStream_t s);
 
 // vector helpers

@@ -387,7 +387,7 @@ void interp16_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
 }  // namespace
 
 void spread16_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s) {
-  if (mode == M_SE) spread16_p<5, 3>(c, a, vin, s);
+  if (mode == M_SE || mode == M_SU) spread16_p<5, 3>(c, a, vin, s);
   else spread16_p<8, 0>(c, a, vin, s);
 }
 

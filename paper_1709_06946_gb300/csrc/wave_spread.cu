@@ -206,10 +206,10 @@ void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cud
     c->nlaunch += 2;
   }
   if (c->prec == PSE_MIXED) {
-    if (mode == M_SE) spread_p<float, 5, 3>(c, ag, vin, s);
+    if (mode == M_SE || mode == M_SU) spread_p<float, 5, 3>(c, ag, vin, s);
     else spread_p<float, 8, 0>(c, ag, vin, s);
   } else {
-    if (mode == M_SE) spread_p<double, 5, 3>(c, ag, vin, s);
+    if (mode == M_SE || mode == M_SU) spread_p<double, 5, 3>(c, ag, vin, s);
     else spread_p<double, 8, 0>(c, ag, vin, s);
   }
 }

@@ -143,6 +143,29 @@ def test_edge_cases(pkg, prec):
         h.close()
 
 
+@pytest.mark.parametrize('prec', ['fp64', 'mixed'])
+def test_mobility_partial_outputs(pkg, prec):
+    """Requests for a part of the outputs take the reduced products: U from S
+    alone, U from [F; S], E from S alone; each against the oracle."""
+    N, phi, xi, tol = 300, 0.2, 0.6, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=17)
+    F, S = pse_inputs.moments(N, seed=18)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision=prec)
+    p = _oracle_params(h, N, L, xi, tol)
+    dt = _dt(prec)
+    x = _cuda(pos, torch.float64)
+    Uo, _ = opse.mobility_apply(pos, 0 * F, S, p)
+    U, E = h.mobility(x, None, _cuda(S, dt), want=('U',))
+    assert E is None and _rel(U.double().cpu().numpy(), Uo) < TOL[prec]
+    Uo, _ = opse.mobility_apply(pos, F, S, p)
+    U, _ = h.mobility(x, _cuda(F, dt), _cuda(S, dt), want=('U',))
+    assert _rel(U.double().cpu().numpy(), Uo) < TOL[prec]
+    _, Eo = opse.mobility_apply(pos, 0 * F, S, p)
+    _, E = h.mobility(x, None, _cuda(S, dt), want=('E',))
+    assert _rel(E.double().cpu().numpy(), Eo) < TOL[prec]
+    h.close()
+
+
 def test_host_arrays_through_the_abi(pkg):
     """numpy (host) arrays are staged by the library and give the same result."""
     N, phi, xi, tol = 100, 0.1, 0.5, 1e-3
