@@ -1,4 +1,5 @@
-// Spreading / interpolation kernels shared by wave_spread.cu and wave_interp.cu.
+// Helpers of the spreading / interpolation kernels (wave_spread.cu and
+// wave_interp.cu for any tile, wave_cubic.cu for 16^3 tiles).
 //
 // Both kernels are persistent: each CTA takes grid tiles (Tx x Ty x Tz points)
 // of any suspension from a work counter and keeps the tile in shared memory,
@@ -10,8 +11,9 @@
 // (bins hold particles by the grid index where their support starts); the warps
 // scan these candidates themselves, 32 at a time with a ballot, so there is no
 // shared particle list and no CTA barrier between the staging of a tile and its
-// read-out.  The 1D Gaussian weights of a particle are computed one per lane and
-// broadcast with shuffles.
+// read-out.  The Gaussian weights of a particle are computed on the lanes: the 1D
+// weights one per lane, broadcast with shuffles, or (16^3 spreading) each lane
+// the weight of its own footprint point.
 #pragma once
 
 #include <cmath>
