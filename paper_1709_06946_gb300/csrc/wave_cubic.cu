@@ -6,12 +6,15 @@
 // the per-particle overhead cut down: the tile strides are compile-time
 // constants, offsets from the tile origin are signed (no periodic wrap tests:
 // a footprint point is in the tile when (x | y) < 16 as unsigned), the three
-// offsets travel in one shuffle, each lane's footprint positions and Gaussian
-// lane roles are fixed per tile, and the candidate ranges of the source bins
-// sit in shared memory.  Interpolation warps take candidate groups from a
-// counter in shared memory (the bins below the tile hold far fewer hits than
-// the tile's own, so a static split leaves warps idle at the tile barrier) and
-// skip the sub-block layers of the bins below the tile that cannot reach it.
+// offsets travel in one shuffle, each lane's footprint positions are fixed for
+// the whole kernel, the candidate ranges of the source bins sit in shared
+// memory, and spreading lanes compute the Gaussian weight of their own point
+// (no weight shuffles; interpolation keeps one 1D weight per lane, shuffled,
+// because it needs the six z weights on every lane).  Interpolation warps take
+// candidate groups from a counter in shared memory (the bins below the tile
+// hold far fewer hits than the tile's own, so a static split leaves warps idle
+// at the tile barrier) and skip the sub-block layers of the bins below the tile
+// that cannot reach it.
 #include "wave_common.cuh"
 
 namespace pse {
