@@ -90,12 +90,14 @@ def test_mobility_dense_many_tiles(pkg, prec):
     h.close()
 
 
-@pytest.mark.parametrize('tol,Ng', [(1e-2, 48), (1e-3, 48), (1e-4, 64)])
-def test_mobility_cubic_tiles(pkg, tol, Ng):
+@pytest.mark.parametrize('tol,Ng,N,xi', [(1e-2, 48, 3000, 0.7), (1e-3, 48, 3000, 0.7), (1e-4, 64, 3000, 0.7),
+                                         (1e-3, 32, 1500, 0.5)])
+def test_mobility_cubic_tiles(pkg, tol, Ng, N, xi):
     """Mixed precision with 16^3 spreading tiles (the kernels specialised for
     them) against the oracle and against the general kernels (16 x 8 x 16
-    tiles); supports of several sizes."""
-    N, phi, xi = 3000, 0.3, 0.7
+    tiles); supports of several sizes, and two tiles per side (N_g = 32: the
+    tile below and the tile above are the same)."""
+    phi = 0.3
     pos, L = pse_inputs.rsa_positions(N, phi, seed=11)
     F, S = pse_inputs.moments(N, seed=12)
     h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng)
