@@ -245,6 +245,18 @@ __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, con
         cy += cy < 0 ? nc : (cy >= nc ? -nc : 0);
       }
       const int rowc = a.cell0 + (cz * nc + cy) * nc;
+      // FP32 with five or more cells per side: the row's y and z cell offsets
+      // (minimum image) are shared by all its candidates; only x varies
+      float offy = 0.f, offz = 0.f;
+      if (sizeof(T) == 4 && wide) {
+        int ty = ci[1] - cy, tz = ci[2] - cz;
+        if (ty > nc / 2) ty -= nc;
+        if (ty < -(nc / 2)) ty += nc;
+        if (tz > nc / 2) tz -= nc;
+        if (tz < -(nc / 2)) tz += nc;
+        offy = ty * a.csf;
+        offz = tz * a.csf;
+      }
       int s1, e1, s2 = 0, e2 = 0;
       if (x0 < 0) {  // cells [x0 + nc, nc) and [0, x1]
         s1 = cell_start[rowc + x0 + nc];
@@ -265,7 +277,16 @@ __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, con
         for (int k = kb; k < ke; ++k) {
           T4 rec;
           bool hit;
-          if (sizeof(T) == 4) {
+          if (sizeof(T) == 4 && wide) {  // as sep(), with the row's y and z offsets
+            const float4 pj = ((const float4 *)rs_cell)[k];
+            int tx = ci[0] - (__float_as_int(pj.w) & 1023);
+            if (tx > nc / 2) tx -= nc;
+            if (tx < -(nc / 2)) tx += nc;
+            rec.x = tx * a.csf + (pf.x - pj.x);
+            rec.y = offy + (pf.y - pj.y);
+            rec.z = offz + (pf.z - pj.z);
+            hit = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z < rc2f;
+          } else if (sizeof(T) == 4) {
             const float3 d = sep(pf, ci, ((const float4 *)rs_cell)[k], a);
             rec.x = d.x;
             rec.y = d.y;
