@@ -406,6 +406,21 @@ int pse_internal_real_functions(double a, double eta, double xi, int n, const do
   return 0;
 }
 
+// Spreading tile for a grid of Ng points per side, support P and real size ts
+// (4 or 8 bytes) under the caps (fixed > 0 forces a side); tile and padded row
+// length in out[0..4) (x, y, z, row).  Returns 0, or 1 when no tile fits.
+int pse_internal_choose_tile(int Ng, int P, int ts, const int *caps, const int *fixed, int *out) {
+  pse::Params p{};
+  p.Ng = Ng;
+  p.P = P;
+  p.ts = ts;
+  std::string err;
+  if (pse::choose_tile(p, caps, fixed, err)) return 1;
+  for (int d = 0; d < 3; ++d) out[d] = p.tile[d];
+  out[3] = pse::tile_row(p.tile[0], P);
+  return 0;
+}
+
 // c = T^{1/2} e_1 for the symmetric tridiagonal T (diagonal d, off-diagonal e).
 int pse_internal_tridiag_sqrt_e1(int n, const double *d, const double *e, double *c) {
   std::vector<double> dd(d, d + n), ee(e, e + (n > 1 ? n - 1 : 0)), Z;

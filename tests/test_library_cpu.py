@@ -105,6 +105,44 @@ def test_tridiagonal_square_root(lib):
         assert np.abs(c - Q @ (np.sqrt(w) * Q[0])).max() < 1e-13
 
 
+def _tile(lib, Ng, P, ts, caps, fixed=(0, 0, 0)):
+    c = (ctypes.c_int * 3)(*caps)
+    f = (ctypes.c_int * 3)(*fixed)
+    out = (ctypes.c_int * 4)()
+    rc = lib.pse_internal_choose_tile(Ng, P, ts, c, f, out)
+    return rc, list(out)
+
+
+def test_spreading_tile_rules(lib):
+    """The tile chosen for every 2^i 3^j grid, support and real size under the
+    autotuner's caps divides N_g, spans at least P - 1 points (or the whole
+    side), fits the shared-memory budget with 8 components, and its rows are
+    padded by the documented rule (rows of 16 or more: length = P mod 8)."""
+    grids = sorted({2 ** i * 3 ** j for i in range(1, 10) for j in range(0, 6) if 8 <= 2 ** i * 3 ** j <= 512})
+    caps_list = [(16, 16, 16), (16, 8, 16), (8, 8, 16), (8, 16, 16), (16, 16, 32), (16, 8, 32), (32, 8, 16)]
+    for Ng in grids:
+        for P in (4, 5, 6, 8, 10):
+            for ts in (4, 8):
+                for caps in caps_list:
+                    rc, (tx, ty, tz, row) = _tile(lib, Ng, P, ts, caps)
+                    if rc:  # refused only when even the smallest admissible tile is too large
+                        m = min(d for d in range(1, Ng + 1) if Ng % d == 0 and (d >= P - 1 or d == Ng))
+                        mrow = m + ((P - m) % 8 if m >= 16 else (2 if m % 4 == 0 else 0))
+                        assert 8 * m * m * mrow * ts > 220 * 1024, (Ng, P, ts, caps)
+                        continue
+                    for t in (tx, ty, tz):
+                        assert Ng % t == 0 and (t >= P - 1 or t == Ng) and t <= 256
+                    if tx >= 16:
+                        assert row % 8 == P % 8 and tx <= row < tx + 8
+                    else:
+                        assert row == tx + (2 if tx % 4 == 0 else 0)
+                    assert 8 * tz * ty * row * ts <= 220 * 1024, (Ng, P, ts, caps, tx, ty, tz)
+    # the benchmark's grid: 16^3 tiles in mixed precision, rows of 22 points for P = 6
+    assert _tile(lib, 256, 6, 4, (16, 16, 16)) == (0, [16, 16, 16, 22])
+    # a forced tile that cannot fit is refused
+    assert _tile(lib, 256, 6, 8, (16, 16, 16), fixed=(32, 32, 32))[0] == 1
+
+
 def test_batch_arguments_checked_on_host(lib):
     """Batch creation checks every suspension before touching the device and
     names the one that fails; the memory estimate needs no device."""
