@@ -205,7 +205,9 @@ pse_status pse_get_system_stats(pse_handle h, int32_t s, pse_stats *out);
 
 /* [U; E] = M [F; S] at positions pos (Sec. 2.2 Eq. pairsums, rigid-particle
  * form).  F or S may be NULL (treated as zero); U or E may be NULL (not
- * written).  Asynchronous on stream. */
+ * written).  A NULL output or a NULL F selects a reduced product (E from S
+ * alone, U from [F; S], U from S alone) with the same result for the outputs
+ * asked for.  Asynchronous on stream. */
 pse_status pse_mobility_apply(pse_handle h, const double *pos, const void *F, const void *S,
                               void *U, void *E, pse_stream stream);
 
