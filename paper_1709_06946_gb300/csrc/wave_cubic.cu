@@ -44,6 +44,30 @@ __device__ __forceinline__ void publish_ranges(Ranges &r, int lane, int beg, int
   if (lane == 0) r.cum[0] = 0;
 }
 
+// Sum of v[0..8) over each 16-lane half of the warp in 8 shuffles: each exchange
+// halves the components a lane keeps, so lane l of a half ends with the total
+// of component 4 b3 + 2 b2 + b1 (b_k = bit k of l), the same in lanes l and l^1.
+__device__ __forceinline__ float half_reduce8(const float v[8], int sub) {
+  const bool b3 = (sub >> 3) & 1, b2 = (sub >> 2) & 1, b1 = (sub >> 1) & 1;
+  float k4[4], k2[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b3 ? v[i + 4] : v[i], send = b3 ? v[i] : v[i + 4];
+    k4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b2 ? k4[i + 2] : k4[i], send = b2 ? k4[i] : k4[i + 2];
+    k2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  float k1 = (b1 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? k2[0] : k2[1], 2);
+  k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+  return k1;
+}
+__device__ __forceinline__ int half_reduce8_component(int sub) {
+  return 4 * ((sub >> 3) & 1) + 2 * ((sub >> 2) & 1) + ((sub >> 1) & 1);
+}
+
 // Particle index of candidate v < cum[8] (binary search over the 8 bins).
 __device__ __forceinline__ int range_candidate(const Ranges &r, int v) {
   int b = v >= r.cum[4] ? 4 : 0;
@@ -217,29 +241,37 @@ __global__ void __launch_bounds__(NT) k_interp16(WaveArgs wa, int *queue, const 
   constexpr int TS = CUBE, RX = tile_rx(TS, P), ZS = TS * RX, NPT = TS * ZS;
   // footprint split: NFULL passes of whole (x, y) columns (P points along z) per
   // lane, then the REM leftover columns' REM * P points one per lane
-  constexpr int NFULL = (P * P) / 32, REM = (P * P) % 32, NMINI = (REM * P + 31) / 32;
+  // two particles at a time, one per 16-lane half-warp: NFULL passes of whole
+  // (x, y) columns (P points along z) per lane, then the REM leftover columns'
+  // REM * P points one per lane over NMINI passes (P = 6: two full passes and
+  // two leftover passes of 16 and 8 points)
+  constexpr int NFULL = (P * P) / 16, REM = (P * P) % 16, NMINI = (REM * P + 15) / 16;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ Ranges s_rng;
   __shared__ int s_next;
   TileL<float, C> tl;
   tl.init(smem_raw, NPT);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, half = lane >> 4, sub = lane & 15;
   int fx[NFULL > 0 ? NFULL : 1], fy[NFULL > 0 ? NFULL : 1];
   int mx[NMINI > 0 ? NMINI : 1], my[NMINI > 0 ? NMINI : 1], mz[NMINI > 0 ? NMINI : 1];
 #pragma unroll
   for (int ps = 0; ps < NFULL; ++ps) {
-    fx[ps] = (ps * 32 + lane) % P;
-    fy[ps] = (ps * 32 + lane) / P;
+    fx[ps] = (ps * 16 + sub) % P;
+    fy[ps] = (ps * 16 + sub) / P;
   }
 #pragma unroll
   for (int ms = 0; ms < NMINI; ++ms) {
-    const int it = ms * 32 + lane;
-    const int col = NFULL * 32 + (it < REM * P ? it / P : 0);
+    const int it = ms * 16 + sub;
+    const int col = NFULL * 16 + (it < REM * P ? it / P : 0);
     mx[ms] = it < REM * P ? col % P : 64;  // invalid: outside every tile
     my[ms] = col / P;
     mz[ms] = it < REM * P ? it % P : 0;
   }
-  const int waxis = lane / P, wj = lane % P;
+  // 1D Gaussian weights of the half's particle: index i < 3P (axis i / P, point
+  // i % P) held by lane i (wa) or lane i - 16 (wb) of the half
+  const int ia = sub, ib = 16 + sub;
+  const int axa = ia / P, axb = ib < 3 * P ? ib / P : 2;
+  const int ja = ia % P, jb = ib < 3 * P ? ib % P : 0;
   for_each_item(queue, wa.ntiles, [&](int item) {
     const int si = find_sys(wa.tile0, wa.nsys, item);
     const SysDev &a = wa.sys[si];
@@ -270,7 +302,7 @@ __global__ void __launch_bounds__(NT) k_interp16(WaveArgs wa, int *queue, const 
       if (lane == 0) s_next = 0;
     }
     const float nal = -(float)a.alpha * LOG2E, hs = (float)a.h, pref = (float)a.pref;
-    const float wjh = (float)wj * hs;
+    const float jah = (float)ja * hs, jbh = (float)jb * hs;
     __syncthreads();  // tile staged, ranges published
     const int total = s_rng.cum[8];
     for (;;) {
@@ -291,24 +323,32 @@ __global__ void __launch_bounds__(NT) k_interp16(WaveArgs wa, int *queue, const 
       }
       unsigned mask = __ballot_sync(0xffffffffu, hit);
       while (mask) {
-        const int src = __ffs(mask) - 1;
+        // the next two hits: the first for half 0, the second (if any) for half 1
+        const int src0 = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int ke = __shfl_sync(0xffffffffu, k, src), pe = __shfl_sync(0xffffffffu, pk, src);
+        const int src1 = mask ? __ffs(mask) - 1 : -1;
+        if (mask) mask &= mask - 1;
+        const int src = half ? src1 : src0;
+        const bool live = src >= 0;
+        const int ke = __shfl_sync(0xffffffffu, k, src & 31), pe = __shfl_sync(0xffffffffu, pk, src & 31);
         const int ex = (pe & 1023) - 512, ey = ((pe >> 10) & 1023) - 512, ez = (pe >> 20) - 512;
         const float4 d0 = sp_d0[ke];
-        const float o = (waxis == 0 ? d0.x : (waxis == 1 ? d0.y : d0.z)) + wjh;
-        const float wl = exp2f(nal * o * o);
+        const float oa = (axa == 0 ? d0.x : (axa == 1 ? d0.y : d0.z)) + jah;
+        const float ob = (axb == 0 ? d0.x : (axb == 1 ? d0.y : d0.z)) + jbh;
+        const float wa = exp2f(nal * oa * oa), wb = exp2f(nal * ob * ob);
         float wz[P];
 #pragma unroll
-        for (int jz = 0; jz < P; ++jz) wz[jz] = __shfl_sync(0xffffffffu, wl, 2 * P + jz);
+        for (int jz = 0; jz < P; ++jz)
+          wz[jz] = 2 * P + jz < 16 ? __shfl_sync(0xffffffffu, wa, 2 * P + jz, 16)
+                                   : __shfl_sync(0xffffffffu, wb, 2 * P + jz - 16, 16);
         const int pb = ez * ZS + ey * RX + ex;
         float acc[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = 0.f;
 #pragma unroll
         for (int ps = 0; ps < NFULL; ++ps) {
-          const float wxy = __shfl_sync(0xffffffffu, wl, fx[ps]) * __shfl_sync(0xffffffffu, wl, P + fy[ps]);
-          if ((unsigned)((ex + fx[ps]) | (ey + fy[ps])) < (unsigned)TS) {
+          const float wxy = __shfl_sync(0xffffffffu, wa, fx[ps], 16) * __shfl_sync(0xffffffffu, wa, P + fy[ps], 16);
+          if (live && (unsigned)((ex + fx[ps]) | (ey + fy[ps])) < (unsigned)TS) {
             const int col = pb + fy[ps] * RX + fx[ps];
 #pragma unroll
             for (int jz = 0; jz < P; ++jz) {
@@ -324,18 +364,20 @@ __global__ void __launch_bounds__(NT) k_interp16(WaveArgs wa, int *queue, const 
         }
 #pragma unroll
         for (int ms = 0; ms < NMINI; ++ms) {
-          const float wt = __shfl_sync(0xffffffffu, wl, mx[ms] & 31) * __shfl_sync(0xffffffffu, wl, P + my[ms]) *
-                           __shfl_sync(0xffffffffu, wl, 2 * P + mz[ms]);
-          if ((unsigned)((ex + mx[ms]) | (ey + my[ms]) | (ez + mz[ms])) < (unsigned)TS) {
+          const int iz = 2 * P + mz[ms];  // the z weight's index: lane iz (wa) or iz - 16 (wb)
+          const float za = __shfl_sync(0xffffffffu, wa, iz & 15, 16), zb = __shfl_sync(0xffffffffu, wb, iz & 15, 16);
+          const float wt = __shfl_sync(0xffffffffu, wa, mx[ms] & 15, 16) * __shfl_sync(0xffffffffu, wa, P + my[ms], 16) *
+                           (iz < 16 ? za : zb);
+          if (live && (unsigned)((ex + mx[ms]) | (ey + my[ms]) | (ez + mz[ms])) < (unsigned)TS) {
             float vv[C];
             tl.load(pb + mz[ms] * ZS + my[ms] * RX + mx[ms], vv);
 #pragma unroll
             for (int c = 0; c < C; ++c) acc[c] += wt * vv[c];
           }
         }
-        const float tot = warp_reduce8(acc, lane);
-        const int comp = reduce8_component(lane);
-        if ((lane & 3) == 0 && comp < C) atomicAdd(vout + 8 * (size_t)ke + SLOT0 + comp, pref * tot);
+        const float tot = half_reduce8(acc, sub);
+        const int comp = half_reduce8_component(sub);
+        if (live && (sub & 1) == 0 && comp < C) atomicAdd(vout + 8 * (size_t)ke + SLOT0 + comp, pref * tot);
       }
     }
     __syncthreads();  // the staged tile is no longer read when the next item overwrites it
