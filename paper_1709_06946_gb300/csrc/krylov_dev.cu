@@ -2,7 +2,8 @@
 // Lanczos square root (Sec. 3.2: tridiagonal T_m, c_m = T_m^{1/2} e1, stopping
 // rule |c_m - [c_{m-1}; 0]| / |c_m| <= tol) and of unrestarted GMRES for the
 // stresslet constraint (Hessenberg column, Givens rotations, |r|/|b| <= tol,
-// back substitution), one thread per suspension.  The dot products they read
+// back substitution), one thread per suspension (one warp for the Lanczos
+// square root).  The dot products they read
 // and the scale factors and combination coefficients they write live in the
 // per-suspension coefficient blocks; loop control sets a flag (and, inside a
 // CUDA graph, the while-node condition) so an iteration needs no host round trip.
