@@ -33,7 +33,10 @@ halves x; 8-vectors per particle are [F_x, F_y, F_z, s_1..s_5].
 
 Parity: pinned against the dense Ewald oracle (within tol) and the direct
 k-sum on the same k set (tests/test_oracle_pse.py); Lanczos against a dense
-symmetric square root; GMRES against the dense Schur complement.
+symmetric square root; GMRES against the dense Schur complement; the mid-point
+scheme (midpoint_step, shared by constrained_step) against the one-step mean
+kT dt div R_FU^{-1} and covariance 2 kT dt R_FU^{-1} of App. B
+(tests/test_oracle_midpoint.py).
 """
 import math
 
@@ -341,30 +344,43 @@ def brownian_sample(pos, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=100, r
     return scale * (yr.reshape(N, 8) + yw), {'lanczos_iters': it, 'lanczos_err': err}
 
 
-def constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=100,
-                     krylov_tol=None, krylov_maxiter=50):
-    """One mid-point step (Sec. 3.4).  Returns (x_{k+1}, S_{k+1/2}, stats)."""
-    N = pos.shape[0]
-    x0 = np.mod(pos, p.L)
-    B, st = brownian_sample(x0, dt, w1, w2, p, lanczos_tol, lanczos_maxiter)
+def midpoint_step(x0, FP, dt, B, mobility_at, solve, L):
+    """Slip, constrained solve and full step of the mid-point scheme (Sec. 3.4, App. B).
+
+    For any mobility: B = [U^B; E^B] (N, 8) is the Brownian slip drawn at x_k;
+    mobility_at(x) returns the product (F, S) -> (U, E) at configuration x;
+    solve(mes, rhs) returns (S, *info) with mes(S) = rhs.  The scheme moves to
+    x_{k+1/2} = x_k + dt/2 U^B, solves M_ES S = -E^B - M_EF F^P there (E = 0 at the
+    mid-point), takes U = U^B + M_UF F^P + M_US S and x_{k+1} = x_k + dt U.
+    Positions are wrapped into [0, L).  Returns (x_{k+1}, S, info).
+    """
+    N = x0.shape[0]
     UB, EB = B[:, :3], B[:, 3:]
-    xh = np.mod(x0 + 0.5 * dt * UB, p.L)
-    op = RealOp(xh, p)
+    xh = np.mod(x0 + 0.5 * dt * UB, L)
+    mob = mobility_at(xh)
     zF = np.zeros((N, 3)) if FP is None else FP
     rhs = -EB
     if FP is not None:
-        _, EF = mobility_apply(xh, zF, np.zeros((N, 5)), p, real_op=op)
-        rhs = rhs - EF
+        rhs = rhs - mob(zF, np.zeros((N, 5)))[1]
+    S, *info = solve(lambda s: mob(np.zeros((N, 3)), s.reshape(N, 5))[1].ravel(), rhs.ravel())
+    S = S.reshape(N, 5)
+    U = UB + mob(zF, S)[0]
+    x1 = np.mod(x0 + dt * U, L)
+    return x1, S, info
 
-    def mes(s):
-        _, E = mobility_apply(xh, np.zeros((N, 3)), s.reshape(N, 5), p, real_op=op)
-        return E.ravel()
+
+def constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=100,
+                     krylov_tol=None, krylov_maxiter=50):
+    """One mid-point step (Sec. 3.4) with the PSE mobility.  Returns (x_{k+1}, S_{k+1/2}, stats)."""
+    x0 = np.mod(pos, p.L)
+    B, st = brownian_sample(x0, dt, w1, w2, p, lanczos_tol, lanczos_maxiter)
+
+    def mobility_at(x):
+        op = RealOp(x, p)
+        return lambda F, S: mobility_apply(x, F, S, p, real_op=op)
 
     ktol = p.tol if krylov_tol is None else krylov_tol
-    S, kit, rel = gmres(mes, rhs.ravel(), ktol, krylov_maxiter)
-    S = S.reshape(N, 5)
-    U, _ = mobility_apply(xh, zF, S, p, real_op=op)
-    U = UB + U
-    x1 = np.mod(x0 + dt * U, p.L)
+    x1, S, (kit, rel) = midpoint_step(x0, FP, dt, B, mobility_at,
+                                      lambda A, b: gmres(A, b, ktol, krylov_maxiter), p.L)
     st.update({'krylov_iters': kit, 'krylov_relres': rel})
     return x1, S, st
