@@ -180,14 +180,18 @@ __global__ void __launch_bounds__(128) k_na_real(NAArgs a, const double *__restr
     for (int m = 0; m < 5; ++m) E[5 * (size_t)i + m] = e[m];
 }
 
-bool on_device(const void *p) {
+// True for NULL, for managed memory, and for device memory of device `dev` (the
+// current device, whose copy of the scratch array the kernels use).  Device
+// memory of another GPU is refused: without peer access the kernels would fault.
+bool on_device(const void *p, int dev) {
   if (!p) return true;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -204,8 +208,15 @@ extern "C" pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, d
     g_na_err = "pse_mobility_real_noalloc: invalid parameter or NULL positions";
     return PSE_ERR_INVALID_ARG;
   }
-  if (!on_device(pos) || !on_device(F) || !on_device(S) || !on_device(U) || !on_device(E)) {
-    g_na_err = "pse_mobility_real_noalloc: all arrays must be device memory (nothing is staged)";
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+    cudaGetLastError();
+    g_na_err = "pse_mobility_real_noalloc: no current CUDA device";
+    return PSE_ERR_CUDA;
+  }
+  if (!on_device(pos, dev) || !on_device(F, dev) || !on_device(S, dev) || !on_device(U, dev) || !on_device(E, dev)) {
+    g_na_err = "pse_mobility_real_noalloc: all arrays must be device memory of the current device "
+               "(nothing is staged)";
     return PSE_ERR_INVALID_ARG;
   }
   pse::Params p{};
@@ -228,12 +239,6 @@ extern "C" pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, d
     return PSE_ERR_INVALID_ARG;
   }
   int nc = std::max(1, std::min(NA_MAX_NC, (int)std::floor(L / p.rcut)));
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
-    cudaGetLastError();
-    g_na_err = "pse_mobility_real_noalloc: no current CUDA device";
-    return PSE_ERR_CUDA;
-  }
   unsigned char *base = nullptr;
   double self_uf = 0, self_es = 0;
   {
@@ -249,6 +254,18 @@ extern "C" pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, d
     base = (unsigned char *)g_na_addr[dev];
     TableKey key{a, eta, xi, p.rcut};
     if (!g_na_has_table[dev] || !(g_na_uploaded[dev] == key)) {
+      // the upload waits for its copy, which a stream being captured cannot do
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        g_na_err = "pse_mobility_real_noalloc: cannot query the stream's capture status";
+        return PSE_ERR_CUDA;
+      }
+      if (cs != cudaStreamCaptureStatusNone) {
+        g_na_err = "pse_mobility_real_noalloc: a new table (a, eta, xi or tol changed) must be uploaded "
+                   "outside stream capture; make one call with these parameters before capturing";
+        return PSE_ERR_INVALID_ARG;
+      }
       if (!(g_host_key == key)) {
         pse::fill_real_table_f32(p, ppa, len, g_host_table, &g_host_self[0], &g_host_self[1]);
         g_host_key = key;
@@ -281,8 +298,13 @@ extern "C" pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, d
   int *key = (int *)(base + OFF_KEY), *cnt = (int *)(base + OFF_CNT), *cur = (int *)(base + OFF_CUR);
   int *list = (int *)(base + OFF_LIST);
   const float *tab = (const float *)(base + OFF_TABLE);
-  cudaMemsetAsync(cnt, 0, sizeof(int) * (ncell + 1), s);
-  cudaMemsetAsync(cur, 0, sizeof(int) * (ncell + 1), s);
+  cudaError_t me = cudaMemsetAsync(cnt, 0, sizeof(int) * (ncell + 1), s);
+  if (me == cudaSuccess) me = cudaMemsetAsync(cur, 0, sizeof(int) * (ncell + 1), s);
+  if (me != cudaSuccess) {
+    cudaGetLastError();
+    g_na_err = std::string("pse_mobility_real_noalloc: clearing the cell counters: ") + cudaGetErrorString(me);
+    return PSE_ERR_CUDA;
+  }
   unsigned nb = (unsigned)((N + 255) / 256);
   k_na_bin<<<nb, 256, 0, s>>>(g, pos, key, cnt);
   k_na_scan<<<1, 1024, 0, s>>>(cnt, ncell);
