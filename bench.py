@@ -56,10 +56,16 @@ def parse():
     ap.add_argument('--dt', type=float, default=1e-3)
     ap.add_argument('--fp64-steps', type=int, default=2)
     ap.add_argument('--e2e-steps', type=int, default=3)
-    ap.add_argument('--cpu-N', type=int, default=1000)
+    ap.add_argument('--cpu-N', type=int, default=3000, help='oracle size of the cpu_baseline sample')
+    ap.add_argument('--ref-N', type=int, default=1000, help='oracle size of each --impl reference step')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='step', choices=['step', 'batch256', 'serve'])
-    ap.add_argument('--serve-seconds', type=float, default=12.0, help='per arrival rate')
+    ap.add_argument('--serve-seconds', type=float, default=12.0, help='per arrival rate (--workload serve)')
+    ap.add_argument('--serve-seconds-default', type=float, default=4.0,
+                    help='per arrival rate of the serving sweep in the default line')
+    ap.add_argument('--eps2', type=float, default=1e-4, help='second PSE tolerance of the default line (0: omit)')
+    ap.add_argument('--batch-steps', type=int, default=3,
+                    help='timed steps of the 256-suspension block of the default line (0: omit)')
     ap.add_argument('--serve-slots', type=int, default=4)
     ap.add_argument('--serve-pool', type=int, default=8, help='distinct resident suspensions')
     ap.add_argument('--serve-rates', default='', help='comma-separated arrival rates (req/s)')
@@ -68,6 +74,9 @@ def parse():
     ap.add_argument('--graph', type=int, default=1, help='1: time the graph-captured step (default)')
     ap.add_argument('--profile-steps', type=int, default=3, help='host-launched steps timed per stage')
     ap.add_argument('--no-accuracy', action='store_true', help='omit the mixed-vs-FP64 error per output')
+    ap.add_argument('--wave-kernel', type=int, default=0,
+                    help='16^3-tile kernels: 0 grid-column spreading and shared-tile interpolation; bit 0: '
+                         'shared-tile spreading; bit 1: grid-column interpolation')
     return ap.parse_args()
 
 
@@ -162,47 +171,94 @@ def measured_peaks():
         return {}
 
 
-def oracle_step_rate(N_s, phi, tol, xi, dt, seed=1):
-    """Seconds for one oracle constrained step at N_s particles (same phi, tol, xi)."""
+def host_description():
+    """Host CPU model, logical cores and the BLAS thread setting the oracle runs with."""
+    model = ''
+    try:
+        with open('/proc/cpuinfo') as f:
+            for ln in f:
+                k = ln.split(':')[0].strip().lower()
+                if k in ('model name', 'cpu model', 'hardware'):
+                    model = ln.split(':', 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    blas = {k: os.environ[k] for k in ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS')
+            if k in os.environ}
+    try:
+        from threadpoolctl import threadpool_info
+        blas['threadpools'] = [(d.get('internal_api'), d.get('num_threads')) for d in threadpool_info()]
+    except ImportError:
+        blas.setdefault('threadpools', 'threadpoolctl not installed; library default (all cores)')
+    return {'cpu_model': model, 'host_cores': os.cpu_count(), 'blas': blas}
+
+
+def oracle_step_time(N_s, phi, tol, xi, dt, seed=1):
+    """(wall s, CPU s, iterations) of one oracle constrained step at N_s particles (same phi, tol, xi)."""
     import pse_inputs
     from oracle import params, philox, pse as opse
     pos, L = pse_inputs.rsa_positions(N_s, phi, seed=seed)
     p = params.choose(N_s, L, 1.0, 1.0, 1.0, xi, tol)
     w1 = philox.lanczos_noise(seed, 0, N_s)
     w2 = philox.wave_noise(seed, 0, p.Ng)
-    t0 = time.perf_counter()
-    opse.constrained_step(pos, None, dt, w1, w2, p)
-    return time.perf_counter() - t0
+    c0, t0 = time.process_time(), time.perf_counter()
+    _, _, st = opse.constrained_step(pos, None, dt, w1, w2, p)
+    wall = time.perf_counter() - t0
+    return wall, time.process_time() - c0, st
 
 
 def cpu_baseline(args):
-    dt_s = oracle_step_rate(args.cpu_N, args.phi, args.tol, args.xi, args.dt)
-    value = (args.cpu_N / args.N) / dt_s          # linear-in-N scaling (PTPS constant, Sec. 4)
-    return {'value': value, 'unit': 'steps/s', 'cores': 1, 'kind': 'oracle',
-            'sample': 'one FP64 oracle constrained step at N=%d (phi=%g, eps=%g, xi=%g) took %.2f s; '
-                      'scaled to N=%d by particle count' % (args.cpu_N, args.phi, args.tol, args.xi, dt_s, args.N)}
+    """The FP64 oracle's constrained step timed on the host cores at N = cpu_N (a bounded
+    sample of the workload), reported in the metric's unit by linear scaling in N
+    (PTPS independent of N, Sec. 4) beside the measured figures."""
+    wall, cpu, st = oracle_step_time(args.cpu_N, args.phi, args.tol, args.xi, args.dt)
+    value = (args.cpu_N / args.N) / wall
+    out = {'value': value, 'unit': 'steps/s', 'cores': round(cpu / wall, 2), 'kind': 'oracle',
+           'sample': 'one FP64 oracle constrained step at N=%d (phi=%g, eps=%g, xi=%g): %.2f s wall, %.2f s CPU; '
+                     'value scaled to N=%d by particle count (PTPS constant in N)'
+                     % (args.cpu_N, args.phi, args.tol, args.xi, wall, cpu, args.N),
+           'measured': {'N': args.cpu_N, 's_per_step': wall, 'ptps': args.cpu_N / wall,
+                        'lanczos_iters': int(st['lanczos_iters']), 'krylov_iters': int(st['krylov_iters'])},
+           'cores_note': 'cores = CPU time / wall time of the timed step (threads the oracle actually used)'}
+    out.update(host_description())
+    return out
 
 
 def run_reference(args, world, rank, pg):
+    """The oracle arm: constrained steps of the FP64 oracle on the host cores at N = cpu_N
+    (the largest size whose K + W steps end within a few minutes); the line names the N it
+    ran and gives the linear-in-N extrapolation to the benchmark size beside it."""
     if rank != 0:
         return
     steps = max(1, args.steps)
-    times = []
+    N_s = args.ref_N
+    times, cpus = [], []
     for k in range(args.warmup + steps):
-        t = oracle_step_rate(args.cpu_N, args.phi, args.tol, args.xi, args.dt, seed=1 + k)
+        wall, cpu, _ = oracle_step_time(N_s, args.phi, args.tol, args.xi, args.dt, seed=1 + k)
         if k >= args.warmup:
-            times.append(t)
+            times.append(wall)
+            cpus.append(cpu)
     per = float(np.mean(times))
-    value = (args.cpu_N / args.N) / per
+    value = 1.0 / per
+    cores = round(float(np.sum(cpus) / np.sum(times)), 2)
     line = {'metric': METRIC, 'value': value, 'unit': 'steps/s', 'n_gpus': args.gpus, 'steps': steps,
-            'warmup': args.warmup, 'ms_per_step': 1000.0 / value, 'higher_is_better': True, 'scaling': 'weak',
+            'warmup': args.warmup, 'ms_per_step': 1000.0 * per, 'higher_is_better': True, 'scaling': 'weak',
             'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic', 'impl': 'reference',
-            'config': {'workload': 'N=%d hard spheres phi=%g eps=%g constrained mid-point step' % (args.N, args.phi, args.tol),
-                       'N': args.N, 'phi': args.phi, 'tol': args.tol, 'xi': args.xi},
-            'cpu_baseline': {'value': value, 'unit': 'steps/s', 'cores': 1, 'kind': 'oracle',
-                             'sample': 'FP64 oracle constrained steps at N=%d, scaled to N=%d by particle count'
-                                       % (args.cpu_N, args.N)},
+            'config': {'workload': 'N=%d hard spheres (RSA) phi=%g eps=%g constrained mid-point step, FP64 oracle on '
+                                   'the host cores (a bounded sample of the N=%d workload)'
+                                   % (N_s, args.phi, args.tol, args.N),
+                       'N': N_s, 'phi': args.phi, 'tol': args.tol, 'xi': args.xi},
+            'ptps': N_s * value,
+            'extrapolated': {'N': args.N, 'steps_per_s': N_s * value / args.N,
+                             'basis': 'linear in N (PTPS constant in N, Sec. 4); not measured'},
+            'cpu_baseline': {'value': value, 'unit': 'steps/s', 'cores': cores, 'kind': 'oracle',
+                             'sample': '%d FP64 oracle constrained steps at N=%d after %d warm-up steps'
+                                       % (steps, N_s, args.warmup)},
             'e2e': {'value': value, 'unit': 'steps/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    line['cpu_baseline'].update(host_description())
     print(json.dumps(line), flush=True)
 
 
@@ -210,7 +266,7 @@ def accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64):
     """Relative L2 error of the mixed form against the all-FP64 form on the same
     seeded inputs and the same external noise: mobility U and E, Brownian U^B and
     E^B, one constrained step's displacement and stresslets; GMRES residuals."""
-    hm = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed')
+    hm = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', wave_kernel=args.wave_kernel)
     N, Ng = args.N, hm.info['Ng']
     g = torch.Generator(device=dev).manual_seed(3)
     F = torch.randn((N, 3), generator=g, device=dev, dtype=torch.float64)
@@ -244,12 +300,13 @@ def accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64):
     return out
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# first launch of each kernel on the benchmark workload (N = 1048576, phi = 0.3, eps = 1e-3,
-# xi = 0.5, N_g = 256, P = 6); reported only for that workload, and to be retaken whenever the
-# kernel changes: 5-component spread and interpolation (16^3 tiles), full-product pair sum.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernel instances on the
+# benchmark workload (N = 1048576, phi = 0.3, eps = 1e-3, xi = 0.5, N_g = 256, P = 6): ncu captures of
+# the N = 524288 case of the same workload (same N_g per particle density is not kept, so grid bytes
+# are taken at N_g = 256 and particle bytes scale with N), scaled to a full launch as stated in the
+# profiles/ summaries.  Empty until retaken for the current kernels; reported only for that workload.
 NCU_TRAFFIC_WORKLOAD = (1048576, 0.3, 1e-3, 0.5, 256, 6)
-NCU_TRAFFIC = {'spread': 351.2e6, 'interp': 435.1e6, 'real': 1900.0e6}
+NCU_TRAFFIC = {}
 
 
 def real_flops_per_pair():
@@ -261,6 +318,54 @@ def real_flops_per_pair():
     return {'full': 178, 'se': 130, 'fsu': 82, 'su': 68}
 
 
+EST_FLOPS_PER_PAIR = 250        # a-priori estimate of the full 8 x 8 block per pair direction
+
+
+def kernel_instances(prof, N, Ng, P, npairs, cubic, wave_kernel=0):
+    """Device time, launches and algorithmic rate of each kernel instance of this library in the
+    profiled steps.  Algorithmic bytes per launch (C components): spreading N(16 + 4C) + 4C N_g^3,
+    interpolation 4C N_g^3 + N(16 + 4C), kernel scaling (C_in + C_out) n_k 8, noise 8 n_k 8 written
+    (n_k = N_g^2 (N_g/2 + 1)); pair sum: formula flops per ordered pair x pairs."""
+    vm, vc = prof['variant_ms'], prof['variant_calls']
+    n3 = Ng ** 3
+    nkh = Ng * Ng * (Ng // 2 + 1)
+    # kernel names: 16^3 tiles take the grid-column spreading and the shared-tile interpolation by
+    # default (wave_kernel bits 0 / 1 swap each), other tiles the general kernels
+    ts = ('16' if wave_kernel & 1 else '_col') if cubic else ''
+    ti = ('_col' if wave_kernel & 2 else '16') if cubic else ''
+    fl = real_flops_per_pair()
+    spec = [('spread', 'k_spread%s<C=8,P=%d>' % (ts, P), ('full', 'fsu'), N * (16 + 32) + 32 * n3),
+            ('spread', 'k_spread%s<C=5,P=%d>' % (ts, P), ('se', 'su'), N * (16 + 20) + 20 * n3),
+            ('interp', 'k_interp%s<C=8,P=%d>' % (ti, P), ('full',), 32 * n3 + N * (16 + 32)),
+            ('interp', 'k_interp%s<C=5,P=%d>' % (ti, P), ('se',), 20 * n3 + N * (16 + 20)),
+            ('interp', 'k_interp%s<C=3,P=%d>' % (ti, P), ('fsu', 'su'), 12 * n3 + N * (16 + 12)),
+            ('scale', 'k_scale<M_FULL>', ('full',), 16 * nkh * 8),
+            ('scale', 'k_scale<M_SE>', ('se',), 10 * nkh * 8),
+            ('scale', 'k_scale<M_FSU>', ('fsu',), 11 * nkh * 8),
+            ('scale', 'k_scale<M_SU>', ('su',), 8 * nkh * 8),
+            ('noise', 'k_noise', ('full',), 8 * nkh * 8)]
+    out = []
+    for stage, name, vs, bytes_per_launch in spec:
+        ms = sum(vm[stage][v] for v in vs)
+        calls = sum(vc[stage][v] for v in vs)
+        if calls == 0 or ms <= 0:
+            continue
+        per = ms / calls / 1e3
+        out.append({'kernel': name, 'stage': stage, 'bound': 'hbm', 'launches': calls, 'ms': ms,
+                    'us_per_launch': per * 1e6, 'algorithmic_bytes_per_launch': bytes_per_launch,
+                    'achieved': bytes_per_launch / per / 1e9, 'unit': 'GB/s'})
+    for v, mode in (('full', 'M_FULL'), ('se', 'M_SE'), ('fsu', 'M_FSU'), ('su', 'M_SU')):
+        ms, calls = vm['real'][v], vc['real'][v]
+        if calls == 0 or ms <= 0:
+            continue
+        per = ms / calls / 1e3
+        out.append({'kernel': 'k_real<float,%s>' % mode, 'stage': 'real', 'bound': 'alu', 'launches': calls,
+                    'ms': ms, 'us_per_launch': per * 1e6, 'flops_per_pair': fl[v],
+                    'algorithmic_flops_per_launch': npairs * fl[v],
+                    'achieved': npairs * fl[v] / per / 1e12, 'unit': 'TFLOP/s'})
+    return out
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
     import pse_inputs
@@ -270,7 +375,8 @@ def run_ours(args, world, rank, local, pg):
     dev = torch.device('cuda', local)
     torch.cuda.set_device(dev)
     pos_np, L = pse_inputs.rsa_positions(args.N, args.phi, seed=1 + rank)
-    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', use_graph=args.graph)
+    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', use_graph=args.graph,
+                wave_kernel=args.wave_kernel)
     inf = h.info
     x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
     stream = torch.cuda.current_stream(dev)
@@ -320,57 +426,63 @@ def run_ours(args, world, rank, local, pg):
     prof = h.profile()
     h.set_profiling(False)
 
-    # roofline of the dominant stage (device time per stage from CUDA events on the launching stream)
+    # roofline of the dominant kernel instance (device time per stage and product variant from
+    # CUDA events on the launching stream; cuFFT excluded, it is library code)
     peaks = measured_peaks()
+    hbm = peaks.get('hbm_gbs')
+    hbm_note = 'of measured hbm_gbs (MEASURED_PEAKS.json)' if hbm else 'of fallback 6800 GB/s'
+    hbm = hbm or 6800.0
     stage_ms = prof['ms']
     Li = sum(i[0] for i in piters)
     Ki = sum(i[1] for i in piters)
     npairs = float(np.mean([i[2] for i in piters]))
     Ng, N = inf['Ng'], args.N
     n3 = Ng ** 3
-    nkh = Ng * Ng * (Ng // 2 + 1)
     K = KP
-    # per step: GMRES products (5 -> 5) Ki/K times, one final S -> U product (no external
-    # force), one noise pass
+    cubic = tuple(inf['tile']) == (16, 16, 16)
+    kernels = kernel_instances(prof, N, Ng, inf['P'], npairs, cubic, args.wave_kernel)
+    traffic_ok = (args.N, args.phi, args.tol, args.xi, Ng, inf['P']) == NCU_TRAFFIC_WORKLOAD
+    for k in kernels:
+        k['share_of_step'] = k['ms'] / (1000.0 * prof_elapsed)
+        if k['bound'] == 'hbm':
+            k['peak'], k['frac'] = hbm, k['achieved'] / hbm
+        else:
+            k['peak'], k['frac'] = FP32_PEAK_TFLOPS_AT_MAX, k['achieved'] / FP32_PEAK_TFLOPS_AT_MAX
+        k['traffic'] = NCU_TRAFFIC.get(k['kernel']) if traffic_ok else None
+    dom = max(kernels, key=lambda k: k['ms'])
+    roof = {'bound': dom['bound'], 'kernel': dom['kernel'], 'achieved': dom['achieved'], 'peak': dom['peak'],
+            'unit': dom['unit'], 'frac': dom['frac'], 'traffic': dom['traffic'], 'launches': dom['launches'],
+            'us_per_launch': dom['us_per_launch'],
+            'peak_note': (hbm_note if dom['bound'] == 'hbm' else
+                          'derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz'),
+            'per_launch': ('algorithmic bytes %.4g (per-particle and per-grid-point bytes x units)' %
+                           dom['algorithmic_bytes_per_launch']) if dom['bound'] == 'hbm' else
+                          ('flops %.4g (%d per ordered pair x %.4g pairs)' %
+                           (dom['algorithmic_flops_per_launch'], dom['flops_per_pair'], npairs))}
+    # the pair sum: all of its instances against the derived FP32 peak, with the formula flops per
+    # pair and the a-priori ~250-flop estimate of the full block beside them
+    fl = real_flops_per_pair()
+    real_flops = npairs * (fl['full'] * Li + fl['se'] * Ki + fl['su'] * K)
+    real_rate = real_flops / (stage_ms['real'] / 1000.0) / 1e12 if stage_ms['real'] > 0 else None
+    roof_real = {'bound': 'alu', 'kernel': 'k_real (real-space pair sum, all instances)', 'achieved': real_rate,
+                 'peak': FP32_PEAK_TFLOPS_AT_MAX, 'unit': 'TFLOP/s',
+                 'frac': real_rate / FP32_PEAK_TFLOPS_AT_MAX if real_rate else None,
+                 'peak_note': 'derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz',
+                 'flops_per_pair': fl, 'estimate_flops_per_pair_full': EST_FLOPS_PER_PAIR,
+                 'achieved_at_estimate_flops': (npairs * EST_FLOPS_PER_PAIR * (Li + Ki + K)
+                                              / (stage_ms['real'] / 1000.0) / 1e12) if stage_ms['real'] > 0 else None}
+    # per-step algorithmic rates of the wave-space stages, and the ceiling that binds spreading and
+    # interpolation: each particle's P^3 footprint x C components in the shared tile, read and
+    # written (spread) or read (interpolation)
     spread_comps = [5] * Ki + [5] * K
     interp_comps = [5] * Ki + [3] * K + [8] * K
+    nkh = Ng * Ng * (Ng // 2 + 1)
     algo = {
-        'spread': sum(N * (32 + 4 * c) + c * n3 * 4 for c in spread_comps),
-        'interp': sum(c * n3 * 4 + N * (32 + 4 * c) for c in interp_comps),
+        'spread': sum(N * (16 + 4 * c) + c * n3 * 4 for c in spread_comps),
+        'interp': sum(c * n3 * 4 + N * (16 + 4 * c) for c in interp_comps),
         'scale': sum((ci + co) * nkh * 8 for ci, co in [(5, 5)] * Ki + [(5, 3)] * K),
         'noise': K * 8 * nkh * 8,
     }
-    dom = max(('real', 'spread', 'interp', 'scale', 'noise', 'fft'), key=lambda s: stage_ms[s])
-    traffic_ok = (args.N, args.phi, args.tol, args.xi, Ng, inf['P']) == NCU_TRAFFIC_WORKLOAD
-    fl = real_flops_per_pair()
-    if dom == 'real' or dom == 'fft':
-        flops = npairs * (fl['full'] * Li + fl['se'] * Ki + fl['su'] * K)
-        achieved = flops / (stage_ms['real'] / 1000.0) / 1e12
-        peak = FP32_PEAK_TFLOPS_AT_MAX
-        roof = {'bound': 'alu', 'kernel': 'k_real (real-space pair sum)', 'achieved': achieved, 'peak': peak,
-                'unit': 'TFLOP/s', 'frac': achieved / peak,
-                'traffic': NCU_TRAFFIC['real'] if traffic_ok else None,
-                'peak_note': 'derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz',
-                'launches': prof['calls']['real'], 'flops_per_pair': fl}
-    else:
-        hbm = peaks.get('hbm_gbs', 6800.0)
-        achieved = algo[dom] / (stage_ms[dom] / 1000.0) / 1e9
-        roof = {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s',
-                'frac': achieved / hbm, 'traffic': NCU_TRAFFIC.get(dom) if traffic_ok else None,
-                'traffic_note': 'DRAM bytes per launch of the 5-component (GMRES) launch, one ncu capture',
-                'peak_note': 'measured hbm_gbs (MEASURED_PEAKS.json)'}
-    # the pair sum's FP32 rate is reported beside the dominant stage's roofline in any case
-    real_flops = npairs * (fl['full'] * Li + fl['se'] * Ki + fl['su'] * K)
-    real_rate = real_flops / (stage_ms['real'] / 1000.0) / 1e12 if stage_ms['real'] > 0 else None
-    roof_real = {'bound': 'alu', 'kernel': 'k_real (real-space pair sum)', 'achieved': real_rate,
-                 'peak': FP32_PEAK_TFLOPS_AT_MAX, 'unit': 'TFLOP/s',
-                 'frac': real_rate / FP32_PEAK_TFLOPS_AT_MAX if real_rate else None,
-                 'traffic': NCU_TRAFFIC['real'] if traffic_ok else None,
-                 'traffic_note': 'DRAM bytes per full-product launch (neighbour records, 16 B per ordered pair)',
-                 'peak_note': 'derived FP32 peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz',
-                 'flops_per_pair': fl}
-    # the ceiling that binds spreading and interpolation: each particle's P^3 footprint x C
-    # components in the shared tile, read and written (spread) or read (interpolation)
     P3 = inf['P'] ** 3
     smem_algo = {'spread': sum(N * P3 * c * 4 * 2 for c in spread_comps),
                  'interp': sum(N * P3 * c * 4 for c in interp_comps)}
@@ -381,7 +493,7 @@ def run_ours(args, world, rank, local, pg):
                       'note': 'shared-memory bytes of the footprint updates (N P^3 C x 4 B, x2 when read and '
                               'written) against the derived 152 SMs x 128 B/clk x 2070 MHz'} for k in smem_algo}
     wave_rates = {k: {'GB/s': algo[k] / (stage_ms[k] / 1000.0) / 1e9 if stage_ms[k] > 0 else None,
-                      'frac_of_measured_hbm': (algo[k] / (stage_ms[k] / 1000.0) / 1e9) / peaks.get('hbm_gbs', 6800.0)
+                      'frac_of_measured_hbm': (algo[k] / (stage_ms[k] / 1000.0) / 1e9) / hbm
                       if stage_ms[k] > 0 else None} for k in algo}
 
     result = {'metric': METRIC, 'value': value, 'unit': 'steps/s', 'n_gpus': world, 'steps': args.steps,
@@ -391,6 +503,7 @@ def run_ours(args, world, rank, local, pg):
                                      'precision' % (args.N, args.phi, args.tol),
                          'N': args.N, 'phi': args.phi, 'tol': args.tol, 'xi': args.xi, 'L': L,
                          'Ng': Ng, 'P': inf['P'], 'rcut': inf['rcut'], 'tile': list(inf['tile']),
+                         'wave_kernel': args.wave_kernel,
                          'precision': 'mixed (FP32 grids/pairs/vectors, FP64 Krylov scalars)',
                          'parallelism': 'replicas' if world > 1 else 'single GPU',
                          'l2': 'inputs larger than L2 (FFT grids %.2f GB)' % (8 * n3 * 4 * 2 / 1e9)},
@@ -407,7 +520,7 @@ def run_ours(args, world, rank, local, pg):
                                     'stage events'},
               'stage_ms_per_step': {k: v / K for k, v in stage_ms.items()},
               'wave_stage_hbm': wave_rates, 'wave_stage_smem': smem_rates,
-              'roofline': roof, 'roofline_pair_sum': roof_real, 'clocks': clk,
+              'roofline': roof, 'roofline_pair_sum': roof_real, 'kernels': kernels, 'clocks': clk,
               'gpu_launches': int(round(prof['launches'] / K * args.steps)),
               'gpu_launches_note': 'kernels of this library per step (counted on the host-launched path) x timed '
                                    'steps; cuFFT kernels excluded',
@@ -441,12 +554,24 @@ def run_ours(args, world, rank, local, pg):
         if not args.no_accuracy:
             result['accuracy'] = accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64)
         h64.close()
+    if rank == 0 and world == 1 and args.eps2 > 0:
+        result['eps_%g' % args.eps2] = eps_measure(pkg, torch, dev, args, pos_np, L, args.eps2)
+    if rank == 0 and world == 1 and args.batch_steps > 0:
+        result['batch256'] = batch_measure(pkg, torch, dev, args, args.batch_steps, 2)
     if rank == 0 and world == 1 and not args.no_serving:
-        res, desc = serving_measure(pkg, args, [8.0], 6, 200000, 10.0)
-        r = res[0]
-        result['serving'] = {'p50_ms': r['p50_ms'], 'p99_ms': r['p99_ms'], 'req_per_s': r['req_per_s'],
-                             'offered_rate': r['offered_rate'], 'requests': r['requests'],
-                             'peak_running': r['peak_running'], 'stream': desc}
+        rates = [float(r) for r in args.serve_rates.split(',')] if args.serve_rates else [8, 32, 128, 512, 1024]
+        res, desc = serving_measure(pkg, args, rates, 6, 200000, args.serve_seconds_default)
+        kept = [r for r in res if r['req_per_s'] >= 0.85 * r['arrival_rate']] or res[:1]
+        best = max(kept, key=lambda r: r['req_per_s'])
+        result['serving'] = {'p50_ms': best['p50_ms'], 'p99_ms': best['p99_ms'], 'req_per_s': best['req_per_s'],
+                             'offered_rate': best['offered_rate'], 'requests': best['requests'],
+                             'peak_running': best['peak_running'],
+                             'saturated_req_per_s': max(r['req_per_s'] for r in res),
+                             'note': 'latency at the highest Poisson rate whose completions kept up with arrivals; '
+                                     'the sweep stops at the first rate that saturated',
+                             'sweep': [{k: r[k] for k in ('offered_rate', 'req_per_s', 'p50_ms', 'p99_ms',
+                                                          'peak_running', 'requests')} for r in res],
+                             'stream': desc}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result['cpu_baseline'] = cpu_baseline(args)
     if rank == 0:
@@ -567,68 +692,126 @@ def batch_suspensions(n, seed):
     return Ns, phis, pos, Ls
 
 
-def run_batch(args):
-    import torch
-    import paper_1709_06946_gb300 as pkg
-    pkg.load()
-    dev = torch.device('cuda', 0)
+def batch_measure(pkg, torch, dev, args, steps, warmup, compare_sequential=False):
+    """Batched constrained steps of the 256-suspension workload through one handle: batch steps/s,
+    suspension-steps/s, particle-steps/s, per-suspension iteration spread and stage times."""
     nsys = 256
     Ns, phis, pos, Ls = batch_suspensions(nsys, seed=4)
-    h = pkg.PSE(Ns, Ls, xi=args.xi, tol=args.tol, precision='mixed', grid_ladder=1)
+    h = pkg.PSE(Ns, Ls, xi=args.xi, tol=args.tol, precision='mixed', grid_ladder=1,
+                wave_kernel=args.wave_kernel)
     x = torch.tensor(np.concatenate(pos), device=dev, dtype=torch.float64)
     stream = torch.cuda.current_stream(dev)
-    for k in range(args.warmup):
+    for k in range(warmup):
         h.step(x, args.dt, seed=11, step=k)
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     h.set_profiling(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     iters = []
     ev0.record(stream)
-    for k in range(args.steps):
-        _, st = h.step(x, args.dt, seed=11, step=args.warmup + k)
-        iters.append([(h.system_stats(s)['lanczos_iters'], h.system_stats(s)['krylov_iters']) for s in range(nsys)])
+    for k in range(steps):
+        _, st = h.step(x, args.dt, seed=11, step=warmup + k)
+        iters.append([(h.system_stats(q)['lanczos_iters'], h.system_stats(q)['krylov_iters']) for q in range(nsys)])
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     clk = clocks.stop()
     prof = h.profile()
-    grids = sorted({h.system_info(s)['Ng'] for s in range(nsys)})
+    grids = sorted({h.system_info(q)['Ng'] for q in range(nsys)})
     it = np.array(iters)
-    value = args.steps / elapsed
-    line = {'metric': 'batched constrained steps/s (256 suspensions, one handle)', 'value': value,
-            'unit': 'batch steps/s', 'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup,
-            'ms_per_step': 1000.0 * elapsed / args.steps, 'higher_is_better': True, 'scaling': 'weak',
-            'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
-            'config': {'workload': '256 suspensions, N log-uniform in [500, 20000] (total %d), phi uniform in '
-                                   '[0.05, 0.45], eps=%g, xi=%g, grids rounded to 2^i 3^j (%d FFT groups)'
-                                   % (sum(Ns), args.tol, args.xi, len(grids)),
-                       'total_N': int(sum(Ns)), 'grids': grids},
-            'suspension_steps_per_s': nsys * value, 'ptps': sum(Ns) * value,
-            'iterations': {'lanczos_min': int(it[..., 0].min()), 'lanczos_max': int(it[..., 0].max()),
-                           'krylov_min': int(it[..., 1].min()), 'krylov_max': int(it[..., 1].max())},
-            'stage_ms_per_step': {k: v / args.steps for k, v in prof['ms'].items()},
-            'gpu_launches_per_step': prof['launches'] / args.steps, 'fft_execs_per_step': prof['fft_execs'] / args.steps,
-            'clocks': clk}
+    value = steps / elapsed
+    out = {'value': value, 'unit': 'batch steps/s', 'steps': steps, 'warmup': warmup,
+           'ms_per_step': 1000.0 * elapsed / steps,
+           'workload': '256 suspensions, N log-uniform in [500, 20000] (total %d), phi uniform in [0.05, 0.45], '
+                       'eps=%g, xi=%g, grids rounded to 2^i 3^j (%d FFT groups)'
+                       % (sum(Ns), args.tol, args.xi, len(grids)),
+           'total_N': int(sum(Ns)), 'grids': grids,
+           'suspension_steps_per_s': nsys * value, 'ptps': sum(Ns) * value,
+           'iterations': {'lanczos_min': int(it[..., 0].min()), 'lanczos_max': int(it[..., 0].max()),
+                          'krylov_min': int(it[..., 1].min()), 'krylov_max': int(it[..., 1].max())},
+           'stage_ms_per_step': {k: v / steps for k, v in prof['ms'].items()},
+           'gpu_launches_per_step': prof['launches'] / steps, 'fft_execs_per_step': prof['fft_execs'] / steps,
+           'clocks': clk}
     h.set_profiling(False)
     h.close()
-    if args.compare_sequential:
-        hs = [pkg.PSE(Ns[s], Ls[s], xi=args.xi, tol=args.tol, precision='mixed') for s in range(nsys)]
-        xs = [torch.tensor(pos[s], device=dev, dtype=torch.float64) for s in range(nsys)]
-        for s in range(nsys):
-            hs[s].step(xs[s], args.dt, seed=11, step=0)
+    if compare_sequential:
+        hs = [pkg.PSE(Ns[q], Ls[q], xi=args.xi, tol=args.tol, precision='mixed') for q in range(nsys)]
+        xs = [torch.tensor(pos[q], device=dev, dtype=torch.float64) for q in range(nsys)]
+        for q in range(nsys):
+            hs[q].step(xs[q], args.dt, seed=11, step=0)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for s in range(nsys):
-            hs[s].step(xs[s], args.dt, seed=11, step=1)
+        for q in range(nsys):
+            hs[q].step(xs[q], args.dt, seed=11, step=1)
         torch.cuda.synchronize(dev)
         tseq = time.perf_counter() - t0
-        line['sequential_handles'] = {'s_per_round': tseq, 'batch_speedup': tseq / (elapsed / args.steps)}
+        out['sequential_handles'] = {'s_per_round': tseq, 'batch_speedup': tseq / (elapsed / steps)}
         for hh in hs:
             hh.close()
+    return out
+
+
+def run_batch(args):
+    import torch
+    import paper_1709_06946_gb300 as pkg
+    pkg.load()
+    dev = torch.device('cuda', 0)
+    b = batch_measure(pkg, torch, dev, args, args.steps, args.warmup, args.compare_sequential)
+    line = {'metric': 'batched constrained steps/s (256 suspensions, one handle)', 'value': b['value'],
+            'unit': 'batch steps/s', 'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup,
+            'ms_per_step': b['ms_per_step'], 'higher_is_better': True, 'scaling': 'weak',
+            'vs_baseline': None, 'dtype': 'f32', 'data': 'synthetic',
+            'config': {'workload': b['workload'], 'total_N': b['total_N'], 'grids': b['grids']}}
+    line.update({k: v for k, v in b.items() if k not in ('value', 'unit', 'steps', 'warmup', 'ms_per_step',
+                                                         'workload', 'total_N', 'grids')})
     print(json.dumps(line), flush=True)
+
+
+def eps_measure(pkg, torch, dev, args, pos_np, L, tol, steps=5, warmup=2, fp64_steps=1):
+    """The constrained step at another PSE tolerance on the same positions: mixed (graph) rate,
+    all-FP64 rate, and the mixed form's error per output against the FP64 form on identical
+    inputs and external noise."""
+    stream = torch.cuda.current_stream(dev)
+    h = pkg.PSE(args.N, L, xi=args.xi, tol=tol, precision='mixed', use_graph=args.graph,
+                wave_kernel=args.wave_kernel)
+    inf = h.info
+    x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+    for k in range(warmup):
+        h.step(x, args.dt, seed=4321, step=k)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    its = []
+    ev0.record(stream)
+    for k in range(steps):
+        _, st = h.step(x, args.dt, seed=4321, step=warmup + k)
+        its.append((st['lanczos_iters'], st['krylov_iters']))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_mixed = ev0.elapsed_time(ev1) / 1000.0 / steps
+    h.close()
+    out = {'tol': tol, 'Ng': inf['Ng'], 'P': inf['P'], 'rcut': inf['rcut'], 'steps_per_s': 1.0 / t_mixed,
+           'ms_per_step': 1000.0 * t_mixed, 'ptps': args.N / t_mixed,
+           'lanczos_mean': float(np.mean([i[0] for i in its])), 'krylov_mean': float(np.mean([i[1] for i in its]))}
+    if fp64_steps > 0:
+        h64 = pkg.PSE(args.N, L, xi=args.xi, tol=tol, precision='fp64')
+        x64 = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+        h64.step(x64, args.dt, seed=99, step=0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(fp64_steps):
+            h64.step(x64, args.dt, seed=99, step=1 + k)
+        torch.cuda.synchronize(dev)
+        t64 = (time.perf_counter() - t0) / fp64_steps
+        out['fp64'] = {'steps_per_s': 1.0 / t64, 'ms_per_step': 1000.0 * t64, 'mixed_speedup': t64 / t_mixed}
+        if not args.no_accuracy:
+            a = argparse.Namespace(**vars(args))
+            a.tol = tol
+            out['accuracy'] = accuracy_vs_fp64(pkg, torch, dev, a, pos_np, L, h64)
+        h64.close()
+    return out
 
 
 def main():

@@ -97,7 +97,12 @@ typedef struct pse_options {
   int32_t use_graph;       /* 1: pse_constrained_step runs as one CUDA graph (captured on first use and
                               again when dt, the presence of a force or the layout changes), with the
                               Krylov loops as conditional while nodes; 0 = launches from the host */
-  int32_t reserved[5];
+  int32_t wave_kernel;     /* kernels for 16^3 tiles (mixed precision), bit mask.  0 (default): spreading
+                              with the grid columns of a tile held in registers, interpolation with the
+                              tile in shared memory (the faster of each, measured).  Bit 0 set:
+                              spreading with the tile in shared memory; bit 1 set: interpolation with
+                              the grid columns in registers */
+  int32_t reserved[4];
 } pse_options;
 
 typedef struct pse_info {
@@ -137,11 +142,20 @@ enum {
   PSE_NSTAGES = 8
 };
 
+/* Each stage's time is also split by product variant, so that one kernel
+ * instance can be timed on its own: variant 0 = full product [F; S] -> [U; E]
+ * (8 components; the wave-space noise interpolation counts here too), 1 = S -> E
+ * (5 components), 2 = [F; S] -> U, 3 = S -> U.  The FFT stage uses the variant of
+ * the product it transforms for; setup, noise and vector use variant 0. */
+#define PSE_NVARIANTS 4
+
 typedef struct pse_profile {
   double ms[PSE_NSTAGES];      /* accumulated device time per stage */
   int64_t calls[PSE_NSTAGES];  /* timed sections per stage */
   int64_t launches;            /* kernels of this library launched (cuFFT's excluded) */
   int64_t fft_execs;           /* cuFFT executions */
+  double variant_ms[PSE_NSTAGES][PSE_NVARIANTS];      /* ms split by product variant */
+  int64_t variant_calls[PSE_NSTAGES][PSE_NVARIANTS];  /* calls split by product variant */
 } pse_profile;
 
 /* Fills *opt with the defaults listed above. */
@@ -261,7 +275,11 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
  * a device looks up its address (call it once before any stream capture); the
  * call clears what must start at zero; calls that overlap on the GPU race on
  * the shared array.  Asynchronous on stream except when the table parameters
- * change (the new table is uploaded and the call waits for the copy). */
+ * change (the new table is uploaded and the call waits for the copy); on a
+ * stream that is being captured such a call returns INVALID_ARG without
+ * touching the capture, so make one call with the same a, eta, xi and tol
+ * before capturing.  Arrays must be device (or managed) memory of the current
+ * device; device memory of another GPU is refused with INVALID_ARG. */
 pse_status pse_mobility_real_noalloc(int64_t N, double L, double a, double eta, double xi, double tol,
                                      const double *pos, const float *F, const float *S, float *U, float *E,
                                      pse_stream stream);

@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
                 ('lanczos_tol', ctypes.c_double), ('lanczos_maxiter', ctypes.c_int32),
                 ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
                 ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('grid_ladder', ctypes.c_int32),
-                ('use_graph', ctypes.c_int32), ('reserved', ctypes.c_int32 * 5)]
+                ('use_graph', ctypes.c_int32), ('wave_kernel', ctypes.c_int32), ('reserved', ctypes.c_int32 * 4)]
 
 
 class Info(ctypes.Structure):
@@ -57,9 +57,15 @@ NSTAGES = 8
 STAGES = ['setup', 'real', 'spread', 'fft', 'scale', 'interp', 'noise', 'vector']
 
 
+NVARIANTS = 4
+VARIANTS = ('full', 'se', 'fsu', 'su')
+
+
 class Profile(ctypes.Structure):
     _fields_ = [('ms', ctypes.c_double * NSTAGES), ('calls', ctypes.c_int64 * NSTAGES),
-                ('launches', ctypes.c_int64), ('fft_execs', ctypes.c_int64)]
+                ('launches', ctypes.c_int64), ('fft_execs', ctypes.c_int64),
+                ('variant_ms', (ctypes.c_double * NVARIANTS) * NSTAGES),
+                ('variant_calls', (ctypes.c_int64 * NVARIANTS) * NSTAGES)]
 
 
 class Request(ctypes.Structure):
@@ -197,18 +203,31 @@ def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
     """
     torch = _torch()
     lib = load()
+    if not isinstance(pos, torch.Tensor) or not pos.is_cuda:
+        raise ValueError('pos must be a CUDA tensor')
+    if pos.dtype != torch.float64 or pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
+        raise ValueError('pos must be a contiguous float64 tensor of shape (N, 3)')
     N = pos.shape[0]
+    for name, x, ncol in (('F', F, 3), ('S', S, 5)):
+        if x is None:
+            continue
+        if not isinstance(x, torch.Tensor) or x.device != pos.device:
+            raise ValueError('%s must be a tensor on %s' % (name, pos.device))
+        if x.dtype != torch.float32 or tuple(x.shape) != (N, ncol) or not x.is_contiguous():
+            raise ValueError('%s must be a contiguous float32 tensor of shape (%d, %d)' % (name, N, ncol))
     U = torch.empty((N, 3), dtype=torch.float32, device=pos.device)
     E = torch.empty((N, 5), dtype=torch.float32, device=pos.device)
-    st = lib.pse_mobility_real_noalloc(int(N), float(L), float(a), float(eta), float(xi), float(tol), _ptr(pos),
-                                       _ptr(F), _ptr(S), _ptr(U), _ptr(E), _stream(pos))
+    with torch.cuda.device(pos.device):       # the library uses the current device's scratch
+        st = lib.pse_mobility_real_noalloc(int(N), float(L), float(a), float(eta), float(xi), float(tol),
+                                           _ptr(pos), _ptr(F), _ptr(S), _ptr(U), _ptr(E), _stream(pos))
     if st != 0:
         raise PSEError(st, lib.pse_noalloc_last_error().decode())
     return U, E
 
 
 def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
-             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=1, use_graph=0):
+             krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=1, use_graph=0,
+             wave_kernel=0):
     o = Options()
     load().pse_default_options(ctypes.byref(o))
     o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
@@ -219,6 +238,7 @@ def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxit
     o.real_lanes = int(real_lanes)
     o.grid_ladder = int(grid_ladder)
     o.use_graph = int(use_graph)
+    o.wave_kernel = int(wave_kernel)
     for d in range(3):
         o.tile[d] = int(tile[d])
     return o
@@ -379,12 +399,18 @@ class PSE:
         self._check(self._lib.pse_set_profiling(self._h, 1 if enable else 0))
 
     def profile(self):
-        """{'ms': {stage: ms}, 'calls': {stage: n}, 'launches': n, 'fft_execs': n}."""
+        """{'ms': {stage: ms}, 'calls': {stage: n}, 'launches': n, 'fft_execs': n,
+        'variant_ms': {stage: {variant: ms}}, 'variant_calls': {stage: {variant: n}}} (variants:
+        'full' [F; S] -> [U; E] and the noise interpolation, 'se' S -> E, 'fsu' [F; S] -> U, 'su' S -> U)."""
         pr = Profile()
         self._check(self._lib.pse_get_profile(self._h, ctypes.byref(pr)))
         return {'ms': {STAGES[i]: pr.ms[i] for i in range(NSTAGES)},
                 'calls': {STAGES[i]: pr.calls[i] for i in range(NSTAGES)},
-                'launches': pr.launches, 'fft_execs': pr.fft_execs}
+                'launches': pr.launches, 'fft_execs': pr.fft_execs,
+                'variant_ms': {STAGES[i]: {VARIANTS[v]: pr.variant_ms[i][v] for v in range(NVARIANTS)}
+                               for i in range(NSTAGES)},
+                'variant_calls': {STAGES[i]: {VARIANTS[v]: pr.variant_calls[i][v] for v in range(NVARIANTS)}
+                                  for i in range(NSTAGES)}}
 
     def sync(self):
         self._check(self._lib.pse_sync(self._h))

@@ -852,7 +852,10 @@ void resolve_profile(pse_ctx *c) {
   for (auto &q : c->pending) {
     cudaEventSynchronize(q.b);
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) c->prof_ms[q.stage] += ms;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      c->prof_ms[q.stage] += ms;
+      c->prof_vms[q.stage][q.variant] += ms;
+    }
     c->ev_pool.push_back(q.a);
     c->ev_pool.push_back(q.b);
   }
@@ -1189,6 +1192,7 @@ pse_status pse_get_system_stats(pse_handle h, int32_t s, pse_stats *o) {
 pse_status pse_mobility_apply_parts(pse_handle h, const double *pos, const void *F, const void *S, void *U, void *E,
                                     int32_t parts, pse_stream stream) {
   if (!h || !pos) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_mobility_apply");
   if (parts < 1 || parts > 3) {
     h->err = "parts must be PSE_PART_REAL, PSE_PART_WAVE or PSE_PART_ALL";
     return PSE_ERR_INVALID_ARG;
@@ -1225,6 +1229,7 @@ pse_status pse_brownian_sample(pse_handle h, const double *pos, double dt, uint6
                                const void *w1, const void *w2, void *UB, void *EB, pse_stats *stats,
                                pse_stream stream) {
   if (!h || !pos || !(dt > 0)) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_brownian_sample");
   cudaStream_t s = (cudaStream_t)stream;
   pse_ctx *c = h;
   const Params &p = c->p;
@@ -1253,12 +1258,14 @@ pse_status pse_brownian_sample(pse_handle h, const double *pos, double dt, uint6
 pse_status pse_constrained_step(pse_handle h, double *pos, const void *FP, double dt, uint64_t seed, uint64_t step,
                                 void *S_out, pse_stats *stats, pse_stream stream) {
   if (!h) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_constrained_step");
   return step_impl(h, pos, FP, dt, nullptr, nullptr, seed, step, S_out, stats, (cudaStream_t)stream);
 }
 
 pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP, double dt, const void *w1,
                                       const void *w2, void *S_out, pse_stats *stats, pse_stream stream) {
   if (!h || !w1 || !w2) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_constrained_step");
   return step_impl(h, pos, FP, dt, w1, w2, 0, 0, S_out, stats, (cudaStream_t)stream);
 }
 
@@ -1293,6 +1300,10 @@ pse_status pse_set_profiling(pse_handle h, int32_t enable) {
   for (int i = 0; i < PSE_NSTAGES; ++i) {
     h->prof_ms[i] = 0;
     h->prof_calls[i] = 0;
+    for (int v = 0; v < PSE_NVARIANTS; ++v) {
+      h->prof_vms[i][v] = 0;
+      h->prof_vcalls[i][v] = 0;
+    }
   }
   h->nlaunch = 0;
   h->nfft = 0;
@@ -1306,6 +1317,10 @@ pse_status pse_get_profile(pse_handle h, pse_profile *out) {
   for (int i = 0; i < PSE_NSTAGES; ++i) {
     out->ms[i] = h->prof_ms[i];
     out->calls[i] = h->prof_calls[i];
+    for (int v = 0; v < PSE_NVARIANTS; ++v) {
+      out->variant_ms[i][v] = h->prof_vms[i][v];
+      out->variant_calls[i][v] = h->prof_vcalls[i][v];
+    }
   }
   out->launches = h->nlaunch;
   out->fft_execs = h->nfft;

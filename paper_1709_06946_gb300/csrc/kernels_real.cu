@@ -308,7 +308,7 @@ pse_status overlap_force(pse_ctx *c, double kspring, void *F, cudaStream_t s) {
 // vout = M_r vin for the current configuration (sorted order, [N][8]); rows of
 // inactive suspensions are left untouched.
 pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStream_t s) {
-  StageTimer timer(c, PSE_STAGE_REAL, s);
+  StageTimer timer(c, PSE_STAGE_REAL, s, mode);
   c->nlaunch += 1;
   RealArgs a;
   a.Ntot = c->p.N;

@@ -243,8 +243,8 @@ ScaleArgs scale_args(const pse_ctx *c) {
 // One batched transform per grid-size group over the leading `comps` components
 // of every suspension in the group.
 template <typename T>
-pse_status fft(pse_ctx *c, bool forward, int comps, cudaStream_t s) {
-  StageTimer timer(c, PSE_STAGE_FFT, s);
+pse_status fft(pse_ctx *c, bool forward, int comps, cudaStream_t s, int variant = 0) {
+  StageTimer timer(c, PSE_STAGE_FFT, s, variant);
   for (FftGroup &g : c->groups) {
     bool any = false;
     for (int q : g.members) any = any || c->h_active[q];
@@ -271,17 +271,17 @@ pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool 
   if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout, 0, sizeof(T) * 8 * (size_t)c->p.N, s));
   int cin = (mode == M_SE || mode == M_SU) ? 5 : 8, cout = mode == M_FULL ? 8 : (mode == M_SE ? 5 : 3);
   {
-    StageTimer timer(c, PSE_STAGE_SPREAD, s);
+    StageTimer timer(c, PSE_STAGE_SPREAD, s, mode);
     c->nlaunch += 2;  // counter reset + kernel
     spread_launch(c, a, vin, mode, s);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
-  PSE_TRY(fft<T>(c, true, cin, s));
+  PSE_TRY(fft<T>(c, true, cin, s, mode));
   ScaleArgs sa = scale_args(c);
   unsigned nb = (unsigned)ceil_div(c->nk_tot, 256);
   using C2 = typename Cx<T>::t;
   {
-    StageTimer timer(c, PSE_STAGE_SCALE, s);
+    StageTimer timer(c, PSE_STAGE_SCALE, s, mode);
     c->nlaunch += 1;
     if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
     else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
@@ -289,9 +289,9 @@ pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool 
     else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
-  PSE_TRY(fft<T>(c, false, cout, s));
+  PSE_TRY(fft<T>(c, false, cout, s, mode));
   {
-    StageTimer timer(c, PSE_STAGE_INTERP, s);
+    StageTimer timer(c, PSE_STAGE_INTERP, s, mode);
     c->nlaunch += 2;
     interp_launch(c, a, vout, mode, s);
   }

@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 PSE library (not part of the C ABI).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -234,8 +235,10 @@ struct pse_ctx {
   bool prof_on = false;
   double prof_ms[PSE_NSTAGES] = {0};
   int64_t prof_calls[PSE_NSTAGES] = {0};
+  double prof_vms[PSE_NSTAGES][PSE_NVARIANTS] = {{0}};
+  int64_t prof_vcalls[PSE_NSTAGES][PSE_NVARIANTS] = {{0}};
   int64_t nlaunch = 0, nfft = 0;
-  struct Pending { int stage; cudaEvent_t a, b; };
+  struct Pending { int stage, variant; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
 };
@@ -243,23 +246,41 @@ struct pse_ctx {
 namespace pse {
 cudaEvent_t prof_event(pse_ctx *c);
 // Records events around one stage section on stream s while profiling is on.
+// Also opens an NVTX range named after the stage for the host-side extent of the
+// section (visible to timeline tools; a no-op when none is attached).
+// Scoped NVTX range around an entry point.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+inline const char *stage_range_name(int stage) {
+  static const char *names[PSE_NSTAGES] = {"pse:setup", "pse:real", "pse:spread", "pse:fft",
+                                           "pse:scale", "pse:interp", "pse:noise", "pse:vector"};
+  return (stage >= 0 && stage < PSE_NSTAGES) ? names[stage] : "pse";
+}
 struct StageTimer {
   pse_ctx *c;
-  int stage;
+  int stage, variant;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
-  StageTimer(pse_ctx *c_, int stage_, cudaStream_t s_) : c(c_), stage(stage_), s(s_) {
+  StageTimer(pse_ctx *c_, int stage_, cudaStream_t s_, int variant_ = 0)
+      : c(c_), stage(stage_), variant(variant_), s(s_) {
+    nvtxRangePushA(stage_range_name(stage));
     if (c->prof_on) {
       a = prof_event(c);
       cudaEventRecord(a, s);
     }
   }
   ~StageTimer() {
+    nvtxRangePop();
     if (c->prof_on && a) {
       cudaEvent_t b = prof_event(c);
       cudaEventRecord(b, s);
-      c->pending.push_back({stage, a, b});
+      c->pending.push_back({stage, variant, a, b});
       c->prof_calls[stage] += 1;
+      c->prof_vcalls[stage][variant] += 1;
     }
   }
 };

@@ -264,6 +264,8 @@ __device__ __forceinline__ bool wave_skip(const WaveArgs &wa, int si, const SysD
   return !wa.active[si] || (wa.want >= 0 && a.cubic != wa.want);
 }
 void spread16_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
+void spread_col_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
+void interp_col_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 void interp16_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 
 // Persistent grid of a wave kernel for a given shared-memory size (occupancy

@@ -214,14 +214,21 @@ void interp_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
 }  // namespace
 
 // mode selects the interpolated components: M_FULL U,E (8), M_SE E (5), M_FSU U (3)
+// Suspensions with 16^3 tiles: the shared-memory tile (default) or grid columns
+// in registers (bit 1 of option wave_kernel).
+void interp_cubic(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
+  if (c->opt.wave_kernel & 2) interp_col_launch(c, a, vout, mode, s);
+  else interp16_launch(c, a, vout, mode, s);
+}
+
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
-  if (c->n_cubic == c->nsys) return interp16_launch(c, a, vout, mode, s);
+  if (c->n_cubic == c->nsys) return interp_cubic(c, a, vout, mode, s);
   WaveArgs ag = a;
   if (c->n_cubic > 0) {  // both kinds of suspensions: one launch each
     WaveArgs ac = a;
     ac.want = 1;
     ag.want = 0;
-    interp16_launch(c, ac, vout, mode, s);
+    interp_cubic(c, ac, vout, mode, s);
     c->nlaunch += 2;
   }
   if (c->prec == PSE_MIXED) {

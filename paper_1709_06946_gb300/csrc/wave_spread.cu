@@ -195,14 +195,21 @@ void spread_p(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
 
 }  // namespace
 
+// Suspensions with 16^3 tiles: grid columns in registers (default) or the
+// shared-memory tile (bit 0 of option wave_kernel).
+void spread_cubic(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s) {
+  if (c->opt.wave_kernel & 1) spread16_launch(c, a, vin, mode, s);
+  else spread_col_launch(c, a, vin, mode, s);
+}
+
 void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s) {
-  if (c->n_cubic == c->nsys) return spread16_launch(c, a, vin, mode, s);
+  if (c->n_cubic == c->nsys) return spread_cubic(c, a, vin, mode, s);
   WaveArgs ag = a;
   if (c->n_cubic > 0) {  // both kinds of suspensions: one launch each
     WaveArgs ac = a;
     ac.want = 1;
     ag.want = 0;
-    spread16_launch(c, ac, vin, mode, s);
+    spread_cubic(c, ac, vin, mode, s);
     c->nlaunch += 2;
   }
   if (c->prec == PSE_MIXED) {

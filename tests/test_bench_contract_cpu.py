@@ -20,14 +20,18 @@ def _run(*args):
 
 
 def test_reference_arm_line():
-    d = _run('--impl', 'reference', '--steps', '1', '--warmup', '0', '--cpu-N', '400')
+    d = _run('--impl', 'reference', '--steps', '1', '--warmup', '0', '--ref-N', '400')
     assert d['impl'] == 'reference' and d['unit'] == 'steps/s' and d['higher_is_better'] is True
     assert d['metric'].startswith('Brownian steps/s') and d['n_gpus'] == 1 and d['steps'] == 1
     assert d['value'] > 0 and abs(d['ms_per_step'] - 1000.0 / d['value']) < 1e-6 * d['ms_per_step']
+    # the line names the size it ran; the extrapolation to the benchmark size is labelled as such
+    assert d['config']['N'] == 400 and d['config']['phi'] == 0.3 and 'N=400' in d['config']['workload']
+    assert abs(d['ptps'] - 400 * d['value']) < 1e-9 * d['ptps']
+    assert d['extrapolated']['N'] == 1048576 and 'not measured' in d['extrapolated']['basis']
     cb = d['cpu_baseline']
-    assert cb['kind'] == 'oracle' and cb['cores'] >= 1 and cb['value'] == d['value'] and 'N=400' in cb['sample']
+    assert cb['kind'] == 'oracle' and cb['cores'] > 0 and cb['value'] == d['value'] and 'N=400' in cb['sample']
+    assert cb['host_cores'] == os.cpu_count() and cb['cpu_model']
     assert d['e2e'] == {'value': d['value'], 'unit': 'steps/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}
-    assert d['config']['N'] == 1048576 and d['config']['phi'] == 0.3
 
 
 def test_reference_arm_other_workloads_unavailable():

@@ -94,24 +94,76 @@ def test_mobility_dense_many_tiles(pkg, prec):
                                          (1e-3, 32, 1500, 0.5)])
 def test_mobility_cubic_tiles(pkg, tol, Ng, N, xi):
     """Mixed precision with 16^3 spreading tiles (the kernels specialised for
-    them) against the oracle and against the general kernels (16 x 8 x 16
-    tiles); supports of several sizes, and two tiles per side (N_g = 32: the
-    tile below and the tile above are the same)."""
+    them: column spreading with shared-tile interpolation by default, and the
+    other form of each with wave_kernel=3) against the oracle and against the general kernels (16 x 8 x
+    16 tiles); supports of several sizes, and two tiles per side (N_g = 32: the
+    tile below and the tile above are the same).  Full product and the reduced
+    products (S -> E, S -> U, [F; S] -> U) whose spreading takes 5 or 8
+    components."""
     phi = 0.3
     pos, L = pse_inputs.rsa_positions(N, phi, seed=11)
     F, S = pse_inputs.moments(N, seed=12)
     h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng)
     assert tuple(h.info['tile']) == (16, 16, 16) and h.info['Ng'] == Ng
+    hs = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, wave_kernel=3)
     hg = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, tile=(16, 8, 16))
     assert hg.info['Ng'] == h.info['Ng'] and hg.info['P'] == h.info['P']
     p = _oracle_params(h, N, L, xi, tol)
     got = _mob(pkg, h, pos, F, S, 'mixed')
+    shared = _mob(pkg, hs, pos, F, S, 'mixed')
     gen = _mob(pkg, hg, pos, F, S, 'mixed')
     Uo, Eo = opse.mobility_apply(pos, F, S, p)
     assert _rel(got, np.concatenate([Uo, Eo], 1)) < TOL['mixed']
-    assert _rel(got, gen) < 5e-6
+    assert _rel(got, gen) < 5e-6 and _rel(shared, gen) < 5e-6
+    x, tF, tS = _cuda(pos, torch.float64), _cuda(F, torch.float32), _cuda(S, torch.float32)
+    for want, FF in ((('E',), None), (('U',), None), (('U',), tF)):
+        Fo = F if FF is not None else 0 * F
+        Uo, Eo = opse.mobility_apply(pos, Fo, S, p, parts=('wave',))
+        for hh in (h, hs):
+            U, E = hh.mobility(x, FF, tS, parts='wave', want=want)
+            out, ref = (E, Eo) if want == ('E',) else (U, Uo)
+            assert _rel(out.double().cpu().numpy(), ref) < TOL['mixed'], (want, FF is None)
     h.close()
+    hs.close()
     hg.close()
+
+
+@pytest.mark.parametrize('Ng,N,xi', [(48, 3000, 0.7), (32, 1500, 0.5)])
+@pytest.mark.parametrize('with_force', [False, True])
+def test_cubic_tiles_sample_and_step(pkg, Ng, N, xi, with_force):
+    """The 16^3-tile kernel instances of the benchmark step (mixed precision,
+    P = 6 at eps = 1e-3): the 8-component noise interpolation of the Brownian
+    sample, the 5-component spread and interpolation of every GMRES product, and
+    the final S -> U product ([F; S] -> U and the 8-component EF product with a
+    force); sample, displacement and stresslets against the oracle with the same
+    external noise.  N_g = 48 has three tiles per side, N_g = 32 two (the tile
+    below and the tile above are the same)."""
+    phi, tol, dt = 0.3, 1e-3, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=11)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, lanczos_tol=0.0, lanczos_maxiter=10,
+                krylov_tol=1e-6, krylov_maxiter=100)
+    assert tuple(h.info['tile']) == (16, 16, 16) and h.info['Ng'] == Ng and h.info['P'] == 6
+    p = _oracle_params(h, N, L, xi, tol)
+    w1 = pse_inputs.lanczos_noise(N, seed=14)
+    w2 = pse_inputs.wave_noise(p.Ng, seed=15)
+    x = _cuda(pos, torch.float64)
+    U, E, _ = h.brownian(x, dt, w1=_cuda(w1, torch.float32), w2=_cuda(w2, torch.float32))
+    B, _ = opse.brownian_sample(pos, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=10)
+    got = np.concatenate([U.double().cpu().numpy(), E.double().cpu().numpy()], 1)
+    assert _rel(got, B) < TOL['mixed']
+    FP = pse_inputs.moments(N, seed=16)[0] * 5.0 if with_force else None
+    S, st = h.step(x, dt, FP=None if FP is None else _cuda(FP, torch.float32), w1=_cuda(w1, torch.float32),
+                   w2=_cuda(w2, torch.float32), want_S=True)
+    x1, So, _ = opse.constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=10,
+                                      krylov_tol=1e-12, krylov_maxiter=200)
+    disp_o = x1 - pos
+    disp_o -= L * np.rint(disp_o / L)
+    disp_g = x.cpu().numpy() - pos
+    disp_g -= L * np.rint(disp_g / L)
+    assert _rel(disp_g, disp_o) < TOL['mixed']
+    assert _rel(S.double().cpu().numpy(), So) < TOL['mixed']
+    assert 1 <= st['krylov_iters'] <= 100
+    h.close()
 
 
 @pytest.mark.parametrize('prec', ['fp64', 'mixed'])
@@ -315,4 +367,75 @@ def test_full_size_sampled(pkg, prec):
     Mu = _mob(pkg, h, pos, u[:, :3], u[:, 3:], prec)
     Mv = _mob(pkg, h, pos, F, S, prec)
     assert abs(np.sum(u * Mv) - np.sum(v * Mu)) < 1e-5 * abs(np.sum(v * Mv))
+    h.close()
+
+
+def _sampled_real(pos, L, p, v, idx):
+    """Oracle real-space rows idx of M_r v (pair sum over the particles within r_cut, plus self)."""
+    from scipy.spatial import cKDTree
+    from oracle import realspace as R
+    tree = cKDTree(np.mod(pos, L), boxsize=L)
+    ref = np.zeros((idx.size, 8))
+    selfb = R.self_block(p.xi, 1.0, 1.0)
+    x = np.mod(pos, L)
+    for n, i in enumerate(idx):
+        nb = np.array([j for j in tree.query_ball_point(x[i], p.rcut) if j != i])
+        d = x[i] - x[nb]
+        d -= L * np.rint(d / L)
+        ref[n] = selfb @ v[i] + np.einsum('pab,pb->a', R.pair_blocks(d, p.xi, 1.0, 1.0), v[nb])
+    return ref
+
+
+def test_full_size_sample_and_step(pkg):
+    """N = 1,048,576 at phi = 0.3, eps = 1e-3 with the benchmark's parameters (N_g = 256,
+    P = 6, 16^3 tiles), mixed precision, external noise:
+    * Brownian sample: the wave-space noise (the sample minus its part with w2 = 0)
+      against the oracle in full; the Lanczos real-space noise (w2 = 0) through
+      ||y||^2 = w1 . M_r w1, with M_r w1 from
+      the real-space product, itself checked against the oracle on sampled rows;
+    * constrained step: the slip equals the sample drawn with the same noise; at the
+      mid-point x_{k+1/2} = x_k + dt/2 U^B the returned stresslets satisfy the
+      constraint, M_ES S = -E^B within the GMRES residual, and the displacement is
+      dt (U^B + M_US S), with M(x_{k+1/2}) [0; S] computed by the full product, whose
+      wave part is checked against the oracle in full and whose real part on sampled rows."""
+    N, phi, xi, tol, dt = 1048576, 0.3, 0.5, 1e-3, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=1)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', lanczos_tol=1e-6, krylov_tol=1e-5, krylov_maxiter=50)
+    assert tuple(h.info['tile']) == (16, 16, 16) and h.info['Ng'] == 256 and h.info['P'] == 6
+    p = _oracle_params(h, N, L, xi, tol)
+    w1 = pse_inputs.lanczos_noise(N, seed=3)
+    w2 = pse_inputs.wave_noise(p.Ng, seed=4)
+    x = _cuda(pos, torch.float64)
+    scale = math.sqrt(2.0 / dt)
+    tw1, tw2 = _cuda(w1, torch.float32), _cuda(w2, torch.float32)
+    UB, EB, _ = h.brownian(x, dt, w1=tw1, w2=tw2)
+    UB, EB = UB.double().cpu().numpy(), EB.double().cpu().numpy()
+    Ur, Er, st = h.brownian(x, dt, w1=tw1, w2=torch.zeros_like(tw2))
+    y = np.concatenate([Ur.double().cpu().numpy(), Er.double().cpu().numpy()], 1) / scale
+    # wave-space noise: the sample minus its real-space part
+    wave = np.concatenate([UB, EB], 1) - scale * y
+    assert _rel(wave, scale * opse.wave_noise(pos, w2, p)) < TOL['mixed']
+    # real-space noise: ||M_r^{1/2} w1||^2 = w1 . M_r w1
+    Mw = _mob(pkg, h, pos, w1[:, :3], w1[:, 3:], 'mixed', 'real')
+    idx = np.random.default_rng(5).choice(N, 64, replace=False)
+    assert _rel(Mw[idx], _sampled_real(pos, L, p, w1, idx)) < TOL['mixed']
+    quad = float(np.sum(w1 * Mw))
+    assert abs(float(np.sum(y * y)) - quad) < 1e-4 * quad, st
+    # the step with the same noise
+    S, st = h.step(x, dt, w1=tw1, w2=tw2, want_S=True)
+    S = S.double().cpu().numpy()
+    xh = np.mod(pos + 0.5 * dt * UB, L)
+    US, ES = (a.double().cpu().numpy() for a in h.mobility(_cuda(xh, torch.float64), torch.zeros((N, 3), device='cuda'),
+                                                           _cuda(S, torch.float32)))
+    assert np.linalg.norm(ES + EB) < 10 * max(st['krylov_relres'], 1e-5) * np.linalg.norm(EB), st
+    disp = x.cpu().numpy() - pos
+    disp -= L * np.rint(disp / L)
+    assert _rel(disp, dt * (UB + US)) < TOL['mixed']
+    zero3 = np.zeros((N, 3))
+    wave = _mob(pkg, h, xh, zero3, S, 'mixed', 'wave')
+    wo = opse.wave_apply(xh, zero3, S, p)
+    assert _rel(wave, np.concatenate([wo['U'], wo['E']], 1)) < TOL['mixed']
+    real = _mob(pkg, h, xh, zero3, S, 'mixed', 'real')
+    v = np.concatenate([zero3, S], 1)
+    assert _rel(real[idx], _sampled_real(xh, L, p, v, idx)) < TOL['mixed']
     h.close()
