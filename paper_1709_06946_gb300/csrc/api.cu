@@ -525,6 +525,7 @@ int64_t estimate_bytes(const pse_ctx *c) {
   const int64_t L = c->lanczos_max, M = c->krylov_max;
   b += (int64_t)c->nsys * 8 * (6 * L + L * L + (M + 1) * M + 3 * M + 8);  // Krylov control state
   b += (int64_t)ts * 8 * Nt + 24 * Nt;                                    // current Krylov vector, output positions
+  b += (int64_t)ts * 8 * Nt;                                              // real-space input in cell order
   return b;
 }
 
@@ -700,6 +701,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_cell_start = (int *)A(sizeof(int) * (c->ncells + 1));
   c->d_cell_cur = (int *)A(sizeof(int) * (c->ncells + 1));
   c->d_cell_list = (int *)A(sizeof(int) * N);
+  c->d_vcell = A(8 * ts * (size_t)N);
   c->d_nbr_start = (int *)A(sizeof(int) * (N + 1));
   c->nbr_cap = layout_neighbours(c);
   if ((double)c->nbr_cap > 2.0e9) {

@@ -306,8 +306,8 @@ __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, con
           if (hit) {
             const int j = cell_list[k];
             if (j != (int)i) {
-              if (n < slots) {  // separation x_i - x_j and the neighbour's index in one record
-                rec.w = index_as_real<T>(j);
+              if (n < slots) {  // separation x_i - x_j and the neighbour's cell-list position in one record
+                rec.w = index_as_real<T>(k);
                 mgeo[n] = rec;
               }
               ++n;

@@ -2,9 +2,12 @@
 // over neighbours closer than r_cut of the 8x8 real-space block (Eqs. MUFr-MDCr)
 // applied to [F; S], plus the real-space self term (App. A, Case 3).
 //
-// G lanes per particle walk its slotted neighbour list; particles are in sorted
-// order (by suspension, then spreading tile) so that neighbours' records are
-// close in memory.  A persistent grid takes blocks of particles from a work
+// G lanes per particle walk its slotted neighbour list.  Outputs are in sorted
+// order (by suspension, then spreading tile); each neighbour record holds the
+// neighbour's position in the cell list, and the input vector is first copied
+// into cell-list order, so the lanes of a particle, walking consecutive entries
+// of the list (runs of cells along x), read neighbouring rows of that copy and
+// share cache lines.  A persistent grid takes blocks of particles from a work
 // counter; particles of suspensions marked inactive are skipped.  The seven scalar functions
 // come from a table on r: linear interpolation in FP32 (mixed form), cubic
 // Lagrange interpolation in FP64 with one-sided stencils at the r = 2a node
@@ -106,8 +109,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
                                               int *queue, int nitems,
                                               const int *__restrict__ nstart,
                                               const typename V4<T>::t *__restrict__ geo,
-                                              const T *__restrict__ vin, T *__restrict__ vout,
-                                              const T *__restrict__ gtab) {
+                                              const T *__restrict__ vin, const T *__restrict__ vcell,
+                                              T *__restrict__ vout, const T *__restrict__ gtab) {
   extern __shared__ __align__(16) unsigned char tab_raw[];
   const T *tab = gtab;
   if (SHT) {
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
     const int si = find_sys(p0, a.nsys, i);
     const bool live = gid < a.Ntot && active[si];
     const SysDev &sd = sys[si];
-    const T4 *v4 = (const T4 *)vin;
+    const T4 *v4 = (const T4 *)vin, *vc4 = (const T4 *)vcell;
     T U[3] = {0, 0, 0}, E[5] = {0, 0, 0, 0, 0};
     // particle i's row of slots; an overflowed list is flagged and redone
     const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots;
@@ -142,8 +145,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (SHT ? 1 : 4) : 1) k_real
       T f[7];
       lookup<SHT, MODE>(tab, a, r, f);
       T4 q0, q1;
-      if constexpr (sizeof(T) == 4) ldg8((const float *)vin + 8 * (size_t)j, q0, q1);  // the 8 slots of row j
-      else q0 = v4[2 * j], q1 = v4[2 * j + 1];
+      if constexpr (sizeof(T) == 4) ldg8((const float *)vcell + 8 * (size_t)j, q0, q1);  // the 8 slots of row j
+      else q0 = vc4[2 * j], q1 = vc4[2 * j + 1];
       T s[5] = {q0.w, q1.x, q1.y, q1.z, q1.w};
       T v[3];
       Smul(s, rh, v);
@@ -223,8 +226,8 @@ void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, c
     unsigned grid = persistent_grid(c, kern, 1024, tab_bytes, items, per_sm);
     int *q = next_queue(c, s);
     kern<<<grid, 1024, tab_bytes, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
-                                       (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout,
-                                       (const T *)c->d_table);
+                                       (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin,
+                                       (const T *)c->d_vcell, (T *)vout, (const T *)c->d_table);
     return;
   }
   auto kern = k_real<T, MODE, G>;
@@ -236,7 +239,8 @@ void launch_real_m(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, c
   unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
   int *q = next_queue(c, s);
   kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
-                            (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (T *)vout, (const T *)tab);
+                            (const typename V4<T>::t *)c->d_nbr_geo, (const T *)vin, (const T *)c->d_vcell,
+                            (T *)vout, (const T *)tab);
 }
 
 template <typename T, int G>
@@ -263,6 +267,17 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
     case 4: launch_real_g<T, 4>(c, a, vin, vout, mode, s); break;
     default: launch_real_g<T, 1>(c, a, vin, vout, mode, s);
   }
+}
+
+// vcell[k] = vin[list[k]]: the 8-real rows of the input vector in cell-list order.
+template <typename T>
+__global__ void k_cell_gather(int64_t N, const int *__restrict__ list, const typename V4<T>::t *__restrict__ vin,
+                              typename V4<T>::t *__restrict__ vcell) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int64_t j = list[k];
+  vcell[2 * k] = vin[2 * j];
+  vcell[2 * k + 1] = vin[2 * j + 1];
 }
 
 // Harmonic overlap repulsion F_i = sum_j k (2a - r_ij) rh_ij over neighbours
@@ -318,8 +333,16 @@ pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStr
   a.inv_dr = 1.0 / c->table_dr;
   a.self_uf = c->self_uf;
   a.self_es = c->self_es;
-  if (c->prec == PSE_MIXED) launch_real<float>(c, a, vin, vout, mode, s);
-  else launch_real<double>(c, a, vin, vout, mode, s);
+  c->nlaunch += 1;
+  const unsigned nb = (unsigned)ceil_div(c->p.N, 256);
+  if (c->prec == PSE_MIXED) {
+    k_cell_gather<float><<<nb, 256, 0, s>>>(c->p.N, c->d_cell_list, (const float4 *)vin, (float4 *)c->d_vcell);
+    launch_real<float>(c, a, vin, vout, mode, s);
+  } else {
+    k_cell_gather<double><<<nb, 256, 0, s>>>(c->p.N, c->d_cell_list, (const double4_32a *)vin,
+                                             (double4_32a *)c->d_vcell);
+    launch_real<double>(c, a, vin, vout, mode, s);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

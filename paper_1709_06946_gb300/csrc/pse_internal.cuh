@@ -181,6 +181,7 @@ struct pse_ctx {
   int *d_fine_start = nullptr, *d_fine_cur = nullptr;   // ntiles * SUB_BLOCKS + 1 (sort by tile and sub-block)
   int *d_cell_start = nullptr, *d_cell_cur = nullptr;   // ncells + 1
   int *d_cell_list = nullptr;
+  void *d_vcell = nullptr;     // the input vector of a real-space product in cell-list order (8N reals)
   void *d_rs_cell = nullptr;   // records of d_rs in cell-list order
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
   void *d_nbr_geo = nullptr;    // neighbour slots, particle i of suspension s owning nbr0 + (i - p0) slots ...:
