@@ -26,6 +26,9 @@ Steps, in the paper's order:
   x_{k+1/2} = x_k + dt/2 U^B, solve M_ES S = -E^B - M_EF F^P at x_{k+1/2} by
   unrestarted GMRES (x0 = 0), then U = U^B + M_UF F^P + M_US S and
   x_{k+1} = x_k + dt U.
+* The alternative the paper weighs against it (Sec. 3.4): Euler-Maruyama with
+  the drift kT div R_FU^{-1} from a random finite difference, three constraint
+  solves per step.
 
 Layout conventions shared with the product through the documented C ABI (not
 through code): grid arrays are [component][z][y][x]; the R2C half spectrum
@@ -36,6 +39,7 @@ k-sum on the same k set (tests/test_oracle_pse.py); Lanczos against a dense
 symmetric square root; GMRES against the dense Schur complement; the mid-point
 scheme (midpoint_step, shared by constrained_step) against the one-step mean
 kT dt div R_FU^{-1} and covariance 2 kT dt R_FU^{-1} of App. B
+(tests/test_oracle_midpoint.py); rfd_em_step, with the same App. B statistics
 (tests/test_oracle_midpoint.py).
 """
 import math
@@ -384,3 +388,57 @@ def constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=1
                                       lambda A, b: gmres(A, b, ktol, krylov_maxiter), p.L)
     st.update({'krylov_iters': kit, 'krylov_relres': rel})
     return x1, S, st
+
+
+# ---------------------------------------------------------------- RFD + Euler-Maruyama
+def constrained_apply(mob, v, solve):
+    """R_FU^{-1} v = M_UF v - M_US M_ES^{-1} M_EF v (Eq. constrained_vel) for one mobility product mob."""
+    N = v.shape[0]
+    U1, E1 = mob(v, np.zeros((N, 5)))
+    S, *info = solve(lambda s: mob(np.zeros((N, 3)), s.reshape(N, 5))[1].ravel(), -E1.ravel())
+    U2, _ = mob(np.zeros((N, 3)), S.reshape(N, 5))
+    return U1 + U2, info
+
+
+def rfd_em_step(x0, FP, dt, B, wt, delta, kT, mobility_at, solve, L):
+    """Euler-Maruyama step with a random-finite-difference drift (Sec. 3.4, the RFD alternative).
+
+    Deterministic and Brownian velocity from one constrained solve at x_k:
+    M_ES S = -E^B - M_EF F^P, U = U^B + M_UF F^P + M_US S (covariance (2kT/dt) R_FU^{-1}).
+    Drift by RFD with the standard normal vector wt (N, 3):
+    kT div R_FU^{-1} ~ (kT/delta) [R_FU^{-1}(x_k + delta/2 wt) - R_FU^{-1}(x_k - delta/2 wt)] wt,
+    two more solves.  x_{k+1} = x_k + dt (U + drift), wrapped into [0, L).
+    Returns (x_{k+1}, S, drift, info) with info the solve outputs of the three solves.
+    """
+    N = x0.shape[0]
+    UB, EB = B[:, :3], B[:, 3:]
+    mob = mobility_at(x0)
+    zF = np.zeros((N, 3)) if FP is None else FP
+    rhs = -EB
+    if FP is not None:
+        rhs = rhs - mob(zF, np.zeros((N, 5)))[1]
+    S, *i0 = solve(lambda s: mob(np.zeros((N, 3)), s.reshape(N, 5))[1].ravel(), rhs.ravel())
+    S = S.reshape(N, 5)
+    U = UB + mob(zF, S)[0]
+    Rp, ip = constrained_apply(mobility_at(np.mod(x0 + 0.5 * delta * wt, L)), wt, solve)
+    Rm, im = constrained_apply(mobility_at(np.mod(x0 - 0.5 * delta * wt, L)), wt, solve)
+    drift = (kT / delta) * (Rp - Rm)
+    x1 = np.mod(x0 + dt * (U + drift), L)
+    return x1, S, drift, (i0, ip, im)
+
+
+def rfd_step(pos, FP, dt, w1, w2, wt, delta, p, lanczos_tol=None, lanczos_maxiter=100, krylov_tol=None,
+             krylov_maxiter=50):
+    """rfd_em_step with the PSE mobility.  Returns (x_{k+1}, S_k, drift, stats)."""
+    x0 = np.mod(pos, p.L)
+    B, st = brownian_sample(x0, dt, w1, w2, p, lanczos_tol, lanczos_maxiter)
+
+    def mobility_at(x):
+        op = RealOp(x, p)
+        return lambda F, S: mobility_apply(x, F, S, p, real_op=op)
+
+    ktol = p.tol if krylov_tol is None else krylov_tol
+    x1, S, drift, info = rfd_em_step(x0, FP, dt, B, wt, delta, p.kT, mobility_at,
+                                     lambda A, b: gmres(A, b, ktol, krylov_maxiter), p.L)
+    st.update({'krylov_iters': sum(i[0] for i in info), 'krylov_relres': max(i[1] for i in info)})
+    return x1, S, drift, st

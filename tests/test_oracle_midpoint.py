@@ -1,4 +1,6 @@
-"""Pins for the oracle's mid-point scheme (oracle.pse.midpoint_step, Sec. 3.4).
+"""Pins for the oracle's integrators: the mid-point scheme (oracle.pse.midpoint_step,
+Sec. 3.4) and the Euler-Maruyama scheme with a random-finite-difference drift
+(oracle.pse.rfd_em_step, the alternative discussed in Sec. 3.4).
 
 App. B states the one-step statistics of the scheme for a smooth SPD grand
 mobility M(x): with [U^B; E^B] of covariance (2kT/dt) M drawn at x_k,
@@ -20,6 +22,13 @@ expectations are formed two ways:
 
 Planted mistakes (a solve at x_k instead of x_{k+1/2}; a slip of dt instead of
 dt/2) are shown to miss the mean by order one.
+
+The RFD scheme evaluates the Brownian and deterministic velocity at x_k (exact
+covariance 2 kT dt R_FU^{-1} at fixed x_k) and adds the drift
+(kT/delta) [R_FU^{-1}(x + delta/2 W) - R_FU^{-1}(x - delta/2 W)] W, whose mean over
+the standard normal W is kT div R_FU^{-1} + O(delta^2); the same cubature over the
+joint noise (8N + 3N components) checks both moments, and a drift taken at x_k, or
+with the two points swapped, misses the mean.
 """
 import math
 
@@ -179,3 +188,50 @@ def test_midpoint_statistics_monte_carlo():
     cov = prod.mean(0)
     cse = prod.std(0, ddof=1) / math.sqrt(K)
     assert np.all(np.abs(cov - 2 * KT * dt * R0) < 5 * cse + 1e-12)
+
+
+def rfd_displacements(x0, dt, noises, delta=1e-4, FP=None, mob=mobility_at):
+    """x_{k+1} - x_k of the RFD scheme for joint noise vectors [w (8N); W (3N)]."""
+    N = x0.shape[0]
+    Mh = sqrt_spd(grand_mobility(x0))
+    out = []
+    for z in noises:
+        w, wt = z[:8 * N], z[8 * N:].reshape(N, 3)
+        B = math.sqrt(2 * KT / dt) * (Mh @ w).reshape(N, 8)
+        x1, _, _, _ = opse.rfd_em_step(x0, FP, dt, B, wt, delta, KT, mob, dense_solve, BOX)
+        out.append((x1 - x0).ravel())
+    return np.array(out)
+
+
+@pytest.mark.parametrize('name', sorted(CONFIGS))
+def test_rfd_mean_and_covariance_by_cubature(name):
+    x0 = CONFIGS[name]
+    N = x0.shape[0]
+    R0 = constrained_mobility(x0)
+    drift = KT * divergence(x0)
+    pts = cubature_points(11 * N)
+    dt = 0.01
+    D = rfd_displacements(x0, dt, pts)
+    mean, cov = D.mean(0), D.T @ D / len(D)
+    assert np.linalg.norm(mean / dt - drift) < 1e-4 * np.linalg.norm(drift)
+    # the RFD estimate's own spread adds dt^2 <drift drift^T>, O(dt) relative to 2 kT dt R_FU^{-1}
+    assert np.linalg.norm(cov - 2 * KT * dt * R0) < 1e-3 * np.linalg.norm(2 * KT * dt * R0)
+    FP = np.array([[0.3, -0.2, 0.1]] * N) * np.arange(1, N + 1)[:, None]
+    mean = rfd_displacements(x0, dt, pts, FP=FP).mean(0)
+    expect = R0 @ FP.ravel() + drift
+    assert np.linalg.norm(mean / dt - expect) < 1e-4 * np.linalg.norm(expect)
+
+
+def test_rfd_planted_mistakes_miss_the_drift():
+    x0 = CONFIGS['pair']
+    drift = KT * divergence(x0)
+    pts = cubature_points(22)
+
+    def at_start(x):                  # both finite-difference points at x_k
+        return mobility_at(x0)
+
+    def swapped(x):                   # x_k + delta/2 W and x_k - delta/2 W exchanged
+        return mobility_at(2.0 * x0 - x)
+    for mob in (at_start, swapped):
+        mean = rfd_displacements(x0, 0.01, pts, mob=mob).mean(0)
+        assert np.linalg.norm(mean / 0.01 - drift) > 0.5 * np.linalg.norm(drift)
