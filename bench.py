@@ -59,11 +59,15 @@ def parse():
     ap.add_argument('--cpu-N', type=int, default=3000, help='oracle size of the cpu_baseline sample')
     ap.add_argument('--ref-N', type=int, default=1000, help='oracle size of each --impl reference step')
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='step', choices=['step', 'batch256', 'serve'])
+    ap.add_argument('--workload', default='step', choices=['step', 'batch256', 'serve', 'equilibrium'])
+    ap.add_argument('--eq-pair-steps', type=int, default=100000, help='equilibrium: spring-pair steps (mid-point)')
+    ap.add_argument('--eq-sq-N', type=int, default=64000, help='equilibrium: ideal spheres for S(q)')
+    ap.add_argument('--eq-sq-steps', type=int, default=600, help='equilibrium: steps per S(q) run')
     ap.add_argument('--serve-seconds', type=float, default=12.0, help='per arrival rate (--workload serve)')
     ap.add_argument('--serve-seconds-default', type=float, default=4.0,
                     help='per arrival rate of the serving sweep in the default line')
     ap.add_argument('--eps2', type=float, default=1e-4, help='second PSE tolerance of the default line (0: omit)')
+    ap.add_argument('--rfd-steps', type=int, default=3, help='timed RFD + Euler-Maruyama steps (0: omit)')
     ap.add_argument('--batch-steps', type=int, default=3,
                     help='timed steps of the 256-suspension block of the default line (0: omit)')
     ap.add_argument('--serve-slots', type=int, default=4)
@@ -554,6 +558,8 @@ def run_ours(args, world, rank, local, pg):
         if not args.no_accuracy:
             result['accuracy'] = accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64)
         h64.close()
+    if rank == 0 and world == 1 and args.rfd_steps > 0:
+        result['rfd'] = rfd_measure(pkg, torch, dev, args, pos_np, L, value)
     if rank == 0 and world == 1 and args.eps2 > 0:
         result['eps_%g' % args.eps2] = eps_measure(pkg, torch, dev, args, pos_np, L, args.eps2)
     if rank == 0 and world == 1 and args.batch_steps > 0:
@@ -769,6 +775,32 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def rfd_measure(pkg, torch, dev, args, pos_np, L, midpoint_rate):
+    """The Euler-Maruyama step with a random-finite-difference drift (three stresslet solves per
+    step, the alternative the paper weighs against the mid-point scheme) on the same workload,
+    launched from the host; its rate beside the mid-point step's."""
+    stream = torch.cuda.current_stream(dev)
+    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', wave_kernel=args.wave_kernel)
+    x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+    h.rfd_step(x, args.dt, seed=77, step=0)
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    its = []
+    ev0.record(stream)
+    for k in range(args.rfd_steps):
+        _, st = h.rfd_step(x, args.dt, seed=77, step=1 + k)
+        its.append(st['krylov_iters'])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = ev0.elapsed_time(ev1) / 1000.0 / args.rfd_steps
+    h.close()
+    return {'steps_per_s': 1.0 / t, 'ms_per_step': 1000.0 * t, 'krylov_iters_total_mean': float(np.mean(its)),
+            'midpoint_speedup': midpoint_rate * t,
+            'note': 'Euler-Maruyama with random-finite-difference drift (3 stresslet solves per step, host-launched) '
+                    'against the graph-captured mid-point step (1 solve)'}
+
+
 def eps_measure(pkg, torch, dev, args, pos_np, L, tol, steps=5, warmup=2, fp64_steps=1):
     """The constrained step at another PSE tolerance on the same positions: mixed (graph) rate,
     all-FP64 rate, and the mixed form's error per output against the FP64 form on identical
@@ -814,13 +846,70 @@ def eps_measure(pkg, torch, dev, args, pos_np, L, tol, steps=5, warmup=2, fp64_s
     return out
 
 
+# ----------------------------------------------------------------------------- equilibrium runs
+def run_equilibrium(args):
+    """The validation runs of Sec. 4: the spring-pair distance distribution against its Boltzmann
+    density (mid-point and RFD schemes), and S(q) of non-interacting spheres at several volume
+    fractions; one JSON line with the statistics and the step rates of the runs."""
+    import torch
+    import pse_inputs
+    import paper_1709_06946_gb300 as pkg
+    from paper_1709_06946_gb300.equilibrium import (boltzmann_pair_reference, pair_distance_run,
+                                                    ideal_structure_factor_run)
+    pkg.load()
+    dev = torch.device('cuda', 0)
+    K, R0, L, dt = 5.0, 3.0, 10.0, 0.01
+    rgrid, cdf, mean_ref = boltzmann_pair_reference(K, R0)
+    dens = np.gradient(cdf, rgrid)
+    pair = {}
+    for scheme, steps in (('midpoint', args.eq_pair_steps), ('rfd', args.eq_pair_steps // 4)):
+        h = pkg.PSE(2, L, xi=1.0, tol=1e-3, precision='mixed', use_graph=1)
+        x = torch.tensor([[3.0, 5.0, 5.0], [3.0 + R0, 5.0, 5.0]], device=dev, dtype=torch.float64)
+        t0 = time.perf_counter()
+        r = pair_distance_run(h, x, L, K, R0, dt, steps, every=10, seed=21, scheme=scheme, delta=0.01, burn=500)
+        wall = time.perf_counter() - t0
+        h.close()
+        rs = np.sort(r)
+        ks = float(np.max(np.abs(np.arange(1, rs.size + 1) / rs.size - np.interp(rs, rgrid, cdf))))
+        bm = np.array([b.mean() for b in np.array_split(r, 20)])
+        hist, edges = np.histogram(r, bins=24, range=(R0 - 1.2, R0 + 1.2), density=True)
+        mid = 0.5 * (edges[1:] + edges[:-1])
+        pair[scheme] = {'steps': steps, 'samples': int(r.size), 'steps_per_s': (steps + 500) / wall,
+                        'mean_r': float(r.mean()), 'mean_r_boltzmann': mean_ref,
+                        'mean_r_se': float(bm.std(ddof=1) / np.sqrt(bm.size)), 'ks_distance': ks,
+                        'histogram': {'r': mid.round(3).tolist(), 'sampled': hist.round(4).tolist(),
+                                      'boltzmann': np.interp(mid, rgrid, dens).round(4).tolist()}}
+    sq = {}
+    for phi in (0.1, 0.3, 0.5):
+        N = args.eq_sq_N
+        Lb = pse_inputs.box_length(N, phi)
+        h = pkg.PSE(N, Lb, xi=0.6, tol=1e-3, precision='mixed', use_graph=1)
+        x = torch.tensor(pse_inputs.random_positions(N, Lb, seed=31), device=dev, dtype=torch.float64)
+        t0 = time.perf_counter()
+        qs, S, cnt = ideal_structure_factor_run(h, x, Lb, 0.05, args.eq_sq_steps, 20, 12, seed=4)
+        wall = time.perf_counter() - t0
+        h.close()
+        grand = float(np.average(S, axis=1, weights=cnt).mean())
+        sq['phi=%g' % phi] = {'N': N, 'L': Lb, 'steps': args.eq_sq_steps, 'snapshots': int(S.shape[0]),
+                              'steps_per_s': args.eq_sq_steps / wall, 'S_mean': grand,
+                              'S_mean_se_one_snapshot': float(1.0 / np.sqrt(cnt.sum())),
+                              'q': qs.round(4).tolist(), 'S_shell': S.mean(0).round(4).tolist()}
+    line = {'metric': 'equilibrium validation (Sec. 4): spring-pair distance distribution, S(q) of ideal spheres',
+            'value': pair['midpoint']['ks_distance'], 'unit': 'Kolmogorov distance to the Boltzmann CDF',
+            'higher_is_better': False, 'n_gpus': 1, 'dtype': 'f32', 'data': 'synthetic',
+            'config': {'workload': 'two spheres, U = k|r - r0| (k = 5 kT, r0 = 3a), L = 10a, dt = 0.01; '
+                                   'N = %d ideal spheres at phi 0.1/0.3/0.5, dt = 0.05' % args.eq_sq_N},
+            'pair': pair, 'structure_factor': sq}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.workload != 'step':
         if args.impl == 'reference':
             print(json.dumps({'impl': 'reference', 'unavailable': 'the oracle arm covers the N=1M step workload only'}))
             return
-        run_batch(args) if args.workload == 'batch256' else run_serve(args)
+        {'batch256': run_batch, 'serve': run_serve, 'equilibrium': run_equilibrium}[args.workload](args)
         return
     world, rank, local, pg = dist_setup(args)
     if args.impl == 'reference':

@@ -101,7 +101,11 @@ typedef struct pse_options {
                               with the grid columns of a tile held in registers, interpolation with the
                               tile in shared memory (the faster of each, measured).  Bit 0 set:
                               spreading with the tile in shared memory; bit 1 set: interpolation with
-                              the grid columns in registers */
+                              the grid columns in registers; bit 2 set: in the register-column
+                              spreading every warp scans the candidate particles itself (otherwise
+                              the CTA scans them once and hands each warp its hit list); bit 3 set:
+                              the 5-component spreading keeps a whole 16-point column per thread
+                              (default: 8 z points, two z halves) */
   int32_t reserved[4];
 } pse_options;
 
@@ -259,6 +263,31 @@ pse_status pse_constrained_step(pse_handle h, double *pos, const void *FP, doubl
 pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP, double dt,
                                       const void *w1, const void *w2, void *S_out, pse_stats *stats,
                                       pse_stream stream);
+
+/* One Euler-Maruyama step with a random-finite-difference drift: the
+ * alternative to the mid-point scheme that Sec. 3.4 discusses (three stresslet
+ * solves per step instead of one).  With [U^B; E^B] drawn at x_k as in
+ * pse_brownian_sample, the velocity U = U^B + M_UF F^P + M_US S with
+ * M_ES S = -E^B - M_EF F^P (one solve at x_k, covariance (2kT/dt) R_FU^{-1} with
+ * R_FU^{-1} = M_UF - M_US M_ES^{-1} M_EF, Eq. constrained_vel), and the drift
+ * kT div R_FU^{-1} ~ (kT/delta) [R_FU^{-1}(x_k + delta/2 W) - R_FU^{-1}(x_k - delta/2 W)] W
+ * with W a standard normal N x 3 vector (two more solves);
+ * x_{k+1} = x_k + dt (U + drift), wrapped.  delta is a length (0: 1e-3 a).
+ * pos is updated in place; FP (N x 3, may be NULL) is the conservative force at
+ * x_k; S_out (N x 5, may be NULL) receives S of the solve at x_k.  Noise from
+ * (seed, step): w1 and dW2 as pse_constrained_step, W from Philox stream 3 at
+ * index 3 u + d.  stats->krylov_iters is the total over the three solves.
+ * Single-suspension handles only (INVALID_ARG otherwise); launched from the
+ * host; waits for its result.  Returns NOT_CONVERGED (after completing the
+ * step) if a Krylov cap was hit. */
+pse_status pse_rfd_step(pse_handle h, double *pos, const void *FP, double dt, double delta, uint64_t seed,
+                        uint64_t step, void *S_out, pse_stats *stats, pse_stream stream);
+
+/* As pse_rfd_step with external noise: w1, w2 as pse_brownian_sample and wt
+ * (N x 3, user order, dtype of the handle's vectors) the direction W; all three
+ * required. */
+pse_status pse_rfd_step_noise(pse_handle h, double *pos, const void *FP, double dt, double delta, const void *w1,
+                              const void *w2, const void *wt, void *S_out, pse_stats *stats, pse_stream stream);
 
 /* Real-space part M_r [F; S] of the mobility product without any device
  * allocation.  No counterpart in the paper: this is a convenience for callers

@@ -10,7 +10,8 @@ Noise streams of the PSE method that are drawn in-kernel use this generator:
     u1 = (w0 + 0.5) 2^-32,  u2 = (w1 + 0.5) 2^-32,
     z0 = sqrt(-2 ln u1) cos(2 pi u2),  z1 = sqrt(-2 ln u1) sin(2 pi u2).
 Stream 1 is the Lanczos start vector (one z0 per entry), stream 2 the
-wave-space noise (z0 -> real part, z1 -> imaginary part per entry).
+wave-space noise (z0 -> real part, z1 -> imaginary part per entry), stream 3
+the direction of the random finite difference (one z0 per entry).
 
 Parity: pinned by the Random123 known-answer vectors (tests/test_oracle_philox.py).
 """
@@ -71,3 +72,9 @@ def wave_noise(seed, step, Ng, index0=0):
     n = 3 * Ng * Ng * (Ng // 2 + 1)
     z0, z1 = normals(seed, step, 2, index0 + np.arange(n, dtype=np.uint64))
     return np.stack([z0, z1], axis=-1).reshape(3, Ng, Ng, Ng // 2 + 1, 2)
+
+
+def rfd_noise(seed, step, N, index0=0):
+    """W: (N, 3) standard normals of stream 3 (indices index0 + 3 n + d), the RFD direction."""
+    z0, _ = normals(seed, step, 3, index0 + np.arange(3 * N, dtype=np.uint64))
+    return z0.reshape(N, 3)

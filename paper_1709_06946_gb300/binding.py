@@ -124,6 +124,8 @@ SIGNATURES = [
     ('pse_brownian_sample', ctypes.c_int, [_P, _P, _D, _U64, _U64, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step', ctypes.c_int, [_P, _P, _P, _D, _U64, _U64, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step_noise', ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_rfd_step', ctypes.c_int, [_P, _P, _P, _D, _D, _U64, _U64, _P, ctypes.POINTER(Stats), _P]),
+    ('pse_rfd_step_noise', ctypes.c_int, [_P, _P, _P, _D, _D, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     ('pse_mobility_real_noalloc', ctypes.c_int, [ctypes.c_int64, _D, _D, _D, _D, _D, _P, _P, _P, _P, _P, _P]),
     ('pse_noalloc_last_error', ctypes.c_char_p, []),
     ('pse_server_create', ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64]),
@@ -372,6 +374,24 @@ class PSE:
         else:
             st = self._lib.pse_constrained_step(self._h, _ptr(pos), _ptr(FP), float(dt), int(seed), int(step),
                                                 _ptr(S), ctypes.byref(stats), _stream(pos))
+        if not (st == 0 or (allow_cap and st == 4)):
+            self._check(st)
+        d = stats.as_dict()
+        d['status'] = st
+        return S, d
+
+    def rfd_step(self, pos, dt, FP=None, delta=0.0, seed=0, step=0, w1=None, w2=None, wt=None, want_S=False,
+                 allow_cap=True):
+        """One Euler-Maruyama step with a random-finite-difference drift (three stresslet solves);
+        pos is updated in place.  External noise needs w1, w2 and wt together."""
+        S = self._like(pos, (self.N, 5), self.dtype) if want_S else None
+        stats = Stats()
+        if w1 is not None or w2 is not None or wt is not None:
+            st = self._lib.pse_rfd_step_noise(self._h, _ptr(pos), _ptr(FP), float(dt), float(delta), _ptr(w1),
+                                              _ptr(w2), _ptr(wt), _ptr(S), ctypes.byref(stats), _stream(pos))
+        else:
+            st = self._lib.pse_rfd_step(self._h, _ptr(pos), _ptr(FP), float(dt), float(delta), int(seed), int(step),
+                                        _ptr(S), ctypes.byref(stats), _stream(pos))
         if not (st == 0 or (allow_cap and st == 4)):
             self._check(st)
         d = stats.as_dict()

@@ -496,6 +496,117 @@ pse_status step_impl(pse_ctx *c, double *pos, const void *FP, double dt, const v
   return ks;
 }
 
+// Euler-Maruyama step with a random-finite-difference drift (the alternative to
+// the mid-point scheme discussed in Sec. 3.4): the Brownian and deterministic
+// velocity from one constrained solve at x_k, and the drift kT div R_FU^{-1} from
+// (kT/delta) [R_FU^{-1}(x_k + delta/2 W) - R_FU^{-1}(x_k - delta/2 W)] W, two more
+// solves.  Host-launched (not captured).  S_out receives the stresslets of the
+// solve at x_k.
+pse_status rfd_impl(pse_ctx *c, double *pos, const void *FP, double dt, double delta, const void *w1,
+                    const void *w2, const void *wt, uint64_t seed, uint64_t stepno, void *S_out, pse_stats *st,
+                    cudaStream_t s) {
+  const Params &p = c->p;
+  const int64_t N = p.N;
+  const size_t vb = c->ts * 8 * N;
+  if (!(dt > 0) || !pos || !(delta >= 0) || !std::isfinite(delta)) {
+    c->err = "dt must be > 0, delta >= 0 and pos non-NULL";
+    return PSE_ERR_INVALID_ARG;
+  }
+  if (delta == 0) delta = 1e-3 * p.a;
+  if (!c->d_rfd) {
+    c->d_rfd = dalloc(c, 4 * vb);
+    if (!c->d_rfd) {
+      c->err = "cannot allocate the RFD work space";
+      return PSE_ERR_OOM;
+    }
+  }
+  char *rb = (char *)c->d_rfd;
+  void *W8 = rb, *U0 = rb + vb, *Rp = rb + 2 * vb, *Rm = rb + 3 * vb;
+  reset_stats(c);
+  PSE_TRY(set_all_active(c, s));
+  void *dpos, *dFP, *dw1, *dw2, *dwt;
+  PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
+  PSE_TRY(stage(c, 1, FP, c->ts * 3 * N, true, s, &dFP));
+  PSE_TRY(stage(c, 2, w1, vb, true, s, &dw1));
+  PSE_TRY(stage(c, 3, w2, w2_bytes(c), true, s, &dw2));
+  PSE_TRY(stage(c, 5, wt, c->ts * 3 * N, true, s, &dwt));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_pos0, dpos, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  PSE_TRY(check_inputs(c, dFP, 3 * N, c->prec == PSE_FP64, s));
+  int kit = 0;
+  double krel = 0.0;
+  bool capped = false;
+  auto solve_stats = [&]() -> pse_status {
+    pse_status ks = read_krylov_stats(c, false, true, s);
+    capped = capped || ks == PSE_ERR_NOT_CONVERGED;
+    for (const pse_stats &q : c->sys_stats) {
+      kit += q.krylov_iters;
+      krel = std::max(krel, q.krylov_relres);
+    }
+    return (ks == PSE_OK || ks == PSE_ERR_NOT_CONVERGED) ? PSE_OK : ks;
+  };
+  // 1. at x_k: slip, constrained solve, U = U^B + M_UF F^P + M_US S
+  PSE_TRY(setup_config(c, c->d_pos0, s));
+  PSE_TRY(sample_sorted(c, dw1, dw2, seed, stepno, c->d_v[2], s));
+  PSE_TRY(scatter_user8(c, c->d_v[2], c->d_B, std::sqrt(2.0 * p.kT / dt), s));
+  PSE_TRY(read_krylov_stats(c, true, false, s) == PSE_ERR_CUDA ? PSE_ERR_CUDA : PSE_OK);
+  const pse_stats lz0 = c->sys_stats.empty() ? pse_stats{} : c->sys_stats[0];
+  PSE_TRY(gather_user8(c, c->d_B, c->d_v[2], s));
+  PSE_TRY(vscale(c, c->d_v[2], c->d_v[2], -1.0, -1, s));
+  if (dFP) {
+    PSE_TRY(gather_in(c, dFP, nullptr, c->d_v[3], s));
+    PSE_TRY(mobility(c, c->d_v[3], c->d_v[4], M_FULL, PSE_PART_ALL, s));
+    PSE_TRY(combine_sub(c, c->d_v[2], c->d_v[4], 1, CO_ONE, s));
+  }
+  PSE_TRY(vzero_slots(c, c->d_v[2], 0, 3, s));
+  PSE_TRY(gmres(c, c->d_v[2], c->d_v[5], c->d_v[1], s));
+  PSE_TRY(vzero_slots(c, c->d_v[5], 0, 3, s));
+  PSE_TRY(solve_stats());
+  if (S_out) {
+    void *dS;
+    PSE_TRY(stage(c, 4, S_out, c->ts * 5 * N, false, s, &dS));
+    PSE_TRY(scatter_out(c, c->d_v[5], nullptr, dS, 1.0, s));
+    PSE_TRY(unstage(c, S_out, dS, c->ts * 5 * N, s));
+  }
+  if (dFP) {
+    PSE_TRY(gather_in(c, dFP, nullptr, c->d_v[3], s));
+    PSE_TRY(combine_sub(c, c->d_v[3], c->d_v[5], 1, CO_MONE, s));
+  } else {
+    PSE_CUDA_TRY(c, cudaMemcpyAsync(c->d_v[3], c->d_v[5], vb, cudaMemcpyDeviceToDevice, s));
+  }
+  PSE_TRY(mobility(c, c->d_v[3], c->d_v[4], dFP ? M_FSU : M_SU, PSE_PART_ALL, s));
+  PSE_TRY(scatter_user8(c, c->d_v[4], U0, 1.0, s));
+  // 2. R_FU^{-1}(x_k +- delta/2 W) W, one solve each
+  PSE_TRY(rfd_noise(c, dwt, seed, stepno, W8, s));
+  for (int side = 0; side < 2; ++side) {
+    PSE_TRY(midpoint(c, c->d_pos0, W8, side ? -0.5 * delta : 0.5 * delta, c->d_posh, s));
+    PSE_TRY(setup_config(c, c->d_posh, s));
+    PSE_TRY(gather_user8(c, W8, c->d_v[0], s));
+    PSE_TRY(mobility(c, c->d_v[0], c->d_v[3], M_FULL, PSE_PART_ALL, s));  // (M_UF W, M_EF W)
+    PSE_TRY(vscale(c, c->d_v[2], c->d_v[3], -1.0, -1, s));
+    PSE_TRY(vzero_slots(c, c->d_v[2], 0, 3, s));
+    PSE_TRY(gmres(c, c->d_v[2], c->d_v[5], c->d_v[1], s));
+    PSE_TRY(vzero_slots(c, c->d_v[5], 0, 3, s));
+    PSE_TRY(solve_stats());
+    PSE_TRY(mobility(c, c->d_v[5], c->d_v[4], M_SU, PSE_PART_ALL, s));     // M_US S
+    PSE_TRY(combine_sub(c, c->d_v[4], c->d_v[3], 1, CO_MONE, s));           // + M_UF W
+    PSE_TRY(scatter_user8(c, c->d_v[4], side ? Rm : Rp, 1.0, s));
+  }
+  // 3. x_{k+1} = x_k + dt (U^B + U + drift)
+  PSE_TRY(rfd_final(c, c->d_pos0, c->d_B, U0, Rp, Rm, dt, p.kT / delta, c->d_posout, s));
+  PSE_CUDA_TRY(c, cudaMemcpyAsync(dpos, c->d_posout, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s));
+  PSE_TRY(unstage(c, pos, dpos, sizeof(double) * 3 * N, s));
+  PSE_CUDA_TRY(c, cudaStreamSynchronize(s));
+  c->h2d_pending = false;
+  for (pse_stats &q : c->sys_stats) {
+    q.lanczos_iters = lz0.lanczos_iters;
+    q.lanczos_change = lz0.lanczos_change;
+    q.krylov_iters = kit;
+    q.krylov_relres = krel;
+  }
+  gather_stats(c, st);
+  return capped ? PSE_ERR_NOT_CONVERGED : PSE_OK;
+}
+
 // Device memory of a handle before it is created (the admission estimate of a
 // serving loop); mirrors the allocations of create_group.
 int64_t estimate_bytes(const pse_ctx *c) {
@@ -1269,6 +1380,28 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
   if (!h || !w1 || !w2) return PSE_ERR_INVALID_ARG;
   NvtxRange range("pse_constrained_step");
   return step_impl(h, pos, FP, dt, w1, w2, 0, 0, S_out, stats, (cudaStream_t)stream);
+}
+
+pse_status pse_rfd_step(pse_handle h, double *pos, const void *FP, double dt, double delta, uint64_t seed,
+                        uint64_t step, void *S_out, pse_stats *stats, pse_stream stream) {
+  if (!h) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_rfd_step");
+  if (h->nsys != 1) {
+    h->err = "the RFD step takes a single suspension";
+    return PSE_ERR_INVALID_ARG;
+  }
+  return rfd_impl(h, pos, FP, dt, delta, nullptr, nullptr, nullptr, seed, step, S_out, stats, (cudaStream_t)stream);
+}
+
+pse_status pse_rfd_step_noise(pse_handle h, double *pos, const void *FP, double dt, double delta, const void *w1,
+                              const void *w2, const void *wt, void *S_out, pse_stats *stats, pse_stream stream) {
+  if (!h || !w1 || !w2 || !wt) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_rfd_step");
+  if (h->nsys != 1) {
+    h->err = "the RFD step takes a single suspension";
+    return PSE_ERR_INVALID_ARG;
+  }
+  return rfd_impl(h, pos, FP, dt, delta, w1, w2, wt, 0, 0, S_out, stats, (cudaStream_t)stream);
 }
 
 pse_status pse_overlap_force(pse_handle h, const double *pos, double kspring, void *F, pse_stream stream) {

@@ -375,6 +375,41 @@ __global__ void k_final(VecArgs va, const int64_t *__restrict__ p0, int64_t N, c
   xo[e] = wrapL(x0[e] + dt * U, L);
 }
 
+// The direction W of the random finite difference as user-order 8-slot rows
+// (slots 0..2, the rest zero): from wt (N x 3) or in-kernel (Philox stream 3,
+// index 3 u + d, first normal of the pair).
+template <typename T>
+__global__ void k_rfd_noise(int64_t N, const T *wt, uint64_t seed, uint64_t counter, T *W8) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 8 * N) return;
+  const int64_t u = e >> 3;
+  const int d = (int)(e & 7);
+  T v = (T)0;
+  if (d < 3) {
+    if (wt) {
+      v = wt[3 * u + d];
+    } else {
+      T z1;
+      normal_pair<T>(seed, counter, 3u, 3ull * (uint64_t)u + (uint64_t)d, v, z1);
+    }
+  }
+  W8[e] = v;
+}
+
+// x_{k+1} = x_k + dt (U^B + U_0 + fac (R_+ - R_-)), wrapped (all rows user order, slots 0..2).
+template <typename T>
+__global__ void k_rfd_final(VecArgs va, const int64_t *__restrict__ p0, int64_t N, const double *x0, const T *B,
+                            const T *U0, const T *Rp, const T *Rm, double dt, double fac, double *xo) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 3 * N) return;
+  const int64_t u = e / 3;
+  const int d = (int)(e % 3);
+  const double L = va.sys[find_sys(p0, va.nsys, u)].L;
+  const size_t r = 8 * (size_t)u + d;
+  const double U = (double)B[r] + (double)U0[r] + fac * ((double)Rp[r] - (double)Rm[r]);
+  xo[e] = wrapL(x0[e] + dt * U, L);
+}
+
 template <typename T>
 __global__ void k_finite(const T *p, int64_t n, int *bad) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -591,6 +626,28 @@ pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const 
   VecArgs va = vec_args(c);
   DISPATCH(c, (k_final<float><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, c->d_inv, x0, (const float *)B_user, (const float *)U_sorted, dt, xout)),
            (k_final<double><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, c->d_inv, x0, (const double *)B_user, (const double *)U_sorted, dt, xout)));
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status rfd_noise(pse_ctx *c, const void *wt, uint64_t seed, uint64_t counter, void *W8, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_rfd_noise<float><<<grid_for(8 * N), 256, 0, s>>>(N, (const float *)wt, seed, counter, (float *)W8)),
+           (k_rfd_noise<double><<<grid_for(8 * N), 256, 0, s>>>(N, (const double *)wt, seed, counter, (double *)W8)));
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status rfd_final(pse_ctx *c, const double *x0, const void *B, const void *U0, const void *Rp, const void *Rm,
+                     double dt, double fac, double *xout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
+  int64_t N = c->p.N;
+  VecArgs va = vec_args(c);
+  DISPATCH(c, (k_rfd_final<float><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, x0, (const float *)B, (const float *)U0, (const float *)Rp, (const float *)Rm, dt, fac, xout)),
+           (k_rfd_final<double><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, x0, (const double *)B, (const double *)U0, (const double *)Rp, (const double *)Rm, dt, fac, xout)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

@@ -95,32 +95,23 @@ __device__ __forceinline__ void project_out(typename Cx<T>::t *g, size_t idx, si
   }
 }
 
+// P^+ B P with the Gaussian deconvolution at one half-spectrum point (Sec. 2.3.2):
+// f = s0 F - 3i s1 S.k,  u = c (I - kk) f,  c = sigma^2/(eta V) (1 + k^2/4xi^2) e^{-(1 - eta_g) k^2/4xi^2} / k^2,
+// then U = s0 u and E = Y : sym(3i s1 u k^T).  vin holds F (slots 0..2, when the mode
+// has a force) and S (the next five slots); vout receives U (slots 0..2) and / or E
+// (slots 0..4 for S -> E, 3..7 for the full product).  Modes k = 0 and on a Nyquist
+// plane give zeros.
 template <typename T, int MODE>
-__global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
-  using C2 = typename Cx<T>::t;
-  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gidx >= sa.nk_tot) return;
-  const int sidx = find_sys(sa.k0, sa.nsys, gidx);
-  if (!sa.active[sidx]) return;
-  const SysDev &s = sa.sys[sidx];
-  const size_t idx = (size_t)(gidx - s.k0);
-  C2 *g = g_all + s.cgrid0;
+__device__ __forceinline__ void scale_point(const ScaleArgs &sa, const SysDev &s, size_t idx,
+                                            const typename Cx<T>::t (&vin)[8], typename Cx<T>::t (&vout)[8]) {
   constexpr bool HF = MODE == M_FULL || MODE == M_FSU, WU = MODE != M_SE, WE = MODE == M_FULL || MODE == M_SE;
-  constexpr int sIn = HF ? 3 : 0, uOut = 0, eOut = (MODE == M_SE) ? 0 : 3;
+  constexpr int sIn = HF ? 3 : 0, eOut = (MODE == M_SE) ? 0 : 3;
   int ix, iy, iz;
-  bool live = kvector(s, idx, ix, iy, iz);
-  const size_t cs = s.cstride;
-  if (!live) {
-    C2 z;
-    z.x = 0;
-    z.y = 0;
-    if (WU)
-      for (int m = 0; m < 3; ++m) g[(uOut + m) * cs + idx] = z;
-    if (WE)
-      for (int m = 0; m < 5; ++m) g[(eOut + m) * cs + idx] = z;
-    return;
-  }
-  int h = s.Ng / 2;
+  const bool live = kvector(s, idx, ix, iy, iz);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) vout[m].x = vout[m].y = (T)0;
+  if (!live) return;
+  const int h = s.Ng / 2;
   T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - s.Ng) * s.kfac), (T)((iz <= h ? iz : iz - s.Ng) * s.kfac)};
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
@@ -132,17 +123,15 @@ __global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
   if (HF) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      C2 v = g[m * cs + idx];
-      fr[m] = s0 * v.x;
-      fi[m] = s0 * v.y;
+      fr[m] = s0 * vin[m].x;
+      fi[m] = s0 * vin[m].y;
     }
   }
   T sr[5], si[5];
 #pragma unroll
   for (int m = 0; m < 5; ++m) {
-    C2 v = g[(sIn + m) * cs + idx];
-    sr[m] = v.x;
-    si[m] = v.y;
+    sr[m] = vin[sIn + m].x;
+    si[m] = vin[sIn + m].y;
   }
   T skr[3], ski[3];
   Smul(sr, k, skr);
@@ -161,7 +150,67 @@ __global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
     ur[m] = c * (fr[m] - kh[m] * pr);
     ui[m] = c * (fi[m] - kh[m] * pi);
   }
-  project_out<T, WU, WE>(g, idx, cs, uOut, eOut, k, s0, s1, ur, ui);
+  if (WU) {  // U = s0 u
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      vout[m].x = s0 * ur[m];
+      vout[m].y = s0 * ui[m];
+    }
+  }
+  if (WE) {  // e = (3i s1 / 2) symY(u, k)
+    T er[5], ei[5];
+    symY(ur, k, er);
+    symY(ui, k, ei);
+    T f = (T)1.5 * s1;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      vout[eOut + m].x = -f * ei[m];
+      vout[eOut + m].y = f * er[m];
+    }
+  }
+}
+
+// In-place scaling of the half spectra, NP consecutive points per thread (FP32:
+// NP = 2, each component read and written as one 16-byte vector; every
+// suspension's point count N_g^2 (N_g/2 + 1) is even, so pairs never straddle two
+// suspensions and stay 16-byte aligned).
+template <typename T, int MODE, int NP>
+__global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
+  using C2 = typename Cx<T>::t;
+  constexpr int NIN = (MODE == M_FULL || MODE == M_FSU) ? 8 : 5;
+  constexpr int NOUT = (MODE == M_FULL) ? 8 : (MODE == M_SE ? 5 : 3);  // outputs occupy slots [0, NOUT)
+  static_assert(NP == 1 || (NP == 2 && sizeof(T) == 4), "pairs in FP32 only");
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * NP;
+  if (g0 >= sa.nk_tot) return;
+  const int sidx = find_sys(sa.k0, sa.nsys, g0);
+  if (!sa.active[sidx]) return;
+  const SysDev &s = sa.sys[sidx];
+  const size_t idx = (size_t)(g0 - s.k0);
+  C2 *g = g_all + s.cgrid0;
+  const size_t cs = s.cstride;
+  C2 vin[NP][8], vout[NP][8];
+#pragma unroll
+  for (int m = 0; m < NIN; ++m) {
+    if constexpr (NP == 2) {
+      const float4 q = *(const float4 *)(g + m * cs + idx);
+      vin[0][m].x = q.x;
+      vin[0][m].y = q.y;
+      vin[1][m].x = q.z;
+      vin[1][m].y = q.w;
+    } else {
+      vin[0][m] = g[m * cs + idx];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) scale_point<T, MODE>(sa, s, idx + p, vin[p], vout[p]);
+#pragma unroll
+  for (int m = 0; m < NOUT; ++m) {
+    if constexpr (NP == 2) {
+      *(float4 *)(g + m * cs + idx) = make_float4(vout[0][m].x, vout[0][m].y, vout[1][m].x, vout[1][m].y);
+    } else {
+      g[m * cs + idx] = vout[0][m];
+    }
+  }
 }
 
 // Wave-space noise: dW2 on the half spectrum (Hermitian partners on kx = 0),
@@ -278,15 +327,16 @@ pse_status wave_apply_t(pse_ctx *c, const void *vin, void *vout, int mode, bool 
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, true, cin, s, mode));
   ScaleArgs sa = scale_args(c);
-  unsigned nb = (unsigned)ceil_div(c->nk_tot, 256);
   using C2 = typename Cx<T>::t;
   {
     StageTimer timer(c, PSE_STAGE_SCALE, s, mode);
     c->nlaunch += 1;
-    if (mode == M_FULL) k_scale<T, M_FULL><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
-    else if (mode == M_SE) k_scale<T, M_SE><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
-    else if (mode == M_SU) k_scale<T, M_SU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
-    else k_scale<T, M_FSU><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    constexpr int NP = sizeof(T) == 4 ? 2 : 1;
+    const unsigned nb = (unsigned)ceil_div(c->nk_tot, 256 * NP);
+    if (mode == M_FULL) k_scale<T, M_FULL, NP><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    else if (mode == M_SE) k_scale<T, M_SE, NP><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    else if (mode == M_SU) k_scale<T, M_SU, NP><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
+    else k_scale<T, M_FSU, NP><<<nb, 256, 0, s>>>(sa, (C2 *)c->d_cgrid);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   PSE_TRY(fft<T>(c, false, cout, s, mode));

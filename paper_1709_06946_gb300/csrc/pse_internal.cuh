@@ -182,6 +182,7 @@ struct pse_ctx {
   int *d_cell_start = nullptr, *d_cell_cur = nullptr;   // ncells + 1
   int *d_cell_list = nullptr;
   void *d_vcell = nullptr;     // the input vector of a real-space product in cell-list order (8N reals)
+  void *d_rfd = nullptr;       // RFD step work space (4 x 8N reals, user order), allocated on first use
   void *d_rs_cell = nullptr;   // records of d_rs in cell-list order
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
   void *d_nbr_geo = nullptr;    // neighbour slots, particle i of suspension s owning nbr0 + (i - p0) slots ...:
@@ -347,6 +348,9 @@ pse_status midpoint(pse_ctx *c, const double *x0, const void *B_user, double fac
 pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const void *U_sorted,
                         double dt, double *xout, cudaStream_t s);
 pse_status check_finite(pse_ctx *c, const void *ptr, int64_t n, bool dbl, int *bad, cudaStream_t s);
+pse_status rfd_noise(pse_ctx *c, const void *wt, uint64_t seed, uint64_t counter, void *W8, cudaStream_t s);
+pse_status rfd_final(pse_ctx *c, const double *x0, const void *B, const void *U0, const void *Rp, const void *Rm,
+                     double dt, double fac, double *xout, cudaStream_t s);
 // Krylov control kernels (krylov_dev.cu); handle = 0 and graph = 0 outside a graph.
 void kd_lz_start(pse_ctx *c, cudaStream_t s);
 void kd_lz_step(pse_ctx *c, cudaStream_t s);

@@ -236,6 +236,156 @@ __global__ void __launch_bounds__(32 * 8 * (16 / ZT), 16 / ZT == 1 ? 2 : 1)
   });
 }
 
+// Bit w set for each warp w whose column block (and z range, for ZT = 8) the P^3
+// support with start offsets (ex, ey, ez) from the tile origin overlaps.
+template <int NW, int ZT, int P>
+__device__ __forceinline__ unsigned region_mask(int ex, int ey, int ez) {
+  constexpr int TS = CUBE;
+  if (ex <= -P || ex >= TS || ey <= -P || ey >= TS || ez <= -P || ez >= TS) return 0u;
+  const unsigned xm = (ex <= 7 ? 1u : 0u) | (ex + P - 1 >= 8 ? 2u : 0u);
+  const int ylo = max(ey, 0) >> 2, yhi = min(ey + P - 1, TS - 1) >> 2;
+  unsigned m = 0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) m |= (b >= ylo && b <= yhi) ? xm << (2 * b) : 0u;
+  if (ZT == TS) return m;
+  const unsigned zm = (ez <= ZT - 1 ? 1u : 0u) | (ez + P - 1 >= ZT ? 2u : 0u);
+  return ((zm & 1u) ? m : 0u) | ((zm & 2u) ? m << 8 : 0u);
+}
+
+// Spreading as k_spread_col, with the candidate scan shared by the CTA: in
+// chunks of two candidates per thread, every thread tests its candidates
+// against all column blocks, writes one record per candidate that reaches the
+// tile, and appends its slot to the hit list of each warp whose block it meets;
+// after a barrier each warp adds the records of its list into its columns.  One
+// scan and one record per candidate instead of one per candidate and warp.
+template <int C, int SLOT0, int P, int ZT>
+__global__ void __launch_bounds__(32 * 8 * (16 / ZT), (16 / ZT == 1 || C <= 5) ? 2 : 1)
+    k_spread_colq(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0, const float4 *__restrict__ sp_d0,
+                  const float *__restrict__ vin, const int *__restrict__ fine_start, float *__restrict__ grid_all) {
+  constexpr int TS = CUBE, NW = 8 * (TS / ZT), NT = 32 * NW, RF = ColRec<C, P>::FLOATS, CH = 2 * NT;
+  static_assert(TS % ZT == 0 && NW <= 32, "z split");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *rec = (float *)smem_raw;                                       // CH records of RF floats
+  unsigned short *lists = (unsigned short *)(rec + (size_t)CH * RF);    // NW lists of up to CH slots
+  __shared__ int s_cnt[2][NW];
+  __shared__ ColRanges s_rng;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wx0 = (w & 1) * 8, wy0 = ((w >> 1) & 3) * 4, wz0 = (w >> 3) * ZT;
+  const int cx = wx0 + (lane & 7), cy = wy0 + (lane >> 3);
+  const unsigned below = (1u << lane) - 1u;
+  for_each_item(queue, wa.ntiles, [&](int item) {
+    const int si = find_sys(wa.tile0, wa.nsys, item);
+    const SysDev &a = wa.sys[si];
+    if (wave_skip(wa, si, a)) return;
+    const int Ng = a.Ng;
+    int t[3], t0[3];
+    tile_of(a, item - a.tile0, t, t0);
+    if (w == 0) col_ranges(a, t, 0, TS, P, lane, fine_start, s_rng);
+    if (tid < 2 * NW) (&s_cnt[0][0])[tid] = 0;
+    const float nal = -(float)a.alpha * COL_LOG2E, hs = (float)a.h, pref = (float)a.pref;
+    float acc[ZT][C];
+#pragma unroll
+    for (int z = 0; z < ZT; ++z)
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[z][c] = 0.f;
+    __syncthreads();  // ranges and counters
+    const int total = s_rng.cum[8];
+    int par = 0;
+    for (int base = 0; base < total; base += CH, par ^= 1) {
+      int kk[2];
+      int4 i0[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int v = base + tid + u * NT;
+        kk[u] = v < total ? col_candidate(s_rng, v) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (kk[u] >= 0) i0[u] = sp_i0[kk[u]];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        unsigned mask = 0;
+        int ex = 0, ey = 0, ez = 0;
+        if (kk[u] >= 0) {
+          ex = col_soff(i0[u].x, t0[0], Ng, P);
+          ey = col_soff(i0[u].y, t0[1], Ng, P);
+          ez = col_soff(i0[u].z, t0[2], Ng, P);
+          mask = region_mask<NW, ZT, P>(ex, ey, ez);
+        }
+        const int slot = tid + u * NT;
+        if (mask) {
+          const int k = kk[u];
+          const float4 d0 = sp_d0[k];
+          const float *row = vin + 8 * (size_t)k + SLOT0;
+          float q[RF];
+#pragma unroll
+          for (int i = 0; i < RF; ++i) q[i] = 0.f;
+          q[0] = __int_as_float((ex + 512) | ((ey + 512) << 10) | ((ez + 512) << 20));
+          q[1] = d0.x;
+          q[2] = d0.y;
+#pragma unroll
+          for (int c = 0; c < C; ++c) q[4 + c] = pref * row[c];
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            const float oz = d0.z + (float)j * hs;
+            q[4 + C + j] = exp2f(nal * oz * oz);
+          }
+          float *r = rec + (size_t)slot * RF;
+#pragma unroll
+          for (int i = 0; i < RF; i += 4) *(float4 *)(r + i) = make_float4(q[i], q[i + 1], q[i + 2], q[i + 3]);
+        }
+        // append the slot to the list of every warp whose block the support meets
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+          const bool b = (mask >> q) & 1u;
+          const unsigned bal = __ballot_sync(0xffffffffu, b);
+          if (bal) {
+            const int lead = __ffs(bal) - 1;
+            int at = 0;
+            if (lane == lead) at = atomicAdd(&s_cnt[par][q], __popc(bal));
+            at = __shfl_sync(0xffffffffu, at, lead);
+            if (b) lists[q * CH + at + __popc(bal & below)] = (unsigned short)slot;
+          }
+        }
+      }
+      __syncthreads();  // records and lists complete
+      const int n = s_cnt[par][w];
+      if (lane == 0) s_cnt[par ^ 1][w] = 0;  // the next chunk's counter (its appends follow the next barrier)
+      for (int h = 0; h < n; ++h) {
+        const float *r = rec + (size_t)lists[w * CH + h] * RF;
+        float q[RF];
+#pragma unroll
+        for (int i = 0; i < RF; i += 4) {
+          const float4 u4 = *(const float4 *)(r + i);
+          q[i] = u4.x;
+          q[i + 1] = u4.y;
+          q[i + 2] = u4.z;
+          q[i + 3] = u4.w;
+        }
+        const int pk = __float_as_int(q[0]);
+        const int px = (pk & 1023) - 512, py = ((pk >> 10) & 1023) - 512, pz = (pk >> 20) - 512 - wz0;
+        const int jx = cx - px, jy = cy - py;
+        const float ox = q[1] + (float)jx * hs, oy = q[2] + (float)jy * hs;
+        float wxy = exp2f(nal * (ox * ox + oy * oy));
+        wxy = ((unsigned)jx < (unsigned)P && (unsigned)jy < (unsigned)P) ? wxy : 0.f;
+        float m[C], wz[P];
+#pragma unroll
+        for (int c = 0; c < C; ++c) m[c] = wxy * q[4 + c];
+#pragma unroll
+        for (int j = 0; j < P; ++j) wz[j] = q[4 + C + j];
+        ZAdd<1 - P, ZT - 1, ZT, P, C>::run(pz, acc, wz, m);
+      }
+      __syncthreads();  // the records and lists are read before the next chunk overwrites them
+    }
+    float *grid = grid_all + a.grid0;
+    const size_t g0 = ((size_t)(t0[2] + wz0) * Ng + (t0[1] + cy)) * Ng + (t0[0] + cx);
+#pragma unroll
+    for (int z = 0; z < ZT; ++z)
+#pragma unroll
+      for (int c = 0; c < C; ++c) grid[c * a.gstride + g0 + (size_t)z * Ng * Ng] = acc[z][c];
+  });
+}
+
 // Floats of one queued interpolation record: [packed offsets, x offset, y
 // offset, particle index, P z weights], padded to whole 16-byte vectors.
 template <int P>
@@ -365,16 +515,37 @@ void interp_col_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   }
 }
 
+template <int C, int SLOT0, int P, int ZT>
+void launch_spread_col_z(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
+  constexpr int NT = 32 * 8 * (CUBE / ZT);
+  int *q = next_queue(c, s);
+  if (c->opt.wave_kernel & 4) {  // every warp scans the candidates itself
+    static OccCache occ;
+    auto kern = k_spread_col<C, SLOT0, P, ZT>;
+    const unsigned grid = wave_grid(c, kern, 0, a.ntiles, occ, NT);
+    kern<<<grid, NT, 0, s>>>(a, q, (const int4 *)c->d_sp_i0, (const float4 *)c->d_sp_d0, (const float *)vin,
+                             c->d_fine_start, (float *)c->d_grid);
+    return;
+  }
+  static std::once_flag once;
+  static OccCache occ;
+  auto kern = k_spread_colq<C, SLOT0, P, ZT>;
+  set_smem(kern, once);
+  constexpr size_t sm = (size_t)2 * NT * ColRec<C, P>::FLOATS * sizeof(float) +
+                        (size_t)(NT / 32) * 2 * NT * sizeof(unsigned short);
+  const unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ, NT);
+  kern<<<grid, NT, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const float4 *)c->d_sp_d0, (const float *)vin,
+                            c->d_fine_start, (float *)c->d_grid);
+}
+
+// ZT: z points per thread, 8 (two z halves: 40 accumulators for 5 components,
+// two 512-thread CTAs per SM; measured 13 % faster than whole columns) by
+// default, 16 (one whole column per thread) for up to 5 components with bit 3
+// of option wave_kernel.
 template <int C, int SLOT0, int P>
 void launch_spread_col(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
-  static OccCache occ;
-  constexpr int ZT = C > 5 ? 8 : 16;
-  constexpr int NT = 32 * 8 * (CUBE / ZT);
-  auto kern = k_spread_col<C, SLOT0, P, ZT>;
-  const unsigned grid = wave_grid(c, kern, 0, a.ntiles, occ, NT);
-  int *q = next_queue(c, s);
-  kern<<<grid, NT, 0, s>>>(a, q, (const int4 *)c->d_sp_i0, (const float4 *)c->d_sp_d0, (const float *)vin,
-                           c->d_fine_start, (float *)c->d_grid);
+  if (C <= 5 && (c->opt.wave_kernel & 8)) launch_spread_col_z<C, SLOT0, P, 16>(c, a, vin, s);
+  else launch_spread_col_z<C, SLOT0, P, 8>(c, a, vin, s);
 }
 
 template <int C, int SLOT0>
