@@ -17,6 +17,7 @@ import math
 import numpy as np
 
 from . import realspace, wavesum
+from .basis import G, Y
 
 
 def cutoffs(xi, tol):
@@ -27,9 +28,11 @@ def cutoffs(xi, tol):
     return rmax, kmax
 
 
-def dense_real(pos, L, a, eta, xi, rmax):
+def dense_real(pos, L, a, eta, xi, rmax, torque=False):
     N = pos.shape[0]
-    M = np.zeros((8 * N, 8 * N))
+    nb = 11 if torque else 8
+    blocks = realspace.pair_blocks11 if torque else realspace.pair_blocks
+    M = np.zeros((nb * N, nb * N))
     nimg = int(math.ceil(rmax / L))
     rng = range(-nimg, nimg + 1)
     ia, ib = np.meshgrid(np.arange(N), np.arange(N), indexing='ij')
@@ -40,22 +43,24 @@ def dense_real(pos, L, a, eta, xi, rmax):
         sel = (r < rmax) & (r > 0)
         if not np.any(sel):
             continue
-        B = realspace.pair_blocks(d[sel], xi, a, eta)
+        B = blocks(d[sel], xi, a, eta)
         for (p, q, blk) in zip(ia[sel], ib[sel], B):
-            M[8 * p:8 * p + 8, 8 * q:8 * q + 8] += blk
-    S = realspace.self_block(xi, a, eta)
+            M[nb * p:nb * p + nb, nb * q:nb * q + nb] += blk
+    S = realspace.self_block11(xi, a, eta) if torque else realspace.self_block(xi, a, eta)
     for p in range(N):
-        M[8 * p:8 * p + 8, 8 * p:8 * p + 8] += S
+        M[nb * p:nb * p + nb, nb * p:nb * p + nb] += S
     return M
 
 
-def dense_mobility(pos, L, a=1.0, eta=1.0, xi=None, tol=1e-14, parts=False):
-    """Exact (to ~tol) periodic grand mobility, 8N x 8N, ordering [F(3), s(5)] per particle."""
+def dense_mobility(pos, L, a=1.0, eta=1.0, xi=None, tol=1e-14, parts=False, torque=False):
+    """Exact (to ~tol) periodic grand mobility, 8N x 8N with ordering [F(3), s(5)] per particle,
+    or with torque=True 11N x 11N with ordering [F(3), L(3), s(5)] (outputs [U, Omega, e])."""
     if xi is None:
         xi = math.sqrt(math.pi) / L * 2.0
     rmax, kmax = cutoffs(xi, tol)
-    Mr = dense_real(np.asarray(pos, float), L, a, eta, xi, rmax)
-    Mw = wavesum.dense_wave(np.asarray(pos, float), L, a, eta, xi, wavesum.kset_sphere(L, kmax))
+    Mr = dense_real(np.asarray(pos, float), L, a, eta, xi, rmax, torque)
+    Mw = wavesum.dense_wave(np.asarray(pos, float), L, a, eta, xi, wavesum.kset_sphere(L, kmax),
+                            basis=G if torque else Y)
     if parts:
         return Mr, Mw
     return Mr + Mw

@@ -49,7 +49,7 @@ from scipy.linalg import eigh_tridiagonal
 from scipy.spatial import cKDTree
 
 from . import realspace
-from .basis import Y
+from .basis import G, Y
 from .wavesum import shape_factors
 
 
@@ -202,9 +202,10 @@ def wave_noise(pos, w2, p):
 
 # ---------------------------------------------------------------- real space
 class RealOp:
-    """Real-space operator M_r for a fixed configuration (pairs with r < r_cut)."""
+    """Real-space operator M_r for a fixed configuration (pairs with r < r_cut); with
+    torque=True the 11-moment form [F, L, S] -> [U, Omega, E]."""
 
-    def __init__(self, pos, p, chunk=20000):
+    def __init__(self, pos, p, chunk=20000, torque=False):
         self.N = pos.shape[0]
         x = np.mod(pos, p.L)
         tree = cKDTree(x, boxsize=p.L)
@@ -215,26 +216,30 @@ class RealOp:
         d -= p.L * np.rint(d / p.L)
         keep = np.linalg.norm(d, axis=1) < p.rcut
         pr, d = pr[keep], d[keep]
-        blocks = np.empty((pr.shape[0], 8, 8))
+        nb = 11 if torque else 8
+        fn = realspace.pair_blocks11 if torque else realspace.pair_blocks
+        blocks = np.empty((pr.shape[0], nb, nb))
         for c0 in range(0, pr.shape[0], chunk):
-            blocks[c0:c0 + chunk] = realspace.pair_blocks(d[c0:c0 + chunk], p.xi, p.a, p.eta)
+            blocks[c0:c0 + chunk] = fn(d[c0:c0 + chunk], p.xi, p.a, p.eta)
+        self.nb = nb
         self.i, self.j, self.B = pr[:, 0], pr[:, 1], blocks
-        self.self = realspace.self_block(p.xi, p.a, p.eta)
+        self.self = (realspace.self_block11 if torque else realspace.self_block)(p.xi, p.a, p.eta)
 
     def apply(self, v):
-        """(N, 8) -> (N, 8) real-space product."""
+        """(N, nb) -> (N, nb) real-space product."""
         out = v @ self.self.T
         np.add.at(out, self.i, np.einsum('pab,pb->pa', self.B, v[self.j]))
         np.add.at(out, self.j, np.einsum('pba,pb->pa', self.B, v[self.i]))
         return out
 
     def dense(self):
-        M = np.zeros((8 * self.N, 8 * self.N))
+        nb = self.nb
+        M = np.zeros((nb * self.N, nb * self.N))
         for n in range(self.N):
-            M[8 * n:8 * n + 8, 8 * n:8 * n + 8] = self.self
+            M[nb * n:nb * n + nb, nb * n:nb * n + nb] = self.self
         for i, j, b in zip(self.i, self.j, self.B):
-            M[8 * i:8 * i + 8, 8 * j:8 * j + 8] += b
-            M[8 * j:8 * j + 8, 8 * i:8 * i + 8] += b.T
+            M[nb * i:nb * i + nb, nb * j:nb * j + nb] += b
+            M[nb * j:nb * j + nb, nb * i:nb * i + nb] += b.T
         return M
 
 
@@ -253,6 +258,43 @@ def mobility_apply(pos, F, S, p, parts=('real', 'wave'), real_op=None):
         U += w['U']
         E += w['E']
     return U, E
+
+
+def wave_apply11(pos, F, Lt, S, p):
+    """Wave-space part of the 11-moment product [U; Omega; E] = M_w [F; L; S] (Sec. 2.3.2, the
+    paper's 11 grids: 3 force + 8 couplet).  The couplet is C = sum_k L_k A_k + sum_l s_l Y_l
+    (basis G), f = s0 F_hat - 3i s1 C.k, u = c (I - kk) f, and the outputs are U = s0 u and the
+    components G_l : D of D = 3i s1 u k^T (the rotation rate through A, the strain through Y)."""
+    comps = np.concatenate([F, Lt, S], axis=1)
+    grid = spread(pos, comps, p)
+    gh = np.fft.rfftn(grid, axes=(1, 2, 3))
+    kvec, kk, keep, s0, s1 = _k_arrays(p)
+    Ch = np.einsum('l...,lij->ij...', gh[3:], G)
+    f = s0[None] * gh[:3] - 3j * s1[None] * np.einsum('ij...,j...->i...', Ch, kvec)
+    u = kk ** 2 / (4 * p.xi ** 2)
+    c = (p.sigma ** 2 / p.V) / p.eta * (1 + u) * np.exp(-(1 - p.eta_g) * u) / kk ** 2
+    kh = kvec / kk[None]
+    f = f - kh * np.sum(kh * f, axis=0)[None]
+    uh = c[None] * f
+    D = 3j * s1[None, None] * uh[:, None] * kvec[None, :]
+    outs = [s0 * uh[i] for i in range(3)] + [np.einsum('ij...,ij->...', D, G[l]) for l in range(8)]
+    outs = [np.where(keep, o, 0.0) for o in outs]
+    n = p.Ng
+    grids = np.stack([np.fft.irfftn(o, s=(n, n, n), axes=(0, 1, 2)) * n ** 3 for o in outs])
+    vals = interpolate(grids, pos, p)
+    return vals[:, :3], vals[:, 3:6], vals[:, 6:]
+
+
+def mobility_apply11(pos, F, Lt, S, p, parts=('real', 'wave'), real_op=None):
+    """[U; Omega; E] = M [F; L; S], the 11-moment grand mobility with the PSE split."""
+    N = pos.shape[0]
+    out = np.zeros((N, 11))
+    if 'real' in parts:
+        op = real_op if real_op is not None else RealOp(pos, p, torque=True)
+        out += op.apply(np.concatenate([F, Lt, S], axis=1))
+    if 'wave' in parts:
+        out += np.concatenate(wave_apply11(pos, F, Lt, S, p), axis=1)
+    return out[:, :3], out[:, 3:6], out[:, 6:]
 
 
 # ---------------------------------------------------------------- Lanczos

@@ -36,7 +36,7 @@ Pairs closer than about 0.2a lose digits to 1/r^7 cancellation (documented).
 import numpy as np
 from scipy.special import erf
 
-from .basis import Y
+from .basis import G, Y
 
 _C = 1.0 / (8.0 * np.pi)
 _SQPI = np.sqrt(np.pi)
@@ -241,4 +241,31 @@ def self_block(xi, a, eta, free_only=False):
     B = np.zeros((8, 8))
     B[:3, :3] = (2.0 / 3.0) * phi_aa0 / eta * np.eye(3)
     B[3:, 3:] = u5_bb / (5.0 * eta) * np.eye(5)
+    return B
+
+
+def pair_blocks11(x, xi, a, eta, free_only=False):
+    """11x11 real-space blocks [[UF, UL, US], [OF, OL, OS], [EF, EL, ES]] for separations x (p, 3):
+    the couplet / gradient basis G = [A (torque, rotation), Y (stresslet, strain)] (Sec. 2.2.1)."""
+    M_UF, M_UC, M_DF, M_DC = cartesian_blocks(x, xi, a, eta, free_only)
+    p = M_UF.shape[0]
+    B = np.zeros((p, 11, 11))
+    B[:, :3, :3] = M_UF
+    B[:, :3, 3:] = np.einsum('pimn,lmn->pil', M_UC, G)
+    B[:, 3:, :3] = np.einsum('kij,pijm->pkm', G, M_DF)
+    B[:, 3:, 3:] = np.einsum('kij,pijmn,lmn->pkl', G, M_DC, G)
+    return B
+
+
+def self_block11(xi, a, eta, free_only=False):
+    """11x11 real-space self mobility: UF as self_block, rotation-torque U_bb^(5)(0)/(6 eta) I_3
+    (from the isotropic r -> 0 limit of M_DC on antisymmetric couplets: D = -Phi''(0)/eta C,
+    Phi''(0) = -U_bb^(5)(0)/3, Omega = A : D), strain-stresslet U_bb^(5)(0)/(5 eta) I_5."""
+    z = np.zeros(1)
+    phi_aa0 = -conv_U('aa', z, xi, a, 3, free_only)[0]
+    u5_bb = conv_U('bb', z, xi, a, 5, free_only)[0]
+    B = np.zeros((11, 11))
+    B[:3, :3] = (2.0 / 3.0) * phi_aa0 / eta * np.eye(3)
+    B[3:6, 3:6] = u5_bb / (6.0 * eta) * np.eye(3)
+    B[6:, 6:] = u5_bb / (5.0 * eta) * np.eye(5)
     return B

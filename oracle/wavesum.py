@@ -52,11 +52,13 @@ def kset_grid(L, Ng):
     return 2 * np.pi * n[keep] / L
 
 
-def dense_wave(pos, L, a, eta, xi, kvecs, chunk=400):
-    """Dense 8N x 8N wave-space mobility over the half-space k set kvecs."""
+def dense_wave(pos, L, a, eta, xi, kvecs, chunk=400, basis=Y):
+    """Dense nN x nN wave-space mobility over the half-space k set kvecs, n = 3 + len(basis):
+    8 with the stresslet basis Y, 11 with the torque + stresslet basis G."""
     N = pos.shape[0]
     V = L ** 3
-    M = np.zeros((8 * N, 8 * N))
+    nb = 3 + basis.shape[0]
+    M = np.zeros((nb * N, nb * N))
     for c0 in range(0, kvecs.shape[0], chunk):
         k = kvecs[c0:c0 + chunk]
         kk = np.linalg.norm(k, axis=1)
@@ -67,11 +69,11 @@ def dense_wave(pos, L, a, eta, xi, kvecs, chunk=400):
         c = H / (eta * V * kk ** 2)
         proj = np.eye(3)[None] - np.einsum('pi,pj->pij', kh, kh)        # (p,3,3)
         # columns: F_m -> s0 e_m ; s_l -> -3i s1 Y_l k
-        A = np.zeros((k.shape[0], 3, 8), dtype=complex)
+        A = np.zeros((k.shape[0], 3, nb), dtype=complex)
         A[:, :, :3] = s0[:, None, None] * np.eye(3)[None]
-        A[:, :, 3:] = (-3j * s1)[:, None, None] * np.einsum('lmn,pn->pml', Y, k)
+        A[:, :, 3:] = (-3j * s1)[:, None, None] * np.einsum('lmn,pn->pml', basis, k)
         A = np.einsum('pij,pjc->pic', proj, A) * np.sqrt(c)[:, None, None]
         phase = np.exp(-1j * pos @ k.T)                                # (N, p)
-        Phi = np.einsum('bp,pic->pibc', phase, A).reshape(k.shape[0] * 3, 8 * N)
+        Phi = np.einsum('bp,pic->pibc', phase, A).reshape(k.shape[0] * 3, nb * N)
         M += 2.0 * np.real(Phi.conj().T @ Phi)
     return M
