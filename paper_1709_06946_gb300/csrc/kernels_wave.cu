@@ -58,10 +58,14 @@ __device__ __forceinline__ void shape(T x, T &s0, T &s1) {
   }
 }
 
+// Half-spectrum indices of point idx (32-bit arithmetic: a suspension's half
+// spectrum has fewer than 2^31 points, and 64-bit division is slow on the GPU).
 __device__ __forceinline__ bool kvector(const SysDev &s, size_t idx, int &ix, int &iy, int &iz) {
-  ix = (int)(idx % s.nkx);
-  iy = (int)((idx / s.nkx) % s.Ng);
-  iz = (int)(idx / ((size_t)s.nkx * s.Ng));
+  const unsigned u = (unsigned)idx, nkx = (unsigned)s.nkx, ng = (unsigned)s.Ng;
+  const unsigned q = u / nkx;
+  ix = (int)(u - q * nkx);
+  iz = (int)(q / ng);
+  iy = (int)(q - (unsigned)iz * ng);
   int h = s.Ng / 2;
   return !(ix == h || iy == h || iz == h || (ix == 0 && iy == 0 && iz == 0));
 }
