@@ -106,7 +106,10 @@ typedef struct pse_options {
                               the CTA scans them once and hands each warp its hit list); bit 3 set:
                               the 5-component spreading keeps a whole 16-point column per thread
                               (default: 8 z points, two z halves) */
-  int32_t reserved[4];
+  int32_t torque;          /* 1: also set up the 11-moment product pse_mobility_apply11 (forces,
+                              torques and stresslets): 11 grids per suspension instead of 8, their
+                              transforms, 12-slot work vectors and the rotation table */
+  int32_t reserved[3];
 } pse_options;
 
 typedef struct pse_info {
@@ -233,6 +236,23 @@ pse_status pse_mobility_apply(pse_handle h, const double *pos, const void *F, co
  * wave-space (PSE_PART_WAVE) part of the split, or both (PSE_PART_ALL). */
 pse_status pse_mobility_apply_parts(pse_handle h, const double *pos, const void *F, const void *S,
                                     void *U, void *E, int32_t parts, pse_stream stream);
+
+/* 11-moment product [U; Omega; E] = M [F; L; S] (Sec. 2.1 Eqs. MUF-MDC with the
+ * torque of the rigid-particle relation, Sec. 2.2.1): the couplet of a particle
+ * is sum_k L_k A_k + sum_k s_k Y_k with A_k = -eps_k../2 (A_k : A_l = delta/2),
+ * the angular velocity is Omega_k = A_k : (grad u) = (curl u / 2)_k, so the
+ * 11 x 11 blocks are symmetric; restricted to [U; E] x [F; S] it is
+ * pse_mobility_apply.  The split and its sums are those of pse_mobility_apply
+ * with 11 components: real space uses the tabulated free-space and Ewald-screened
+ * rotation functions, wave space 11 grids.  Needs a handle created with
+ * option torque = 1 (else PSE_ERR_INVALID_ARG).  F, L (N x 3) and S (N x 5)
+ * may each be NULL (zero); U, Omega (N x 3) and E (N x 5) may each be NULL
+ * (not written).  parts: PSE_PART_REAL, PSE_PART_WAVE or PSE_PART_ALL.
+ * Element type as for pse_mobility_apply.  Single-suspension handles only.
+ * Asynchronous on stream. */
+pse_status pse_mobility_apply11(pse_handle h, const double *pos, const void *F, const void *L,
+                                const void *S, void *U, void *Omega, void *E, int32_t parts,
+                                pse_stream stream);
 
 /* Brownian slip velocities [U^B; E^B] = sqrt(2 kT/dt) (M_r^{1/2} w1 + M_w^{1/2} dW2)
  * (Sec. 3 Eq. split, Sec. 3.2-3.3).  Noise is either external or drawn in-kernel:

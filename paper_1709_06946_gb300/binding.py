@@ -29,7 +29,8 @@ class Options(ctypes.Structure):
                 ('lanczos_tol', ctypes.c_double), ('lanczos_maxiter', ctypes.c_int32),
                 ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
                 ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('grid_ladder', ctypes.c_int32),
-                ('use_graph', ctypes.c_int32), ('wave_kernel', ctypes.c_int32), ('reserved', ctypes.c_int32 * 4)]
+                ('use_graph', ctypes.c_int32), ('wave_kernel', ctypes.c_int32), ('torque', ctypes.c_int32),
+                ('reserved', ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):
@@ -121,6 +122,7 @@ SIGNATURES = [
     ('pse_get_system_stats', ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Stats)]),
     ('pse_mobility_apply', ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ('pse_mobility_apply_parts', ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
+    ('pse_mobility_apply11', ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     ('pse_brownian_sample', ctypes.c_int, [_P, _P, _D, _U64, _U64, _P, _P, _P, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step', ctypes.c_int, [_P, _P, _P, _D, _U64, _U64, _P, ctypes.POINTER(Stats), _P]),
     ('pse_constrained_step_noise', ctypes.c_int, [_P, _P, _P, _D, _P, _P, _P, ctypes.POINTER(Stats), _P]),
@@ -187,6 +189,22 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _checked(x, shape, dtype, name):
+    """x itself after checking its shape and element type (numpy array or torch tensor)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        ok = x.dtype == np.dtype(dtype)
+    else:
+        torch = _torch()
+        ok = x.dtype == (torch.float64 if dtype == np.float64 else torch.float32)
+    if not ok:
+        raise ValueError(f'{name} must hold {np.dtype(dtype).name} elements, not {x.dtype}')
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f'{name} must have shape {tuple(shape)}, not {tuple(x.shape)}')
+    return x
+
+
 def _stream(x):
     try:
         torch = _torch()
@@ -229,7 +247,7 @@ def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
 
 def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
              krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=1, use_graph=0,
-             wave_kernel=0):
+             wave_kernel=0, torque=0):
     o = Options()
     load().pse_default_options(ctypes.byref(o))
     o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
@@ -241,6 +259,7 @@ def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxit
     o.grid_ladder = int(grid_ladder)
     o.use_graph = int(use_graph)
     o.wave_kernel = int(wave_kernel)
+    o.torque = int(torque)
     for d in range(3):
         o.tile[d] = int(tile[d])
     return o
@@ -346,12 +365,26 @@ class PSE:
 
     def mobility(self, pos, F=None, S=None, parts='all', want=('U', 'E')):
         """[U, E] = M [F; S] (or its real / wave part)."""
+        _checked(pos, (self.N, 3), np.float64, 'pos')
+        _checked(F, (self.N, 3), self.dtype, 'F')
+        _checked(S, (self.N, 5), self.dtype, 'S')
         U = self._like(pos, (self.N, 3), self.dtype) if 'U' in want else None
         E = self._like(pos, (self.N, 5), self.dtype) if 'E' in want else None
         st = self._lib.pse_mobility_apply_parts(self._h, _ptr(pos), _ptr(F), _ptr(S), _ptr(U), _ptr(E),
                                                 PARTS[parts], _stream(pos))
         self._check(st)
         return U, E
+
+    def mobility11(self, pos, F=None, Lt=None, S=None, parts='all'):
+        """[U, Omega, E] = M [F; L; S] with torques (handle created with torque=1)."""
+        N, dt = self.N, self.dtype
+        _checked(pos, (N, 3), np.float64, 'pos')
+        F, Lt, S = _checked(F, (N, 3), dt, 'F'), _checked(Lt, (N, 3), dt, 'L'), _checked(S, (N, 5), dt, 'S')
+        U, Om, E = self._like(pos, (N, 3), dt), self._like(pos, (N, 3), dt), self._like(pos, (N, 5), dt)
+        st = self._lib.pse_mobility_apply11(self._h, _ptr(pos), _ptr(F), _ptr(Lt), _ptr(S), _ptr(U), _ptr(Om),
+                                            _ptr(E), PARTS[parts], _stream(pos))
+        self._check(st)
+        return U, Om, E
 
     def brownian(self, pos, dt, seed=0, counter=0, w1=None, w2=None):
         """Brownian slip velocities (U^B, E^B) with covariance (2kT/dt) M."""

@@ -628,7 +628,8 @@ int64_t estimate_bytes(const pse_ctx *c) {
   b += Nt * (24 + 4 * 6 + 16 + 12 * (int64_t)ts);  // positions, keys, perm/inv, cells, records (two orders)
   b += nbr * 4 * (int64_t)ts + (Nt + 1) * 4;
   b += (ntile * (8 + 8 * SUB_BLOCKS) + ncell * 8);
-  b += (int64_t)ts * 8 * n3 + 2 * (int64_t)ts * 8 * nk;   // grids and half spectra
+  const int64_t ncomp = c->opt.torque ? 11 : 8;
+  b += (int64_t)ts * ncomp * n3 + 2 * (int64_t)ts * ncomp * nk;   // grids and half spectra
   b += (int64_t)ts * 8 * n3;                               // cuFFT work area (upper bound)
   b += (int64_t)ts * 8 * Nt * (7 + rows);                 // vectors and Krylov basis
   b += Nt * 48;                                            // FP64 positions (x_k, x_{k+1/2})
@@ -637,6 +638,7 @@ int64_t estimate_bytes(const pse_ctx *c) {
   b += (int64_t)c->nsys * 8 * (6 * L + L * L + (M + 1) * M + 3 * M + 8);  // Krylov control state
   b += (int64_t)ts * 8 * Nt + 24 * Nt;                                    // current Krylov vector, output positions
   b += (int64_t)ts * 8 * Nt;                                              // real-space input in cell order
+  if (c->opt.torque) b += (int64_t)ts * (36 * Nt + 4 * 2048 * 16);     // 12-slot vectors, rotation table
   return b;
 }
 
@@ -764,8 +766,9 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
       d.cgrid0 = cg0 + j * nk;
       d.cstride = g.nsys * nk;
     }
-    g0 += 8 * g.nsys * n3;
-    cg0 += 8 * g.nsys * nk;
+    const int ncomp = o.torque ? 11 : 8;  // grids per suspension
+    g0 += ncomp * g.nsys * n3;
+    cg0 += ncomp * g.nsys * nk;
     c->groups.push_back(g);
   }
   c->grid_elems = g0;
@@ -813,6 +816,21 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   c->d_cell_cur = (int *)A(sizeof(int) * (c->ncells + 1));
   c->d_cell_list = (int *)A(sizeof(int) * N);
   c->d_vcell = A(8 * ts * (size_t)N);
+  if (o.torque) {
+    std::vector<double> rot;
+    build_rot_table(c->p, ppa, t.len, rot, &c->self_ol);
+    c->d_table_rot = A(ts * 4 * (size_t)t.len);
+    if (c->d_table_rot) {
+      if (c->prec == PSE_MIXED) {
+        std::vector<float> rf(rot.begin(), rot.end());
+        PSE_CUDA_TRY(c, cudaMemcpy(c->d_table_rot, rf.data(), sizeof(float) * rf.size(), cudaMemcpyHostToDevice));
+      } else {
+        PSE_CUDA_TRY(c, cudaMemcpy(c->d_table_rot, rot.data(), sizeof(double) * rot.size(), cudaMemcpyHostToDevice));
+      }
+    }
+    for (int i = 0; i < 2; ++i) c->d_v12[i] = A(12 * ts * (size_t)N);
+    c->d_vcell12 = A(12 * ts * (size_t)N);
+  }
   c->d_nbr_start = (int *)A(sizeof(int) * (N + 1));
   c->nbr_cap = layout_neighbours(c);
   if ((double)c->nbr_cap > 2.0e9) {
@@ -926,7 +944,11 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   }
   // cuFFT plans per group (shared work area)
   size_t work = 0;
-  const int comps_r2c[2] = {5, 8}, comps_c2r[3] = {3, 5, 8};
+  std::vector<int> comps_r2c = {5, 8}, comps_c2r = {3, 5, 8};
+  if (o.torque) {
+    comps_r2c.push_back(11);
+    comps_c2r.push_back(11);
+  }
   cufftType tr = c->prec == PSE_MIXED ? CUFFT_R2C : CUFFT_D2Z, tc = c->prec == PSE_MIXED ? CUFFT_C2R : CUFFT_Z2D;
   for (FftGroup &g : c->groups) {
     int n[3] = {g.Ng, g.Ng, g.Ng};
@@ -981,7 +1003,7 @@ void destroy_impl(pse_ctx *c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
   for (FftGroup &g : c->groups)
-    for (int b = 0; b < 9; ++b) {
+    for (int b = 0; b < 12; ++b) {
       if (g.ok[0][b]) cufftDestroy(g.r2c[b]);
       if (g.ok[1][b]) cufftDestroy(g.c2r[b]);
     }
@@ -1380,6 +1402,48 @@ pse_status pse_constrained_step_noise(pse_handle h, double *pos, const void *FP,
   if (!h || !w1 || !w2) return PSE_ERR_INVALID_ARG;
   NvtxRange range("pse_constrained_step");
   return step_impl(h, pos, FP, dt, w1, w2, 0, 0, S_out, stats, (cudaStream_t)stream);
+}
+
+pse_status pse_mobility_apply11(pse_handle h, const double *pos, const void *F, const void *L, const void *S,
+                                void *U, void *Om, void *E, int32_t parts, pse_stream stream) {
+  if (!h || !pos) return PSE_ERR_INVALID_ARG;
+  NvtxRange range("pse_mobility_apply11");
+  pse_ctx *c = h;
+  if (!c->opt.torque || !c->d_table_rot) {
+    c->err = "the 11-moment product needs a handle created with option torque = 1";
+    return PSE_ERR_INVALID_ARG;
+  }
+  if (c->nsys != 1) {
+    c->err = "the 11-moment product takes single-suspension handles";
+    return PSE_ERR_INVALID_ARG;
+  }
+  if (parts < 1 || parts > 3) {
+    c->err = "parts must be PSE_PART_REAL, PSE_PART_WAVE or PSE_PART_ALL";
+    return PSE_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = c->p.N;
+  PSE_TRY(set_all_active(c, s));
+  void *dpos, *dF, *dL, *dS, *dU, *dO, *dE;
+  PSE_TRY(stage(c, 0, pos, sizeof(double) * 3 * N, true, s, &dpos));
+  PSE_TRY(stage(c, 1, F, c->ts * 3 * N, true, s, &dF));
+  PSE_TRY(stage(c, 5, L, c->ts * 3 * N, true, s, &dL));
+  PSE_TRY(stage(c, 2, S, c->ts * 5 * N, true, s, &dS));
+  PSE_TRY(check_inputs(c, dF, 3 * N, c->prec == PSE_FP64, s));
+  PSE_TRY(check_inputs(c, dL, 3 * N, c->prec == PSE_FP64, s));
+  PSE_TRY(check_inputs(c, dS, 5 * N, c->prec == PSE_FP64, s));
+  PSE_TRY(setup_config(c, (const double *)dpos, s));
+  PSE_TRY(gather12(c, dF, dL, dS, c->d_v12[0], s));
+  if (parts & PSE_PART_REAL) PSE_TRY(real_apply11(c, c->d_v12[0], c->d_v12[1], s));
+  if (parts & PSE_PART_WAVE) PSE_TRY(wave_apply11(c, c->d_v12[0], c->d_v12[1], (parts & PSE_PART_REAL) != 0, s));
+  PSE_TRY(stage(c, 3, U, c->ts * 3 * N, false, s, &dU));
+  PSE_TRY(stage(c, 4, E, c->ts * 5 * N, false, s, &dE));
+  PSE_TRY(stage(c, 6, Om, c->ts * 3 * N, false, s, &dO));
+  PSE_TRY(scatter12(c, c->d_v12[1], dU, dO, dE, s));
+  PSE_TRY(unstage(c, U, dU, c->ts * 3 * N, s));
+  PSE_TRY(unstage(c, Om, dO, c->ts * 3 * N, s));
+  PSE_TRY(unstage(c, E, dE, c->ts * 5 * N, s));
+  return PSE_OK;
 }
 
 pse_status pse_rfd_step(pse_handle h, double *pos, const void *FP, double dt, double delta, uint64_t seed,

@@ -269,6 +269,127 @@ void launch_real(pse_ctx *c, const RealArgs &a, const void *vin, void *vout, int
   }
 }
 
+// The three rotation scalars of the 11-moment form at r (4 reals per node): linear
+// interpolation in FP32; in FP64 cubic Lagrange interpolation with the same
+// one-sided stencils at the r = 2a node as lookup().
+__device__ __forceinline__ void rot_lookup(const float *tab, const RealArgs &a, float r, float g[3]) {
+  float x = r * (float)a.inv_dr;
+  int q = min((int)x, a.len - 2);
+  float t = x - (float)q;
+  const float4 u = ((const float4 *)tab)[q], v = ((const float4 *)tab)[q + 1];
+  g[0] = fmaf(t, v.x - u.x, u.x);
+  g[1] = fmaf(t, v.y - u.y, u.y);
+  g[2] = fmaf(t, v.z - u.z, u.z);
+}
+__device__ __forceinline__ void rot_lookup(const double *tab, const RealArgs &a, double r, double g[3]) {
+  double x = r * a.inv_dr;
+  int q = min((int)x, a.len - 2);
+  int b = q - 1;
+  if (q < a.k2) b = min(b, a.k2 - 3);
+  else b = max(b, a.k2);
+  b = max(0, min(b, a.len - 4));
+  double t = x - (double)b;
+  double w0 = -(t - 1) * (t - 2) * (t - 3) / 6.0, w1 = t * (t - 2) * (t - 3) / 2.0;
+  double w2 = -t * (t - 1) * (t - 3) / 2.0, w3 = t * (t - 1) * (t - 2) / 6.0;
+  const double *r0 = tab + 4 * (size_t)b;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    g[k] = w0 * __ldg(r0 + k) + w1 * __ldg(r0 + 4 + k) + w2 * __ldg(r0 + 8 + k) + w3 * __ldg(r0 + 12 + k);
+}
+
+// The 11-moment real-space product (Sec. 2.2.1 rigid-particle relation): rows of 12
+// slots, [F(3), L(3), s(5), -] in and [U(3), Omega(3), e(5), -] out.  Per pair, the
+// 8 x 8 force-stresslet terms of k_real plus the rotation couplings
+//   U += gF rh x L,   Omega += gF rh x F + gL1 L + gL2 (rh.L) rh + 2 gL2 (S rh) x rh,
+//   e += gL2 symY(rh x L, rh)
+// (gF, gL1, gL2 the rotation scalars); self terms self_uf, self_ol, self_es.  G lanes
+// per particle walk its neighbour records, neighbours' rows from the cell-ordered copy.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_real11(RealArgs a, const SysDev *__restrict__ sys,
+                                                const int64_t *__restrict__ p0, const int *__restrict__ active,
+                                                int *queue, int nitems, const int *__restrict__ nstart,
+                                                const typename V4<T>::t *__restrict__ geo,
+                                                const T *__restrict__ vin, const T *__restrict__ vcell,
+                                                T *__restrict__ vout, const T *__restrict__ tab,
+                                                const T *__restrict__ rtab, T self_ol) {
+  using T4 = typename V4<T>::t;
+  for_each_item(queue, nitems, [&](int item) {
+    const int64_t gid = ((int64_t)item * 256 + threadIdx.x) / G;
+    const int sub = threadIdx.x % G;
+    const int64_t i = gid < a.Ntot ? gid : a.Ntot - 1;
+    const int si = find_sys(p0, a.nsys, i);
+    const bool live = gid < a.Ntot && active[si];
+    const SysDev &sd = sys[si];
+    T o[11];
+#pragma unroll
+    for (int m = 0; m < 11; ++m) o[m] = 0;
+    const int64_t k0 = sd.nbr0 + (i - sd.p0) * sd.slots;
+    const int cnt = live ? min(nstart[i], sd.slots) : 0;
+    for (int n = sub; n < cnt; n += G) {
+      const T4 gg = geo[k0 + n];
+      const int j = real_as_index<T>(gg.w);
+      const T r2 = gg.x * gg.x + gg.y * gg.y + gg.z * gg.z;
+      const T ir = sizeof(T) == 4 ? (T)rsqrtf((float)r2) : (T)1 / sqrt(r2), r = r2 * ir;
+      const T rh[3] = {gg.x * ir, gg.y * ir, gg.z * ir};
+      T f[7], gr[3];
+      lookup<false, M_FULL>(tab, a, r, f);
+      rot_lookup(rtab, a, r, gr);
+      const T *row = vcell + 12 * (size_t)j;
+      const T F[3] = {row[0], row[1], row[2]}, Lv[3] = {row[3], row[4], row[5]};
+      const T s[5] = {row[6], row[7], row[8], row[9], row[10]};
+      T v[3];
+      Smul(s, rh, v);
+      const T q = rh[0] * v[0] + rh[1] * v[1] + rh[2] * v[2];
+      const T rf = rh[0] * F[0] + rh[1] * F[1] + rh[2] * F[2];
+      const T rl = rh[0] * Lv[0] + rh[1] * Lv[1] + rh[2] * Lv[2];
+      const T rxL[3] = {rh[1] * Lv[2] - rh[2] * Lv[1], rh[2] * Lv[0] - rh[0] * Lv[2], rh[0] * Lv[1] - rh[1] * Lv[0]};
+      const T rxF[3] = {rh[1] * F[2] - rh[2] * F[1], rh[2] * F[0] - rh[0] * F[2], rh[0] * F[1] - rh[1] * F[0]};
+      const T vxr[3] = {v[1] * rh[2] - v[2] * rh[1], v[2] * rh[0] - v[0] * rh[2], v[0] * rh[1] - v[1] * rh[0]};
+      const T cu = f[3] * q + (f[1] - f[0]) * rf;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        o[m] += f[2] * v[m] + f[0] * F[m] + cu * rh[m] + gr[0] * rxL[m];
+        o[3 + m] += gr[0] * rxF[m] + gr[1] * Lv[m] + gr[2] * rl * rh[m] + (T)2 * gr[2] * vxr[m];
+      }
+      T pv[3], sy[5], yr[5], yl[5];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) pv[m] = f[5] * v[m] - (T)0.5 * f[2] * F[m];
+      symY(pv, rh, sy);
+      symY(rh, rh, yr);
+      symY(rxL, rh, yl);
+      const T cy = (T)0.5 * (f[6] * q - f[3] * rf);
+#pragma unroll
+      for (int m = 0; m < 5; ++m) o[6 + m] += f[4] * s[m] + sy[m] + cy * yr[m] + gr[2] * yl[m];
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int m = 0; m < 11; ++m) o[m] += __shfl_xor_sync(0xffffffffu, o[m], off, G);
+    if (live && sub == 0) {
+      const T *me = vin + 12 * (size_t)i;
+      T *out = vout + 12 * (size_t)i;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        out[m] = o[m] + (T)a.self_uf * me[m];
+        out[3 + m] = o[3 + m] + self_ol * me[3 + m];
+      }
+#pragma unroll
+      for (int m = 0; m < 5; ++m) out[6 + m] = o[6 + m] + (T)a.self_es * me[6 + m];
+      out[11] = 0;
+    }
+  });
+}
+
+// vcell12[k] = vin12[list[k]] (12-real rows).
+template <typename T>
+__global__ void k_cell_gather12(int64_t N, const int *__restrict__ list, const T *__restrict__ vin,
+                                T *__restrict__ vcell) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 12 * N) return;
+  const int64_t k = e / 12;
+  vcell[e] = vin[12 * (int64_t)list[k] + (e - 12 * k)];
+}
+
 // vcell[k] = vin[list[k]]: the 8-real rows of the input vector in cell-list order.
 template <typename T>
 __global__ void k_cell_gather(int64_t N, const int *__restrict__ list, const typename V4<T>::t *__restrict__ vin,
@@ -342,6 +463,46 @@ pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStr
     k_cell_gather<double><<<nb, 256, 0, s>>>(c->p.N, c->d_cell_list, (const double4_32a *)vin,
                                              (double4_32a *)c->d_vcell);
     launch_real<double>(c, a, vin, vout, mode, s);
+  }
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+// vout12 = M_r vin12 for the 11-moment form (12-slot rows, sorted order).
+pse_status real_apply11(pse_ctx *c, const void *vin12, void *vout12, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_REAL, s);
+  c->nlaunch += 2;
+  RealArgs a;
+  a.Ntot = c->p.N;
+  a.nsys = c->nsys;
+  a.len = c->table_len;
+  a.k2 = c->table_k2;
+  a.inv_dr = 1.0 / c->table_dr;
+  a.self_uf = c->self_uf;
+  a.self_es = c->self_es;
+  constexpr int G = 4;
+  const int64_t items = ceil_div(a.Ntot * G, 256);
+  const unsigned ng = (unsigned)ceil_div(12 * c->p.N, 256);
+  int *q = next_queue(c, s);
+  if (c->prec == PSE_MIXED) {
+    static std::atomic<int> per_sm{0};
+    k_cell_gather12<float><<<ng, 256, 0, s>>>(c->p.N, c->d_cell_list, (const float *)vin12, (float *)c->d_vcell12);
+    auto kern = k_real11<float, G>;
+    const unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
+    kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
+                              (const float4 *)c->d_nbr_geo, (const float *)vin12, (const float *)c->d_vcell12,
+                              (float *)vout12, (const float *)c->d_table, (const float *)c->d_table_rot,
+                              (float)c->self_ol);
+  } else {
+    static std::atomic<int> per_sm{0};
+    k_cell_gather12<double><<<ng, 256, 0, s>>>(c->p.N, c->d_cell_list, (const double *)vin12,
+                                               (double *)c->d_vcell12);
+    auto kern = k_real11<double, G>;
+    const unsigned grid = persistent_grid(c, kern, 256, 0, items, per_sm);
+    kern<<<grid, 256, 0, s>>>(a, c->d_sys, c->d_p0, c->d_active, q, (int)items, c->d_nbr_start,
+                              (const double4_32a *)c->d_nbr_geo, (const double *)vin12,
+                              (const double *)c->d_vcell12, (double *)vout12, (const double *)c->d_table,
+                              (const double *)c->d_table_rot, c->self_ol);
   }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;

@@ -39,6 +39,34 @@ __global__ void k_scatter_out(int64_t N, const int *perm, const T *in, T *U, T *
     for (int m = 0; m < 5; ++m) E[5 * (size_t)u + m] = scale * v[3 + m];
 }
 
+// 12-slot sorted rows [F(3), L(3), S(5), 0] from user-order arrays (any may be NULL: zero).
+template <typename T>
+__global__ void k_gather12(int64_t N, const int *perm, const T *F, const T *L, const T *S, T *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t u = perm[i];
+  T *o = out + 12 * (size_t)i;
+  for (int m = 0; m < 3; ++m) o[m] = F ? F[3 * u + m] : (T)0;
+  for (int m = 0; m < 3; ++m) o[3 + m] = L ? L[3 * u + m] : (T)0;
+  for (int m = 0; m < 5; ++m) o[6 + m] = S ? S[5 * u + m] : (T)0;
+  o[11] = (T)0;
+}
+
+// user-order U, Omega, E (any may be NULL: not written) from 12-slot sorted rows.
+template <typename T>
+__global__ void k_scatter12(int64_t N, const int *perm, const T *in, T *U, T *Om, T *E) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t u = perm[i];
+  const T *v = in + 12 * (size_t)i;
+  if (U)
+    for (int m = 0; m < 3; ++m) U[3 * u + m] = v[m];
+  if (Om)
+    for (int m = 0; m < 3; ++m) Om[3 * u + m] = v[3 + m];
+  if (E)
+    for (int m = 0; m < 5; ++m) E[5 * u + m] = v[6 + m];
+}
+
 template <typename T>
 __global__ void k_gather8(int64_t N, const int *perm, const T *in, T *out) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -455,6 +483,26 @@ pse_status gather_in(pse_ctx *c, const void *F, const void *S, void *vout, cudaS
   int64_t N = c->p.N;
   DISPATCH(c, (k_gather_in<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)F, (const float *)S, (float *)vout)),
            (k_gather_in<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)F, (const double *)S, (double *)vout)));
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status gather12(pse_ctx *c, const void *F, const void *L, const void *S, void *vout, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_gather12<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)F, (const float *)L, (const float *)S, (float *)vout)),
+           (k_gather12<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)F, (const double *)L, (const double *)S, (double *)vout)));
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
+pse_status scatter12(pse_ctx *c, const void *vin, void *U, void *Om, void *E, cudaStream_t s) {
+  StageTimer timer(c, PSE_STAGE_VECTOR, s);
+  c->nlaunch += 1;
+  int64_t N = c->p.N;
+  DISPATCH(c, (k_scatter12<float><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const float *)vin, (float *)U, (float *)Om, (float *)E)),
+           (k_scatter12<double><<<grid_for(N), 256, 0, s>>>(N, c->d_perm, (const double *)vin, (double *)U, (double *)Om, (double *)E)));
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

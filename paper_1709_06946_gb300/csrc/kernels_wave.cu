@@ -217,6 +217,92 @@ __global__ void k_scale(ScaleArgs sa, typename Cx<T>::t *g_all) {
   }
 }
 
+// P^+ B P of the 11-moment product at every half-spectrum point (Sec. 2.3.2, the
+// paper's 11 grids): grids 0..2 F, 3..5 L, 6..10 S in, 0..2 U, 3..5 Omega, 6..10 E
+// out.  With the torque in the couplet as sum_k L_k A_k (A_k = -eps_k/2),
+// f = s0 F - 3i s1 S.k + (3i/2) s1 k x L, u = c (I - kk) f, U = s0 u, and from
+// D = 3i s1 u k^T: Omega = A : D = -(3i/2) s1 u x k, e = Y : D = (3i s1/2) symY(u, k).
+template <typename T>
+__global__ void k_scale11(ScaleArgs sa, typename Cx<T>::t *g_all) {
+  using C2 = typename Cx<T>::t;
+  const int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gidx >= sa.nk_tot) return;
+  const int sidx = find_sys(sa.k0, sa.nsys, gidx);
+  if (!sa.active[sidx]) return;
+  const SysDev &s = sa.sys[sidx];
+  const size_t idx = (size_t)(gidx - s.k0);
+  C2 *g = g_all + s.cgrid0;
+  const size_t cs = s.cstride;
+  int ix, iy, iz;
+  const bool live = kvector(s, idx, ix, iy, iz);
+  C2 o[11];
+#pragma unroll
+  for (int m = 0; m < 11; ++m) o[m].x = o[m].y = (T)0;
+  if (live) {
+    const int h = s.Ng / 2;
+    T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - s.Ng) * s.kfac), (T)((iz <= h ? iz : iz - s.Ng) * s.kfac)};
+    const T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const T kk = sqrt(k2), ik = (T)1 / kk;
+    T s0, s1;
+    shape<T>(kk * (T)sa.a, s0, s1);
+    const T u = k2 * (T)sa.q4;
+    const T c = (T)s.c_apply * ((T)1 + u) * exp(-((T)1 - (T)s.eta_g) * u) / k2;
+    T fr[3], fi[3], Lr[3], Li[3], sr[5], si[5];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const C2 F = g[m * cs + idx], Lv = g[(3 + m) * cs + idx];
+      fr[m] = s0 * F.x;
+      fi[m] = s0 * F.y;
+      Lr[m] = Lv.x;
+      Li[m] = Lv.y;
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const C2 v = g[(6 + m) * cs + idx];
+      sr[m] = v.x;
+      si[m] = v.y;
+    }
+    T skr[3], ski[3];
+    Smul(sr, k, skr);
+    Smul(si, k, ski);
+    const T t3 = (T)3 * s1, t15 = (T)1.5 * s1;
+    const T kLr[3] = {k[1] * Lr[2] - k[2] * Lr[1], k[2] * Lr[0] - k[0] * Lr[2], k[0] * Lr[1] - k[1] * Lr[0]};
+    const T kLi[3] = {k[1] * Li[2] - k[2] * Li[1], k[2] * Li[0] - k[0] * Li[2], k[0] * Li[1] - k[1] * Li[0]};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {  // f = s0 F - 3i s1 S.k + (3i/2) s1 k x L
+      fr[m] += t3 * ski[m] - t15 * kLi[m];
+      fi[m] += -t3 * skr[m] + t15 * kLr[m];
+    }
+    const T kh[3] = {k[0] * ik, k[1] * ik, k[2] * ik};
+    const T pr = kh[0] * fr[0] + kh[1] * fr[1] + kh[2] * fr[2], pi = kh[0] * fi[0] + kh[1] * fi[1] + kh[2] * fi[2];
+    T ur[3], ui[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      ur[m] = c * (fr[m] - kh[m] * pr);
+      ui[m] = c * (fi[m] - kh[m] * pi);
+    }
+    const T ukr[3] = {ur[1] * k[2] - ur[2] * k[1], ur[2] * k[0] - ur[0] * k[2], ur[0] * k[1] - ur[1] * k[0]};
+    const T uki[3] = {ui[1] * k[2] - ui[2] * k[1], ui[2] * k[0] - ui[0] * k[2], ui[0] * k[1] - ui[1] * k[0]};
+    T er[5], ei[5];
+    symY(ur, k, er);
+    symY(ui, k, ei);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      o[m].x = s0 * ur[m];
+      o[m].y = s0 * ui[m];
+      o[3 + m].x = t15 * uki[m];   // Omega = -(3i/2) s1 u x k
+      o[3 + m].y = -t15 * ukr[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      o[6 + m].x = -t15 * ei[m];
+      o[6 + m].y = t15 * er[m];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 11; ++m) g[m * cs + idx] = o[m];
+}
+
 // Wave-space noise: dW2 on the half spectrum (Hermitian partners on kx = 0),
 // u = sigma e^{eta_g k^2/8xi^2} sqrt(H/(eta V k^2)) (I - kk) dW2, then P^+.
 template <typename T, bool EXT>
@@ -377,7 +463,37 @@ pse_status wave_noise_t(pse_ctx *c, const void *w2, uint64_t seed, uint64_t coun
   return PSE_OK;
 }
 
+template <typename T>
+pse_status wave_apply11_t(pse_ctx *c, const void *vin12, void *vout12, bool add, cudaStream_t s) {
+  if (!add) PSE_CUDA_TRY(c, cudaMemsetAsync(vout12, 0, sizeof(T) * 12 * (size_t)c->p.N, s));
+  {
+    StageTimer timer(c, PSE_STAGE_SPREAD, s);
+    spread11_launch(c, vin12, s);
+  }
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  PSE_TRY(fft<T>(c, true, 11, s));
+  ScaleArgs sa = scale_args(c);
+  {
+    StageTimer timer(c, PSE_STAGE_SCALE, s);
+    c->nlaunch += 1;
+    k_scale11<T><<<(unsigned)ceil_div(c->nk_tot, 256), 256, 0, s>>>(sa, (typename Cx<T>::t *)c->d_cgrid);
+  }
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  PSE_TRY(fft<T>(c, false, 11, s));
+  {
+    StageTimer timer(c, PSE_STAGE_INTERP, s);
+    interp11_launch(c, vout12, s);
+  }
+  PSE_CUDA_TRY(c, cudaGetLastError());
+  return PSE_OK;
+}
+
 }  // namespace
+
+pse_status wave_apply11(pse_ctx *c, const void *vin12, void *vout12, bool add, cudaStream_t s) {
+  return c->prec == PSE_MIXED ? wave_apply11_t<float>(c, vin12, vout12, add, s)
+                              : wave_apply11_t<double>(c, vin12, vout12, add, s);
+}
 
 WaveArgs wave_args(const pse_ctx *c) {
   WaveArgs a;

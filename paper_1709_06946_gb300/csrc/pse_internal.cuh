@@ -52,6 +52,16 @@ void fill_real_table_f32(const Params &p, int points_per_2a, int len, float *out
                          double *self_es);
 // Direct evaluation of the 7 functions at r > 0 (host, FP64); used for the table and tests.
 void real_functions(const Params &p, double r, double out[7]);
+// The three scalars of the rotation couplings of the 11-moment form at r > 0:
+// out[0] = Phi_ab'/(2 eta) (Omega from F: out[0] rh x F; U from L: out[0] rh x L),
+// out[1] = -(Phi_bb'' + Phi_bb'/r)/(4 eta), out[2] = (Phi_bb'' - Phi_bb'/r)/(4 eta)
+// (Omega from L: out[1] L + out[2] (rh.L) rh; Omega from S: 2 out[2] (S rh) x rh;
+// E from L: out[2] symY(rh x L, rh)).
+void rot_functions(const Params &p, double r, double out[3]);
+// Table of the rotation scalars, 4 reals per node (the three, then 0), len nodes of
+// spacing 2a / points_per_2a from r = 0 (where the values are the r -> 0 limits:
+// 0, the rotation self mobility U_bb^(5)(0)/(6 eta), 0).
+void build_rot_table(const Params &p, int points_per_2a, int len, std::vector<double> &v, double *self_ol);
 
 // Small dense algebra on the host (FP64).
 // Symmetric tridiagonal eigen-decomposition (implicit QL, Wilkinson shifts).
@@ -102,8 +112,8 @@ struct FftGroup {
   int Ng = 0, nsys = 0;
   std::vector<int> members;           // suspensions of the group, in slot order
   int64_t grid0 = 0, cgrid0 = 0;
-  cufftHandle r2c[9] = {0}, c2r[9] = {0};  // indexed by components per suspension
-  bool ok[2][9] = {{false}};
+  cufftHandle r2c[12] = {0}, c2r[12] = {0};  // indexed by components per suspension
+  bool ok[2][12] = {{false}};
 };
 
 constexpr int VEC_CHUNK = 16384;   // vector elements per block of the chunked vector kernels
@@ -183,6 +193,9 @@ struct pse_ctx {
   int *d_cell_list = nullptr;
   void *d_vcell = nullptr;     // the input vector of a real-space product in cell-list order (8N reals)
   void *d_rfd = nullptr;       // RFD step work space (4 x 8N reals, user order), allocated on first use
+  // 11-moment product (option torque): rotation table (4 reals per node), 12-slot vectors
+  void *d_table_rot = nullptr, *d_v12[2] = {nullptr, nullptr}, *d_vcell12 = nullptr;
+  double self_ol = 0;
   void *d_rs_cell = nullptr;   // records of d_rs in cell-list order
   int *d_nbr_start = nullptr;   // neighbour counts (N + 1 ints)
   void *d_nbr_geo = nullptr;    // neighbour slots, particle i of suspension s owning nbr0 + (i - p0) slots ...:
@@ -217,8 +230,8 @@ struct pse_ctx {
   bool h2d_pending = false;     // a host-to-device copy from pinned staging may still be queued
 
   double *d_pos0 = nullptr, *d_posh = nullptr;  // FP64 positions, user order
-  void *d_stage[6] = {nullptr}; // staging for host arrays
-  size_t stage_bytes[6] = {0};
+  void *d_stage[8] = {nullptr}; // staging for host arrays
+  size_t stage_bytes[8] = {0};
   int *d_nrows = nullptr;       // per suspension: vectors in the final Krylov combination
   pse::KDev kd{};               // Krylov control state (device arrays)
   int *h_flag = nullptr;        // pinned copy of kd.flag and kd.active
@@ -320,6 +333,9 @@ pse_status real_apply(pse_ctx *c, const void *vin, void *vout, int mode, cudaStr
 // Harmonic overlap force of the current configuration into F (user order, N x 3).
 pse_status overlap_force(pse_ctx *c, double kspring, void *F, cudaStream_t s);
 pse_status wave_apply(pse_ctx *c, const void *vin, void *vout, int mode, bool add, cudaStream_t s);
+// 11-moment product (option torque): 12-slot rows [F, L, S] -> [U, Omega, E], sorted order
+pse_status wave_apply11(pse_ctx *c, const void *vin12, void *vout12, bool add, cudaStream_t s);
+pse_status real_apply11(pse_ctx *c, const void *vin12, void *vout12, cudaStream_t s);
 pse_status wave_noise(pse_ctx *c, const void *w2, uint64_t seed, uint64_t counter, void *vout,
                       cudaStream_t s);
 // mode flags for real/wave products
@@ -349,6 +365,8 @@ pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const 
                         double dt, double *xout, cudaStream_t s);
 pse_status check_finite(pse_ctx *c, const void *ptr, int64_t n, bool dbl, int *bad, cudaStream_t s);
 pse_status rfd_noise(pse_ctx *c, const void *wt, uint64_t seed, uint64_t counter, void *W8, cudaStream_t s);
+pse_status gather12(pse_ctx *c, const void *F, const void *L, const void *S, void *vout, cudaStream_t s);
+pse_status scatter12(pse_ctx *c, const void *vin, void *U, void *Om, void *E, cudaStream_t s);
 pse_status rfd_final(pse_ctx *c, const double *x0, const void *B, const void *U0, const void *Rp, const void *Rm,
                      double dt, double fac, double *xout, cudaStream_t s);
 // Krylov control kernels (krylov_dev.cu); handle = 0 and graph = 0 outside a graph.

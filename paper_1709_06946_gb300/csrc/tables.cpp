@@ -324,6 +324,48 @@ void real_functions(const Params &p, double r, double out[7]) {
   out[6] = -(Dp(2) - 3 * D(2) / r) / eta;                               // kR
 }
 
+void rot_functions(const Params &p, double r, double out[3]) {
+  static const GL gl(40);
+  const double a = p.a, xi = p.xi, eta = p.eta;
+  // Phi = V/r, V = -U'' for the shell*ball (k = 1) and ball*ball (k = 2) convolutions
+  double U[3][5];
+  for (int k = 1; k < 3; ++k)
+    for (int n = 2; n < 5; ++n) U[k][n] = conv(gl, k, n, r, xi, a);
+  const double r2 = r * r, r3 = r2 * r;
+  double Phi1[3], Phi2[3];
+  for (int k = 1; k < 3; ++k) {
+    const double V0 = -U[k][2], V1 = -U[k][3], V2 = -U[k][4];
+    Phi1[k] = V1 / r - V0 / r2;
+    Phi2[k] = V2 / r - 2 * V1 / r2 + 2 * V0 / r3;
+  }
+  out[0] = Phi1[1] / (2 * eta);
+  out[1] = -(Phi2[2] + Phi1[2] / r) / (4 * eta);
+  out[2] = (Phi2[2] - Phi1[2] / r) / (4 * eta);
+}
+
+void build_rot_table(const Params &p, int points_per_2a, int len, std::vector<double> &v, double *self_ol) {
+  static const GL gl(40);
+  const double dr = 2.0 * p.a / points_per_2a;
+  const double sol = conv(gl, 2, 5, 0.0, p.xi, p.a) / (6.0 * p.eta);
+  v.assign((size_t)len * 4, 0.0);
+  const double z[3] = {0.0, sol, 0.0};
+  const int ismall = (int)std::ceil(0.05 * p.a / dr);
+  double f[3], fs[3] = {0, 0, 0};
+  rot_functions(p, ismall * dr, fs);
+  for (int i = 0; i < len; ++i) {
+    if (i == 0) {
+      for (int q = 0; q < 3; ++q) f[q] = z[q];
+    } else if (i < ismall) {  // below 0.05a the formulas cancel badly: interpolate to the r -> 0 limit
+      const double w = (double)i / ismall;
+      for (int q = 0; q < 3; ++q) f[q] = (1 - w) * z[q] + w * fs[q];
+    } else {
+      rot_functions(p, i * dr, f);
+    }
+    for (int q = 0; q < 3; ++q) v[(size_t)i * 4 + q] = f[q];
+  }
+  *self_ol = sol;
+}
+
 void build_real_table(const Params &p, int points_per_2a, RealTable &t) {
   static const GL gl(40);
   t.dr = 2.0 * p.a / points_per_2a;

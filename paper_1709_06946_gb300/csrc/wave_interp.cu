@@ -20,7 +20,8 @@ __device__ __forceinline__ void add_out(T *dst, T v) {
 
 // NT threads per CTA: 1024 for 8 components (whose tile leaves room for one CTA
 // per SM), 512 otherwise.
-template <typename T, int C, int SLOT0, int PT, int NT>
+// ROW: slots per particle row of vout; COMP0: first grid component read
+template <typename T, int C, int SLOT0, int PT, int NT, int ROW = 8, int COMP0 = 0>
 __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
                                                const typename V4<T>::t *__restrict__ sp_d0,
                                                const int *__restrict__ tile_start, const T *__restrict__ grid_all,
@@ -54,7 +55,7 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
       size_t g = ((size_t)(t0[2] + z) * Ng + (t0[1] + y)) * Ng + (t0[0] + x);
       T v[C];
 #pragma unroll
-      for (int c = 0; c < C; ++c) v[c] = grid[c * a.gstride + g];
+      for (int c = 0; c < C; ++c) v[c] = grid[(COMP0 + c) * a.gstride + g];
       tl.store((z * Ty + y) * RX + x, v);
     }
     __syncthreads();
@@ -180,19 +181,19 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
         }
         const T tot = warp_reduce8(acc, lane);
         const int comp = reduce8_component(lane);
-        if ((lane & 3) == 0 && comp < C) add_out(vout + 8 * (size_t)ke + SLOT0 + comp, pref * tot);
+        if ((lane & 3) == 0 && comp < C) add_out(vout + ROW * (size_t)ke + SLOT0 + comp, pref * tot);
       }
     }
     __syncthreads();  // the staged tile is no longer read when the next item overwrites it
   });
 }
 
-template <typename T, int C, int SLOT0, int PT>
+template <typename T, int C, int SLOT0, int PT, int ROW = 8, int COMP0 = 0>
 void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   static std::once_flag once;
   static OccCache occ;
   constexpr int NT = C == 8 ? 1024 : WAVE_THREADS;
-  auto kern = k_interp<T, C, SLOT0, PT, NT>;
+  auto kern = k_interp<T, C, SLOT0, PT, NT, ROW, COMP0>;
   set_smem(kern, once);
   size_t sm = wave_smem_max<T, C>(c, a.want);
   unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ, NT);
@@ -201,13 +202,13 @@ void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
                             c->d_tile_start, (const T *)c->d_grid, (T *)vout);
 }
 
-template <typename T, int C, int SLOT0>
+template <typename T, int C, int SLOT0, int ROW = 8, int COMP0 = 0>
 void interp_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   switch (a.P) {
-    case 5: launch_interp<T, C, SLOT0, 5>(c, a, vout, s); break;
-    case 6: launch_interp<T, C, SLOT0, 6>(c, a, vout, s); break;
-    case 8: launch_interp<T, C, SLOT0, 8>(c, a, vout, s); break;
-    default: launch_interp<T, C, SLOT0, 0>(c, a, vout, s);
+    case 5: launch_interp<T, C, SLOT0, 5, ROW, COMP0>(c, a, vout, s); break;
+    case 6: launch_interp<T, C, SLOT0, 6, ROW, COMP0>(c, a, vout, s); break;
+    case 8: launch_interp<T, C, SLOT0, 8, ROW, COMP0>(c, a, vout, s); break;
+    default: launch_interp<T, C, SLOT0, 0, ROW, COMP0>(c, a, vout, s);
   }
 }
 
@@ -240,6 +241,20 @@ void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStre
     else if (mode == M_SE) interp_p<double, 5, 3>(c, ag, vout, s);
     else interp_p<double, 3, 0>(c, ag, vout, s);
   }
+}
+
+// Grids 0..10 interpolated into the 11 components [U, Omega, E] of 12-slot rows
+// (general kernels, two passes: 8 and 3 components; outputs are added).
+void interp11_launch(pse_ctx *c, void *vout12, cudaStream_t s) {
+  WaveArgs a = wave_args(c);
+  if (c->prec == PSE_MIXED) {
+    interp_p<float, 8, 0, 12, 0>(c, a, vout12, s);
+    interp_p<float, 3, 8, 12, 8>(c, a, vout12, s);
+  } else {
+    interp_p<double, 8, 0, 12, 0>(c, a, vout12, s);
+    interp_p<double, 3, 8, 12, 8>(c, a, vout12, s);
+  }
+  c->nlaunch += 4;
 }
 
 }  // namespace pse

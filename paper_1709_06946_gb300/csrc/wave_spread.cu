@@ -15,10 +15,11 @@
 namespace pse {
 namespace {
 
-// moments [SLOT0, SLOT0 + C) of particle k (an 8-slot row), read by the whole warp
-template <typename T, int C, int SLOT0>
+// moments [SLOT0, SLOT0 + C) of particle k (a ROW-slot row: 8, or 12 in the
+// 11-moment product), read by the whole warp
+template <typename T, int C, int SLOT0, int ROW = 8>
 __device__ __forceinline__ void load_moments(const T *__restrict__ vin, int k, T mv[C]) {
-  const T *row = vin + 8 * (size_t)k;
+  const T *row = vin + ROW * (size_t)k;
   if (sizeof(T) == 4 && SLOT0 == 3 && C == 5) {
     mv[0] = row[3];
     const float4 q = *(const float4 *)(row + 4);
@@ -42,7 +43,8 @@ __device__ __forceinline__ void load_moments(const T *__restrict__ vin, int k, T
   }
 }
 
-template <typename T, int C, int SLOT0, int PT>
+// ROW: slots per particle row of vin; COMP0: first grid component written
+template <typename T, int C, int SLOT0, int PT, int ROW = 8, int COMP0 = 0>
 __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0,
                                                          const typename V4<T>::t *__restrict__ sp_d0,
                                                          const T *__restrict__ vin, const int *__restrict__ fine_start,
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
           ey += ey < 0 ? Ng : 0;
           const T4 d0 = sp_d0[ke];
           T mv[C];
-          load_moments<T, C, SLOT0>(vin, ke, mv);
+          load_moments<T, C, SLOT0, ROW>(vin, ke, mv);
           if (PT > 0) {
             const T wl = lane_weight(lane, PZ, alpha, hs, d0);
             const T wz = pref * __shfl_sync(0xffffffffu, wl, 2 * PZ + ez);
@@ -164,17 +166,17 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
       T v[C];
       tl.load((z * Ty + y) * RX + x, v);
 #pragma unroll
-      for (int c = 0; c < C; ++c) grid[c * a.gstride + g] = v[c];
+      for (int c = 0; c < C; ++c) grid[(COMP0 + c) * a.gstride + g] = v[c];
     }
     __syncthreads();  // the tile is read out before the next item clears it
   });
 }
 
-template <typename T, int C, int SLOT0, int PT>
+template <typename T, int C, int SLOT0, int PT, int ROW = 8, int COMP0 = 0>
 void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
   static std::once_flag once;
   static OccCache occ;
-  auto kern = k_spread<T, C, SLOT0, PT>;
+  auto kern = k_spread<T, C, SLOT0, PT, ROW, COMP0>;
   set_smem(kern, once);
   size_t sm = wave_smem_max<T, C>(c, a.want);
   unsigned grid = wave_grid(c, kern, sm, a.ntiles, occ);
@@ -183,13 +185,13 @@ void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t 
                                       (const T *)vin, c->d_fine_start, (T *)c->d_grid);
 }
 
-template <typename T, int C, int SLOT0>
+template <typename T, int C, int SLOT0, int ROW = 8, int COMP0 = 0>
 void spread_p(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
   switch (a.P) {
-    case 5: launch_spread<T, C, SLOT0, 5>(c, a, vin, s); break;
-    case 6: launch_spread<T, C, SLOT0, 6>(c, a, vin, s); break;
-    case 8: launch_spread<T, C, SLOT0, 8>(c, a, vin, s); break;
-    default: launch_spread<T, C, SLOT0, 0>(c, a, vin, s);
+    case 5: launch_spread<T, C, SLOT0, 5, ROW, COMP0>(c, a, vin, s); break;
+    case 6: launch_spread<T, C, SLOT0, 6, ROW, COMP0>(c, a, vin, s); break;
+    case 8: launch_spread<T, C, SLOT0, 8, ROW, COMP0>(c, a, vin, s); break;
+    default: launch_spread<T, C, SLOT0, 0, ROW, COMP0>(c, a, vin, s);
   }
 }
 
@@ -219,6 +221,20 @@ void spread_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cud
     if (mode == M_SE || mode == M_SU) spread_p<double, 5, 3>(c, ag, vin, s);
     else spread_p<double, 8, 0>(c, ag, vin, s);
   }
+}
+
+// The 11 components [F, L, S] of 12-slot rows onto grids 0..10 of every suspension
+// (general kernels for any tile, two passes: 8 and 3 components).
+void spread11_launch(pse_ctx *c, const void *vin12, cudaStream_t s) {
+  WaveArgs a = wave_args(c);
+  if (c->prec == PSE_MIXED) {
+    spread_p<float, 8, 0, 12, 0>(c, a, vin12, s);
+    spread_p<float, 3, 8, 12, 8>(c, a, vin12, s);
+  } else {
+    spread_p<double, 8, 0, 12, 0>(c, a, vin12, s);
+    spread_p<double, 3, 8, 12, 8>(c, a, vin12, s);
+  }
+  c->nlaunch += 4;
 }
 
 }  // namespace pse
