@@ -66,6 +66,8 @@ def parse():
     ap.add_argument('--serve-seconds', type=float, default=12.0, help='per arrival rate (--workload serve)')
     ap.add_argument('--serve-seconds-default', type=float, default=4.0,
                     help='per arrival rate of the serving sweep in the default line')
+    ap.add_argument('--torque-reps', type=int, default=5,
+                    help='timed 11-moment (torque) products on the workload for the default line (0: omit)')
     ap.add_argument('--eps2', type=float, default=1e-4, help='second PSE tolerance of the default line (0: omit)')
     ap.add_argument('--rfd-steps', type=int, default=3, help='timed RFD + Euler-Maruyama steps (0: omit)')
     ap.add_argument('--batch-steps', type=int, default=3,
@@ -333,10 +335,11 @@ def kernel_instances(prof, N, Ng, P, npairs, cubic, wave_kernel=0):
     vm, vc = prof['variant_ms'], prof['variant_calls']
     n3 = Ng ** 3
     nkh = Ng * Ng * (Ng // 2 + 1)
-    # kernel names: 16^3 tiles take the grid-column spreading and the shared-tile interpolation by
-    # default (wave_kernel bits 0 / 1 swap each), other tiles the general kernels
+    # kernel names: 16^3 tiles take the grid-column spreading and the staged-region interpolation
+    # by default (wave_kernel bit 0: shared-tile spreading; bit 1: column, bit 4: tile-owned
+    # interpolation), other tiles the general kernels
     ts = ('16' if wave_kernel & 1 else '_col') if cubic else ''
-    ti = ('_col' if wave_kernel & 2 else '16') if cubic else ''
+    ti = ('_col' if wave_kernel & 2 else ('16' if wave_kernel & 16 else '_halo')) if cubic else ''
     fl = real_flops_per_pair()
     spec = [('spread', 'k_spread%s<C=8,P=%d>' % (ts, P), ('full', 'fsu'), N * (16 + 32) + 32 * n3),
             ('spread', 'k_spread%s<C=5,P=%d>' % (ts, P), ('se', 'su'), N * (16 + 20) + 20 * n3),
@@ -560,6 +563,8 @@ def run_ours(args, world, rank, local, pg):
         h64.close()
     if rank == 0 and world == 1 and args.rfd_steps > 0:
         result['rfd'] = rfd_measure(pkg, torch, dev, args, pos_np, L, value)
+    if rank == 0 and world == 1 and args.torque_reps > 0:
+        result['torque'] = torque_measure(pkg, torch, dev, args, pos_np, L, args.torque_reps)
     if rank == 0 and world == 1 and args.eps2 > 0:
         result['eps_%g' % args.eps2] = eps_measure(pkg, torch, dev, args, pos_np, L, args.eps2)
     if rank == 0 and world == 1 and args.batch_steps > 0:
@@ -799,6 +804,38 @@ def rfd_measure(pkg, torch, dev, args, pos_np, L, midpoint_rate):
             'midpoint_speedup': midpoint_rate * t,
             'note': 'Euler-Maruyama with random-finite-difference drift (3 stresslet solves per step, host-launched) '
                     'against the graph-captured mid-point step (1 solve)'}
+
+
+def torque_measure(pkg, torch, dev, args, pos_np, L, reps, warmup=2):
+    """The 11-moment product [U; Omega; E] = M [F; L; S] (forces, torques, stresslets) on the
+    workload's positions, mixed precision, against the 8-moment product [U; E] = M [F; S] of
+    the same handle; each timed with CUDA events over `reps` calls."""
+    stream = torch.cuda.current_stream(dev)
+    h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', torque=1,
+                wave_kernel=args.wave_kernel)
+    x = torch.tensor(pos_np, device=dev, dtype=torch.float64)
+    g = torch.Generator(device=dev).manual_seed(5)
+    F = torch.randn((args.N, 3), device=dev, generator=g)
+    Lt = torch.randn((args.N, 3), device=dev, generator=g)
+    S = torch.randn((args.N, 5), device=dev, generator=g)
+    out = {}
+    for name, call in (('eleven', lambda: h.mobility11(x, F, Lt, S)), ('eight', lambda: h.mobility(x, F, S))):
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            call()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        out[name] = ev0.elapsed_time(ev1) / reps
+    h.close()
+    return {'ms_per_product': out['eleven'], 'ms_per_product_8': out['eight'],
+            'ratio_11_over_8': out['eleven'] / out['eight'], 'reps': reps,
+            'note': '11-moment product (11 grids, rotation couplings in the pair sum) and the 8-moment '
+                    'product of the same handle; each call includes the cell and neighbour lists'}
 
 
 def eps_measure(pkg, torch, dev, args, pos_np, L, tol, steps=5, warmup=2, fp64_steps=1):

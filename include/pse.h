@@ -99,9 +99,11 @@ typedef struct pse_options {
                               Krylov loops as conditional while nodes; 0 = launches from the host */
   int32_t wave_kernel;     /* kernels for 16^3 tiles (mixed precision), bit mask.  0 (default): spreading
                               with the grid columns of a tile held in registers, interpolation with the
-                              tile in shared memory (the faster of each, measured).  Bit 0 set:
-                              spreading with the tile in shared memory; bit 1 set: interpolation with
-                              the grid columns in registers; bit 2 set: in the register-column
+                              whole support region of a z-layer of a tile staged in shared memory (one
+                              read-out per particle, no atomics).  Bit 0 set: spreading with the tile
+                              in shared memory; bit 1 set: interpolation with the grid columns in
+                              registers; bit 4 set: interpolation with the 16^3 tile in shared memory
+                              (a support split over the tiles it meets); bit 2 set: in the register-column
                               spreading every warp scans the candidate particles itself (otherwise
                               the CTA scans them once and hands each warp its hit list); bit 3 set:
                               the 5-component spreading keeps a whole 16-point column per thread

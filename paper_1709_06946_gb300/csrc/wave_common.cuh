@@ -270,6 +270,7 @@ void interp_col_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cuda
 void spread11_launch(pse_ctx *c, const void *vin12, cudaStream_t s);
 void interp11_launch(pse_ctx *c, void *vout12, cudaStream_t s);
 void interp16_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
+void interp_halo_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 
 // Persistent grid of a wave kernel for a given shared-memory size (occupancy
 // looked up once per kernel and size; handles on several threads share the cache).

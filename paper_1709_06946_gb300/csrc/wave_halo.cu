@@ -1,0 +1,168 @@
+// Interpolation sigma Q^T (Sec. 2.3.2, Eq. WSops2) for 16^3 tiles, mixed precision,
+// with the whole support region of a group of particles staged in shared memory.
+//
+// Work item: one z-layer of a tile, i.e. the particles whose support starts lie in
+// the tile and in one of its SUB_SIDE layers of 16/SUB_SIDE planes (one contiguous
+// range of the sort by tile and sub-block).  Their supports lie inside the region
+// [t0x, t0x + 16 + P - 1) x [t0y, t0y + 16 + P - 1) x [z0, z0 + 16/SUB_SIDE + P - 1),
+// which the CTA copies from the grid (periodic wrap) into shared memory in the
+// TileL layout.  Each particle is then read out once and complete by one quarter
+// warp: its 8 lanes take the P x P columns of the support (column l + 8 s on lane
+// l), walk each column along z, and the quarter sums its lanes with three
+// shuffles, so every output row is written by one lane with no atomic addition
+// (the tile-owned kernel splits a support over up to 8 tiles and adds the parts).
+// Two CTAs share an SM (about 83 KB each for 5 components, P = 6), so one CTA's
+// staging overlaps the other's read-out.
+#include "wave_common.cuh"
+
+namespace pse {
+namespace {
+
+constexpr int HALO_THREADS = 512;
+constexpr float HALO_LOG2E = 1.4426950408889634f;  // log2(e): exp(-x) = exp2(-x log2 e)
+constexpr int LAYER = CUBE / SUB_SIDE;  // planes of support starts per work item
+
+template <int P> struct Halo {
+  static constexpr int R = CUBE + P - 1;           // region side along x and y
+  static constexpr int RZ = LAYER + P - 1;         // region depth along z
+  static constexpr int RX = tile_rx(R, P);         // padded row (RX = P mod 8: conflict-free quarter reads)
+  static constexpr int ZS = R * RX;                // plane stride (points)
+  static constexpr int NPT = RZ * ZS;              // points of the staged region
+  static constexpr int NCOL = (P * P + 7) / 8;     // column passes per lane
+};
+
+template <int C, int SLOT0, int P>
+__global__ void __launch_bounds__(HALO_THREADS, 2)
+    k_interp_halo(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0, const float4 *__restrict__ sp_d0,
+                  const int *__restrict__ fine_start, const float *__restrict__ grid_all, float *__restrict__ vout) {
+  using H = Halo<P>;
+  constexpr int R = H::R, RZ = H::RZ, RX = H::RX, ZS = H::ZS;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  TileL<float, C> tl;
+  tl.init(smem_raw, H::NPT);
+  const int lane = threadIdx.x & 31, quarter = lane >> 3, sub = lane & 7, warp = threadIdx.x >> 5;
+  for_each_item(queue, wa.ntiles * SUB_SIDE, [&](int item) {
+    const int tile = item / SUB_SIDE, kz = item % SUB_SIDE;
+    const int si = find_sys(wa.tile0, wa.nsys, tile);
+    const SysDev &a = wa.sys[si];
+    if (wave_skip(wa, si, a)) return;
+    const int Ng = a.Ng;
+    int t[3], t0[3];
+    tile_of(a, tile - a.tile0, t, t0);
+    const int z0 = t0[2] + kz * LAYER;
+    const float *grid = grid_all + a.grid0;
+    // stage the region: UNR points per thread in flight (C loads each)
+    constexpr int NREG = RZ * R * R, UNR = P >= 8 ? 2 : (C <= 3 ? 4 : (C <= 5 ? 3 : 2));
+    for (int q0 = threadIdx.x; q0 < NREG; q0 += UNR * HALO_THREADS) {
+      float vv[UNR][C];
+      int dst[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int q = q0 + u * HALO_THREADS;
+        dst[u] = -1;
+        if (q < NREG) {
+          const int x = q % R, y = (q / R) % R, z = q / (R * R);
+          int gx = t0[0] + x, gy = t0[1] + y, gz = z0 + z;
+          gx -= gx >= Ng ? Ng : 0;
+          gy -= gy >= Ng ? Ng : 0;
+          gz -= gz >= Ng ? Ng : 0;
+          const size_t g = ((size_t)gz * Ng + gy) * Ng + gx;
+#pragma unroll
+          for (int c = 0; c < C; ++c) vv[u][c] = __ldg(grid + c * a.gstride + g);
+          dst[u] = z * ZS + y * RX + x;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+        if (dst[u] >= 0) tl.store(dst[u], vv[u]);
+    }
+    const int64_t fb = (int64_t)tile * SUB_BLOCKS + kz * SUB_SIDE * SUB_SIDE;
+    const int beg = fine_start[fb], end = fine_start[fb + SUB_SIDE * SUB_SIDE];
+    const float nal = -(float)a.alpha * HALO_LOG2E, hs = (float)a.h, pref = (float)a.pref;
+    __syncthreads();  // region staged
+    // four particles per warp per round, one per quarter (warp-uniform loop: the
+    // shuffles below run on all 32 lanes)
+    for (int base = beg + 4 * warp; base < end; base += 4 * (HALO_THREADS / 32)) {
+      const int k = base + quarter;
+      const bool live = k < end;
+      const int ke = live ? k : end - 1;
+      const int4 i0 = sp_i0[ke];
+      const float4 d0 = sp_d0[ke];
+      const int ex = i0.x - t0[0], ey = i0.y - t0[1], ez = i0.z - z0;  // in [0, 16) and [0, LAYER)
+      // 1D weights: lane sub < P holds the x, y and z weights of point sub
+      const float fs = (float)(sub < P ? sub : 0) * hs;
+      const float ox = d0.x + fs, oy = d0.y + fs, oz = d0.z + fs;
+      const float wx = exp2f(nal * ox * ox), wy = exp2f(nal * oy * oy), wzl = exp2f(nal * oz * oz);
+      float wz[P];
+#pragma unroll
+      for (int j = 0; j < P; ++j) wz[j] = __shfl_sync(0xffffffffu, wzl, j, 8);
+      float acc[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = 0.f;
+      const int pb = ez * ZS + ey * RX + ex;
+      constexpr int CU = P >= 8 ? 2 : H::NCOL;  // P = 8: partial unroll (register pressure)
+#pragma unroll CU
+      for (int s = 0; s < H::NCOL; ++s) {
+        // this lane's column (px, py) = (c mod P, c / P) of the support, c = sub + 8 s
+        const int cc = sub + 8 * s, px = cc % P, py = cc < P * P ? cc / P : 0;
+        const float wxy = __shfl_sync(0xffffffffu, wx, px, 8) * __shfl_sync(0xffffffffu, wy, py, 8);
+        if (cc < P * P) {
+          const int col = pb + py * RX + px;
+#pragma unroll
+          for (int jz = 0; jz < P; ++jz) {
+            float vv[C];
+            tl.load(col + jz * ZS, vv);
+            const float w = wxy * wz[jz];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = fmaf(w, vv[c], acc[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+      // lane c of the quarter adds component c
+      float mine = acc[0];
+#pragma unroll
+      for (int c = 1; c < C; ++c) mine = sub == c ? acc[c] : mine;
+      if (live && sub < C) {
+        float *o = vout + 8 * (size_t)k + SLOT0 + sub;
+        *o += pref * mine;
+      }
+    }
+    __syncthreads();  // the region is no longer read when the next item overwrites it
+  });
+}
+
+template <int C, int SLOT0, int P>
+void launch_interp_halo(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
+  static std::once_flag once;
+  static OccCache occ;
+  auto kern = k_interp_halo<C, SLOT0, P>;
+  set_smem(kern, once);
+  const size_t sm = TileL<float, C>::bytes((size_t)Halo<P>::NPT);
+  const unsigned grid = wave_grid(c, kern, sm, a.ntiles * SUB_SIDE, occ, HALO_THREADS);
+  int *q = next_queue(c, s);
+  kern<<<grid, HALO_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const float4 *)c->d_sp_d0, c->d_fine_start,
+                                      (const float *)c->d_grid, (float *)vout);
+}
+
+template <int C, int SLOT0>
+void interp_halo_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
+  switch (a.P) {
+    case 5: launch_interp_halo<C, SLOT0, 5>(c, a, vout, s); break;
+    case 6: launch_interp_halo<C, SLOT0, 6>(c, a, vout, s); break;
+    default: launch_interp_halo<C, SLOT0, 8>(c, a, vout, s);
+  }
+}
+
+}  // namespace
+
+void interp_halo_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
+  if (mode == M_FULL) interp_halo_p<8, 0>(c, a, vout, s);
+  else if (mode == M_SE) interp_halo_p<5, 3>(c, a, vout, s);
+  else interp_halo_p<3, 0>(c, a, vout, s);
+}
+
+}  // namespace pse

@@ -219,7 +219,8 @@ void interp_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
 // in registers (bit 1 of option wave_kernel).
 void interp_cubic(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
   if (c->opt.wave_kernel & 2) interp_col_launch(c, a, vout, mode, s);
-  else interp16_launch(c, a, vout, mode, s);
+  else if (c->opt.wave_kernel & 16) interp16_launch(c, a, vout, mode, s);
+  else interp_halo_launch(c, a, vout, mode, s);
 }
 
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {

@@ -94,8 +94,9 @@ def test_mobility_dense_many_tiles(pkg, prec):
                                          (1e-3, 32, 1500, 0.5)])
 def test_mobility_cubic_tiles(pkg, tol, Ng, N, xi):
     """Mixed precision with 16^3 spreading tiles (the kernels specialised for
-    them: column spreading with shared-tile interpolation by default, and the
-    other form of each with wave_kernel=3) against the oracle and against the general kernels (16 x 8 x
+    them: column spreading with staged-region interpolation by default, shared-tile
+    spreading with column interpolation (wave_kernel=3) and the tile-owned
+    interpolation (wave_kernel=16)) against the oracle and against the general kernels (16 x 8 x
     16 tiles); supports of several sizes, and two tiles per side (N_g = 32: the
     tile below and the tile above are the same).  Full product and the reduced
     products (S -> E, S -> U, [F; S] -> U) whose spreading takes 5 or 8
@@ -106,25 +107,28 @@ def test_mobility_cubic_tiles(pkg, tol, Ng, N, xi):
     h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng)
     assert tuple(h.info['tile']) == (16, 16, 16) and h.info['Ng'] == Ng
     hs = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, wave_kernel=3)
+    ht = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, wave_kernel=16)
     hg = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, tile=(16, 8, 16))
     assert hg.info['Ng'] == h.info['Ng'] and hg.info['P'] == h.info['P']
     p = _oracle_params(h, N, L, xi, tol)
     got = _mob(pkg, h, pos, F, S, 'mixed')
     shared = _mob(pkg, hs, pos, F, S, 'mixed')
+    towned = _mob(pkg, ht, pos, F, S, 'mixed')
     gen = _mob(pkg, hg, pos, F, S, 'mixed')
     Uo, Eo = opse.mobility_apply(pos, F, S, p)
     assert _rel(got, np.concatenate([Uo, Eo], 1)) < TOL['mixed']
-    assert _rel(got, gen) < 5e-6 and _rel(shared, gen) < 5e-6
+    assert _rel(got, gen) < 5e-6 and _rel(shared, gen) < 5e-6 and _rel(towned, gen) < 5e-6
     x, tF, tS = _cuda(pos, torch.float64), _cuda(F, torch.float32), _cuda(S, torch.float32)
     for want, FF in ((('E',), None), (('U',), None), (('U',), tF)):
         Fo = F if FF is not None else 0 * F
         Uo, Eo = opse.mobility_apply(pos, Fo, S, p, parts=('wave',))
-        for hh in (h, hs):
+        for hh in (h, hs, ht):
             U, E = hh.mobility(x, FF, tS, parts='wave', want=want)
             out, ref = (E, Eo) if want == ('E',) else (U, Uo)
             assert _rel(out.double().cpu().numpy(), ref) < TOL['mixed'], (want, FF is None)
     h.close()
     hs.close()
+    ht.close()
     hg.close()
 
 
