@@ -160,7 +160,7 @@ __global__ void k_derive(const SysDev *__restrict__ sys, const int64_t *__restri
 // offsets or positions) in the same order, so that the neighbour search reads
 // contiguous records.
 template <typename T>
-__global__ void k_cell_scatter(int64_t N, const int *cell_key, const int *start, int *cur, int *list,
+__global__ void k_cell_scatter(int64_t N, int *cell_key, const int *start, int *cur, int *list,
                                const typename V4<T>::t *rs, typename V4<T>::t *rs_cell) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -168,6 +168,7 @@ __global__ void k_cell_scatter(int64_t N, const int *cell_key, const int *start,
   const int k = start[ck] + atomicAdd(&cur[ck], 1);
   list[k] = (int)i;
   rs_cell[k] = rs[i];
+  cell_key[i] = k;  // from here on: the particle's own position in the cell list
 }
 
 __device__ __forceinline__ void unpack_cell(float w, int c[3]) {
@@ -205,16 +206,19 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
 // capacity check.  The stencil is 5 x 5 x 5 cells (every cell once when there
 // are fewer than 5 per side); each of its 25 x runs of cells is one range of
 // the cell-ordered records, or two where it wraps, so a thread streams through
-// contiguous records.
-template <typename T>
+// contiguous records, NB of them loaded before the first is tested.  The
+// particle itself is recognised by its own position in the cell list (no read of
+// the list per hit).
+template <typename T, int NB = 4>
 __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0,
                                              int nsys, int64_t Ntot, float rc2f, double rc2, const void *rs,
                                              const void *rs_cell, const int *__restrict__ cell_start,
-                                             const int *__restrict__ cell_list, int *cnt, typename V4<T>::t *geo,
+                                             const int *__restrict__ cell_pos, int *cnt, typename V4<T>::t *geo,
                                              unsigned long long *tot, int *ovf) {
   using T4 = typename V4<T>::t;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= Ntot) return;
+  const int kself = cell_pos[i];  // i's own record in the cell-ordered copy (skipped)
   const int si = find_sys(p0, nsys, i);
   const SysDev &a = sys[si];
   const int nc = a.nc, slots = a.slots;
@@ -274,40 +278,46 @@ __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, con
       }
       for (int part = 0; part < 2; ++part) {
         const int kb = part ? s2 : s1, ke = part ? e2 : e1;
-        for (int k = kb; k < ke; ++k) {
-          T4 rec;
-          bool hit;
-          if (sizeof(T) == 4 && wide) {  // as sep(), with the row's y and z offsets
-            const float4 pj = ((const float4 *)rs_cell)[k];
-            int tx = ci[0] - (__float_as_int(pj.w) & 1023);
-            if (tx > nc / 2) tx -= nc;
-            if (tx < -(nc / 2)) tx += nc;
-            rec.x = tx * a.csf + (pf.x - pj.x);
-            rec.y = offy + (pf.y - pj.y);
-            rec.z = offz + (pf.z - pj.z);
-            hit = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z < rc2f;
-          } else if (sizeof(T) == 4) {
-            const float3 d = sep(pf, ci, ((const float4 *)rs_cell)[k], a);
-            rec.x = d.x;
-            rec.y = d.y;
-            rec.z = d.z;
-            hit = d.x * d.x + d.y * d.y + d.z * d.z < rc2f;
-          } else {
-            const double4_32a qj = ((const double4_32a *)rs_cell)[k];
-            double rx = pd.x - qj.x, ry = pd.y - qj.y, rz = pd.z - qj.z;
-            rx -= a.L * rint(rx / a.L);
-            ry -= a.L * rint(ry / a.L);
-            rz -= a.L * rint(rz / a.L);
-            rec.x = (T)rx;
-            rec.y = (T)ry;
-            rec.z = (T)rz;
-            hit = rx * rx + ry * ry + rz * rz < rc2;
-          }
-          if (hit) {
-            const int j = cell_list[k];
-            if (j != (int)i) {
+        // NB candidate records loaded before any is tested: NB reads in flight per thread
+        for (int k = kb; k < ke; k += NB) {
+          T4 q[NB];
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+            if (k + u < ke) q[u] = ((const T4 *)rs_cell)[k + u];
+#pragma unroll
+          for (int u = 0; u < NB; ++u) {
+            if (k + u >= ke) break;
+            T4 rec;
+            bool hit;
+            if (sizeof(T) == 4 && wide) {  // as sep(), with the row's y and z offsets
+              const float4 pj = *(const float4 *)&q[u];
+              int tx = ci[0] - (__float_as_int(pj.w) & 1023);
+              if (tx > nc / 2) tx -= nc;
+              if (tx < -(nc / 2)) tx += nc;
+              rec.x = tx * a.csf + (pf.x - pj.x);
+              rec.y = offy + (pf.y - pj.y);
+              rec.z = offz + (pf.z - pj.z);
+              hit = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z < rc2f;
+            } else if (sizeof(T) == 4) {
+              const float3 d = sep(pf, ci, *(const float4 *)&q[u], a);
+              rec.x = d.x;
+              rec.y = d.y;
+              rec.z = d.z;
+              hit = d.x * d.x + d.y * d.y + d.z * d.z < rc2f;
+            } else {
+              const double4_32a qj = *(const double4_32a *)&q[u];
+              double rx = pd.x - qj.x, ry = pd.y - qj.y, rz = pd.z - qj.z;
+              rx -= a.L * rint(rx / a.L);
+              ry -= a.L * rint(ry / a.L);
+              rz -= a.L * rint(rz / a.L);
+              rec.x = (T)rx;
+              rec.y = (T)ry;
+              rec.z = (T)rz;
+              hit = rx * rx + ry * ry + rz * rz < rc2;
+            }
+            if (hit && k + u != kself) {
               if (n < slots) {  // separation x_i - x_j and the neighbour's cell-list position in one record
-                rec.w = index_as_real<T>(k);
+                rec.w = index_as_real<T>(k + u);
                 mgeo[n] = rec;
               }
               ++n;
@@ -432,11 +442,11 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
     PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long) * ns, s));
     if (c->prec == PSE_MIXED)
       k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell,
-                                         c->d_cell_start, c->d_cell_list, c->d_nbr_start, (float4 *)c->d_nbr_geo,
+                                         c->d_cell_start, c->d_cell_key, c->d_nbr_start, (float4 *)c->d_nbr_geo,
                                          c->d_nbr_tot, c->d_flag + 1);
     else
       k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell,
-                                          c->d_cell_start, c->d_cell_list, c->d_nbr_start, (double4_32a *)c->d_nbr_geo,
+                                          c->d_cell_start, c->d_cell_key, c->d_nbr_start, (double4_32a *)c->d_nbr_geo,
                                           c->d_nbr_tot, c->d_flag + 1);
     if (c->capturing) return PSE_OK;  // the graph's caller checks the flags and the totals afterwards
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
