@@ -18,11 +18,25 @@ Follows
   P from the bound at eps/10, which keeps the measured error below eps for
   xi a in [0.45, 0.8] at phi = 0.1 and 0.3.
 
+* Deformed lattices (Sec. 2.3.3): the periodic cell is spanned by the columns of
+  L A; grid nodes sit at h A n and the support is the P^3 nodes nearest the
+  particle in lattice coordinates z = A^{-1} x.  The support rule takes
+  Eq. (bound) with lambda_max, the largest eigenvalue of A^T A (lambda_aware,
+  default), or with lambda_max = 1 (the orthorhombic rule the paper compares
+  against in Fig. fig:shear).  Readings where the paper is silent: the grid
+  must hold every wave vector with |k| <= k_cut, k = (2 pi/L) A^{-T} m with
+  |m_i| < Ng/2, so Ng >= k_cut L max_i |A e_i| / pi; the real-space sum needs
+  r_cut <= L sqrt(lambda_min)/2 (the smallest half-width of the cell), so that a
+  pair closer than r_cut has one image only; V = L^3 det A and sigma = h^3 det A.
+
 Parity: pinned (tests/test_oracle_params.py: Table tab:lmax P=5 at 1e-3, P=6 at
-1e-4; eta < 1; the lambda_max closed forms).
+1e-4; eta < 1; the lambda_max closed forms; tests/test_oracle_lattice.py: the
+lattice metrics against the closed forms of Eqs. lmax1 and lmax2).
 """
 import math
 from dataclasses import dataclass
+
+import numpy as np
 
 from scipy.special import erfc
 from scipy.optimize import brentq
@@ -71,6 +85,23 @@ def lambda_max_ext(eps):
     return eps * eps if eps >= 1.0 else 1.0 / (eps * eps)
 
 
+def shear_tensor(gamma):
+    """Deformation tensor of simple shear with strain gamma (Sec. 2.3.3)."""
+    return np.array([[1.0, gamma, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+
+
+def extension_tensor(eps):
+    """Deformation tensor of planar extension with stretch eps (Sec. 2.3.3)."""
+    return np.diag([eps, 1.0 / eps, 1.0])
+
+
+def lattice_metrics(A):
+    """(lambda_min, lambda_max) of A^T A, det A and the largest column norm of A."""
+    A = np.asarray(A, dtype=float)
+    ev = np.linalg.eigvalsh(A.T @ A)
+    return float(ev[0]), float(ev[-1]), float(np.linalg.det(A)), float(np.max(np.linalg.norm(A, axis=0)))
+
+
 def _smooth(n):
     for p in (2, 3, 5, 7):
         while n % p == 0:
@@ -102,22 +133,33 @@ class Params:
     Ng: int
     h: float
     eta_g: float    # Gaussian width parameter of the spreading kernel
+    A: object = None    # lattice deformation (3 x 3), None for the cubic box
+    detA: float = 1.0
 
     @property
     def V(self):
-        return self.L ** 3
+        return self.L ** 3 * self.detA
 
     @property
     def sigma(self):
-        return self.h ** 3
+        return self.h ** 3 * self.detA
 
 
-def choose(N, L, a, eta, kT, xi, tol, Ng=None, P=None, rcut=None, rule='strict'):
-    """All PSE parameters for a cubic periodic box of side L."""
+def choose(N, L, a, eta, kT, xi, tol, Ng=None, P=None, rcut=None, rule='strict', A=None,
+           lambda_aware=True):
+    """All PSE parameters for a periodic box of side L, cubic (A None) or the
+    lattice spanned by the columns of L A."""
+    lam_min, lam, detA, cmax = 1.0, 1.0, 1.0, 1.0
+    if A is not None:
+        A = np.array(A, dtype=float).reshape(3, 3)
+        lam_min, lam, detA, cmax = lattice_metrics(A)
+        if not detA > 0:
+            raise ValueError('the lattice deformation needs det A > 0')
+    lam_P = lam if lambda_aware else 1.0
     if rule == 'paper':
-        rc_auto, P_auto = rcut_rule(xi, tol), support_rule(tol)
+        rc_auto, P_auto = rcut_rule(xi, tol), support_rule(tol, lam_P)
     elif rule == 'strict':
-        rc_auto, P_auto = a + rcut_rule(xi, tol / 10.0), support_rule(tol / 10.0)
+        rc_auto, P_auto = a + rcut_rule(xi, tol / 10.0), support_rule(tol / 10.0, lam_P)
     else:
         raise ValueError(rule)
     rc = rc_auto if rcut is None else rcut
@@ -125,7 +167,7 @@ def choose(N, L, a, eta, kT, xi, tol, Ng=None, P=None, rcut=None, rule='strict')
     PP = P_auto if P is None else int(P)
     m = math.sqrt(math.pi * PP)
     if Ng is None:
-        Ng = next_grid(kc * L / math.pi)
+        Ng = next_grid(kc * L * cmax / math.pi)
         while True:
             h = L / Ng
             eg = (h * PP * xi / m) ** 2
@@ -134,8 +176,9 @@ def choose(N, L, a, eta, kT, xi, tol, Ng=None, P=None, rcut=None, rule='strict')
             Ng = next_grid(Ng + 1)
     h = L / Ng
     eg = (h * PP * xi / m) ** 2
-    if rc > 0.5 * L:
-        raise ValueError('r_cut = %.4g exceeds L/2 = %.4g: the minimum-image pair sum '
-                         'needs a larger box or a larger xi' % (rc, 0.5 * L))
+    half = 0.5 * L * math.sqrt(lam_min)
+    if rc > half * (1 + 1e-12):
+        raise ValueError('r_cut = %.4g exceeds the half-width %.4g of the cell: the minimum-image pair sum '
+                         'needs a larger box or a larger xi' % (rc, half))
     return Params(N=N, L=L, a=a, eta=eta, kT=kT, xi=xi, tol=tol, rcut=rc, kcut=kc,
-                  P=PP, m=m, Ng=int(Ng), h=h, eta_g=eg)
+                  P=PP, m=m, Ng=int(Ng), h=h, eta_g=eg, A=A, detA=detA)

@@ -30,6 +30,12 @@ Steps, in the paper's order:
   the drift kT div R_FU^{-1} from a random finite difference, three constraint
   solves per step.
 
+* Deformed lattices (Sec. 2.3.3): with the cell spanned by the columns of L A,
+  the grid nodes sit at h A n; the support is taken in lattice coordinates
+  z = A^{-1} x, the Gaussian weight is K(A d) for the lattice displacement d
+  (not separable), the wave vectors are (2 pi/L) A^{-T} m, V = L^3 det A,
+  sigma = h^3 det A, and the real-space pairs are found over the lattice images.
+
 Layout conventions shared with the product through the documented C ABI (not
 through code): grid arrays are [component][z][y][x]; the R2C half spectrum
 halves x; 8-vectors per particle are [F_x, F_y, F_z, s_1..s_5].
@@ -54,13 +60,32 @@ from .wavesum import shape_factors
 
 
 # ---------------------------------------------------------------- wave space
+def lattice_coords(pos, p):
+    """Wrapped lattice coordinates in [0, L)^3: the positions themselves in the cubic
+    box; on a deformed lattice (Sec. 2.3.3, nodes at h A n) z = A^{-1} x mod L, the
+    particle's place relative to the undeformed grid."""
+    if p.A is None:
+        return np.mod(pos, p.L)
+    z = np.mod(pos @ np.linalg.inv(p.A).T, p.L)
+    return np.where(z >= p.L, z - p.L, z)
+
+
+def wrap_positions(pos, p):
+    """Positions moved into the periodic cell: [0, L)^3 for the cube, A [0, L)^3 on a
+    deformed lattice (a lattice translation of each particle)."""
+    if p.A is None:
+        return np.mod(pos, p.L)
+    return lattice_coords(pos, p) @ p.A.T
+
+
 def _support(pos, p):
     """Base index i0 and displacements of the P support points per dimension.
 
     Reading: the P grid points nearest the particle; i0 = round(x/h) - (P-1)/2 for
-    odd P, floor(x/h) - P/2 + 1 for even P (taken mod Ng).
+    odd P, floor(x/h) - P/2 + 1 for even P (taken mod Ng).  On a deformed lattice
+    x is the lattice coordinate z and the displacements are those of z.
     """
-    x = np.mod(pos, p.L)
+    x = lattice_coords(pos, p)
     q = x / p.h
     if p.P % 2:
         i0 = np.rint(q).astype(np.int64) - (p.P - 1) // 2
@@ -75,9 +100,15 @@ def _support(pos, p):
 def _weights(pos, p):
     idx, disp = _support(pos, p)
     alpha = 2 * p.xi ** 2 / p.eta_g
-    w1 = np.exp(-alpha * disp ** 2)                            # (N, 3, P)
     pref = (2 * p.xi ** 2 / (np.pi * p.eta_g)) ** 1.5
-    W = pref * np.einsum('ni,nj,nk->nijk', w1[:, 2], w1[:, 1], w1[:, 0])   # [z][y][x]
+    if p.A is None:
+        w1 = np.exp(-alpha * disp ** 2)                        # (N, 3, P)
+        W = pref * np.einsum('ni,nj,nk->nijk', w1[:, 2], w1[:, 1], w1[:, 0])   # [z][y][x]
+    else:  # K(A d): |A d|^2 = d . (A^T A) d, not separable on a deformed lattice
+        Gm = p.A.T @ p.A
+        d = [disp[:, 0][:, None, None, :], disp[:, 1][:, None, :, None], disp[:, 2][:, :, None, None]]
+        q = sum(Gm[i, j] * d[i] * d[j] for i in range(3) for j in range(3))
+        W = pref * np.exp(-alpha * q)                          # (N, P, P, P) [z][y][x]
     flat = ((idx[:, 2, :, None, None] * p.Ng + idx[:, 1, None, :, None]) * p.Ng
             + idx[:, 0, None, None, :])
     return flat.reshape(pos.shape[0], -1), W.reshape(pos.shape[0], -1)
@@ -111,6 +142,9 @@ def kgrid(p):
     keep = (np.abs(kz) != n // 2) & (np.abs(ky) != n // 2) & (kx != n // 2)
     keep &= ~((kz == 0) & (ky == 0) & (kx == 0))
     scale = 2 * np.pi / p.L
+    if p.A is not None:  # k = (2 pi/L) A^{-T} m
+        B = np.linalg.inv(p.A).T
+        kx, ky, kz = (B[i, 0] * kx + B[i, 1] * ky + B[i, 2] * kz for i in range(3))
     return kx * scale, ky * scale, kz * scale, keep
 
 
@@ -201,21 +235,46 @@ def wave_noise(pos, w2, p):
 
 
 # ---------------------------------------------------------------- real space
+def _lattice_pairs(pos, p):
+    """Pairs (i < j) and separations x_i - x_j + L A n closer than r_cut on a deformed
+    lattice.  Candidates: pairs whose lattice coordinates lie within r_cut/sigma_min
+    (|A dz| >= sigma_min |dz|); for each, every image n in {-1, 0, 1}^3 around the
+    nearest lattice image is tested in Cartesian space."""
+    z = lattice_coords(pos, p)
+    smin = math.sqrt(np.linalg.eigvalsh(p.A.T @ p.A)[0])
+    tree = cKDTree(z, boxsize=p.L)
+    pr = tree.query_pairs(p.rcut / smin * (1 + 1e-12), output_type='ndarray')
+    if pr.size == 0:
+        return np.zeros((0, 2), dtype=np.int64), np.zeros((0, 3))
+    dz = z[pr[:, 0]] - z[pr[:, 1]]
+    dz -= p.L * np.rint(dz / p.L)
+    ps, ds = [], []
+    for n in np.array(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing='ij')).reshape(3, -1).T:
+        r = (dz + p.L * n) @ p.A.T
+        keep = np.linalg.norm(r, axis=1) < p.rcut
+        ps.append(pr[keep])
+        ds.append(r[keep])
+    return np.concatenate(ps), np.concatenate(ds)
+
+
 class RealOp:
     """Real-space operator M_r for a fixed configuration (pairs with r < r_cut); with
     torque=True the 11-moment form [F, L, S] -> [U, Omega, E]."""
 
     def __init__(self, pos, p, chunk=20000, torque=False):
         self.N = pos.shape[0]
-        x = np.mod(pos, p.L)
-        tree = cKDTree(x, boxsize=p.L)
-        pr = tree.query_pairs(p.rcut, output_type='ndarray')
-        if pr.size == 0:
-            pr = np.zeros((0, 2), dtype=np.int64)
-        d = x[pr[:, 0]] - x[pr[:, 1]]
-        d -= p.L * np.rint(d / p.L)
-        keep = np.linalg.norm(d, axis=1) < p.rcut
-        pr, d = pr[keep], d[keep]
+        if p.A is None:
+            x = np.mod(pos, p.L)
+            tree = cKDTree(x, boxsize=p.L)
+            pr = tree.query_pairs(p.rcut, output_type='ndarray')
+            if pr.size == 0:
+                pr = np.zeros((0, 2), dtype=np.int64)
+            d = x[pr[:, 0]] - x[pr[:, 1]]
+            d -= p.L * np.rint(d / p.L)
+            keep = np.linalg.norm(d, axis=1) < p.rcut
+            pr, d = pr[keep], d[keep]
+        else:
+            pr, d = _lattice_pairs(pos, p)
         nb = 11 if torque else 8
         fn = realspace.pair_blocks11 if torque else realspace.pair_blocks
         blocks = np.empty((pr.shape[0], nb, nb))
@@ -398,11 +457,13 @@ def midpoint_step(x0, FP, dt, B, mobility_at, solve, L):
     solve(mes, rhs) returns (S, *info) with mes(S) = rhs.  The scheme moves to
     x_{k+1/2} = x_k + dt/2 U^B, solves M_ES S = -E^B - M_EF F^P there (E = 0 at the
     mid-point), takes U = U^B + M_UF F^P + M_US S and x_{k+1} = x_k + dt U.
-    Positions are wrapped into [0, L).  Returns (x_{k+1}, S, info).
+    Positions are wrapped into [0, L) (L a number) or by the callable L.  Returns
+    (x_{k+1}, S, info).
     """
     N = x0.shape[0]
+    wrap = L if callable(L) else (lambda x: np.mod(x, L))
     UB, EB = B[:, :3], B[:, 3:]
-    xh = np.mod(x0 + 0.5 * dt * UB, L)
+    xh = wrap(x0 + 0.5 * dt * UB)
     mob = mobility_at(xh)
     zF = np.zeros((N, 3)) if FP is None else FP
     rhs = -EB
@@ -411,14 +472,14 @@ def midpoint_step(x0, FP, dt, B, mobility_at, solve, L):
     S, *info = solve(lambda s: mob(np.zeros((N, 3)), s.reshape(N, 5))[1].ravel(), rhs.ravel())
     S = S.reshape(N, 5)
     U = UB + mob(zF, S)[0]
-    x1 = np.mod(x0 + dt * U, L)
+    x1 = wrap(x0 + dt * U)
     return x1, S, info
 
 
 def constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=100,
                      krylov_tol=None, krylov_maxiter=50):
     """One mid-point step (Sec. 3.4) with the PSE mobility.  Returns (x_{k+1}, S_{k+1/2}, stats)."""
-    x0 = np.mod(pos, p.L)
+    x0 = wrap_positions(pos, p)
     B, st = brownian_sample(x0, dt, w1, w2, p, lanczos_tol, lanczos_maxiter)
 
     def mobility_at(x):
@@ -427,7 +488,8 @@ def constrained_step(pos, FP, dt, w1, w2, p, lanczos_tol=None, lanczos_maxiter=1
 
     ktol = p.tol if krylov_tol is None else krylov_tol
     x1, S, (kit, rel) = midpoint_step(x0, FP, dt, B, mobility_at,
-                                      lambda A, b: gmres(A, b, ktol, krylov_maxiter), p.L)
+                                      lambda A, b: gmres(A, b, ktol, krylov_maxiter),
+                                      p.L if p.A is None else (lambda x: wrap_positions(x, p)))
     st.update({'krylov_iters': kit, 'krylov_relres': rel})
     return x1, S, st
 
@@ -449,10 +511,12 @@ def rfd_em_step(x0, FP, dt, B, wt, delta, kT, mobility_at, solve, L):
     M_ES S = -E^B - M_EF F^P, U = U^B + M_UF F^P + M_US S (covariance (2kT/dt) R_FU^{-1}).
     Drift by RFD with the standard normal vector wt (N, 3):
     kT div R_FU^{-1} ~ (kT/delta) [R_FU^{-1}(x_k + delta/2 wt) - R_FU^{-1}(x_k - delta/2 wt)] wt,
-    two more solves.  x_{k+1} = x_k + dt (U + drift), wrapped into [0, L).
+    two more solves.  x_{k+1} = x_k + dt (U + drift), wrapped into [0, L) (L a number)
+    or by the callable L.
     Returns (x_{k+1}, S, drift, info) with info the solve outputs of the three solves.
     """
     N = x0.shape[0]
+    wrap = L if callable(L) else (lambda x: np.mod(x, L))
     UB, EB = B[:, :3], B[:, 3:]
     mob = mobility_at(x0)
     zF = np.zeros((N, 3)) if FP is None else FP
@@ -462,17 +526,17 @@ def rfd_em_step(x0, FP, dt, B, wt, delta, kT, mobility_at, solve, L):
     S, *i0 = solve(lambda s: mob(np.zeros((N, 3)), s.reshape(N, 5))[1].ravel(), rhs.ravel())
     S = S.reshape(N, 5)
     U = UB + mob(zF, S)[0]
-    Rp, ip = constrained_apply(mobility_at(np.mod(x0 + 0.5 * delta * wt, L)), wt, solve)
-    Rm, im = constrained_apply(mobility_at(np.mod(x0 - 0.5 * delta * wt, L)), wt, solve)
+    Rp, ip = constrained_apply(mobility_at(wrap(x0 + 0.5 * delta * wt)), wt, solve)
+    Rm, im = constrained_apply(mobility_at(wrap(x0 - 0.5 * delta * wt)), wt, solve)
     drift = (kT / delta) * (Rp - Rm)
-    x1 = np.mod(x0 + dt * (U + drift), L)
+    x1 = wrap(x0 + dt * (U + drift))
     return x1, S, drift, (i0, ip, im)
 
 
 def rfd_step(pos, FP, dt, w1, w2, wt, delta, p, lanczos_tol=None, lanczos_maxiter=100, krylov_tol=None,
              krylov_maxiter=50):
     """rfd_em_step with the PSE mobility.  Returns (x_{k+1}, S_k, drift, stats)."""
-    x0 = np.mod(pos, p.L)
+    x0 = wrap_positions(pos, p)
     B, st = brownian_sample(x0, dt, w1, w2, p, lanczos_tol, lanczos_maxiter)
 
     def mobility_at(x):
@@ -481,6 +545,7 @@ def rfd_step(pos, FP, dt, w1, w2, wt, delta, p, lanczos_tol=None, lanczos_maxite
 
     ktol = p.tol if krylov_tol is None else krylov_tol
     x1, S, drift, info = rfd_em_step(x0, FP, dt, B, wt, delta, p.kT, mobility_at,
-                                     lambda A, b: gmres(A, b, ktol, krylov_maxiter), p.L)
+                                     lambda A, b: gmres(A, b, ktol, krylov_maxiter),
+                                     p.L if p.A is None else (lambda x: wrap_positions(x, p)))
     st.update({'krylov_iters': sum(i[0] for i in info), 'krylov_relres': max(i[1] for i in info)})
     return x1, S, drift, st

@@ -7,8 +7,12 @@ with the projector of Sec. 2.3.2 (Eq. for P_ii):
 restricted to the (U, E) x (F, S) block in the stresslet basis Y.  The k and -k
 terms are complex conjugates, so the sum is taken over a half space as 2 Re(.).
 
+On a deformed lattice (Sec. 2.3.3, cell spanned by the columns of L A) the
+reciprocal vectors are k = (2 pi/L) A^{-T} m for integer m and V = L^3 det A.
+
 Parity: pinned (xi-independence of the total with the real-space part, and
-equality with the NUFFT evaluation on the same k set).
+equality with the NUFFT evaluation on the same k set; on deformed lattices the
+same, plus lattice identities in tests/test_oracle_lattice.py).
 """
 import numpy as np
 
@@ -33,30 +37,41 @@ def half_space(n):
     return (n3 > 0) | ((n3 == 0) & (n2 > 0)) | ((n3 == 0) & (n2 == 0) & (n1 > 0))
 
 
-def kset_sphere(L, kmax):
-    """Half-space wave vectors 2 pi n / L with 0 < |k| <= kmax."""
-    nm = int(np.ceil(kmax * L / (2 * np.pi)))
-    g = np.arange(-nm, nm + 1)
-    n = np.stack(np.meshgrid(g, g, g, indexing='ij'), -1).reshape(-1, 3)
-    k = 2 * np.pi * n / L
+def _to_k(n, L, A):
+    """Wave vectors (2 pi/L) A^{-T} n of integer vectors n (rows); A None: 2 pi n/L."""
+    if A is None:
+        return 2 * np.pi * n / L
+    return (2 * np.pi / L) * (n @ np.linalg.inv(np.asarray(A, float)))
+
+
+def kset_sphere(L, kmax, A=None):
+    """Half-space reciprocal vectors with 0 < |k| <= kmax (cubic, or of the lattice L A)."""
+    if A is None:
+        nm = [int(np.ceil(kmax * L / (2 * np.pi)))] * 3
+    else:  # |m_i| = (L/2pi) |A e_i . k| <= (L/2pi) |A e_i| kmax
+        nm = [int(np.ceil(kmax * L * np.linalg.norm(np.asarray(A, float)[:, i]) / (2 * np.pi))) for i in range(3)]
+    gx, gy, gz = (np.arange(-q, q + 1) for q in nm)
+    n = np.stack(np.meshgrid(gx, gy, gz, indexing='ij'), -1).reshape(-1, 3)
+    k = _to_k(n, L, A)
     kk = np.linalg.norm(k, axis=1)
     keep = half_space(n) & (kk <= kmax) & (kk > 0)
     return k[keep]
 
 
-def kset_grid(L, Ng):
+def kset_grid(L, Ng, A=None):
     """Half-space wave vectors of an Ng^3 FFT grid without Nyquist modes and k = 0."""
     g = np.arange(-Ng // 2 + 1, Ng // 2)
     n = np.stack(np.meshgrid(g, g, g, indexing='ij'), -1).reshape(-1, 3)
     keep = half_space(n)
-    return 2 * np.pi * n[keep] / L
+    return _to_k(n[keep], L, A)
 
 
-def dense_wave(pos, L, a, eta, xi, kvecs, chunk=400, basis=Y):
+def dense_wave(pos, L, a, eta, xi, kvecs, chunk=400, basis=Y, V=None):
     """Dense nN x nN wave-space mobility over the half-space k set kvecs, n = 3 + len(basis):
-    8 with the stresslet basis Y, 11 with the torque + stresslet basis G."""
+    8 with the stresslet basis Y, 11 with the torque + stresslet basis G.  V: cell
+    volume (default L^3)."""
     N = pos.shape[0]
-    V = L ** 3
+    V = L ** 3 if V is None else V
     nb = 3 + basis.shape[0]
     M = np.zeros((nb * N, nb * N))
     for c0 in range(0, kvecs.shape[0], chunk):
