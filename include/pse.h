@@ -111,7 +111,15 @@ typedef struct pse_options {
   int32_t torque;          /* 1: also set up the 11-moment product pse_mobility_apply11 (forces,
                               torques and stresslets): 11 grids per suspension instead of 8, their
                               transforms, 12-slot work vectors and the rotation table */
-  int32_t reserved[3];
+  int32_t lambda_support;  /* deformed lattices only: 1 (default) = support size P from Eq. bound with
+                              lambda_max of A^T A (Sec. 2.3.3); 0 = with lambda_max = 1, the orthorhombic
+                              rule (the comparison of Fig. fig:shear; the NUFFT error then exceeds tol) */
+  int32_t reserved[2];
+  double deform[9];        /* deformation A of the periodic lattice, row-major (Sec. 2.3.3): the cell is
+                              spanned by the columns of L A (simple shear: A = [[1, gamma, 0], [0, 1, 0],
+                              [0, 0, 1]]; planar extension: diag(e, 1/e, 1)); det A > 0.  All zero (the
+                              default) or the identity: the cubic box.  Every suspension of a handle
+                              shares it.  See "Deformed lattices" before pse_create_batch. */
 } pse_options;
 
 typedef struct pse_info {
@@ -125,6 +133,12 @@ typedef struct pse_info {
   int32_t table_len;
   double table_dr;
   int64_t device_bytes;    /* bytes allocated on the device by this handle */
+  int32_t deformed;        /* 1: the lattice is deformed (options.deform or pse_set_deformation) */
+  int32_t reserved_i;
+  double deform[9];        /* current deformation A (row-major; the identity for the cube) */
+  double lambda_max;       /* largest eigenvalue of A^T A that the support size P was chosen for */
+  double lambda_min_cells; /* smallest eigenvalue of A^T A that the cells and r_cut allow */
+  double colnorm_max;      /* largest column norm of A that the grid resolves to k_cut */
 } pse_info;
 
 typedef struct pse_stats {
@@ -180,6 +194,22 @@ void pse_default_options(pse_options *opt);
 pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT,
                       double xi, double tol, pse_precision prec, const pse_options *opt);
 
+/* Deformed lattices (Sec. 2.3.3; Lees-Edwards shear, Kraynik-Reinelt extension).
+ * With options.deform = A the periodic cell is spanned by the columns of L A
+ * (volume V = L^3 det A).  Positions are Cartesian; internally each particle
+ * has the lattice coordinate z = A^{-1} x wrapped into [0, L)^3, the FFT grid
+ * nodes sit at h A n (h = L/Ng), a particle's support is the P^3 nodes nearest
+ * z, its Gaussian weight is K(A d) for the lattice displacement d, the wave
+ * vectors are (2 pi/L) A^{-T} m, and the real-space pairs are the lattice images
+ * closer than r_cut.  Parameter rules on top of those of pse_create: P from
+ * Eq. bound with lambda_max of A^T A (option lambda_support); Ng >= k_cut L c / pi
+ * with c the largest column norm of A (every |k| <= k_cut on the grid); cells of
+ * side >= r_cut / (2 sqrt(lambda_min)) in lattice coordinates and
+ * r_cut <= L sqrt(lambda_min) / 2 (a pair closer than r_cut has one image).
+ * Deformed handles run the general spreading / interpolation kernels (weights
+ * evaluated per support point); positions written back by the step calls are
+ * wrapped into the cell (A z with z in [0, L)^3). */
+
 /* Creates one handle for nsys independent suspensions (no counterpart in the
  * paper, which treats one suspension: this is the batching layer).  Suspension s
  * has N[s] particles in a cubic box of side L[s]; a, eta, kT, xi and tol are
@@ -208,6 +238,20 @@ pse_status pse_destroy(pse_handle h);
 
 /* For a batch handle: N is the total and the grid fields are suspension 0's. */
 pse_status pse_get_info(pse_handle h, pse_info *out);
+
+/* Changes the lattice deformation of a handle to A (row-major, det A > 0) for
+ * the following calls, without new allocation: a Lees-Edwards run creates the
+ * handle at its largest strain and sets the current one before each step.
+ * Allowed when the handle's parameters still hold for A: lambda_max(A^T A) no
+ * larger than the one P was chosen for, lambda_min(A^T A) no smaller than the
+ * one the cells allow, the largest column norm of A no larger than the one the
+ * grid resolves (the pse_info fields lambda_max, lambda_min_cells,
+ * colnorm_max); else INVALID_ARG and nothing changes.  Only for handles created
+ * with a deformation (options.deform not zero).  The device copy of the
+ * parameters is updated in stream order on `stream`: work queued before the
+ * call uses the old lattice, work queued after it the new one (a captured step
+ * graph reads them at its next launch). */
+pse_status pse_set_deformation(pse_handle h, const double *A, pse_stream stream);
 
 /* Number of suspensions of a handle (0 for NULL). */
 int32_t pse_num_systems(pse_handle h);
@@ -344,7 +388,7 @@ const char *pse_noalloc_last_error(void);
  * suspensions of any size arrive at any time and run concurrently on the
  * device; a request starts when a slot is free and its suspension's state fits
  * the device-memory budget.  State stays resident: a later request with the
- * same parameters (N, L, a, eta, kT, xi, tol, precision) reuses the handle
+ * same parameters (N, L, a, eta, kT, xi, tol, precision and options) reuses the handle
  * (tables, cuFFT plans, grids, neighbour lists); a new handle is created when
  * its estimate (pse_estimate_bytes) fits, after evicting idle resident handles,
  * least recently used first.  Requests that do not fit yet wait in arrival

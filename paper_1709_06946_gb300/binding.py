@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
                 ('krylov_tol', ctypes.c_double), ('krylov_maxiter', ctypes.c_int32),
                 ('tile', ctypes.c_int32 * 3), ('real_lanes', ctypes.c_int32), ('grid_ladder', ctypes.c_int32),
                 ('use_graph', ctypes.c_int32), ('wave_kernel', ctypes.c_int32), ('torque', ctypes.c_int32),
-                ('reserved', ctypes.c_int32 * 3)]
+                ('lambda_support', ctypes.c_int32), ('reserved', ctypes.c_int32 * 2),
+                ('deform', ctypes.c_double * 9)]
 
 
 class Info(ctypes.Structure):
@@ -41,7 +42,9 @@ class Info(ctypes.Structure):
                 ('eta_g', ctypes.c_double), ('m', ctypes.c_double), ('Ng', ctypes.c_int32),
                 ('P', ctypes.c_int32), ('cells_per_side', ctypes.c_int32), ('tile', ctypes.c_int32 * 3),
                 ('table_len', ctypes.c_int32), ('table_dr', ctypes.c_double),
-                ('device_bytes', ctypes.c_int64)]
+                ('device_bytes', ctypes.c_int64), ('deformed', ctypes.c_int32), ('reserved_i', ctypes.c_int32),
+                ('deform', ctypes.c_double * 9), ('lambda_max', ctypes.c_double),
+                ('lambda_min_cells', ctypes.c_double), ('colnorm_max', ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -115,6 +118,7 @@ SIGNATURES = [
                                           ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_int64)]),
     ('pse_destroy', ctypes.c_int, [_P]),
     ('pse_get_info', ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    ('pse_set_deformation', ctypes.c_int, [_P, _P, _P]),
     ('pse_num_systems', ctypes.c_int32, [_P]),
     ('pse_graph_ready', ctypes.c_int32, [_P]),
     ('pse_graph_error', ctypes.c_char_p, [_P]),
@@ -247,7 +251,7 @@ def mobility_real_noalloc(pos, F, S, L, a=1.0, eta=1.0, xi=0.5, tol=1e-3):
 
 def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxiter=100, krylov_tol=-1.0,
              krylov_maxiter=50, table_points=0, tile=(0, 0, 0), real_lanes=0, grid_ladder=1, use_graph=0,
-             wave_kernel=0, torque=0):
+             wave_kernel=0, torque=0, deform=None, lambda_support=1):
     o = Options()
     load().pse_default_options(ctypes.byref(o))
     o.rule = PSE_RULE_PAPER if rule == 'paper' else PSE_RULE_STRICT
@@ -260,6 +264,11 @@ def _options(rule='strict', Ng=0, P=0, rcut=0.0, lanczos_tol=-1.0, lanczos_maxit
     o.use_graph = int(use_graph)
     o.wave_kernel = int(wave_kernel)
     o.torque = int(torque)
+    o.lambda_support = int(lambda_support)
+    if deform is not None:
+        A = np.asarray(deform, dtype=np.float64).reshape(9)
+        for i in range(9):
+            o.deform[i] = float(A[i])
     for d in range(3):
         o.tile[d] = int(tile[d])
     return o
@@ -323,8 +332,9 @@ class PSE:
         """Parameters of suspension s (grid, cells, tiles, ...)."""
         inf = Info()
         self._check(self._lib.pse_get_system_info(self._h, int(s), ctypes.byref(inf)))
-        d = {k: getattr(inf, k) for k, _ in Info._fields_}
+        d = {k: getattr(inf, k) for k, _ in Info._fields_ if k != 'reserved_i'}
         d['tile'] = tuple(inf.tile)
+        d['deform'] = np.array(inf.deform[:]).reshape(3, 3)
         return d
 
     def system_stats(self, s):
@@ -340,9 +350,21 @@ class PSE:
     def get_info(self):
         inf = Info()
         self._check(self._lib.pse_get_info(self._h, ctypes.byref(inf)))
-        d = {k: getattr(inf, k) for k, _ in Info._fields_}
+        d = {k: getattr(inf, k) for k, _ in Info._fields_ if k != 'reserved_i'}
         d['tile'] = tuple(inf.tile)
+        d['deform'] = np.array(inf.deform[:]).reshape(3, 3)
         return d
+
+    def set_deformation(self, A, stream=None):
+        """Lattice deformation A (3 x 3; the cell is spanned by the columns of L A) for
+        the following calls; the handle must have been created with deform=..."""
+        Am = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(9))
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        st = self._lib.pse_set_deformation(self._h, Am.ctypes.data, stream)
+        self._check(st)
+        self.info = self.get_info()
 
     def close(self):
         if getattr(self, '_h', None):
@@ -546,6 +568,17 @@ class Server:
 
     def reset_stats(self):
         self._lib.pse_server_reset_stats(self._h)
+
+    def set_deformation(self, A, stream=None):
+        """Lattice deformation A (3 x 3; the cell is spanned by the columns of L A) for
+        the following calls; the handle must have been created with deform=..."""
+        Am = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(9))
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        st = self._lib.pse_set_deformation(self._h, Am.ctypes.data, stream)
+        self._check(st)
+        self.info = self.get_info()
 
     def close(self):
         if getattr(self, '_h', None):

@@ -642,11 +642,47 @@ int64_t estimate_bytes(const pse_ctx *c) {
   return b;
 }
 
+}  // namespace
+
+// Lattice fields of a suspension's device constants (Sec. 2.3.3): the cube has
+// def = 0, A = I and qa = alpha (1, 1, 1, 0, 0, 0).
+void pse::fill_lattice(const Params &p, SysDev &d) {
+  d.def = p.def;
+  const double kf = 2.0 * M_PI / p.L;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      d.A[3 * i + j] = p.A[3 * i + j];
+      d.Ai[3 * i + j] = p.Ai[3 * i + j];
+      d.Bt[3 * i + j] = kf * p.Ai[3 * j + i];  // (2 pi/L) (A^{-1})^T
+      d.Af[3 * i + j] = (float)d.A[3 * i + j];
+      d.Btf[3 * i + j] = (float)d.Bt[3 * i + j];
+    }
+  // G = A^T A: alpha |A d|^2 = alpha d.G d
+  double G[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) G[3 * i + j] = p.A[i] * p.A[j] + p.A[3 + i] * p.A[3 + j] + p.A[6 + i] * p.A[6 + j];
+  const double al = 2.0 * p.xi * p.xi / p.eta_g;
+  d.qa[0] = al * G[0];
+  d.qa[1] = al * G[4];
+  d.qa[2] = al * G[8];
+  d.qa[3] = 2.0 * al * G[1];
+  d.qa[4] = 2.0 * al * G[2];
+  d.qa[5] = 2.0 * al * G[5];
+  if (!p.def) {  // exact cube values
+    d.qa[0] = d.qa[1] = d.qa[2] = al;
+    d.qa[3] = d.qa[4] = d.qa[5] = 0.0;
+  }
+  d.c_apply = p.sigma() * p.sigma() / (p.V() * p.eta);
+  d.c_noise = p.sigma() / std::sqrt(p.eta * p.V());
+}
+
+namespace {
+
 // Marks a suspension for the spreading / interpolation kernels specialised for
 // 16^3 tiles (mixed precision, P = 5, 6 or 8, at least two tiles per side) and
 // counts it in c->n_cubic.
 void set_cubic(pse_ctx *c, SysDev &d) {
-  bool ok = c->prec == PSE_MIXED && (c->p.P == 5 || c->p.P == 6 || c->p.P == 8);
+  bool ok = c->prec == PSE_MIXED && (c->p.P == 5 || c->p.P == 6 || c->p.P == 8) && !c->lattice;
   for (int k = 0; k < 3; ++k) ok = ok && d.T[k] == CUBE_TILE && d.nt[k] >= 2;
   d.cubic = ok ? 1 : 0;
   c->n_cubic += d.cubic;
@@ -697,6 +733,8 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
   // per-suspension layout: particles, tiles, cells, half spectra, vector blocks
   c->hs.assign(ns, SysDev{});
   c->n_cubic = 0;
+  c->lattice = 0;
+  for (int i = 0; i < 9; ++i) c->lattice |= o.deform[i] != 0.0 ? 1 : 0;
   std::vector<int64_t> p0(ns + 1, 0), k0(ns + 1, 0);
   std::vector<int> tile0(ns + 1, 0), blk0(ns + 1, 0);
   int64_t cell_tot = 0;
@@ -722,8 +760,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
     d.pref = std::pow(2.0 * p.xi * p.xi / (M_PI * p.eta_g), 1.5);
     d.kfac = 2.0 * M_PI / p.L;
     d.eta_g = p.eta_g;
-    d.c_apply = p.sigma() * p.sigma() / (p.V() * p.eta);
-    d.c_noise = p.sigma() / std::sqrt(p.eta * p.V());
+    fill_lattice(p, d);
     double mean = 4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * p.N / p.V();
     d.slots = (int)std::min<double>(std::max<int64_t>(p.N, 8), std::ceil((1.4 * mean + 24) / 8.0) * 8.0);
     d.slots = std::max(d.slots, 8);
@@ -1249,6 +1286,11 @@ void fill_info(const pse_ctx *h, const Params &p, int64_t bytes, pse_info *o) {
   o->table_len = h->table_len;
   o->table_dr = h->table_dr;
   o->device_bytes = bytes;
+  o->deformed = p.def;
+  for (int i = 0; i < 9; ++i) o->deform[i] = p.A[i];
+  o->lambda_max = p.lam_P;
+  o->lambda_min_cells = p.lam_cells;
+  o->colnorm_max = p.cmax_grid;
 }
 
 }  // namespace
@@ -1264,6 +1306,7 @@ void pse_default_options(pse_options *o) {
   o->lanczos_maxiter = 100;
   o->krylov_maxiter = 50;
   o->grid_ladder = 1;
+  o->lambda_support = 1;
 }
 
 pse_status pse_create(pse_handle *out, int64_t N, double L, double a, double eta, double kT, double xi, double tol,
@@ -1303,6 +1346,48 @@ pse_status pse_get_info(pse_handle h, pse_info *o) {
   if (!h || !o) return PSE_ERR_INVALID_ARG;
   fill_info(h, h->ps.empty() ? h->p : h->ps[0], h->dev_bytes, o);
   o->N = h->p.N;
+  return PSE_OK;
+}
+
+pse_status pse_set_deformation(pse_handle h, const double *A, pse_stream stream) {
+  if (!h || !A) return PSE_ERR_INVALID_ARG;
+  bool created_deformed = false;
+  for (int i = 0; i < 9; ++i) created_deformed = created_deformed || h->opt.deform[i] != 0.0;
+  if (!created_deformed) {
+    h->err = "pse_set_deformation: the handle was created for the cube (options.deform all zero)";
+    return PSE_ERR_INVALID_ARG;
+  }
+  std::vector<Params> ps = h->ps;
+  for (Params &p : ps) {
+    std::string e;
+    if (set_lattice(p, A, e)) {
+      h->err = "pse_set_deformation: " + e;
+      return PSE_ERR_INVALID_ARG;
+    }
+    const double tiny = 1e-12;
+    if (p.lam_max > p.lam_P * (1 + tiny) && h->opt.lambda_support && h->opt.P <= 0) {
+      h->err = "pse_set_deformation: lambda_max " + std::to_string(p.lam_max) + " exceeds the " +
+               std::to_string(p.lam_P) + " the support size was chosen for";
+      return PSE_ERR_INVALID_ARG;
+    }
+    if (p.lam_min < p.lam_cells * (1 - tiny)) {
+      h->err = "pse_set_deformation: lambda_min " + std::to_string(p.lam_min) + " is below the " +
+               std::to_string(p.lam_cells) + " the cells and r_cut were chosen for";
+      return PSE_ERR_INVALID_ARG;
+    }
+    if (p.cmax > p.cmax_grid * (1 + tiny) && h->opt.Ng <= 0) {
+      h->err = "pse_set_deformation: column norm " + std::to_string(p.cmax) + " exceeds the " +
+               std::to_string(p.cmax_grid) + " the grid was chosen for";
+      return PSE_ERR_INVALID_ARG;
+    }
+  }
+  h->ps = ps;
+  for (int q = 0; q < h->nsys; ++q) fill_lattice(h->ps[q], h->hs[q]);
+  Params shared = h->ps[0];
+  shared.N = h->p.N;
+  h->p = shared;
+  cudaStream_t s = (cudaStream_t)stream;
+  PSE_CUDA_TRY(h, cudaMemcpyAsync(h->d_sys, h->hs.data(), sizeof(SysDev) * h->nsys, cudaMemcpyHostToDevice, s));
   return PSE_OK;
 }
 

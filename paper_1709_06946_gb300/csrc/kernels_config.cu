@@ -86,13 +86,24 @@ __global__ void k_bin(const SysDev *__restrict__ sys, const int64_t *__restrict_
   if (u >= Ntot) return;
   const SysDev &b = sys[find_sys(p0, nsys, u)];
   int iw[3];
+  double xin[3];
   for (int d = 0; d < 3; ++d) {
-    double x = pos[3 * u + d];
-    if (!isfinite(x)) {
+    xin[d] = pos[3 * u + d];
+    if (!isfinite(xin[d])) {
       atomicOr(bad, 1);
-      x = 0.0;
+      xin[d] = 0.0;
     }
-    x = wrap_coord(x, b.L);
+  }
+  if (b.def) {  // lattice coordinates z = A^{-1} x (Sec. 2.3.3); everything below works on z
+    const double z0 = b.Ai[0] * xin[0] + b.Ai[1] * xin[1] + b.Ai[2] * xin[2];
+    const double z1 = b.Ai[3] * xin[0] + b.Ai[4] * xin[1] + b.Ai[5] * xin[2];
+    const double z2 = b.Ai[6] * xin[0] + b.Ai[7] * xin[1] + b.Ai[8] * xin[2];
+    xin[0] = z0;
+    xin[1] = z1;
+    xin[2] = z2;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const double x = wrap_coord(xin[d], b.L);
     posw[3 * u + d] = x;
     iw[d] = wrapi(support_start(x, b.h, P), b.Ng);
   }
@@ -209,7 +220,29 @@ __device__ __forceinline__ float3 sep(const float4 &pi, const int ci[3], const f
 // contiguous records, NB of them loaded before the first is tested.  The
 // particle itself is recognised by its own position in the cell list (no read of
 // the list per hit).
-template <typename T, int NB = 4>
+// DEF: deformed lattice (Sec. 2.3.3): records and cells hold lattice coordinates z,
+// and each candidate's separation is mapped to x_i - x_j = A (z_i - z_j) before the
+// test, so the stored separations are Cartesian as for the cube.
+template <typename T4>
+__device__ __forceinline__ void to_cartesian(const SysDev &a, T4 &r) {
+  if (sizeof(r.x) == 4) {
+    const float x = a.Af[0] * r.x + a.Af[1] * r.y + a.Af[2] * r.z;
+    const float y = a.Af[3] * r.x + a.Af[4] * r.y + a.Af[5] * r.z;
+    const float z = a.Af[6] * r.x + a.Af[7] * r.y + a.Af[8] * r.z;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+  } else {
+    const double x = a.A[0] * r.x + a.A[1] * r.y + a.A[2] * r.z;
+    const double y = a.A[3] * r.x + a.A[4] * r.y + a.A[5] * r.z;
+    const double z = a.A[6] * r.x + a.A[7] * r.y + a.A[8] * r.z;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+  }
+}
+
+template <typename T, int NB = 4, bool DEF = false>
 __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, const int64_t *__restrict__ p0,
                                              int nsys, int64_t Ntot, float rc2f, double rc2, const void *rs,
                                              const void *rs_cell, const int *__restrict__ cell_start,
@@ -297,19 +330,29 @@ __global__ void __launch_bounds__(128) k_nbr(const SysDev *__restrict__ sys, con
               rec.x = tx * a.csf + (pf.x - pj.x);
               rec.y = offy + (pf.y - pj.y);
               rec.z = offz + (pf.z - pj.z);
+              if (DEF) to_cartesian(a, rec);
               hit = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z < rc2f;
             } else if (sizeof(T) == 4) {
               const float3 d = sep(pf, ci, *(const float4 *)&q[u], a);
               rec.x = d.x;
               rec.y = d.y;
               rec.z = d.z;
-              hit = d.x * d.x + d.y * d.y + d.z * d.z < rc2f;
+              if (DEF) to_cartesian(a, rec);
+              hit = rec.x * rec.x + rec.y * rec.y + rec.z * rec.z < rc2f;
             } else {
               const double4_32a qj = *(const double4_32a *)&q[u];
               double rx = pd.x - qj.x, ry = pd.y - qj.y, rz = pd.z - qj.z;
               rx -= a.L * rint(rx / a.L);
               ry -= a.L * rint(ry / a.L);
               rz -= a.L * rint(rz / a.L);
+              if (DEF) {
+                const double x = a.A[0] * rx + a.A[1] * ry + a.A[2] * rz;
+                const double y = a.A[3] * rx + a.A[4] * ry + a.A[5] * rz;
+                const double z = a.A[6] * rx + a.A[7] * ry + a.A[8] * rz;
+                rx = x;
+                ry = y;
+                rz = z;
+              }
               rec.x = (T)rx;
               rec.y = (T)ry;
               rec.z = (T)rz;
@@ -440,14 +483,15 @@ pse_status setup_config(pse_ctx *c, const double *d_pos, cudaStream_t s) {
   const unsigned nb128 = (unsigned)ceil_div(N, 128);
   for (int attempt = 0; attempt < 2; ++attempt) {
     PSE_CUDA_TRY(c, cudaMemsetAsync(c->d_nbr_tot, 0, 2 * sizeof(unsigned long long) * ns, s));
+    const bool def = c->lattice != 0;
     if (c->prec == PSE_MIXED)
-      k_nbr<float><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell,
-                                         c->d_cell_start, c->d_cell_key, c->d_nbr_start, (float4 *)c->d_nbr_geo,
-                                         c->d_nbr_tot, c->d_flag + 1);
+      (def ? k_nbr<float, 4, true> : k_nbr<float, 4, false>)<<<nb128, 128, 0, s>>>(
+          c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell, c->d_cell_start, c->d_cell_key,
+          c->d_nbr_start, (float4 *)c->d_nbr_geo, c->d_nbr_tot, c->d_flag + 1);
     else
-      k_nbr<double><<<nb128, 128, 0, s>>>(c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell,
-                                          c->d_cell_start, c->d_cell_key, c->d_nbr_start, (double4_32a *)c->d_nbr_geo,
-                                          c->d_nbr_tot, c->d_flag + 1);
+      (def ? k_nbr<double, 4, true> : k_nbr<double, 4, false>)<<<nb128, 128, 0, s>>>(
+          c->d_sys, c->d_p0, ns, N, (float)rc2, rc2, c->d_rs, c->d_rs_cell, c->d_cell_start, c->d_cell_key,
+          c->d_nbr_start, (double4_32a *)c->d_nbr_geo, c->d_nbr_tot, c->d_flag + 1);
     if (c->capturing) return PSE_OK;  // the graph's caller checks the flags and the totals afterwards
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned_int + 1, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSE_CUDA_TRY(c, cudaMemcpyAsync(c->h_nbr_tot, c->d_nbr_tot, 2 * sizeof(unsigned long long) * ns,

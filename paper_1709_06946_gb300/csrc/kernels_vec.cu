@@ -387,8 +387,9 @@ __global__ void k_midpoint(VecArgs va, const int64_t *__restrict__ p0, int64_t N
   if (e >= 3 * N) return;
   int64_t u = e / 3;
   int d = (int)(e % 3);
-  const double L = va.sys[find_sys(p0, va.nsys, u)].L;
-  xo[e] = wrapL(x0[e] + fac * (double)B[8 * (size_t)u + d], L);
+  const SysDev &sd = va.sys[find_sys(p0, va.nsys, u)];
+  const double x = x0[e] + fac * (double)B[8 * (size_t)u + d];
+  xo[e] = sd.def ? x : wrapL(x, sd.L);  // on a deformed lattice the set-up wraps lattice coordinates
 }
 
 template <typename T>
@@ -398,9 +399,24 @@ __global__ void k_final(VecArgs va, const int64_t *__restrict__ p0, int64_t N, c
   if (e >= 3 * N) return;
   int64_t u = e / 3;
   int d = (int)(e % 3);
-  const double L = va.sys[find_sys(p0, va.nsys, u)].L;
+  const SysDev &sd = va.sys[find_sys(p0, va.nsys, u)];
   double U = (double)B[8 * (size_t)u + d] + (double)Us[8 * (size_t)inv[u] + d];
-  xo[e] = wrapL(x0[e] + dt * U, L);
+  const double x = x0[e] + dt * U;
+  xo[e] = sd.def ? x : wrapL(x, sd.L);
+}
+
+// Positions of a deformed cell (Sec. 2.3.3) wrapped per particle: x = A (A^{-1} x mod L).
+__global__ void k_wrap_lattice(VecArgs va, const int64_t *__restrict__ p0, int64_t N, double *x) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= N) return;
+  const SysDev &sd = va.sys[find_sys(p0, va.nsys, u)];
+  if (!sd.def) return;
+  double *xu = x + 3 * u;
+  double z[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) z[i] = wrapL(sd.Ai[3 * i] * xu[0] + sd.Ai[3 * i + 1] * xu[1] + sd.Ai[3 * i + 2] * xu[2], sd.L);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) xu[i] = sd.A[3 * i] * z[0] + sd.A[3 * i + 1] * z[1] + sd.A[3 * i + 2] * z[2];
 }
 
 // The direction W of the random finite difference as user-order 8-slot rows
@@ -432,10 +448,11 @@ __global__ void k_rfd_final(VecArgs va, const int64_t *__restrict__ p0, int64_t 
   if (e >= 3 * N) return;
   const int64_t u = e / 3;
   const int d = (int)(e % 3);
-  const double L = va.sys[find_sys(p0, va.nsys, u)].L;
+  const SysDev &sd = va.sys[find_sys(p0, va.nsys, u)];
   const size_t r = 8 * (size_t)u + d;
   const double U = (double)B[r] + (double)U0[r] + fac * ((double)Rp[r] - (double)Rm[r]);
-  xo[e] = wrapL(x0[e] + dt * U, L);
+  const double x = x0[e] + dt * U;
+  xo[e] = sd.def ? x : wrapL(x, sd.L);
 }
 
 template <typename T>
@@ -674,6 +691,10 @@ pse_status final_update(pse_ctx *c, const double *x0, const void *B_user, const 
   VecArgs va = vec_args(c);
   DISPATCH(c, (k_final<float><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, c->d_inv, x0, (const float *)B_user, (const float *)U_sorted, dt, xout)),
            (k_final<double><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, c->d_inv, x0, (const double *)B_user, (const double *)U_sorted, dt, xout)));
+  if (c->lattice) {
+    c->nlaunch += 1;
+    k_wrap_lattice<<<grid_for(N), 256, 0, s>>>(va, c->d_p0, N, xout);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }
@@ -696,6 +717,10 @@ pse_status rfd_final(pse_ctx *c, const double *x0, const void *B, const void *U0
   VecArgs va = vec_args(c);
   DISPATCH(c, (k_rfd_final<float><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, x0, (const float *)B, (const float *)U0, (const float *)Rp, (const float *)Rm, dt, fac, xout)),
            (k_rfd_final<double><<<grid_for(3 * N), 256, 0, s>>>(va, c->d_p0, N, x0, (const double *)B, (const double *)U0, (const double *)Rp, (const double *)Rm, dt, fac, xout)));
+  if (c->lattice) {
+    c->nlaunch += 1;
+    k_wrap_lattice<<<grid_for(N), 256, 0, s>>>(va, c->d_p0, N, xout);
+  }
   PSE_CUDA_TRY(c, cudaGetLastError());
   return PSE_OK;
 }

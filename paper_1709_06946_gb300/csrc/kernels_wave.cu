@@ -70,6 +70,26 @@ __device__ __forceinline__ bool kvector(const SysDev &s, size_t idx, int &ix, in
   return !(ix == h || iy == h || iz == h || (ix == 0 && iy == 0 && iz == 0));
 }
 
+// Wave vector of half-spectrum indices (ix, iy, iz): k = (2 pi/L) m for the cube,
+// k = (2 pi/L) A^{-T} m on a deformed lattice (Sec. 2.3.3), m the signed indices.
+template <typename T>
+__device__ __forceinline__ void kcart(const SysDev &s, int ix, int iy, int iz, T k[3]) {
+  const int h = s.Ng / 2;
+  const int my = iy <= h ? iy : iy - s.Ng, mz = iz <= h ? iz : iz - s.Ng;
+  if (!s.def) {
+    k[0] = (T)(ix * s.kfac);
+    k[1] = (T)(my * s.kfac);
+    k[2] = (T)(mz * s.kfac);
+  } else if (sizeof(T) == 4) {
+    const float fx = (float)ix, fy = (float)my, fz = (float)mz;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) k[d] = (T)(s.Btf[3 * d] * fx + s.Btf[3 * d + 1] * fy + s.Btf[3 * d + 2] * fz);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) k[d] = (T)(s.Bt[3 * d] * ix + s.Bt[3 * d + 1] * my + s.Bt[3 * d + 2] * mz);
+  }
+}
+
 // P^+ of a velocity mode uh: U = s0 uh, e = (3i s1 / 2) symY(uh, k)   (D = 3i s1 uh k^T)
 template <typename T, bool WU, bool WE>
 __device__ __forceinline__ void project_out(typename Cx<T>::t *g, size_t idx, size_t cs, int slotU, int slotE,
@@ -115,8 +135,8 @@ __device__ __forceinline__ void scale_point(const ScaleArgs &sa, const SysDev &s
 #pragma unroll
   for (int m = 0; m < 8; ++m) vout[m].x = vout[m].y = (T)0;
   if (!live) return;
-  const int h = s.Ng / 2;
-  T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - s.Ng) * s.kfac), (T)((iz <= h ? iz : iz - s.Ng) * s.kfac)};
+  T k[3];
+  kcart<T>(s, ix, iy, iz, k);
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
   T s0, s1;
@@ -239,8 +259,8 @@ __global__ void k_scale11(ScaleArgs sa, typename Cx<T>::t *g_all) {
 #pragma unroll
   for (int m = 0; m < 11; ++m) o[m].x = o[m].y = (T)0;
   if (live) {
-    const int h = s.Ng / 2;
-    T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - s.Ng) * s.kfac), (T)((iz <= h ? iz : iz - s.Ng) * s.kfac)};
+    T k[3];
+    kcart<T>(s, ix, iy, iz, k);
     const T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
     const T kk = sqrt(k2), ik = (T)1 / kk;
     T s0, s1;
@@ -349,7 +369,8 @@ __global__ void k_noise(ScaleArgs sa, const T *__restrict__ w2, uint64_t seed, u
     dr[m] = re * isq2;
     di[m] = (partner ? -im : im) * isq2;
   }
-  T k[3] = {(T)(ix * s.kfac), (T)((iy <= h ? iy : iy - Ng) * s.kfac), (T)((iz <= h ? iz : iz - Ng) * s.kfac)};
+  T k[3];
+  kcart<T>(s, ix, iy, iz, k);
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
   T s0, s1;

@@ -27,9 +27,22 @@ struct Params {
   double cs;               // cell side
   int tile[3], ntile[3];   // spreading tile and tiles per side
   int ts;                  // bytes per real (4 mixed, 8 FP64)
-  double V() const { return L * L * L; }
-  double sigma() const { return h * h * h; }
+  // lattice deformation (Sec. 2.3.3): the cell is spanned by the columns of L A
+  int def = 0;             // 1: deformed lattice
+  double A[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, Ai[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // row-major
+  double detA = 1, lam_min = 1, lam_max = 1, cmax = 1;  // of the current A
+  double lam_P = 1, lam_cells = 1, cmax_grid = 1;       // what P, the cells and the grid were chosen for
+  double V() const { return L * L * L * detA; }
+  double sigma() const { return h * h * h * detA; }
 };
+
+// Lattice quantities of a deformation A (row-major 3 x 3): inverse, determinant,
+// extreme eigenvalues of A^T A and the largest column norm.  Returns 1 (with a
+// message) unless det A > 0 and every entry is finite.
+int lattice_of(const double A[9], double Ai[9], double &det, double &lam_min, double &lam_max, double &cmax,
+               std::string &err);
+// Sets p.A and its derived quantities (not the budgets lam_P, lam_cells, cmax_grid).
+int set_lattice(Params &p, const double A[9], std::string &err);
 
 // Host-side parameter rules (Sec. 2.3.1 real-space cutoff, Eq. bound support size).
 int choose_params(Params &p, const pse_options &opt, std::string &err);
@@ -91,7 +104,17 @@ struct SysDev {
   double alpha, pref;      // spreading Gaussian exp(-alpha r^2) and its prefactor
   double kfac, eta_g;      // 2 pi / L, Gaussian width
   double c_apply, c_noise; // sigma^2/(V eta) and sigma/sqrt(eta V)
+  // deformed lattice (Sec. 2.3.3); def = 0 for the cube, where only qa is read
+  int def;
+  double A[9], Ai[9];      // deformation and its inverse, row-major (x = A z)
+  double Bt[9];            // (2 pi / L) A^{-T}, row-major: wave vector k = Bt m
+  float Af[9], Btf[9];
+  double qa[6];            // Gaussian exponent alpha |A d|^2 = qa0 dx^2 + qa1 dy^2 + qa2 dz^2
+                           //   + qa3 dx dy + qa4 dx dz + qa5 dy dz (cube: alpha, alpha, alpha, 0, 0, 0)
 };
+
+// Fills the lattice fields of d (def, A, Ai, Bt, qa, c_apply, c_noise) from p.
+void fill_lattice(const Params &p, SysDev &d);
 
 // Index s with start[s] <= x < start[s + 1] (start has n + 1 entries).
 template <typename I>
@@ -148,6 +171,8 @@ struct KDev {
 struct pse_ctx {
   pse::Params p;           // shared parameters; p.N = total particles (per-suspension values in ps)
   int n_cubic = 0;         // suspensions with SysDev::cubic set
+  int lattice = 0;         // 1: created with a lattice deformation (options.deform): general spreading and
+                           // interpolation kernels, Cartesian mapping in the neighbour search, lattice wrap
   int prec;                // pse_precision
   size_t ts;               // sizeof real type (4 or 8)
   pse_options opt;

@@ -9,6 +9,7 @@
 // that do not fit yet wait in arrival order while later ones that fit go ahead.
 // The paper has no serving layer; this is the request loop around its method.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -32,12 +33,32 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
+// The options a handle is created with, as numbers (a request without options
+// has the defaults), so that requests that differ in them get their own handles.
+using OptVec = std::array<double, 32>;
+OptVec opt_vec(const pse_options *q) {
+  pse_options o;
+  pse_default_options(&o);
+  if (q) o = *q;
+  OptVec v{};
+  int n = 0;
+  for (double x : {(double)o.rule, (double)o.Ng, (double)o.P, (double)o.table_points, o.rcut, o.lanczos_tol,
+                   (double)o.lanczos_maxiter, o.krylov_tol, (double)o.krylov_maxiter, (double)o.tile[0],
+                   (double)o.tile[1], (double)o.tile[2], (double)o.real_lanes, (double)o.grid_ladder,
+                   (double)o.use_graph, (double)o.wave_kernel, (double)o.torque, (double)o.lambda_support})
+    v[n++] = x;
+  for (int i = 0; i < 9; ++i) v[n++] = o.deform[i];
+  return v;
+}
+
 struct Key {
   int64_t N;
   double L, a, eta, kT, xi, tol;
   int prec;
+  OptVec opt;
   bool operator<(const Key &o) const {
-    return std::tie(N, L, a, eta, kT, xi, tol, prec) < std::tie(o.N, o.L, o.a, o.eta, o.kT, o.xi, o.tol, o.prec);
+    return std::tie(N, L, a, eta, kT, xi, tol, prec, opt) <
+           std::tie(o.N, o.L, o.a, o.eta, o.kT, o.xi, o.tol, o.prec, o.opt);
   }
   bool operator==(const Key &o) const { return !(*this < o) && !(o < *this); }
 };
@@ -61,7 +82,7 @@ struct Job {
 };
 
 Key key_of(const pse_request &r) {
-  return Key{r.N, r.L, r.a, r.eta, r.kT, r.xi, r.tol, r.precision};
+  return Key{r.N, r.L, r.a, r.eta, r.kT, r.xi, r.tol, r.precision, opt_vec(r.options)};
 }
 
 double percentile(std::vector<double> v, double q) {

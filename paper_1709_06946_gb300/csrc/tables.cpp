@@ -44,13 +44,44 @@ double kcut_rule(double xi, double tol) {
   return 2.0 * xi * std::sqrt(hi);
 }
 
-int support_rule(double tol) {
+// Smallest P meeting Eq. bound (C = 1, m = sqrt(pi P)) with the largest eigenvalue
+// lam of A^T A of the lattice deformation (lam = 1: orthorhombic grids).
+int support_rule(double tol, double lam) {
   for (int P = 1; P < 64; ++P) {
     double m = std::sqrt(kPi * P);
-    double b = std::exp(-kPi * P / 2.0) + std::erfc(m / std::sqrt(2.0));
+    double b = std::exp(-kPi * kPi * P * P / (2.0 * m * m * lam)) + std::erfc(m / std::sqrt(2.0 * lam));
     if (b <= tol) return P;
   }
   return 64;
+}
+
+// Eigenvalues of a symmetric 3 x 3 matrix (row-major) by cyclic Jacobi rotations.
+void sym3_eigenvalues(const double S[9], double ev[3]) {
+  double a[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) a[i][j] = S[3 * i + j];
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = std::fabs(a[0][1]) + std::fabs(a[0][2]) + std::fabs(a[1][2]);
+    if (off < 1e-300) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (a[p][q] == 0.0) continue;
+        const double th = 0.5 * (a[q][q] - a[p][p]) / a[p][q];
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < 3; ++k) {  // columns p, q
+          const double akp = a[k][p], akq = a[k][q];
+          a[k][p] = c * akp - sn * akq;
+          a[k][q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < 3; ++k) {  // rows p, q
+          const double apk = a[p][k], aqk = a[q][k];
+          a[p][k] = c * apk - sn * aqk;
+          a[q][k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  for (int i = 0; i < 3; ++i) ev[i] = a[i][i];
 }
 
 bool smooth2357(int n) {
@@ -201,6 +232,56 @@ double conv(const GL &gl, int k, int n, double r, double xi, double a) {
 
 }  // namespace
 
+int lattice_of(const double A[9], double Ai[9], double &det, double &lam_min, double &lam_max, double &cmax,
+               std::string &err) {
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(A[i])) {
+      err = "lattice deformation has a non-finite entry";
+      return 1;
+    }
+  det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+  if (!(det > 1e-12)) {
+    err = "lattice deformation needs det A > 0";
+    return 1;
+  }
+  // inverse by cofactors
+  Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+  Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+  Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+  Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+  Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+  Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+  Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+  Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+  Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  double G[9], ev[3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) G[3 * i + j] = A[i] * A[j] + A[3 + i] * A[3 + j] + A[6 + i] * A[6 + j];
+  sym3_eigenvalues(G, ev);
+  lam_min = std::min(ev[0], std::min(ev[1], ev[2]));
+  lam_max = std::max(ev[0], std::max(ev[1], ev[2]));
+  cmax = 0;
+  for (int j = 0; j < 3; ++j) cmax = std::max(cmax, std::sqrt(G[4 * j]));
+  return 0;
+}
+
+int set_lattice(Params &p, const double A[9], std::string &err) {
+  double Ai[9], det, lmin, lmax, cm;
+  if (lattice_of(A, Ai, det, lmin, lmax, cm, err)) return 1;
+  bool ident = true;
+  for (int i = 0; i < 9; ++i) ident = ident && A[i] == ((i % 4 == 0) ? 1.0 : 0.0);
+  p.def = ident ? 0 : 1;
+  for (int i = 0; i < 9; ++i) {
+    p.A[i] = A[i];
+    p.Ai[i] = Ai[i];
+  }
+  p.detA = det;
+  p.lam_min = lmin;
+  p.lam_max = lmax;
+  p.cmax = cm;
+  return 0;
+}
+
 int choose_params(Params &p, const pse_options &opt, std::string &err) {
   if (!(p.N >= 1) || !(p.L > 0) || !(p.a > 0) || !(p.eta > 0) || !(p.kT >= 0) || !(p.xi > 0) ||
       !(p.tol > 0 && p.tol <= 0.1)) {
@@ -208,17 +289,26 @@ int choose_params(Params &p, const pse_options &opt, std::string &err) {
     return 1;
   }
   p.rule = opt.rule;
+  {  // lattice deformation (Sec. 2.3.3); all zero = the cube
+    bool any = false;
+    for (int i = 0; i < 9; ++i) any = any || opt.deform[i] != 0.0;
+    const double I3[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (set_lattice(p, any ? opt.deform : I3, err)) return 1;
+    p.lam_P = (p.def && opt.lambda_support) ? p.lam_max : 1.0;
+    p.lam_cells = p.lam_min;
+    p.cmax_grid = p.cmax;
+  }
   double tq = p.rule == PSE_RULE_PAPER ? p.tol : p.tol / 10.0;
   p.rcut = opt.rcut > 0 ? opt.rcut
                         : (p.rule == PSE_RULE_PAPER ? std::sqrt(std::log(1.0 / p.tol)) / p.xi
                                                     : p.a + std::sqrt(std::log(10.0 / p.tol)) / p.xi);
   p.kcut = kcut_rule(p.xi, p.tol);
-  p.P = opt.P > 0 ? opt.P : support_rule(tq);
+  p.P = opt.P > 0 ? opt.P : support_rule(tq, p.lam_P);
   p.m = std::sqrt(kPi * p.P);
   if (opt.Ng > 0) {
     p.Ng = opt.Ng;
   } else {
-    p.Ng = next_grid(p.kcut * p.L / kPi);
+    p.Ng = next_grid(p.kcut * p.L * p.cmax / kPi);  // every |k| <= k_cut on the grid (cmax = 1 for the cube)
     while (true) {
       double h = p.L / p.Ng, eg = (h * p.P * p.xi / p.m) * (h * p.P * p.xi / p.m);
       if (eg < 1.0) break;
@@ -226,22 +316,37 @@ int choose_params(Params &p, const pse_options &opt, std::string &err) {
     }
     if (opt.grid_ladder) p.Ng = ladder_grid(p.Ng);  // a finer grid only lowers the NUFFT error
   }
-  p.h = p.L / p.Ng;
-  p.eta_g = (p.h * p.P * p.xi / p.m) * (p.h * p.P * p.xi / p.m);
-  p.nkx = p.Ng / 2 + 1;
-  if (p.Ng % 2 || p.Ng < 4 || p.Ng > 4096) { err = "grid size must be even, 4..4096"; return 1; }
-  if (p.P < 1 || p.P > 32 || p.P > p.Ng) { err = "support size out of range"; return 1; }
-  if (!(p.eta_g < 1.0)) { err = "Gaussian width eta_g >= 1 (refine the grid)"; return 1; }
-  if (p.rcut > 0.5 * p.L) {
-    err = "r_cut " + std::to_string(p.rcut) + " exceeds L/2 " + std::to_string(0.5 * p.L) +
-          " (minimum-image pair sum): enlarge the box or increase xi";
+  // half-width of the cell: L/2 for the cube, L sqrt(lambda_min)/2 on a deformed lattice
+  const double half = 0.5 * p.L * std::sqrt(p.lam_cells);
+  if (p.rcut > half * (1.0 + 1e-12)) {
+    err = "r_cut " + std::to_string(p.rcut) + " exceeds the half-width " + std::to_string(half) +
+          " of the cell (minimum-image pair sum): enlarge the box or increase xi";
     return 1;
   }
-  // linked cells of side >= r_cut/2, searched with a 5 x 5 x 5 stencil (all cells when nc < 5)
-  p.nc = std::max(1, std::min(1023, (int)std::floor(2.0 * p.L / p.rcut)));
+  // linked cells of side >= r_cut/2, searched with a 5 x 5 x 5 stencil (all cells when nc < 5); on a
+  // deformed lattice the cells are cubes in lattice coordinates, where a pair closer than r_cut is
+  // closer than r_cut / sqrt(lambda_min)
+  p.nc = std::max(1, std::min(1023, (int)std::floor(2.0 * p.L * std::sqrt(p.lam_cells) / p.rcut)));
   p.cs = p.L / p.nc;
   const int caps[3] = {16, 16, 16};
-  return choose_tile(p, caps, opt.tile, err);
+  // The spreading tile must hold P - 1 points per side and fit shared memory; a
+  // large support (deformed lattices) may need a grid with a suitable divisor: the
+  // next 2,3,5,7-smooth sizes are tried (a finer grid only lowers the NUFFT error).
+  for (int attempt = 0;; ++attempt) {
+    p.h = p.L / p.Ng;
+    p.eta_g = (p.h * p.P * p.xi / p.m) * (p.h * p.P * p.xi / p.m);
+    p.nkx = p.Ng / 2 + 1;
+    if (p.Ng % 2 || p.Ng < 4 || p.Ng > 4096) { err = "grid size must be even, 4..4096"; return 1; }
+    if (p.P < 1 || p.P > 32 || p.P > p.Ng) { err = "support size out of range"; return 1; }
+    if (!(p.eta_g < 1.0)) { err = "Gaussian width eta_g >= 1 (refine the grid)"; return 1; }
+    std::string terr;
+    if (choose_tile(p, caps, opt.tile, terr) == 0) return 0;
+    if (opt.Ng > 0 || attempt >= 64) {
+      err = terr;
+      return 1;
+    }
+    p.Ng = next_grid(p.Ng + 1);
+  }
 }
 
 // Spreading tile of a suspension: the largest divisors of Ng within caps (x

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
               for (int c = 0; c < C; ++c) acc[c] += wt * vv[c];
             }
           }
-        } else {  // any support size: weights on the fly
+        } else {  // any support size and any lattice: weights on the fly, exp(-alpha |A d|^2)
           for (int b0 = 0; b0 < P * P; b0 += 32) {
             const int it = b0 + lane;
             const int jx = it % P, jy = it / P;
@@ -162,14 +162,15 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
             if (ly >= Ng) ly -= Ng;
             if (it < P * P && lx < Tx && ly < Ty) {
               const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-              const T wxy = exp(-alpha * (dx * dx + dy * dy));
+              const T qxy = (T)a.qa[0] * dx * dx + (T)a.qa[1] * dy * dy + (T)a.qa[3] * dx * dy;
+              const T lin = (T)a.qa[4] * dx + (T)a.qa[5] * dy, q2 = (T)a.qa[2];
               const int col = ly * RX + lx;
               for (int jz = 0; jz < P; ++jz) {
                 int lz = ez + jz;
                 if (lz >= Ng) lz -= Ng;
                 if (lz < Tz) {
                   const T dz = d0.z + (T)jz * hs;
-                  const T wt = wxy * exp(-alpha * dz * dz);
+                  const T wt = exp(-(qxy + dz * (lin + q2 * dz)));
                   T vv[C];
                   tl.load(col + lz * zstride, vv);
 #pragma unroll
@@ -204,6 +205,7 @@ void launch_interp(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
 
 template <typename T, int C, int SLOT0, int ROW = 8, int COMP0 = 0>
 void interp_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
+  if (c->lattice) return launch_interp<T, C, SLOT0, 0, ROW, COMP0>(c, a, vout, s);  // non-separable weights
   switch (a.P) {
     case 5: launch_interp<T, C, SLOT0, 5, ROW, COMP0>(c, a, vout, s); break;
     case 6: launch_interp<T, C, SLOT0, 6, ROW, COMP0>(c, a, vout, s); break;

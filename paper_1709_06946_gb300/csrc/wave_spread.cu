@@ -132,9 +132,9 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
                 tl.store(i, vv);
               }
             }
-          } else {  // any support size: weights on the fly
+          } else {  // any support size and any lattice: weights on the fly, exp(-alpha |A d|^2)
             const T dz = d0.z + (T)ez * hs;
-            const T wz = pref * exp(-alpha * dz * dz);
+            const T qz = (T)a.qa[2] * dz * dz, q4 = (T)a.qa[4] * dz, q5 = (T)a.qa[5] * dz;
             for (int ib = 0; ib < nitem; ib += 32) {
               const int it = ib + lane;
               const int jx = it % P, jy = it / P;
@@ -143,7 +143,8 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
               if (ly >= Ng) ly -= Ng;
               if (it < nitem && lx < Tx && ly < Ty) {
                 const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-                const T wt = exp(-alpha * (dx * dx + dy * dy)) * wz;
+                const T q = (T)a.qa[0] * dx * dx + (T)a.qa[1] * dy * dy + (T)a.qa[3] * dx * dy + q4 * dx + q5 * dy + qz;
+                const T wt = pref * exp(-q);
                 const int i = plane + ly * RX + lx;
                 T vv[C];
                 tl.load(i, vv);
@@ -187,6 +188,7 @@ void launch_spread(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t 
 
 template <typename T, int C, int SLOT0, int ROW = 8, int COMP0 = 0>
 void spread_p(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
+  if (c->lattice) return launch_spread<T, C, SLOT0, 0, ROW, COMP0>(c, a, vin, s);  // non-separable weights
   switch (a.P) {
     case 5: launch_spread<T, C, SLOT0, 5, ROW, COMP0>(c, a, vin, s); break;
     case 6: launch_spread<T, C, SLOT0, 6, ROW, COMP0>(c, a, vin, s); break;

@@ -44,7 +44,18 @@ def test_invalid_arguments_rejected(lib):
     lib.pse_default_options(ctypes.byref(o))
     # r_cut = 1 + sqrt(ln(1e4))/0.5 = 7.07 > L/2 = 5: rejected before any device call
     assert lib.pse_create(ctypes.byref(h), 10, 10.0, 1.0, 1.0, 1.0, 0.5, 1e-3, 0, ctypes.byref(o)) == 1
-    assert b'exceeds L/2' in lib.pse_last_error(None)
+    assert b'exceeds the half-width 5.0' in lib.pse_last_error(None)
+    # a sheared cell (strain 1/2) is narrower: L sqrt(lambda_min)/2 = 7.81 < r_cut 7.98 at L = 20, xi = 0.43
+    for i, v in enumerate([1.0, 0.5, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0, 1.0]):
+        o.deform[i] = v
+    assert lib.pse_create(ctypes.byref(h), 10, 20.0, 1.0, 1.0, 1.0, 0.43, 1e-3, 0, ctypes.byref(o)) == 1
+    assert b'half-width 7.8' in lib.pse_last_error(None)
+    # det A <= 0 is refused
+    for i, v in enumerate([1.0, 0.0, 0.0, 0.0, -1.0, 0.0, 0.0, 0.0, 1.0]):
+        o.deform[i] = v
+    assert lib.pse_create(ctypes.byref(h), 10, 20.0, 1.0, 1.0, 1.0, 0.8, 1e-3, 0, ctypes.byref(o)) == 1
+    assert b'det A > 0' in lib.pse_last_error(None)
+    lib.pse_default_options(ctypes.byref(o))
     assert lib.pse_create(ctypes.byref(h), 0, 30.0, 1.0, 1.0, 1.0, 0.5, 1e-3, 0, ctypes.byref(o)) == 1
     assert lib.pse_create(ctypes.byref(h), 10, 30.0, 1.0, 1.0, 1.0, 0.5, 0.5, 0, ctypes.byref(o)) == 1
     assert lib.pse_status_string(4) == b'Krylov iteration cap reached'
