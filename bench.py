@@ -69,6 +69,8 @@ def parse():
     ap.add_argument('--torque-reps', type=int, default=5,
                     help='timed 11-moment (torque) products on the workload for the default line (0: omit)')
     ap.add_argument('--eps2', type=float, default=1e-4, help='second PSE tolerance of the default line (0: omit)')
+    ap.add_argument('--shear-steps', type=int, default=5,
+                    help='timed steps on the sheared cell (strain 0.5) for the default line (0: omit)')
     ap.add_argument('--rfd-steps', type=int, default=3, help='timed RFD + Euler-Maruyama steps (0: omit)')
     ap.add_argument('--batch-steps', type=int, default=3,
                     help='timed steps of the 256-suspension block of the default line (0: omit)')
@@ -565,6 +567,8 @@ def run_ours(args, world, rank, local, pg):
         result['rfd'] = rfd_measure(pkg, torch, dev, args, pos_np, L, value)
     if rank == 0 and world == 1 and args.torque_reps > 0:
         result['torque'] = torque_measure(pkg, torch, dev, args, pos_np, L, args.torque_reps)
+    if rank == 0 and world == 1 and args.shear_steps > 0:
+        result['lattice'] = lattice_measure(pkg, torch, dev, args, pos_np, L, value, steps=args.shear_steps)
     if rank == 0 and world == 1 and args.eps2 > 0:
         result['eps_%g' % args.eps2] = eps_measure(pkg, torch, dev, args, pos_np, L, args.eps2)
     if rank == 0 and world == 1 and args.batch_steps > 0:
@@ -804,6 +808,43 @@ def rfd_measure(pkg, torch, dev, args, pos_np, L, midpoint_rate):
             'midpoint_speedup': midpoint_rate * t,
             'note': 'Euler-Maruyama with random-finite-difference drift (3 stresslet solves per step, host-launched) '
                     'against the graph-captured mid-point step (1 solve)'}
+
+
+def lattice_measure(pkg, torch, dev, args, pos_np, L, cubic_rate, gamma=0.5, steps=5, warmup=2):
+    """The constrained step on a sheared cell (strain gamma, Sec. 2.3.3; the workload's particles
+    mapped into the cell), mixed precision, graph-captured: with the support size from Eq. bound
+    with lambda_max (the default) and with the orthorhombic rule lambda_max = 1 (fewer support
+    points, but past the tolerance on this lattice)."""
+    stream = torch.cuda.current_stream(dev)
+    A = np.array([[1.0, gamma, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    out = {'strain': gamma, 'lambda_max': 1 + gamma * gamma / 2 + gamma * np.sqrt(1 + gamma * gamma / 4)}
+    for key, aware in (('lambda_aware', 1), ('orthorhombic_rule', 0)):
+        h = pkg.PSE(args.N, L, xi=args.xi, tol=args.tol, precision='mixed', use_graph=args.graph, deform=A,
+                    lambda_support=aware)
+        inf = h.info
+        x = torch.tensor(pos_np @ A.T, device=dev, dtype=torch.float64)
+        for k in range(warmup):
+            h.step(x, args.dt, seed=2468, step=k)
+        torch.cuda.synchronize(dev)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        its = []
+        ev0.record(stream)
+        for k in range(steps):
+            _, st = h.step(x, args.dt, seed=2468, step=warmup + k)
+            its.append((st['lanczos_iters'], st['krylov_iters']))
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        t = ev0.elapsed_time(ev1) / 1000.0 / steps
+        h.close()
+        out[key] = {'steps_per_s': 1.0 / t, 'ms_per_step': 1000.0 * t, 'P': inf['P'], 'Ng': inf['Ng'],
+                    'rcut': inf['rcut'], 'cells_per_side': inf['cells_per_side'],
+                    'lanczos_mean': float(np.mean([i[0] for i in its])),
+                    'krylov_mean': float(np.mean([i[1] for i in its]))}
+    out['cubic_over_sheared'] = cubic_rate / out['lambda_aware']['steps_per_s']
+    out['note'] = ('sheared cell: general spreading / interpolation kernels (non-separable Gaussian weights '
+                   'per support point), grid resolving k_cut along the longest lattice column')
+    return out
 
 
 def torque_measure(pkg, torch, dev, args, pos_np, L, reps, warmup=2):

@@ -219,3 +219,27 @@ def test_graph_step_equals_host_step_deformed(pkg):
         assert _rel(dg, de) < 1e-5
     he.close()
     hg.close()
+
+
+@pytest.mark.parametrize('name', ['shear', 'extension'])
+def test_sedimentation_error_follows_support_rule(pkg, name):
+    """The comparison of Fig. fig:shear on the GPU: the sedimentation velocity (equal forces on all
+    particles) against the dense Ewald sum on the deformed lattice is within the tolerance with the
+    lambda_max-aware support, and worse with the orthorhombic rule (for lambda_max = 2.25 by more
+    than an order of magnitude past the tolerance)."""
+    N, phi, xi, tol = 100, 0.1, 0.7, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=1)
+    A = LATTICES[name]
+    F = np.tile([0.0, 0.0, 1.0], (N, 1))
+    M = ewald.dense_mobility(pos, L, xi=0.6, tol=1e-15, A=A)
+    ref = (M @ np.concatenate([F, np.zeros((N, 5))], 1).ravel()).reshape(N, 8)[:, :3]
+    errs = {}
+    for aware in (1, 0):
+        h = pkg.PSE(N, L, xi=xi, tol=tol, precision='fp64', deform=A, lambda_support=aware)
+        U, _ = h.mobility(_cuda(pos, torch.float64), _cuda(F, torch.float64), None)
+        errs[aware] = _rel(U.cpu().numpy(), ref)
+        h.close()
+    assert errs[1] < tol
+    assert errs[0] > 3 * errs[1]
+    if name == 'extension':
+        assert errs[0] > 10 * tol
