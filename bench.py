@@ -842,8 +842,9 @@ def lattice_measure(pkg, torch, dev, args, pos_np, L, cubic_rate, gamma=0.5, ste
                     'lanczos_mean': float(np.mean([i[0] for i in its])),
                     'krylov_mean': float(np.mean([i[1] for i in its]))}
     out['cubic_over_sheared'] = cubic_rate / out['lambda_aware']['steps_per_s']
-    out['note'] = ('sheared cell: general spreading / interpolation kernels (non-separable Gaussian weights '
-                   'per support point), grid resolving k_cut along the longest lattice column')
+    out['note'] = ('sheared cell: the 16^3-tile spreading / interpolation kernels with x-y coupled Gaussian '
+                   'weights (the 8-component interpolation on the general kernels), grid resolving k_cut along '
+                   'the longest lattice column')
     return out
 
 

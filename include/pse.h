@@ -134,7 +134,9 @@ typedef struct pse_info {
   double table_dr;
   int64_t device_bytes;    /* bytes allocated on the device by this handle */
   int32_t deformed;        /* 1: the lattice is deformed (options.deform or pse_set_deformation) */
-  int32_t reserved_i;
+  int32_t tile_kernels;    /* 1: spreading and interpolation run the kernels specialised for 16^3 tiles
+                              (mixed precision, P = 5, 6, 8 or 10, at least two tiles per side; on a
+                              deformed lattice only with z orthogonal to the deformed plane) */
   double deform[9];        /* current deformation A (row-major; the identity for the cube) */
   double lambda_max;       /* largest eigenvalue of A^T A that the support size P was chosen for */
   double lambda_min_cells; /* smallest eigenvalue of A^T A that the cells and r_cut allow */

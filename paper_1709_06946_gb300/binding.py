@@ -42,7 +42,7 @@ class Info(ctypes.Structure):
                 ('eta_g', ctypes.c_double), ('m', ctypes.c_double), ('Ng', ctypes.c_int32),
                 ('P', ctypes.c_int32), ('cells_per_side', ctypes.c_int32), ('tile', ctypes.c_int32 * 3),
                 ('table_len', ctypes.c_int32), ('table_dr', ctypes.c_double),
-                ('device_bytes', ctypes.c_int64), ('deformed', ctypes.c_int32), ('reserved_i', ctypes.c_int32),
+                ('device_bytes', ctypes.c_int64), ('deformed', ctypes.c_int32), ('tile_kernels', ctypes.c_int32),
                 ('deform', ctypes.c_double * 9), ('lambda_max', ctypes.c_double),
                 ('lambda_min_cells', ctypes.c_double), ('colnorm_max', ctypes.c_double)]
 
@@ -332,7 +332,7 @@ class PSE:
         """Parameters of suspension s (grid, cells, tiles, ...)."""
         inf = Info()
         self._check(self._lib.pse_get_system_info(self._h, int(s), ctypes.byref(inf)))
-        d = {k: getattr(inf, k) for k, _ in Info._fields_ if k != 'reserved_i'}
+        d = {k: getattr(inf, k) for k, _ in Info._fields_}
         d['tile'] = tuple(inf.tile)
         d['deform'] = np.array(inf.deform[:]).reshape(3, 3)
         return d
@@ -350,7 +350,7 @@ class PSE:
     def get_info(self):
         inf = Info()
         self._check(self._lib.pse_get_info(self._h, ctypes.byref(inf)))
-        d = {k: getattr(inf, k) for k, _ in Info._fields_ if k != 'reserved_i'}
+        d = {k: getattr(inf, k) for k, _ in Info._fields_}
         d['tile'] = tuple(inf.tile)
         d['deform'] = np.array(inf.deform[:]).reshape(3, 3)
         return d

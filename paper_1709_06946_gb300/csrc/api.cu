@@ -681,8 +681,20 @@ namespace {
 // Marks a suspension for the spreading / interpolation kernels specialised for
 // 16^3 tiles (mixed precision, P = 5, 6 or 8, at least two tiles per side) and
 // counts it in c->n_cubic.
-void set_cubic(pse_ctx *c, SysDev &d) {
-  bool ok = c->prec == PSE_MIXED && (c->p.P == 5 || c->p.P == 6 || c->p.P == 8) && !c->lattice;
+// Whether A^T A couples z with x or y (the 16^3-tile kernels on a deformed
+// lattice need the z axis orthogonal to the deformed plane, as in shear and
+// planar extension).
+bool z_coupled(const double A[9]) {
+  const double g13 = A[0] * A[2] + A[3] * A[5] + A[6] * A[8], g23 = A[1] * A[2] + A[4] * A[5] + A[7] * A[8];
+  return g13 != 0.0 || g23 != 0.0;
+}
+
+void set_cubic(pse_ctx *c, SysDev &d, const Params &p) {
+  // P = 10 and deformed lattices only with the default kernels (the optional
+  // 16^3 variants have neither)
+  const bool defaults = c->opt.wave_kernel == 0;
+  bool ok = c->prec == PSE_MIXED && (c->p.P == 5 || c->p.P == 6 || c->p.P == 8 || (c->p.P == 10 && defaults));
+  if (c->lattice) ok = ok && defaults && !z_coupled(p.A);
   for (int k = 0; k < 3; ++k) ok = ok && d.T[k] == CUBE_TILE && d.nt[k] >= 2;
   d.cubic = ok ? 1 : 0;
   c->n_cubic += d.cubic;
@@ -750,7 +762,7 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
       d.T[k] = p.tile[k];
       d.nt[k] = p.ntile[k];
     }
-    set_cubic(c, d);
+    set_cubic(c, d, p);
     d.L = p.L;
     d.h = p.h;
     d.cs = p.cs;
@@ -1107,7 +1119,7 @@ pse_status retile(pse_ctx *c, const int caps[3]) {
       c->hs[q].T[d] = ps[q].tile[d];
       c->hs[q].nt[d] = ps[q].ntile[d];
     }
-    set_cubic(c, c->hs[q]);
+    set_cubic(c, c->hs[q], c->ps[q]);
     c->hs[q].tile0 = tile0[q];
   }
   c->ntiles = nt;
@@ -1346,6 +1358,7 @@ pse_status pse_get_info(pse_handle h, pse_info *o) {
   if (!h || !o) return PSE_ERR_INVALID_ARG;
   fill_info(h, h->ps.empty() ? h->p : h->ps[0], h->dev_bytes, o);
   o->N = h->p.N;
+  o->tile_kernels = h->hs.empty() ? 0 : h->hs[0].cubic;
   return PSE_OK;
 }
 
@@ -1375,6 +1388,11 @@ pse_status pse_set_deformation(pse_handle h, const double *A, pse_stream stream)
                std::to_string(p.lam_cells) + " the cells and r_cut were chosen for";
       return PSE_ERR_INVALID_ARG;
     }
+    if (h->n_cubic > 0 && z_coupled(p.A)) {
+      h->err = "pse_set_deformation: the handle runs the 16^3-tile kernels, which need A^T A to leave z "
+               "uncoupled (shear or extension in the x-y plane)";
+      return PSE_ERR_INVALID_ARG;
+    }
     if (p.cmax > p.cmax_grid * (1 + tiny) && h->opt.Ng <= 0) {
       h->err = "pse_set_deformation: column norm " + std::to_string(p.cmax) + " exceeds the " +
                std::to_string(p.cmax_grid) + " the grid was chosen for";
@@ -1400,6 +1418,7 @@ const char *pse_graph_error(pse_handle h) { return h ? h->graph_error.c_str() : 
 pse_status pse_get_system_info(pse_handle h, int32_t s, pse_info *o) {
   if (!h || !o || s < 0 || s >= h->nsys) return PSE_ERR_INVALID_ARG;
   fill_info(h, h->ps[s], h->dev_bytes, o);
+  o->tile_kernels = h->hs[s].cubic;
   return PSE_OK;
 }
 

@@ -258,7 +258,11 @@ __device__ __forceinline__ unsigned region_mask(int ex, int ey, int ez) {
 // tile, and appends its slot to the hit list of each warp whose block it meets;
 // after a barrier each warp adds the records of its list into its columns.  One
 // scan and one record per candidate instead of one per candidate and warp.
-template <int C, int SLOT0, int P, int ZT>
+// DEF: deformed lattice (Sec. 2.3.3) with the z axis orthogonal to the sheared
+// plane (A^T A couples x and y only): the x-y weight of a column is
+// exp(-alpha (G_xx dx^2 + 2 G_xy dx dy + G_yy dy^2)) and the z weights use G_zz,
+// from the suspension's coefficients SysDev::qa.
+template <int C, int SLOT0, int P, int ZT, bool DEF = false>
 __global__ void __launch_bounds__(32 * 8 * (16 / ZT), (16 / ZT == 1 || C <= 5) ? 2 : 1)
     k_spread_colq(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0, const float4 *__restrict__ sp_d0,
                   const float *__restrict__ vin, const int *__restrict__ fine_start, float *__restrict__ grid_all) {
@@ -283,6 +287,9 @@ __global__ void __launch_bounds__(32 * 8 * (16 / ZT), (16 / ZT == 1 || C <= 5) ?
     if (w == 0) col_ranges(a, t, 0, TS, P, lane, fine_start, s_rng);
     if (tid < 2 * NW) (&s_cnt[0][0])[tid] = 0;
     const float nal = -(float)a.alpha * COL_LOG2E, hs = (float)a.h, pref = (float)a.pref;
+    // deformed lattice: exponent coefficients (base 2) of the x-y form and of z
+    const float kxx = DEF ? -(float)a.qa[0] * COL_LOG2E : nal, kyy = DEF ? -(float)a.qa[1] * COL_LOG2E : nal;
+    const float kxy = DEF ? -(float)a.qa[3] * COL_LOG2E : 0.f, kzz = DEF ? -(float)a.qa[2] * COL_LOG2E : nal;
     float acc[ZT][C];
 #pragma unroll
     for (int z = 0; z < ZT; ++z)
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(32 * 8 * (16 / ZT), (16 / ZT == 1 || C <= 5) ?
 #pragma unroll
           for (int j = 0; j < P; ++j) {
             const float oz = d0.z + (float)j * hs;
-            q[4 + C + j] = exp2f(nal * oz * oz);
+            q[4 + C + j] = exp2f((DEF ? kzz : nal) * oz * oz);
           }
           float *r = rec + (size_t)slot * RF;
 #pragma unroll
@@ -366,7 +373,7 @@ __global__ void __launch_bounds__(32 * 8 * (16 / ZT), (16 / ZT == 1 || C <= 5) ?
         const int px = (pk & 1023) - 512, py = ((pk >> 10) & 1023) - 512, pz = (pk >> 20) - 512 - wz0;
         const int jx = cx - px, jy = cy - py;
         const float ox = q[1] + (float)jx * hs, oy = q[2] + (float)jy * hs;
-        float wxy = exp2f(nal * (ox * ox + oy * oy));
+        float wxy = DEF ? exp2f(kxx * ox * ox + kxy * ox * oy + kyy * oy * oy) : exp2f(nal * (ox * ox + oy * oy));
         wxy = ((unsigned)jx < (unsigned)P && (unsigned)jy < (unsigned)P) ? wxy : 0.f;
         float m[C], wz[P];
 #pragma unroll
@@ -515,11 +522,11 @@ void interp_col_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   }
 }
 
-template <int C, int SLOT0, int P, int ZT>
+template <int C, int SLOT0, int P, int ZT, bool DEF = false>
 void launch_spread_col_z(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
   constexpr int NT = 32 * 8 * (CUBE / ZT);
   int *q = next_queue(c, s);
-  if (c->opt.wave_kernel & 4) {  // every warp scans the candidates itself
+  if (!DEF && (c->opt.wave_kernel & 4)) {  // every warp scans the candidates itself
     static OccCache occ;
     auto kern = k_spread_col<C, SLOT0, P, ZT>;
     const unsigned grid = wave_grid(c, kern, 0, a.ntiles, occ, NT);
@@ -529,7 +536,7 @@ void launch_spread_col_z(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStr
   }
   static std::once_flag once;
   static OccCache occ;
-  auto kern = k_spread_colq<C, SLOT0, P, ZT>;
+  auto kern = k_spread_colq<C, SLOT0, P, ZT, DEF>;
   set_smem(kern, once);
   constexpr size_t sm = (size_t)2 * NT * ColRec<C, P>::FLOATS * sizeof(float) +
                         (size_t)(NT / 32) * 2 * NT * sizeof(unsigned short);
@@ -544,15 +551,22 @@ void launch_spread_col_z(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStr
 // of option wave_kernel.
 template <int C, int SLOT0, int P>
 void launch_spread_col(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
-  if (C <= 5 && (c->opt.wave_kernel & 8)) launch_spread_col_z<C, SLOT0, P, 16>(c, a, vin, s);
+  if (c->lattice) launch_spread_col_z<C, SLOT0, P, 8, true>(c, a, vin, s);  // default split only
+  else if (C <= 5 && (c->opt.wave_kernel & 8)) launch_spread_col_z<C, SLOT0, P, 16>(c, a, vin, s);
   else launch_spread_col_z<C, SLOT0, P, 8>(c, a, vin, s);
 }
 
+// P = 10 (the support Eq. bound gives on a cell sheared by 1/2) only with the
+// default kernels (set_cubic admits it only then).
 template <int C, int SLOT0>
 void spread_col_p(pse_ctx *c, const WaveArgs &a, const void *vin, cudaStream_t s) {
   switch (a.P) {
     case 5: launch_spread_col<C, SLOT0, 5>(c, a, vin, s); break;
     case 6: launch_spread_col<C, SLOT0, 6>(c, a, vin, s); break;
+    case 10:
+      if (c->lattice) launch_spread_col_z<C, SLOT0, 10, 8, true>(c, a, vin, s);
+      else launch_spread_col_z<C, SLOT0, 10, 8>(c, a, vin, s);
+      break;
     default: launch_spread_col<C, SLOT0, 8>(c, a, vin, s);
   }
 }

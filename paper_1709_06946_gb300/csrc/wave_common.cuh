@@ -266,6 +266,9 @@ __device__ __forceinline__ bool wave_skip(const WaveArgs &wa, int si, const SysD
 void spread16_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
 void spread_col_launch(pse_ctx *c, const WaveArgs &a, const void *vin, int mode, cudaStream_t s);
 void interp_col_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
+// General interpolation kernels (any tile) for the suspensions a selects; the
+// 16^3-tile kernels fall back to them where their staging does not fit.
+void interp_general_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s);
 // 11-moment product (12-slot rows [F, L, S] / [U, Omega, E]), general kernels
 void spread11_launch(pse_ctx *c, const void *vin12, cudaStream_t s);
 void interp11_launch(pse_ctx *c, void *vout12, cudaStream_t s);

@@ -31,7 +31,10 @@ template <int P> struct Halo {
   static constexpr int NCOL = (P * P + 7) / 8;     // column passes per lane
 };
 
-template <int C, int SLOT0, int P>
+// DEF: deformed lattice with z orthogonal to the sheared plane (as the
+// register-column spreading): the x-y weight of each support column is its own
+// exponential of the x-y quadratic form; the z weights use G_zz.
+template <int C, int SLOT0, int P, bool DEF = false>
 __global__ void __launch_bounds__(HALO_THREADS, 2)
     k_interp_halo(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0, const float4 *__restrict__ sp_d0,
                   const int *__restrict__ fine_start, const float *__restrict__ grid_all, float *__restrict__ vout) {
@@ -79,6 +82,8 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
     const int64_t fb = (int64_t)tile * SUB_BLOCKS + kz * SUB_SIDE * SUB_SIDE;
     const int beg = fine_start[fb], end = fine_start[fb + SUB_SIDE * SUB_SIDE];
     const float nal = -(float)a.alpha * HALO_LOG2E, hs = (float)a.h, pref = (float)a.pref;
+    const float kxx = DEF ? -(float)a.qa[0] * HALO_LOG2E : nal, kyy = DEF ? -(float)a.qa[1] * HALO_LOG2E : nal;
+    const float kxy = DEF ? -(float)a.qa[3] * HALO_LOG2E : 0.f, kzz = DEF ? -(float)a.qa[2] * HALO_LOG2E : nal;
     __syncthreads();  // region staged
     // four particles per warp per round, one per quarter (warp-uniform loop: the
     // shuffles below run on all 32 lanes)
@@ -89,13 +94,24 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
       const int4 i0 = sp_i0[ke];
       const float4 d0 = sp_d0[ke];
       const int ex = i0.x - t0[0], ey = i0.y - t0[1], ez = i0.z - z0;  // in [0, 16) and [0, LAYER)
-      // 1D weights: lane sub < P holds the x, y and z weights of point sub
-      const float fs = (float)(sub < P ? sub : 0) * hs;
-      const float ox = d0.x + fs, oy = d0.y + fs, oz = d0.z + fs;
-      const float wx = exp2f(nal * ox * ox), wy = exp2f(nal * oy * oy), wzl = exp2f(nal * oz * oz);
-      float wz[P];
+      // 1D weights: lane sub < P holds the x, y and z weights of point sub (P <= 8,
+      // the lanes of a quarter); a larger support has every lane form its own
+      float wz[P], wx = 0.f, wy = 0.f;
+      if constexpr (P <= 8) {
+        const float fs = (float)(sub < P ? sub : 0) * hs;
+        const float ox = d0.x + fs, oy = d0.y + fs, oz = d0.z + fs;
+        wx = exp2f(nal * ox * ox);
+        wy = exp2f(nal * oy * oy);
+        const float wzl = exp2f(kzz * oz * oz);
 #pragma unroll
-      for (int j = 0; j < P; ++j) wz[j] = __shfl_sync(0xffffffffu, wzl, j, 8);
+        for (int j = 0; j < P; ++j) wz[j] = __shfl_sync(0xffffffffu, wzl, j, 8);
+      } else {
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const float oz = d0.z + (float)j * hs;
+          wz[j] = exp2f(kzz * oz * oz);
+        }
+      }
       float acc[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) acc[c] = 0.f;
@@ -105,7 +121,13 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
       for (int s = 0; s < H::NCOL; ++s) {
         // this lane's column (px, py) = (c mod P, c / P) of the support, c = sub + 8 s
         const int cc = sub + 8 * s, px = cc % P, py = cc < P * P ? cc / P : 0;
-        const float wxy = __shfl_sync(0xffffffffu, wx, px, 8) * __shfl_sync(0xffffffffu, wy, py, 8);
+        float wxy;
+        if (DEF || P > 8) {  // the column's own x-y weight
+          const float cx = d0.x + (float)px * hs, cy = d0.y + (float)py * hs;
+          wxy = exp2f(kxx * cx * cx + kxy * cx * cy + kyy * cy * cy);
+        } else {
+          wxy = __shfl_sync(0xffffffffu, wx, px, 8) * __shfl_sync(0xffffffffu, wy, py, 8);
+        }
         if (cc < P * P) {
           const int col = pb + py * RX + px;
 #pragma unroll
@@ -135,26 +157,34 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
   });
 }
 
-template <int C, int SLOT0, int P>
+template <int C, int SLOT0, int P, bool DEF = false>
 void launch_interp_halo(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   static std::once_flag once;
   static OccCache occ;
-  auto kern = k_interp_halo<C, SLOT0, P>;
-  set_smem(kern, once);
   const size_t sm = TileL<float, C>::bytes((size_t)Halo<P>::NPT);
+  if (sm > c->smem_optin) return interp_general_launch(c, a, vout, C == 8 ? M_FULL : (C == 5 ? M_SE : M_FSU), s);
+  auto kern = k_interp_halo<C, SLOT0, P, DEF>;
+  set_smem(kern, once);
   const unsigned grid = wave_grid(c, kern, sm, a.ntiles * SUB_SIDE, occ, HALO_THREADS);
   int *q = next_queue(c, s);
   kern<<<grid, HALO_THREADS, sm, s>>>(a, q, (const int4 *)c->d_sp_i0, (const float4 *)c->d_sp_d0, c->d_fine_start,
                                       (const float *)c->d_grid, (float *)vout);
 }
 
+template <int C, int SLOT0, bool DEF>
+void interp_halo_pd(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
+  switch (a.P) {
+    case 5: launch_interp_halo<C, SLOT0, 5, DEF>(c, a, vout, s); break;
+    case 6: launch_interp_halo<C, SLOT0, 6, DEF>(c, a, vout, s); break;
+    case 10: launch_interp_halo<C, SLOT0, 10, DEF>(c, a, vout, s); break;
+    default: launch_interp_halo<C, SLOT0, 8, DEF>(c, a, vout, s);
+  }
+}
+
 template <int C, int SLOT0>
 void interp_halo_p(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
-  switch (a.P) {
-    case 5: launch_interp_halo<C, SLOT0, 5>(c, a, vout, s); break;
-    case 6: launch_interp_halo<C, SLOT0, 6>(c, a, vout, s); break;
-    default: launch_interp_halo<C, SLOT0, 8>(c, a, vout, s);
-  }
+  if (c->lattice) interp_halo_pd<C, SLOT0, true>(c, a, vout, s);
+  else interp_halo_pd<C, SLOT0, false>(c, a, vout, s);
 }
 
 }  // namespace

@@ -225,6 +225,18 @@ void interp_cubic(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStrea
   else interp_halo_launch(c, a, vout, mode, s);
 }
 
+void interp_general_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
+  if (c->prec == PSE_MIXED) {
+    if (mode == M_FULL) interp_p<float, 8, 0>(c, a, vout, s);
+    else if (mode == M_SE) interp_p<float, 5, 3>(c, a, vout, s);
+    else interp_p<float, 3, 0>(c, a, vout, s);
+  } else {
+    if (mode == M_FULL) interp_p<double, 8, 0>(c, a, vout, s);
+    else if (mode == M_SE) interp_p<double, 5, 3>(c, a, vout, s);
+    else interp_p<double, 3, 0>(c, a, vout, s);
+  }
+}
+
 void interp_launch(pse_ctx *c, const WaveArgs &a, void *vout, int mode, cudaStream_t s) {
   if (c->n_cubic == c->nsys) return interp_cubic(c, a, vout, mode, s);
   WaveArgs ag = a;

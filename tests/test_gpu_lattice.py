@@ -243,3 +243,46 @@ def test_sedimentation_error_follows_support_rule(pkg, name):
     assert errs[0] > 3 * errs[1]
     if name == 'extension':
         assert errs[0] > 10 * tol
+
+
+@pytest.mark.parametrize('Ng,cell', [(48, 'shear'), (64, 'shear'), (48, 'cube')])
+def test_tile_kernels_with_ten_point_support(pkg, Ng, cell):
+    """Mixed precision with 16^3 tiles and P = 10 (the support Eq. bound gives on a cell sheared by
+    1/2; for the cube set explicitly): the register-column spreading and the staged-region
+    interpolation, with the x-y coupled weights on the sheared cell and weights formed per lane
+    beyond 8 support points; the full product's interpolation (whose 8-component staging does not
+    fit) falls back to the general kernels.  Products per part, E and U from S alone, and the step
+    against the oracle at 2e-5."""
+    N, phi, xi, tol, dt = 3000, 0.3, 0.6, 1e-3, 1e-3
+    A = LATTICES['shear'] if cell == 'shear' else np.eye(3)
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=61)
+    pos = pos @ A.T
+    F, S = pse_inputs.moments(N, seed=62)
+    kw = dict(deform=A) if cell == 'shear' else dict(P=10)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='mixed', Ng=Ng, lanczos_tol=0.0, lanczos_maxiter=8,
+                krylov_tol=1e-6, krylov_maxiter=100, **kw)
+    assert h.info['P'] == 10 and h.info['tile_kernels'] == 1
+    if cell == 'cube':
+        A = None
+    p = _oracle_params(h, N, L, xi, tol, A)
+    op = opse.RealOp(pos, p)
+    for parts in ('wave', 'all'):
+        got = _mob(h, pos, F, S, 'mixed', parts)
+        Uo, Eo = opse.mobility_apply(pos, F, S, p, parts=('wave',) if parts == 'wave' else ('real', 'wave'),
+                                     real_op=op)
+        assert _rel(got, np.concatenate([Uo, Eo], 1)) < TOL['mixed'], parts
+    # E from S alone and U from S alone take the 5- and 3-component kernels
+    U, E = h.mobility(_cuda(pos, torch.float64), None, _cuda(S, torch.float32))
+    Uo, Eo = opse.mobility_apply(pos, np.zeros((N, 3)), S, p, real_op=op)
+    assert _rel(E.double().cpu().numpy(), Eo) < TOL['mixed']
+    assert _rel(U.double().cpu().numpy(), Uo) < TOL['mixed']
+    w1 = pse_inputs.lanczos_noise(N, seed=63)
+    w2 = pse_inputs.wave_noise(p.Ng, seed=64)
+    x = _cuda(pos, torch.float64)
+    Sg, st = h.step(x, dt, w1=_cuda(w1, torch.float32), w2=_cuda(w2, torch.float32), want_S=True)
+    x1, So, _ = opse.constrained_step(pos, None, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=8,
+                                      krylov_tol=1e-12, krylov_maxiter=200)
+    Ad = np.eye(3) if A is None else A
+    assert _rel(_lattice_disp(x.cpu().numpy(), pos, Ad, L), _lattice_disp(x1, pos, Ad, L)) < 2e-5
+    assert _rel(Sg.double().cpu().numpy(), So) < 2e-5
+    h.close()
