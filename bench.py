@@ -310,11 +310,12 @@ def accuracy_vs_fp64(pkg, torch, dev, args, pos_np, L, h64):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernel instances on the
 # benchmark workload (N = 1048576, phi = 0.3, eps = 1e-3, xi = 0.5, N_g = 256, P = 6): ncu captures of
-# the N = 524288 case of the same workload (same N_g per particle density is not kept, so grid bytes
-# are taken at N_g = 256 and particle bytes scale with N), scaled to a full launch as stated in the
-# profiles/ summaries.  Empty until retaken for the current kernels; reported only for that workload.
+# the N = 524288 case of the same workload (profiles/dram_bytes_N524288_phi0.3_eps1e-3.md), scaled to a
+# full launch by the ordered pairs (1.1017e8 / 5.5086e7): the pair sum's DRAM bytes are its neighbour
+# records.  The wave-space kernels are left out (their grid bytes stay partly in L2 between launches,
+# so they do not scale with N_g^3).  Reported only for that workload.
 NCU_TRAFFIC_WORKLOAD = (1048576, 0.3, 1e-3, 0.5, 256, 6)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {'k_real<float,M_FULL>': 1.926e9, 'k_real<float,M_SE>': 1.926e9, 'k_real<float,M_SU>': 1.892e9}
 
 
 def real_flops_per_pair():
@@ -843,8 +844,8 @@ def lattice_measure(pkg, torch, dev, args, pos_np, L, cubic_rate, gamma=0.5, ste
                     'krylov_mean': float(np.mean([i[1] for i in its]))}
     out['cubic_over_sheared'] = cubic_rate / out['lambda_aware']['steps_per_s']
     out['note'] = ('sheared cell: the 16^3-tile spreading / interpolation kernels with x-y coupled Gaussian '
-                   'weights (the 8-component interpolation on the general kernels), grid resolving k_cut along '
-                   'the longest lattice column')
+                   'weights (the 8-component interpolation in passes of 5 and 3 components), grid resolving '
+                   'k_cut along the longest lattice column')
     return out
 
 

@@ -34,7 +34,9 @@ template <int P> struct Halo {
 // DEF: deformed lattice with z orthogonal to the sheared plane (as the
 // register-column spreading): the x-y weight of each support column is its own
 // exponential of the x-y quadratic form; the z weights use G_zz.
-template <int C, int SLOT0, int P, bool DEF = false>
+// COMP0: first grid component read (grid components COMP0 .. COMP0 + C - 1 go
+// to output slots SLOT0 .. SLOT0 + C - 1).
+template <int C, int SLOT0, int P, bool DEF = false, int COMP0 = 0>
 __global__ void __launch_bounds__(HALO_THREADS, 2)
     k_interp_halo(WaveArgs wa, int *queue, const int4 *__restrict__ sp_i0, const float4 *__restrict__ sp_d0,
                   const int *__restrict__ fine_start, const float *__restrict__ grid_all, float *__restrict__ vout) {
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
           gz -= gz >= Ng ? Ng : 0;
           const size_t g = ((size_t)gz * Ng + gy) * Ng + gx;
 #pragma unroll
-          for (int c = 0; c < C; ++c) vv[u][c] = __ldg(grid + c * a.gstride + g);
+          for (int c = 0; c < C; ++c) vv[u][c] = __ldg(grid + (COMP0 + c) * a.gstride + g);
           dst[u] = z * ZS + y * RX + x;
         }
       }
@@ -157,13 +159,25 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
   });
 }
 
-template <int C, int SLOT0, int P, bool DEF = false>
+template <int C, int SLOT0, int P, bool DEF = false, int COMP0 = 0>
 void launch_interp_halo(pse_ctx *c, const WaveArgs &a, void *vout, cudaStream_t s) {
   static std::once_flag once;
   static OccCache occ;
   const size_t sm = TileL<float, C>::bytes((size_t)Halo<P>::NPT);
-  if (sm > c->smem_optin) return interp_general_launch(c, a, vout, C == 8 ? M_FULL : (C == 5 ? M_SE : M_FSU), s);
-  auto kern = k_interp_halo<C, SLOT0, P, DEF>;
+  if (sm > c->smem_optin) {
+    // the staged region of all components does not fit: components 0-4 and 5-7 in two passes
+    // (a region of 5 components is the largest that fits), else the general kernel
+    if constexpr (C == 8 && COMP0 == 0) {
+      if (TileL<float, 5>::bytes((size_t)Halo<P>::NPT) <= c->smem_optin) {
+        launch_interp_halo<5, SLOT0, P, DEF, 0>(c, a, vout, s);
+        launch_interp_halo<3, SLOT0 + 5, P, DEF, 5>(c, a, vout, s);
+        c->nlaunch += 1;
+        return;
+      }
+    }
+    return interp_general_launch(c, a, vout, C == 8 ? M_FULL : (C == 5 ? M_SE : M_FSU), s);
+  }
+  auto kern = k_interp_halo<C, SLOT0, P, DEF, COMP0>;
   set_smem(kern, once);
   const unsigned grid = wave_grid(c, kern, sm, a.ntiles * SUB_SIDE, occ, HALO_THREADS);
   int *q = next_queue(c, s);

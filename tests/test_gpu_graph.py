@@ -93,3 +93,28 @@ def test_graph_step_host_arrays(pkg):
     d = _disp(x, pos, L)
     assert np.isfinite(d).all() and 0 < np.abs(d).max() < 0.5
     h.close()
+
+
+def test_graph_step_equals_oracle(pkg):
+    """The graph-captured step with in-kernel noise against the oracle's mid-point step driven by the
+    same Philox4x32-10 streams (counter = step), FP64, fixed Lanczos length, tight GMRES."""
+    from oracle import params, philox, pse as opse
+    N, phi, xi, tol, dt = 150, 0.2, 0.7, 1e-3, 1e-3
+    pos, L = pse_inputs.rsa_positions(N, phi, seed=13)
+    h = pkg.PSE(N, L, xi=xi, tol=tol, precision='fp64', use_graph=1, lanczos_tol=0.0, lanczos_maxiter=10,
+                krylov_tol=1e-10, krylov_maxiter=100)
+    inf = h.info
+    p = params.choose(N, L, 1.0, 1.0, 1.0, xi, tol, Ng=inf['Ng'], P=inf['P'], rcut=inf['rcut'])
+    seed = 0x5EED
+    x = torch.tensor(pos, device='cuda', dtype=torch.float64)
+    xo = pos.copy()
+    for k in range(2):                      # capture, then a replay with the next step's noise
+        S, st = h.step(x, dt, seed=seed, step=k, want_S=True)
+        w1 = philox.lanczos_noise(seed, k, N)
+        w2 = philox.wave_noise(seed, k, p.Ng)
+        xo, So, _ = opse.constrained_step(xo, None, dt, w1, w2, p, lanczos_tol=0.0, lanczos_maxiter=10,
+                                          krylov_tol=1e-13, krylov_maxiter=200)
+        assert h.graph_ready() == (True, '')
+        assert _rel(_disp(x.cpu().numpy(), pos, L), _disp(xo, pos, L)) < 1e-9
+        assert _rel(S.cpu().numpy(), So) < 1e-9
+    h.close()

@@ -251,7 +251,7 @@ def test_tile_kernels_with_ten_point_support(pkg, Ng, cell):
     1/2; for the cube set explicitly): the register-column spreading and the staged-region
     interpolation, with the x-y coupled weights on the sheared cell and weights formed per lane
     beyond 8 support points; the full product's interpolation (whose 8-component staging does not
-    fit) falls back to the general kernels.  Products per part, E and U from S alone, and the step
+    fit) runs as two passes of 5 and 3 components.  Products per part, E and U from S alone, and the step
     against the oracle at 2e-5."""
     N, phi, xi, tol, dt = 3000, 0.3, 0.6, 1e-3, 1e-3
     A = LATTICES['shear'] if cell == 'shear' else np.eye(3)
