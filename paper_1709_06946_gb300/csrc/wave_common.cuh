@@ -69,6 +69,12 @@ struct TileL {
     a = (T4 *)base;
     b = (void *)(a + npts);
   }
+  // address of component c of point i
+  __device__ __forceinline__ T *comp(int i, int c) const {
+    if (c < 4) return &a[i].x + c;
+    if (EXTRA == 1) return (T *)b + i;
+    return &((T4 *)b)[i].x + (c - 4);
+  }
   __device__ __forceinline__ void load(int i, T v[C]) const {
     const T4 x = a[i];
     v[0] = x.x;

@@ -19,6 +19,14 @@ namespace pse {
 namespace {
 
 constexpr int HALO_THREADS = 512;
+
+// 4 bytes from global to shared memory without a register round trip (cp.async,
+// cached in L1); completion is awaited with cp_async_wait_all before a barrier.
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 constexpr float HALO_LOG2E = 1.4426950408889634f;  // log2(e): exp(-x) = exp2(-x log2 e)
 constexpr int LAYER = CUBE / SUB_SIDE;  // planes of support starts per work item
 
@@ -56,31 +64,21 @@ __global__ void __launch_bounds__(HALO_THREADS, 2)
     tile_of(a, tile - a.tile0, t, t0);
     const int z0 = t0[2] + kz * LAYER;
     const float *grid = grid_all + a.grid0;
-    // stage the region: UNR points per thread in flight (C loads each)
-    constexpr int NREG = RZ * R * R, UNR = P >= 8 ? 2 : (C <= 3 ? 4 : (C <= 5 ? 3 : 2));
-    for (int q0 = threadIdx.x; q0 < NREG; q0 += UNR * HALO_THREADS) {
-      float vv[UNR][C];
-      int dst[UNR];
+    // stage the region with asynchronous 4-byte copies straight into the tile layout
+    // (no register round trip: every copy of the thread is in flight before the wait)
+    constexpr int NREG = RZ * R * R;
+    for (int q = threadIdx.x; q < NREG; q += HALO_THREADS) {
+      const int x = q % R, y = (q / R) % R, z = q / (R * R);
+      int gx = t0[0] + x, gy = t0[1] + y, gz = z0 + z;
+      gx -= gx >= Ng ? Ng : 0;
+      gy -= gy >= Ng ? Ng : 0;
+      gz -= gz >= Ng ? Ng : 0;
+      const size_t g = ((size_t)gz * Ng + gy) * Ng + gx;
+      const int d = z * ZS + y * RX + x;
 #pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int q = q0 + u * HALO_THREADS;
-        dst[u] = -1;
-        if (q < NREG) {
-          const int x = q % R, y = (q / R) % R, z = q / (R * R);
-          int gx = t0[0] + x, gy = t0[1] + y, gz = z0 + z;
-          gx -= gx >= Ng ? Ng : 0;
-          gy -= gy >= Ng ? Ng : 0;
-          gz -= gz >= Ng ? Ng : 0;
-          const size_t g = ((size_t)gz * Ng + gy) * Ng + gx;
-#pragma unroll
-          for (int c = 0; c < C; ++c) vv[u][c] = __ldg(grid + (COMP0 + c) * a.gstride + g);
-          dst[u] = z * ZS + y * RX + x;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u)
-        if (dst[u] >= 0) tl.store(dst[u], vv[u]);
+      for (int c = 0; c < C; ++c) cp_async4(tl.comp(d, c), grid + (COMP0 + c) * a.gstride + g);
     }
+    cp_async_wait_all();
     const int64_t fb = (int64_t)tile * SUB_BLOCKS + kz * SUB_SIDE * SUB_SIDE;
     const int beg = fine_start[fb], end = fine_start[fb + SUB_SIDE * SUB_SIDE];
     const float nal = -(float)a.alpha * HALO_LOG2E, hs = (float)a.h, pref = (float)a.pref;
