@@ -674,6 +674,9 @@ void pse::fill_lattice(const Params &p, SysDev &d) {
   }
   d.c_apply = p.sigma() * p.sigma() / (p.V() * p.eta);
   d.c_noise = p.sigma() / std::sqrt(p.eta * p.V());
+  d.c_applyf = (float)d.c_apply;
+  d.c_noisef = (float)d.c_noise;
+  for (int k = 0; k < 6; ++k) d.qaf[k] = (float)d.qa[k];
 }
 
 namespace {
@@ -772,6 +775,11 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
     d.pref = std::pow(2.0 * p.xi * p.xi / (M_PI * p.eta_g), 1.5);
     d.kfac = 2.0 * M_PI / p.L;
     d.eta_g = p.eta_g;
+    d.hf = (float)d.h;
+    d.alphaf = (float)d.alpha;
+    d.preff = (float)d.pref;
+    d.kfacf = (float)d.kfac;
+    d.eta_gf = (float)d.eta_g;
     fill_lattice(p, d);
     double mean = 4.0 / 3.0 * M_PI * p.rcut * p.rcut * p.rcut * p.N / p.V();
     d.slots = (int)std::min<double>(std::max<int64_t>(p.N, 8), std::ceil((1.4 * mean + 24) / 8.0) * 8.0);

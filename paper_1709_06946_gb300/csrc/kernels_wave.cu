@@ -28,10 +28,39 @@ struct ScaleArgs {
   int nsys;
   int64_t nk_tot;
   double a, q4;
+  float af, q4f;       // FP32 copies for the mixed-precision kernels
   const SysDev *sys;
   const int64_t *k0;   // nsys + 1 prefix of half-spectrum points
   const int *active;
 };
+
+// Per-suspension constants in the arithmetic type of the kernel: the FP32 form
+// reads the FP32 copies, so no FP64 conversion runs per half-spectrum point.
+template <typename T>
+__device__ __forceinline__ T sa_a(const ScaleArgs &sa) {
+  if constexpr (sizeof(T) == 4) return sa.af;
+  else return sa.a;
+}
+template <typename T>
+__device__ __forceinline__ T sa_q4(const ScaleArgs &sa) {
+  if constexpr (sizeof(T) == 4) return sa.q4f;
+  else return sa.q4;
+}
+template <typename T>
+__device__ __forceinline__ T sd_c_apply(const SysDev &s) {
+  if constexpr (sizeof(T) == 4) return s.c_applyf;
+  else return s.c_apply;
+}
+template <typename T>
+__device__ __forceinline__ T sd_c_noise(const SysDev &s) {
+  if constexpr (sizeof(T) == 4) return s.c_noisef;
+  else return s.c_noise;
+}
+template <typename T>
+__device__ __forceinline__ T sd_eta_g(const SysDev &s) {
+  if constexpr (sizeof(T) == 4) return s.eta_gf;
+  else return s.eta_g;
+}
 
 template <typename T>
 __device__ __forceinline__ void shape(T x, T &s0, T &s1) {
@@ -76,7 +105,11 @@ template <typename T>
 __device__ __forceinline__ void kcart(const SysDev &s, int ix, int iy, int iz, T k[3]) {
   const int h = s.Ng / 2;
   const int my = iy <= h ? iy : iy - s.Ng, mz = iz <= h ? iz : iz - s.Ng;
-  if (!s.def) {
+  if (!s.def && sizeof(T) == 4) {  // no FP64 instruction in the FP32 form
+    k[0] = (T)((float)ix * s.kfacf);
+    k[1] = (T)((float)my * s.kfacf);
+    k[2] = (T)((float)mz * s.kfacf);
+  } else if (!s.def) {
     k[0] = (T)(ix * s.kfac);
     k[1] = (T)(my * s.kfac);
     k[2] = (T)(mz * s.kfac);
@@ -140,9 +173,9 @@ __device__ __forceinline__ void scale_point(const ScaleArgs &sa, const SysDev &s
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
   T s0, s1;
-  shape<T>(kk * (T)sa.a, s0, s1);
-  T u = k2 * (T)sa.q4;
-  T c = (T)s.c_apply * ((T)1 + u) * exp(-((T)1 - (T)s.eta_g) * u) / k2;
+  shape<T>(kk * sa_a<T>(sa), s0, s1);
+  T u = k2 * sa_q4<T>(sa);
+  T c = sd_c_apply<T>(s) * ((T)1 + u) * exp(-((T)1 - sd_eta_g<T>(s)) * u) / k2;
   T fr[3] = {0, 0, 0}, fi[3] = {0, 0, 0};
   if (HF) {
 #pragma unroll
@@ -264,9 +297,9 @@ __global__ void k_scale11(ScaleArgs sa, typename Cx<T>::t *g_all) {
     const T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
     const T kk = sqrt(k2), ik = (T)1 / kk;
     T s0, s1;
-    shape<T>(kk * (T)sa.a, s0, s1);
-    const T u = k2 * (T)sa.q4;
-    const T c = (T)s.c_apply * ((T)1 + u) * exp(-((T)1 - (T)s.eta_g) * u) / k2;
+    shape<T>(kk * sa_a<T>(sa), s0, s1);
+    const T u = k2 * sa_q4<T>(sa);
+    const T c = sd_c_apply<T>(s) * ((T)1 + u) * exp(-((T)1 - sd_eta_g<T>(s)) * u) / k2;
     T fr[3], fi[3], Lr[3], Li[3], sr[5], si[5];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -374,9 +407,9 @@ __global__ void k_noise(ScaleArgs sa, const T *__restrict__ w2, uint64_t seed, u
   T k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
   T kk = sqrt(k2), ik = (T)1 / kk;
   T s0, s1;
-  shape<T>(kk * (T)sa.a, s0, s1);
-  T u = k2 * (T)sa.q4;
-  T c = (T)s.c_noise * sqrt(((T)1 + u) / k2) * exp(-(T)0.5 * ((T)1 - (T)s.eta_g) * u);
+  shape<T>(kk * sa_a<T>(sa), s0, s1);
+  T u = k2 * sa_q4<T>(sa);
+  T c = sd_c_noise<T>(s) * sqrt(((T)1 + u) / k2) * exp(-(T)0.5 * ((T)1 - sd_eta_g<T>(s)) * u);
   T kh[3] = {k[0] * ik, k[1] * ik, k[2] * ik};
   T pr = kh[0] * dr[0] + kh[1] * dr[1] + kh[2] * dr[2], pi = kh[0] * di[0] + kh[1] * di[1] + kh[2] * di[2];
   T ur[3], ui[3];
@@ -394,6 +427,8 @@ ScaleArgs scale_args(const pse_ctx *c) {
   s.nk_tot = c->nk_tot;
   s.a = c->p.a;
   s.q4 = 1.0 / (4.0 * c->p.xi * c->p.xi);
+  s.af = (float)s.a;
+  s.q4f = (float)s.q4;
   s.sys = c->d_sys;
   s.k0 = c->d_k0;
   s.active = c->d_active;

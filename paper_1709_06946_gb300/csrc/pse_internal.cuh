@@ -111,9 +111,14 @@ struct SysDev {
   float Af[9], Btf[9];
   double qa[6];            // Gaussian exponent alpha |A d|^2 = qa0 dx^2 + qa1 dy^2 + qa2 dz^2
                            //   + qa3 dx dy + qa4 dx dz + qa5 dy dz (cube: alpha, alpha, alpha, 0, 0, 0)
+  // FP32 copies for the mixed-precision kernels, which then run no FP64
+  // instruction per grid point or particle (FP64 issues at a small fraction of
+  // the FP32 rate on sm_103a)
+  float hf, alphaf, preff, kfacf, eta_gf, c_applyf, c_noisef;
+  float qaf[6];
 };
 
-// Fills the lattice fields of d (def, A, Ai, Bt, qa, c_apply, c_noise) from p.
+// Fills the lattice fields of d (def, A, Ai, Bt, qa, c_apply, c_noise and their FP32 copies) from p.
 void fill_lattice(const Params &p, SysDev &d);
 
 // Index s with start[s] <= x < start[s + 1] (start has n + 1 entries).

@@ -23,6 +23,30 @@
 
 namespace pse {
 
+// Gaussian constants of a suspension in the arithmetic type of a kernel: the
+// FP32 form reads the FP32 copies, so no FP64 conversion runs per particle or
+// support point.
+template <typename T>
+__device__ __forceinline__ T sd_alpha(const SysDev &a) {
+  if constexpr (sizeof(T) == 4) return a.alphaf;
+  else return a.alpha;
+}
+template <typename T>
+__device__ __forceinline__ T sd_h(const SysDev &a) {
+  if constexpr (sizeof(T) == 4) return a.hf;
+  else return a.h;
+}
+template <typename T>
+__device__ __forceinline__ T sd_pref(const SysDev &a) {
+  if constexpr (sizeof(T) == 4) return a.preff;
+  else return a.pref;
+}
+template <typename T>
+__device__ __forceinline__ T sd_qa(const SysDev &a, int k) {
+  if constexpr (sizeof(T) == 4) return a.qaf[k];
+  else return a.qa[k];
+}
+
 template <typename T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
 template <> struct Cx<double> { using t = double2; };

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
     const int nb = tile_bins(a, t, tile_start, beg, cum);
     const int total = cum[nb];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
+    const T alpha = sd_alpha<T>(a), hs = sd_h<T>(a), pref = sd_pref<T>(a);
     const int zstride = Ty * RX;
     // this lane's columns (full passes) and points (leftover passes)
     int fjx[NFULL > 0 ? NFULL : 1], fjy[NFULL > 0 ? NFULL : 1];
@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(NT) k_interp(WaveArgs wa, int *queue, const in
             if (ly >= Ng) ly -= Ng;
             if (it < P * P && lx < Tx && ly < Ty) {
               const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-              const T qxy = (T)a.qa[0] * dx * dx + (T)a.qa[1] * dy * dy + (T)a.qa[3] * dx * dy;
-              const T lin = (T)a.qa[4] * dx + (T)a.qa[5] * dy, q2 = (T)a.qa[2];
+              const T qxy = sd_qa<T>(a, 0) * dx * dx + sd_qa<T>(a, 1) * dy * dy + sd_qa<T>(a, 3) * dx * dy;
+              const T lin = sd_qa<T>(a, 4) * dx + sd_qa<T>(a, 5) * dy, q2 = sd_qa<T>(a, 2);
               const int col = ly * RX + lx;
               for (int jz = 0; jz < P; ++jz) {
                 int lz = ez + jz;

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
     int t[3], t0[3], beg[8], cum[9];
     tile_of(a, item - a.tile0, t, t0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T alpha = (T)a.alpha, hs = (T)a.h, pref = (T)a.pref;
+    const T alpha = sd_alpha<T>(a), hs = sd_h<T>(a), pref = sd_pref<T>(a);
     // this lane's (x, y) footprint point in every pass (fixed for the whole tile)
     int pjx[NPASS], pjy[NPASS];
     bool pok[NPASS];
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
             }
           } else {  // any support size and any lattice: weights on the fly, exp(-alpha |A d|^2)
             const T dz = d0.z + (T)ez * hs;
-            const T qz = (T)a.qa[2] * dz * dz, q4 = (T)a.qa[4] * dz, q5 = (T)a.qa[5] * dz;
+            const T qz = sd_qa<T>(a, 2) * dz * dz, q4 = sd_qa<T>(a, 4) * dz, q5 = sd_qa<T>(a, 5) * dz;
             for (int ib = 0; ib < nitem; ib += 32) {
               const int it = ib + lane;
               const int jx = it % P, jy = it / P;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(WAVE_THREADS) k_spread(WaveArgs wa, int *queue
               if (ly >= Ng) ly -= Ng;
               if (it < nitem && lx < Tx && ly < Ty) {
                 const T dx = d0.x + (T)jx * hs, dy = d0.y + (T)jy * hs;
-                const T q = (T)a.qa[0] * dx * dx + (T)a.qa[1] * dy * dy + (T)a.qa[3] * dx * dy + q4 * dx + q5 * dy + qz;
+                const T q = sd_qa<T>(a, 0) * dx * dx + sd_qa<T>(a, 1) * dy * dy + sd_qa<T>(a, 3) * dx * dy + q4 * dx + q5 * dy + qz;
                 const T wt = pref * exp(-q);
                 const int i = plane + ly * RX + lx;
                 T vv[C];
