@@ -769,6 +769,8 @@ pse_status create_group(pse_ctx *c, const pse_options &o) {
     d.L = p.L;
     d.h = p.h;
     d.cs = p.cs;
+    d.inv_h = 1.0 / p.h;
+    d.inv_cs = 1.0 / p.cs;
     d.Lf = (float)p.L;
     d.csf = (float)p.cs;
     d.alpha = 2.0 * p.xi * p.xi / p.eta_g;

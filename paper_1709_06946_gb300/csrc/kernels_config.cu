@@ -65,15 +65,30 @@ __global__ void k_scan_add(int *out, int64_t n, const int *offs) {
 }
 
 __device__ __forceinline__ double wrap_coord(double x, double L) {
+  if (x >= 0.0 && x < L) return x;  // already inside: fmod would return x itself
   x = fmod(x, L);
   if (x < 0) x += L;
   if (x >= L) x = 0.0;
   return x;
 }
 
-__device__ __forceinline__ int support_start(double x, double h, int P) {
-  double q = x / h;
-  return (P & 1) ? (int)rint(q) - (P - 1) / 2 : (int)floor(q) - P / 2 + 1;
+// floor(x / y) and rint(x / y) of the rounded FP64 quotient, for 0 <= x / y < 2^20,
+// mostly without the FP64 division (a long instruction sequence at sm_103a's
+// FP64 rate): q = x * (1/y) lies within a few units in the last place of the
+// rounded quotient, so its floor (rint) is the same unless q lies that close to
+// an integer (a half-integer); there the division decides.
+__device__ __forceinline__ double quot_floor(double x, double y, double iy) {
+  const double q = x * iy, f = floor(q), e = 1e-12 * (q + 1.0);
+  return (q - f < e || q - f > 1.0 - e) ? floor(x / y) : f;
+}
+__device__ __forceinline__ double quot_rint(double x, double y, double iy) {
+  const double q = x * iy, e = 1e-12 * (q + 1.0);
+  return fabs(q - floor(q) - 0.5) < e ? rint(x / y) : rint(q);
+}
+
+// First grid index of the support of a particle at wrapped coordinate x.
+__device__ __forceinline__ int support_start(double x, double h, double ih, int P) {
+  return (P & 1) ? (int)quot_rint(x, h, ih) - (P - 1) / 2 : (int)quot_floor(x, h, ih) - P / 2 + 1;
 }
 
 // Wraps particle u (user order) of its suspension into [0, L) and counts it in
@@ -105,7 +120,7 @@ __global__ void k_bin(const SysDev *__restrict__ sys, const int64_t *__restrict_
   for (int d = 0; d < 3; ++d) {
     const double x = wrap_coord(xin[d], b.L);
     posw[3 * u + d] = x;
-    iw[d] = wrapi(support_start(x, b.h, P), b.Ng);
+    iw[d] = wrapi(support_start(x, b.h, b.inv_h, P), b.Ng);
   }
   int tk = b.tile0 + ((iw[2] / b.T[2]) * b.nt[1] + iw[1] / b.T[1]) * b.nt[0] + iw[0] / b.T[0];
   int sub = (((iw[2] % b.T[2]) * SUB_SIDE / b.T[2]) * SUB_SIDE + (iw[1] % b.T[1]) * SUB_SIDE / b.T[1]) * SUB_SIDE +
@@ -143,10 +158,10 @@ __global__ void k_derive(const SysDev *__restrict__ sys, const int64_t *__restri
   T d0[3];
   for (int d = 0; d < 3; ++d) {
     x[d] = posw[3 * (int64_t)u + d];
-    int i0 = support_start(x[d], b.h, P);
+    int i0 = support_start(x[d], b.h, b.inv_h, P);
     iw[d] = wrapi(i0, b.Ng);
     d0[d] = (T)(i0 * b.h - x[d]);
-    c[d] = min((int)(x[d] / b.cs), b.nc - 1);
+    c[d] = min((int)quot_floor(x[d], b.cs, b.inv_cs), b.nc - 1);
   }
   sp_i0[i] = make_int4(iw[0], iw[1], iw[2], 0);
   typename V4<T>::t dd;

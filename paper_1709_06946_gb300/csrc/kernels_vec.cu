@@ -374,6 +374,7 @@ __global__ void k_zero_slots(T *v, int64_t N, int slot0, int nslot) {
 }
 
 __device__ __forceinline__ double wrapL(double x, double L) {
+  if (x >= 0.0 && x < L) return x;  // already inside: fmod would return x itself
   x = fmod(x, L);
   if (x < 0) x += L;
   if (x >= L) x = 0.0;

@@ -100,6 +100,7 @@ struct SysDev {
   int T[3], nt[3];
   int cubic;               // 1: mixed precision, P in {5, 6, 8}, 16^3 tiles, >= 2 tiles per side
   double L, h, cs;
+  double inv_h, inv_cs;    // 1/h and 1/cs (binning without FP64 divisions)
   float Lf, csf;
   double alpha, pref;      // spreading Gaussian exp(-alpha r^2) and its prefactor
   double kfac, eta_g;      // 2 pi / L, Gaussian width
