@@ -338,10 +338,11 @@ def kernel_instances(prof, N, Ng, P, npairs, cubic, wave_kernel=0):
     vm, vc = prof['variant_ms'], prof['variant_calls']
     n3 = Ng ** 3
     nkh = Ng * Ng * (Ng // 2 + 1)
-    # kernel names: 16^3 tiles take the grid-column spreading and the staged-region interpolation
-    # by default (wave_kernel bit 0: shared-tile spreading; bit 1: column, bit 4: tile-owned
-    # interpolation), other tiles the general kernels
-    ts = ('16' if wave_kernel & 1 else '_col') if cubic else ''
+    # kernel names: 16^3 tiles take the grid-column spreading with the CTA-wide candidate scan and
+    # the staged-region interpolation by default (wave_kernel bit 0: shared-tile spreading; bit 2:
+    # column spreading with a scan per warp; bit 1: column, bit 4: tile-owned interpolation), other
+    # tiles the general kernels
+    ts = ('16' if wave_kernel & 1 else ('_col' if wave_kernel & 4 else '_colq')) if cubic else ''
     ti = ('_col' if wave_kernel & 2 else ('16' if wave_kernel & 16 else '_halo')) if cubic else ''
     fl = real_flops_per_pair()
     spec = [('spread', 'k_spread%s<C=8,P=%d>' % (ts, P), ('full', 'fsu'), N * (16 + 32) + 32 * n3),
