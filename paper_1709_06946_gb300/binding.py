@@ -209,6 +209,17 @@ def _checked(x, shape, dtype, name):
     return x
 
 
+def _checked_size(x, n, dtype, name):
+    """x itself after checking its element type and element count (any shape)."""
+    if x is None:
+        return None
+    size = x.size if isinstance(x, np.ndarray) else x.numel()
+    _checked(x.reshape(-1), (size,), dtype, name)
+    if size != n:
+        raise ValueError(f'{name} must hold {n} elements, not {size}')
+    return x
+
+
 def _stream(x):
     try:
         torch = _torch()
@@ -408,8 +419,24 @@ class PSE:
         self._check(st)
         return U, Om, E
 
+    def _noise_points(self):
+        """Half-spectrum points of all suspensions, sum of Ng^2 (Ng/2 + 1)."""
+        ngs = [self.system_info(s)['Ng'] for s in range(self.nsys)]
+        return int(sum(g * g * (g // 2 + 1) for g in ngs))
+
+    def _check_step_args(self, pos, FP=None, w1=None, w2=None, wt=None):
+        """Shapes and element types of the arrays a sample or step reads (positions FP64; forces and
+        noise in the handle's precision): a wrong one would be read past its end."""
+        _checked(pos, (self.N, 3), np.float64, 'pos')
+        _checked(FP, (self.N, 3), self.dtype, 'FP')
+        _checked_size(w1, 8 * self.N, self.dtype, 'w1')
+        if w2 is not None:
+            _checked_size(w2, 6 * self._noise_points(), self.dtype, 'w2')
+        _checked(wt, (self.N, 3), self.dtype, 'wt')
+
     def brownian(self, pos, dt, seed=0, counter=0, w1=None, w2=None):
         """Brownian slip velocities (U^B, E^B) with covariance (2kT/dt) M."""
+        self._check_step_args(pos, w1=w1, w2=w2)
         U = self._like(pos, (self.N, 3), self.dtype)
         E = self._like(pos, (self.N, 5), self.dtype)
         stats = Stats()
@@ -421,6 +448,7 @@ class PSE:
 
     def step(self, pos, dt, FP=None, seed=0, step=0, w1=None, w2=None, want_S=False, allow_cap=True):
         """One constrained mid-point step; pos (N x 3 float64) is updated in place."""
+        self._check_step_args(pos, FP, w1, w2)
         S = self._like(pos, (self.N, 5), self.dtype) if want_S else None
         stats = Stats()
         if w1 is not None or w2 is not None:
@@ -439,6 +467,7 @@ class PSE:
                  allow_cap=True):
         """One Euler-Maruyama step with a random-finite-difference drift (three stresslet solves);
         pos is updated in place.  External noise needs w1, w2 and wt together."""
+        self._check_step_args(pos, FP, w1, w2, wt)
         S = self._like(pos, (self.N, 5), self.dtype) if want_S else None
         stats = Stats()
         if w1 is not None or w2 is not None or wt is not None:
@@ -455,12 +484,14 @@ class PSE:
 
     def overlap_force(self, pos, k):
         """Harmonic overlap repulsion k (2a - r) rh summed over pairs closer than contact."""
+        _checked(pos, (self.N, 3), np.float64, 'pos')
         F = self._like(pos, (self.N, 3), self.dtype)
         self._check(self._lib.pse_overlap_force(self._h, _ptr(pos), float(k), _ptr(F), _stream(pos)))
         return F
 
     def autotune(self, pos, reps=3):
         """Times the pair-sum lanes and spreading-tile candidates on `pos` and keeps the fastest."""
+        _checked(pos, (self.N, 3), np.float64, 'pos')
         t = Tuning()
         self._check(self._lib.pse_autotune(self._h, _ptr(pos), int(reps), ctypes.byref(t), _stream(pos)))
         self.info = self.get_info()
@@ -513,6 +544,9 @@ class Server:
         prec = _precision(precision)
         dtype = np.float64 if prec == PSE_FP64 else np.float32
         N = pos.shape[0]
+        _checked(pos, (N, 3), np.float64, 'pos')
+        _checked(F, (N, 3), dtype, 'F')
+        _checked(S, (N, 5), dtype, 'S')
         out = {}
         r = Request()
         r.kind = REQ_KINDS[kind]
